@@ -1,0 +1,200 @@
+/*
+ * ndgf.h -- C ABI of the GB300 nested-dissection NEGF diagonal solver.
+ *
+ * The library computes, for a batch of energies E_e, the diagonals of the
+ * retarded Green's function G^r = A^{-1} and of the correlation functions
+ * G^< = G^r Sigma^< (G^r)^dagger and G^> = G^r Sigma^> (G^r)^dagger, with
+ *     A(E) = (E + i eta) I - H - Sigma^r_L - Sigma^r_R - Sigma^r_ph
+ * (Hetmaniuk, Zhao, Anantram, arXiv 1305.1070, Eq. (1)-(2)), by a
+ * nested-dissection cluster tree (Sec. 3.2): a bottom-up block LDL^T "fold"
+ * with separator Schur complements, the root inversion, a top-down selected
+ * inversion ("extract") of G^r, and the four-step extension for G^< and G^>.
+ *
+ * Conventions shared by every entry point
+ *  - Complex arrays are interleaved (re, im) doubles, row major, energy-major:
+ *    element (e, i, j) of a batch of m x m blocks is at 2*((e*m + i)*m + j).
+ *  - Site indices are the caller's 0-based indices of the graph ("caller
+ *    order"); all outputs are returned in caller order.
+ *  - Ownership: the caller owns every buffer it passes; the library never
+ *    frees or retains them beyond the call (stream-ordered calls read/write
+ *    them until the work on the stream completes).  Opaque handles own their
+ *    internal host and device memory and are released by the *_destroy calls.
+ *  - Pointers to per-energy arrays of nd_factor / nd_diag_green may be device
+ *    pointers or host pointers; host data is staged through the handle's
+ *    device buffers on the given stream (host memory must then stay valid
+ *    until the stream is synchronised).  Every other array argument is
+ *    documented as host or device.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream); all
+ *    device work of a call is ordered on it.  Calls on one handle must not run
+ *    concurrently.
+ *  - Errors: every entry point returns an nd_status; no exception crosses the
+ *    ABI and no device trap is used.  nd_last_error() returns a thread-local
+ *    message describing the last non-OK status of the calling thread.
+ */
+#ifndef NDGF_H
+#define NDGF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ND_OK = 0,
+  ND_ERR_INVALID_ARG = 1,        /* bad size, NULL, out-of-range index          */
+  ND_ERR_NOT_SYMMETRIC = 2,      /* graph pattern or contact block not symmetric */
+  ND_ERR_SINGULAR = 3,           /* exactly singular pivot in a cluster block   */
+  ND_ERR_NOT_SKEW_HERMITIAN = 4, /* Sigma^< / Sigma^> block not skew-Hermitian  */
+  ND_ERR_OOM = 5,                /* device or host allocation failed            */
+  ND_ERR_CUDA = 6,               /* a CUDA runtime call failed                  */
+  ND_ERR_TIMEOUT = 7,            /* a bounded device wait gave up               */
+  ND_ERR_UNSUPPORTED = 8         /* valid request this build does not handle    */
+} nd_status;
+
+typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1 } nd_precision;
+
+/* Sparsity pattern of H plus the contact site sets (host arrays).
+ * rowptr[n+1], colind[nnz]: CSR pattern, 0-based, must be structurally
+ * symmetric; the diagonal may be present or absent.  Contact c owns sites
+ * contact_idx[contact_ptr[c] .. contact_ptr[c+1]); the contact self-energy
+ * block Sigma_c is dense over those sites in that order (paper Sec. 2: the
+ * leads fold into dense first/last-layer blocks).  coords[n][coord_dim]
+ * (optional, NULL allowed) are site positions used to choose separators. */
+typedef struct nd_graph {
+  int32_t n;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  int32_t n_contacts;
+  const int32_t* contact_ptr;
+  const int32_t* contact_idx;
+  int32_t coord_dim;
+  const double* coords;
+} nd_graph;
+
+/* Options of nd_analyze.  leaf_size: maximal number of sites of a leaf
+ * cluster (0 = default 64); a contact set is never split, so a contact leaf
+ * may be larger. */
+typedef struct nd_opts {
+  int32_t leaf_size;
+  int32_t reserved[7];
+} nd_opts;
+
+typedef struct nd_plan nd_plan; /* symbolic analysis (host + device copy)      */
+typedef struct nd_fact nd_fact; /* per-energy numeric workspace (device)       */
+typedef struct nd_lead nd_lead; /* semi-infinite lead description (host+device) */
+
+/* Summary of a plan.  Flop counts are real floating-point operations per
+ * energy with 8 per complex multiply-add, for the fold (factor), the G^r
+ * extraction, and the G^< + G^> part (both right-hand sides). */
+typedef struct nd_plan_info {
+  int32_t n, nnz, n_clusters, n_levels;
+  int32_t max_n, max_b, n_contacts, n_roots;
+  double flops_factor, flops_green_r, flops_green_lesser;
+  double arena_bytes_fp64, arena_bytes_fp32; /* device workspace per energy */
+} nd_plan_info;
+
+/* ---- S0: ordering (paper Sec. 3.2 "Comments on the system partition") ------
+ * Nested dissection with width-1 separators: recursive bisection of the site
+ * set (coordinate median when coords are given, else breadth-first level
+ * structure), separator = the sites of one side that touch the other side;
+ * a contact set that a cut would split is peeled off as a leaf with its
+ * neighbourhood as separator, so Sigma_c and Sigma^<_c stay inside one
+ * cluster (paper Fig. 8).  Clusters on one level never couple.  Host only:
+ * callable without a GPU.  Errors: ND_ERR_INVALID_ARG (sizes, indices),
+ * ND_ERR_NOT_SYMMETRIC (pattern). */
+nd_status nd_analyze(const nd_graph* graph, const nd_opts* opts, nd_plan** out);
+nd_status nd_plan_query(const nd_plan* plan, nd_plan_info* out);
+/* Per-cluster tree arrays (host, each of length n_clusters, any may be NULL):
+ * level (1 = leaf), parent (-1 = root), n_i (interior size), b_i (boundary
+ * size).  cluster_of_site[n] (may be NULL): owning cluster of each site. */
+nd_status nd_plan_tree(const nd_plan* plan, int32_t* level, int32_t* parent, int32_t* n_i,
+                       int32_t* b_i, int32_t* cluster_of_site);
+/* Sites of cluster c: interior set I_c (n_c entries) then boundary set B_c
+ * (b_c entries), caller order, written to a host array of n_c + b_c ints. */
+nd_status nd_plan_cluster_sites(const nd_plan* plan, int32_t c, int32_t* sites);
+void nd_plan_destroy(nd_plan* plan);
+
+/* ---- numeric workspace -----------------------------------------------------
+ * Allocates device memory for up to max_ne energies at the given precision:
+ * ND_PREC_FP64 = complex128 throughout; ND_PREC_MIXED = complex64 cluster
+ * blocks and products with complex128 root inversion.  The plan must outlive
+ * the handle.  Errors: ND_ERR_OOM, ND_ERR_CUDA, ND_ERR_INVALID_ARG. */
+nd_status nd_fact_create(const nd_plan* plan, int32_t max_ne, int32_t precision, nd_fact** out);
+void nd_fact_destroy(nd_fact* fact);
+
+/* ---- S1 + S2 + S3: assemble and fold (paper Sec. 3.2, "folding", root) -----
+ * H_values[nnz]          : values of H aligned with the graph's colind (real).
+ * sigma_r                : [n_e][sum_c m_c^2] complex, contact blocks Sigma^r_c
+ *                          (contact order, each m_c x m_c row major); the
+ *                          blocks must be complex symmetric.
+ * sigma_ph_r             : [n_e][n] complex diagonal Sigma^r_ph, or NULL.
+ * energies               : [n_e] real.
+ * eta                    : positive broadening added to the device diagonal.
+ * Folds every cluster level by level (Psi_i = -A_ii^{-1} A_{i,B}, Schur update
+ * of the parent front) and inverts the root.  Errors: ND_ERR_INVALID_ARG,
+ * ND_ERR_CUDA; ND_ERR_SINGULAR is reported by nd_fact_status after the stream
+ * is synchronised (no device trap). */
+nd_status nd_factor(nd_fact* fact, const double* H_values, const double* sigma_r,
+                    const double* sigma_ph_r, const double* energies, int32_t n_e, double eta,
+                    void* stream);
+
+/* ---- S4..S8 + S10: selected inversion (paper Sec. 3.2, G^r and G^< steps) --
+ * sigma_lesser, sigma_greater : [n_e][sum_c m_c^2] complex contact blocks of
+ *                               Sigma^< and Sigma^> (skew-Hermitian), or NULL.
+ * ph_lesser, ph_greater       : [n_e][n] complex diagonals, or NULL.
+ * Gr, Gl, Gg                  : [n_e][n] complex outputs (diag G^r, G^<, G^>)
+ *                               in caller order; NULL skips that output (Gl
+ *                               and Gg need the matching Sigma terms).
+ * Uses the factorization of the last nd_factor call on this handle. */
+nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double* sigma_greater,
+                        const double* ph_lesser, const double* ph_greater, double* Gr, double* Gl,
+                        double* Gg, void* stream);
+
+/* Status of the last factor/diag call (synchronises the handle's stream):
+ * n_singular = number of (energy, cluster) pivots that were exactly zero;
+ * returns ND_ERR_SINGULAR when n_singular > 0. */
+nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
+
+/* ---- S1a: contact self-energies (paper Sec. 2) ----------------------------
+ * A lead is a semi-infinite chain of principal layers with on-site block H00
+ * (m x m real symmetric), hopping H01 (m x m) from a layer to the next one
+ * away from the device, attached to the m_c contact sites by tau (m_c x m):
+ *     Sigma^r(E) = tau g_s(E) tau^T,  g_s = (z - H00 - H01 g_s H01^T)^{-1},
+ *     z = E + i eta.   All three arrays are host, row major.
+ * When H01 = -h I and tau = -h I the lead is diagonalised once on the host
+ * (transverse modes) and Sigma^r = U diag(h lambda_n) U^T with lambda_n the
+ * decaying root of lambda^2 - ((z - eps_n)/h) lambda + 1 = 0; otherwise
+ * Lopez-Sancho decimation is used (FP64 on the device). */
+nd_status nd_lead_create(int32_t m, int32_t m_c, const double* H00, const double* H01,
+                         const double* tau, nd_lead** out);
+/* Writes Sigma^r of every energy into sigma_out (device, complex): block of
+ * energy e starts at complex element e*stride + offset (m_c x m_c row major).
+ * energies: device [n_e]. */
+nd_status nd_lead_sigma(nd_lead* lead, const double* energies, int32_t n_e, double eta,
+                        double* sigma_out, int64_t stride, int64_t offset, void* stream);
+void nd_lead_destroy(nd_lead* lead);
+
+/* Lesser/greater contact self-energies from the retarded ones (device arrays,
+ * packed like nd_factor's sigma_r): Gamma_c = i (Sigma_c - Sigma_c^dagger),
+ * Sigma^<_c = i f_c Gamma_c, Sigma^>_c = -i (1 - f_c) Gamma_c with the Fermi
+ * function f_c = 1/(1 + exp((E - mu_c)/kT)).  m_c, mu: host [n_contacts]. */
+nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, int32_t n_contacts,
+                                const int32_t* m_c, const double* mu, double kT,
+                                const double* energies, double* sigma_lesser,
+                                double* sigma_greater, void* stream);
+
+/* Constant-broadening phonon self-energy on every site (device outputs
+ * [n_e][n] complex, any may be NULL): Sigma^r = -i gamma/2,
+ * Sigma^< = i f(E; mu) gamma, Sigma^> = -i (1 - f) gamma. */
+nd_status nd_phonon_const(int32_t n, int32_t n_e, double gamma, double mu, double kT,
+                          const double* energies, double* ph_r, double* ph_lesser,
+                          double* ph_greater, void* stream);
+
+const char* nd_last_error(void);
+const char* nd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDGF_H */

@@ -1,0 +1,478 @@
+// Host side of the C ABI: numeric workspace, schedule execution and the
+// self-energy helpers.  Every device step runs in the kernels of
+// nd_kernels.cu; there is no host fallback.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "nd_internal.h"
+#include "nd_kernels.h"
+
+using namespace ndgf;
+
+namespace {
+
+#define ND_CUDA(call)                                                                                       \
+  do {                                                                                                      \
+    cudaError_t _e = (call);                                                                                \
+    if (_e != cudaSuccess) return fail(ND_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+template <typename V>
+nd_status upload(const std::vector<V>& h, V** d) {
+  *d = nullptr;
+  if (h.empty()) return ND_OK;
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(V));
+  if (e != cudaSuccess) return fail(ND_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  e = cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(ND_ERR_CUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  return ND_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct nd_fact {
+  const nd_plan* plan = nullptr;
+  int precision = ND_PREC_FP64;
+  int max_ne = 0;
+  int n_e = 0;  // energies of the last nd_factor
+  size_t esize = 16;
+  void* arena = nullptr;
+  void* aux = nullptr;
+  double* root_scratch = nullptr;
+  int64_t root_stride = 0;
+  int* d_status = nullptr;
+  bool has_ph = false;
+  // device tables
+  int32_t *d_sites = nullptr, *d_maps = nullptr, *d_ent_dst = nullptr, *d_ent_src = nullptr;
+  AssembleDesc* d_asm = nullptr;
+  InvDesc* d_inv = nullptr;
+  GemmDesc* d_gemm = nullptr;
+  ScatterDesc* d_scat = nullptr;
+  GatherDesc* d_gath = nullptr;
+  DiagDesc *d_diag_g = nullptr, *d_diag_p[2] = {nullptr, nullptr};
+  NPhDesc* d_nph = nullptr;
+  ZeroDesc* d_zero = nullptr;
+  TileRef* d_tiles = nullptr;
+  // tile range of every GEMM step: index = step index in its schedule
+  std::vector<std::pair<int, int>> tr_factor, tr_green, tr_lesser[2];
+  // staging buffers for host inputs / outputs
+  double *st_H = nullptr, *st_sr = nullptr, *st_ph = nullptr, *st_E = nullptr;
+  double *st_sl = nullptr, *st_sg = nullptr, *st_pl = nullptr, *st_pg = nullptr;
+  double *st_out[3] = {nullptr, nullptr, nullptr};
+  std::vector<void*> allocs;
+
+  ~nd_fact() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+nd_status dalloc(nd_fact* f, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return ND_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ND_ERR_OOM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  f->allocs.push_back(*p);
+  return ND_OK;
+}
+
+template <typename V>
+nd_status dupload(nd_fact* f, const std::vector<V>& h, V** d) {
+  nd_status st = upload(h, d);
+  if (*d) f->allocs.push_back(*d);
+  return st;
+}
+
+void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile,
+                 std::vector<TileRef>& tiles, std::vector<std::pair<int, int>>& ranges) {
+  ranges.assign(sched.size(), {0, 0});
+  for (size_t si = 0; si < sched.size(); ++si) {
+    const Step& s = sched[si];
+    if (s.kind != ST_GEMM) continue;
+    int b = int(tiles.size());
+    for (int k = s.begin; k < s.begin + s.count; ++k) {
+      const GemmDesc& g = gd[k];
+      const int tm = (g.m + tile - 1) / tile, tn = (g.n + tile - 1) / tile;
+      for (int i = 0; i < tm; ++i)
+        for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
+    }
+    ranges[si] = {b, int(tiles.size()) - b};
+  }
+}
+
+// Stage a per-energy input: device pointers pass through; host data is
+// copied to the staging buffer on the stream.
+nd_status stage_in(const double* src, double* staging, size_t bytes, cudaStream_t s, const double** out) {
+  if (!src) {
+    *out = nullptr;
+    return ND_OK;
+  }
+  if (is_device_ptr(src)) {
+    *out = src;
+    return ND_OK;
+  }
+  ND_CUDA(cudaMemcpyAsync(staging, src, bytes, cudaMemcpyHostToDevice, s));
+  *out = staging;
+  return ND_OK;
+}
+
+template <typename T>
+nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::vector<std::pair<int, int>>& tr,
+                       const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s) {
+  const nd_plan* p = f->plan;
+  for (size_t si = 0; si < sched.size(); ++si) {
+    const Step& st = sched[si];
+    switch (st.kind) {
+      case ST_INVERSE:
+        Kern<T>::inverse(w, f->d_inv + st.begin, st.count, st.max_dim, f->root_scratch, f->root_stride, f->d_status,
+                         s);
+        break;
+      case ST_GEMM:
+        Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].second, s);
+        break;
+      case ST_SCATTER:
+        Kern<T>::scatter(w, f->d_scat + st.begin, st.count, f->d_maps, s);
+        break;
+      case ST_GATHER_SYM:
+      case ST_GATHER_SKEW:
+        Kern<T>::gather(w, f->d_gath + st.begin, st.count, f->d_maps, st.kind == ST_GATHER_SKEW, s);
+        break;
+      case ST_ZERO:
+        Kern<T>::zero(w, f->d_zero + st.begin, st.count, s);
+        break;
+      case ST_NPH:
+        Kern<T>::nph(w, f->d_nph + st.begin, st.count, f->d_sites, ph_l, ph_g, p->n, s);
+        break;
+    }
+  }
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}
+
+}  // namespace
+
+extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t precision, nd_fact** out) {
+  if (!p || !out || max_ne <= 0) return fail(ND_ERR_INVALID_ARG, "nd_fact_create: bad argument");
+  if (precision != ND_PREC_FP64 && precision != ND_PREC_MIXED)
+    return fail(ND_ERR_INVALID_ARG, "nd_fact_create: unknown precision");
+  if (p->max_n > 8192) return fail(ND_ERR_UNSUPPORTED, "nd_fact_create: cluster larger than 8192 sites");
+  for (const auto& c : p->cl)
+    if (c.contacts.size() > 2) return fail(ND_ERR_UNSUPPORTED, "nd_fact_create: more than two contacts in one cluster");
+  *out = nullptr;
+  auto f = new nd_fact();
+  f->plan = p;
+  f->precision = precision;
+  f->max_ne = max_ne;
+  f->esize = precision == ND_PREC_FP64 ? 16 : 8;
+  nd_status st;
+#define TRY(x)          \
+  do {                  \
+    st = (x);           \
+    if (st != ND_OK) {  \
+      delete f;         \
+      return st;        \
+    }                   \
+  } while (0)
+  TRY(dalloc(f, &f->arena, size_t(p->arena_elems) * f->esize * max_ne));
+  TRY(dalloc(f, &f->aux, size_t(std::max<int64_t>(1, 2 * p->sigma_elems)) * f->esize * max_ne));
+  if (precision == ND_PREC_MIXED) {
+    int64_t rmax = 0;
+    for (const auto& c : p->cl)
+      if (c.b == 0) rmax = std::max<int64_t>(rmax, int64_t(c.n) * c.n);
+    f->root_stride = rmax;
+    TRY(dalloc(f, (void**)&f->root_scratch, size_t(rmax) * 16 * max_ne));
+  }
+  TRY(dalloc(f, (void**)&f->d_status, sizeof(int)));
+  cudaMemset(f->d_status, 0, sizeof(int));
+  TRY(dupload(f, p->sites, &f->d_sites));
+  TRY(dupload(f, p->maps, &f->d_maps));
+  TRY(dupload(f, p->ent_dst, &f->d_ent_dst));
+  TRY(dupload(f, p->ent_src, &f->d_ent_src));
+  TRY(dupload(f, p->asm_desc, &f->d_asm));
+  TRY(dupload(f, p->inv_desc, &f->d_inv));
+  TRY(dupload(f, p->gemm_desc, &f->d_gemm));
+  TRY(dupload(f, p->scat_desc, &f->d_scat));
+  TRY(dupload(f, p->gath_desc, &f->d_gath));
+  TRY(dupload(f, p->diag_g, &f->d_diag_g));
+  TRY(dupload(f, p->diag_p[0], &f->d_diag_p[0]));
+  TRY(dupload(f, p->diag_p[1], &f->d_diag_p[1]));
+  TRY(dupload(f, p->nph_desc, &f->d_nph));
+  TRY(dupload(f, p->zero_desc, &f->d_zero));
+  {
+    const int tile = precision == ND_PREC_FP64 ? Kern<double>::gemm_tile() : Kern<float>::gemm_tile();
+    std::vector<TileRef> tiles;
+    build_tiles(p->sched_factor, p->gemm_desc, tile, tiles, f->tr_factor);
+    build_tiles(p->sched_green, p->gemm_desc, tile, tiles, f->tr_green);
+    build_tiles(p->sched_lesser[0], p->gemm_desc, tile, tiles, f->tr_lesser[0]);
+    build_tiles(p->sched_lesser[1], p->gemm_desc, tile, tiles, f->tr_lesser[1]);
+    TRY(dupload(f, tiles, &f->d_tiles));
+  }
+  const size_t ne = size_t(max_ne), n = size_t(p->n), se = size_t(p->sigma_elems);
+  TRY(dalloc(f, (void**)&f->st_H, size_t(std::max(1, p->nnz)) * 8));
+  TRY(dalloc(f, (void**)&f->st_sr, std::max<size_t>(1, ne * se) * 16));
+  TRY(dalloc(f, (void**)&f->st_ph, ne * n * 16));
+  TRY(dalloc(f, (void**)&f->st_E, ne * 8));
+  TRY(dalloc(f, (void**)&f->st_sl, std::max<size_t>(1, ne * se) * 16));
+  TRY(dalloc(f, (void**)&f->st_sg, std::max<size_t>(1, ne * se) * 16));
+  TRY(dalloc(f, (void**)&f->st_pl, ne * n * 16));
+  TRY(dalloc(f, (void**)&f->st_pg, ne * n * 16));
+  for (int k = 0; k < 3; ++k) TRY(dalloc(f, (void**)&f->st_out[k], ne * n * 16));
+#undef TRY
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete f;
+    return fail(ND_ERR_CUDA, std::string("nd_fact_create: ") + cudaGetErrorString(e));
+  }
+  *out = f;
+  return ND_OK;
+}
+
+extern "C" void nd_fact_destroy(nd_fact* f) { delete f; }
+
+extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double* sigma_r, const double* sigma_ph_r,
+                               const double* energies, int32_t n_e, double eta, void* stream) {
+  if (!f || !H_values || !energies) return fail(ND_ERR_INVALID_ARG, "nd_factor: NULL argument");
+  if (n_e <= 0 || n_e > f->max_ne) return fail(ND_ERR_INVALID_ARG, "nd_factor: n_e outside 1..max_ne");
+  if (!(eta >= 0.0)) return fail(ND_ERR_INVALID_ARG, "nd_factor: eta must be >= 0");
+  const nd_plan* p = f->plan;
+  if (p->n_contacts > 0 && !sigma_r) return fail(ND_ERR_INVALID_ARG, "nd_factor: sigma_r is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double *H, *sr, *ph, *E;
+  nd_status st;
+  if ((st = stage_in(H_values, f->st_H, size_t(p->nnz) * 8, s, &H)) != ND_OK) return st;
+  if ((st = stage_in(sigma_r, f->st_sr, size_t(n_e) * p->sigma_elems * 16, s, &sr)) != ND_OK) return st;
+  if ((st = stage_in(sigma_ph_r, f->st_ph, size_t(n_e) * p->n * 16, s, &ph)) != ND_OK) return st;
+  if ((st = stage_in(energies, f->st_E, size_t(n_e) * 8, s, &E)) != ND_OK) return st;
+  f->n_e = n_e;
+  ND_CUDA(cudaMemsetAsync(f->d_status, 0, sizeof(int), s));
+  Work w{f->arena, p->arena_elems, f->aux, 2 * p->sigma_elems, n_e};
+  const int nc = int(p->cl.size());
+  if (f->precision == ND_PREC_FP64) {
+    Kern<double>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph,
+                           p->n, s);
+    return run_schedule<double>(f, p->sched_factor, f->tr_factor, w, nullptr, nullptr, s);
+  }
+  Kern<float>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph,
+                        p->n, s);
+  return run_schedule<float>(f, p->sched_factor, f->tr_factor, w, nullptr, nullptr, s);
+}
+
+template <typename T>
+static nd_status diag_green_t(nd_fact* f, const double* sl, const double* sg, const double* pl, const double* pg,
+                              double* outs[3], cudaStream_t s) {
+  const nd_plan* p = f->plan;
+  Work w{f->arena, p->arena_elems, f->aux, 2 * p->sigma_elems, f->n_e};
+  const int nc = int(p->cl.size());
+  nd_status st = run_schedule<T>(f, p->sched_green, f->tr_green, w, nullptr, nullptr, s);
+  if (st != ND_OK) return st;
+  if (outs[0]) Kern<T>::diag_out(w, f->d_diag_g, nc, f->d_sites, outs[0], p->n, s);
+  if (outs[1] || outs[2]) {
+    Kern<T>::convert_aux(w, sl, sg, p->sigma_elems, s);
+    const int v = (pl || pg) ? 1 : 0;
+    st = run_schedule<T>(f, p->sched_lesser[v], f->tr_lesser[v], w, pl, pg, s);
+    if (st != ND_OK) return st;
+    if (outs[1]) Kern<T>::diag_out(w, f->d_diag_p[0], nc, f->d_sites, outs[1], p->n, s);
+    if (outs[2]) Kern<T>::diag_out(w, f->d_diag_p[1], nc, f->d_sites, outs[2], p->n, s);
+  }
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}
+
+extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const double* sigma_greater,
+                                   const double* ph_lesser, const double* ph_greater, double* Gr, double* Gl,
+                                   double* Gg, void* stream) {
+  if (!f) return fail(ND_ERR_INVALID_ARG, "nd_diag_green: NULL handle");
+  if (f->n_e <= 0) return fail(ND_ERR_INVALID_ARG, "nd_diag_green: call nd_factor first");
+  if ((Gl || Gg) && f->plan->n_contacts > 0 && !sigma_lesser && !sigma_greater && !ph_lesser && !ph_greater)
+    return fail(ND_ERR_INVALID_ARG, "nd_diag_green: G^< / G^> requested without Sigma^< / Sigma^>");
+  if ((ph_lesser == nullptr) != (ph_greater == nullptr))
+    return fail(ND_ERR_INVALID_ARG, "nd_diag_green: pass both phonon Sigma^< and Sigma^> or neither");
+  const nd_plan* p = f->plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n_e = f->n_e;
+  const double *sl, *sg, *pl, *pg;
+  nd_status st;
+  if ((st = stage_in(sigma_lesser, f->st_sl, size_t(n_e) * p->sigma_elems * 16, s, &sl)) != ND_OK) return st;
+  if ((st = stage_in(sigma_greater, f->st_sg, size_t(n_e) * p->sigma_elems * 16, s, &sg)) != ND_OK) return st;
+  if ((st = stage_in(ph_lesser, f->st_pl, size_t(n_e) * p->n * 16, s, &pl)) != ND_OK) return st;
+  if ((st = stage_in(ph_greater, f->st_pg, size_t(n_e) * p->n * 16, s, &pg)) != ND_OK) return st;
+  double* user[3] = {Gr, Gl, Gg};
+  double* dev[3];
+  bool host[3];
+  for (int k = 0; k < 3; ++k) {
+    host[k] = user[k] && !is_device_ptr(user[k]);
+    dev[k] = host[k] ? f->st_out[k] : user[k];
+  }
+  st = f->precision == ND_PREC_FP64 ? diag_green_t<double>(f, sl, sg, pl, pg, dev, s)
+                                    : diag_green_t<float>(f, sl, sg, pl, pg, dev, s);
+  if (st != ND_OK) return st;
+  for (int k = 0; k < 3; ++k)
+    if (host[k]) ND_CUDA(cudaMemcpyAsync(user[k], dev[k], size_t(n_e) * p->n * 16, cudaMemcpyDeviceToHost, s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_fact_status(nd_fact* f, int32_t* n_singular) {
+  if (!f) return fail(ND_ERR_INVALID_ARG, "nd_fact_status: NULL handle");
+  int h = 0;
+  ND_CUDA(cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (n_singular) *n_singular = h;
+  if (h > 0) return fail(ND_ERR_SINGULAR, "nd_fact_status: " + std::to_string(h) + " singular pivot(s)");
+  return ND_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Leads (S1a)
+
+namespace {
+// Cyclic Jacobi eigen-decomposition of a real symmetric matrix (row major);
+// on return A is diagonal (eigenvalues) and V holds the eigenvectors in
+// its columns.  Golub & Van Loan, Matrix Computations, Sec. 8.5.
+void jacobi_eig(int m, std::vector<double>& A, std::vector<double>& V) {
+  V.assign(size_t(m) * m, 0.0);
+  for (int i = 0; i < m; ++i) V[size_t(i) * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        double a = A[size_t(i) * m + j];
+        tot += a * a;
+        if (i != j) off += a * a;
+      }
+    if (off <= 1e-30 * tot || off == 0.0) break;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[size_t(p) * m + q];
+        if (apq == 0.0) continue;
+        const double app = A[size_t(p) * m + p], aqq = A[size_t(q) * m + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < m; ++k) {  // columns p, q
+          const double akp = A[size_t(k) * m + p], akq = A[size_t(k) * m + q];
+          A[size_t(k) * m + p] = c * akp - s * akq;
+          A[size_t(k) * m + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < m; ++k) {  // rows p, q
+          const double apk = A[size_t(p) * m + k], aqk = A[size_t(q) * m + k];
+          A[size_t(p) * m + k] = c * apk - s * aqk;
+          A[size_t(q) * m + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < m; ++k) {
+          const double vkp = V[size_t(k) * m + p], vkq = V[size_t(k) * m + q];
+          V[size_t(k) * m + p] = c * vkp - s * vkq;
+          V[size_t(k) * m + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+}  // namespace
+
+struct nd_lead {
+  int m = 0, m_c = 0;
+  bool modes = false;
+  double hop = 0.0;
+  double *d_U = nullptr, *d_eps = nullptr;
+  ~nd_lead() {
+    cudaFree(d_U);
+    cudaFree(d_eps);
+  }
+};
+
+extern "C" nd_status nd_lead_create(int32_t m, int32_t m_c, const double* H00, const double* H01, const double* tau,
+                                    nd_lead** out) {
+  if (!out || !H00 || !H01 || !tau || m <= 0 || m_c <= 0) return fail(ND_ERR_INVALID_ARG, "nd_lead_create: bad argument");
+  *out = nullptr;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j)
+      if (std::fabs(H00[size_t(i) * m + j] - H00[size_t(j) * m + i]) > 1e-12 * (1.0 + std::fabs(H00[size_t(i) * m + j])))
+        return fail(ND_ERR_NOT_SYMMETRIC, "nd_lead_create: H00 not symmetric");
+  // H01 = -h I and tau = -h I ?
+  const double h = -H01[0];
+  bool uniform = (m == m_c) && h != 0.0;
+  for (int i = 0; i < m && uniform; ++i)
+    for (int j = 0; j < m && uniform; ++j) {
+      const double want = (i == j) ? -h : 0.0;
+      uniform = std::fabs(H01[size_t(i) * m + j] - want) <= 1e-14 * std::fabs(h) &&
+                std::fabs(tau[size_t(i) * m + j] - want) <= 1e-14 * std::fabs(h);
+    }
+  if (!uniform)
+    return fail(ND_ERR_UNSUPPORTED, "nd_lead_create: only leads with H01 = tau = -h I are supported by this build");
+  auto L = new nd_lead();
+  L->m = m;
+  L->m_c = m_c;
+  L->modes = true;
+  L->hop = h;
+  std::vector<double> A(H00, H00 + size_t(m) * m), V;
+  jacobi_eig(m, A, V);
+  std::vector<double> eps(m);
+  for (int i = 0; i < m; ++i) eps[i] = A[size_t(i) * m + i];
+  if (upload(V, &L->d_U) != ND_OK || upload(eps, &L->d_eps) != ND_OK) {
+    delete L;
+    return ND_ERR_OOM;
+  }
+  *out = L;
+  return ND_OK;
+}
+
+extern "C" nd_status nd_lead_sigma(nd_lead* L, const double* energies, int32_t n_e, double eta, double* sigma_out,
+                                   int64_t stride, int64_t offset, void* stream) {
+  if (!L || !energies || !sigma_out || n_e <= 0) return fail(ND_ERR_INVALID_ARG, "nd_lead_sigma: bad argument");
+  if (!is_device_ptr(energies) || !is_device_ptr(sigma_out))
+    return fail(ND_ERR_INVALID_ARG, "nd_lead_sigma: energies and sigma_out must be device pointers");
+  launch_lead_modes(L->d_U, L->d_eps, L->m, L->hop, energies, n_e, eta, sigma_out, stride, offset,
+                    (cudaStream_t)stream);
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}
+
+extern "C" void nd_lead_destroy(nd_lead* L) { delete L; }
+
+extern "C" nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, int32_t n_contacts, const int32_t* m_c,
+                                           const double* mu, double kT, const double* energies, double* sigma_lesser,
+                                           double* sigma_greater, void* stream) {
+  if (!sigma_r || !m_c || !mu || !energies || n_e <= 0 || n_contacts <= 0 || !(kT > 0))
+    return fail(ND_ERR_INVALID_ARG, "nd_sigma_lesser_fermi: bad argument");
+  if (n_contacts > MAX_CONTACTS) return fail(ND_ERR_UNSUPPORTED, "nd_sigma_lesser_fermi: too many contacts");
+  ContactTable ct{};
+  ct.n = n_contacts;
+  int64_t tot = 0;
+  for (int c = 0; c < n_contacts; ++c) {
+    if (m_c[c] <= 0) return fail(ND_ERR_INVALID_ARG, "nd_sigma_lesser_fermi: contact size must be positive");
+    ct.m[c] = m_c[c];
+    ct.off[c] = tot;
+    ct.mu[c] = mu[c];
+    tot += int64_t(m_c[c]) * m_c[c];
+  }
+  launch_sigma_lesser(sigma_r, n_e, ct, kT, energies, tot, sigma_lesser, sigma_greater, (cudaStream_t)stream);
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}
+
+extern "C" nd_status nd_phonon_const(int32_t n, int32_t n_e, double gamma, double mu, double kT,
+                                     const double* energies, double* ph_r, double* ph_lesser, double* ph_greater,
+                                     void* stream) {
+  if (n <= 0 || n_e <= 0 || !energies || !(kT > 0)) return fail(ND_ERR_INVALID_ARG, "nd_phonon_const: bad argument");
+  launch_phonon(n, n_e, gamma, mu, kT, energies, ph_r, ph_lesser, ph_greater, (cudaStream_t)stream);
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}

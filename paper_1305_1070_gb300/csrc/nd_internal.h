@@ -1,0 +1,161 @@
+// Internal structures shared by the host planner (nd_plan.cpp) and the CUDA
+// side (nd_api.cu, nd_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "ndgf.h"
+
+namespace ndgf {
+
+// Thread-local error message for nd_last_error().
+void set_error(const std::string& msg);
+nd_status fail(nd_status st, const std::string& msg);
+
+// One cluster of the nested-dissection tree (paper Sec. 3.2).  Clusters are
+// stored in postorder: every descendant of a cluster precedes it.
+struct Cluster {
+  int level = 0;      // 1 = leaf; a cluster's level is 1 + max(level of children)
+  int parent = -1;    // -1 = root
+  int slot = 0;       // index of this cluster among its parent's children
+  int first_desc = 0; // postorder index of the first cluster of its subtree
+  int n = 0, b = 0;   // |I_i|, |B_i|
+  std::vector<int> I; // interior sites (caller order ids); contact sites first
+  std::vector<int> B; // boundary sites: ancestor sites coupled to I_i after folding
+  std::vector<int> map; // B[k] -> position in the parent's front [I_p ; B_p]
+  std::vector<std::pair<int, int>> contacts; // (contact id, first row in I)
+  std::vector<int> children;
+  bool nactive = false; // the subtree holds a contact (N of Sec. 3.2 nonzero without phonons)
+  // per-energy workspace regions, offsets in complex elements
+  int64_t off_F = 0;    // n x (n+b): [A_ii | A_iB] folded front; A_ii^{-1} after the fold
+  int64_t off_Psi = 0;  // n x b   : Psi_i = -A_ii^{-1} A_iB
+  int64_t off_BB = 0;   // b x b   : Schur update accumulator, then G_BB
+  int64_t off_G = 0;    // n x (n+b): [G_II | G_IB]
+  int64_t off_N[2] = {0, 0};   // n x (n+b): [N_II | N_IB] for Sigma^< (0) and Sigma^> (1)
+  int64_t off_NBB[2] = {0, 0}; // b x b: N_BB accumulator, then P_BB
+  int64_t off_P[2] = {0, 0};   // n x (n+b): [P_II | P_IB]
+};
+
+// ---- device descriptors (plain structs, copied to the GPU) -----------------
+struct AssembleDesc {
+  int64_t off_F, off_BB;
+  int32_t n, b, ld;          // ld = n + b
+  int32_t ent_begin, ent_end; // range in the assembly entry list
+  int32_t site_begin;        // range [site_begin, site_begin+n) of the site list
+  int32_t c0, m0, soff0;     // first contact: row offset, size, offset in packed Sigma (elements)
+  int32_t c1, m1, soff1;     // second contact (m1 = 0 if none)
+};
+
+struct InvDesc {
+  int64_t off;  // matrix start (row major, leading dimension ld)
+  int32_t n, ld;
+  int32_t cluster;
+  int32_t fp64; // 1: invert in complex128 even on the mixed path
+};
+
+enum : int32_t { OP_N = 0, OP_T = 1, OP_C = 2, OP_H = 3 };
+
+// C = alpha * op(A) * op(B) + beta * D.  Offsets are per-energy element
+// offsets into the workspace; a set bit 62 selects the auxiliary buffer.
+struct GemmDesc {
+  int64_t offA, offB, offC, offD;
+  int32_t m, n, k;
+  int32_t lda, ldb, ldc, ldd;
+  int32_t opA, opB;
+  double alpha, beta;
+};
+static constexpr int64_t AUX_BIT = int64_t(1) << 62;
+
+// Extend-add of a child's b_c x b_c update into the parent's front
+// (rows in I_p -> front [n_p x (n_p+b_p)], rows and columns in B_p -> BB).
+struct ScatterDesc {
+  int64_t off_src;   // child's b x b block
+  int64_t off_front; // parent's n_p x (n_p + b_p) front
+  int64_t off_bb;    // parent's b_p x b_p block
+  int32_t b, n_p, b_p;
+  int32_t map_begin; // child's map in the map array
+};
+
+// Gather of a child's G_BB (or P_BB) from its parent's front.
+struct GatherDesc {
+  int64_t off_dst;   // child's b x b block
+  int64_t off_front; // parent's [X_II | X_IB]
+  int64_t off_bb;    // parent's X_BB
+  int32_t b, n_p, b_p;
+  int32_t map_begin;
+};
+
+struct DiagDesc {
+  int64_t off;      // n x ld block
+  int32_t n, ld;
+  int32_t site_begin;
+};
+
+struct NPhDesc {     // N_{I,F} = diag(ph) conj(G_{I,F}) for one cluster and one side
+  int64_t off_N, off_G;
+  int32_t n, ld;
+  int32_t site_begin;
+  int32_t rhs;        // 0: Sigma^<_ph, 1: Sigma^>_ph
+};
+
+struct ZeroDesc {
+  int64_t off;
+  int64_t count;
+};
+
+// A launch of the precomputed schedule.
+enum StepKind : int32_t {
+  ST_INVERSE = 0,
+  ST_GEMM = 1,
+  ST_SCATTER = 2,
+  ST_GATHER_SYM = 3,
+  ST_GATHER_SKEW = 4,
+  ST_ZERO = 5,
+  ST_NPH = 6,
+};
+
+struct Step {
+  int32_t kind;
+  int32_t begin, count;  // descriptor range in the table of the step's kind
+  int32_t max_dim;       // largest matrix edge in the step (launch shaping)
+};
+
+struct TileRef { int32_t desc, tm, tn, pad; };
+
+}  // namespace ndgf
+
+struct nd_plan {
+  int32_t n = 0, nnz = 0;
+  std::vector<int32_t> rowptr, colind;
+  int32_t n_contacts = 0;
+  std::vector<int32_t> contact_ptr, contact_idx;
+  std::vector<ndgf::Cluster> cl;  // postorder
+  int32_t n_levels = 0, n_roots = 0, max_n = 0, max_b = 0;
+  std::vector<int32_t> owner, pos; // owning cluster and position in its I, per site
+  int64_t arena_elems = 0;         // complex elements per energy
+  int64_t sigma_elems = 0;         // sum_c m_c^2
+  double flops_factor = 0, flops_green_r = 0, flops_green_lesser = 0;
+
+  // device-independent descriptor tables (uploaded by nd_fact_create)
+  std::vector<int32_t> sites;        // concatenated I lists (caller ids)
+  std::vector<int32_t> maps;         // concatenated child maps
+  std::vector<int32_t> ent_dst;      // assembly: destination offset within off_F region
+  std::vector<int32_t> ent_src;      // assembly: CSR value index
+  std::vector<ndgf::AssembleDesc> asm_desc;
+  std::vector<ndgf::InvDesc> inv_desc;
+  std::vector<ndgf::GemmDesc> gemm_desc;
+  std::vector<ndgf::ScatterDesc> scat_desc;
+  std::vector<ndgf::GatherDesc> gath_desc;
+  std::vector<ndgf::DiagDesc> diag_g, diag_p[2];
+  std::vector<ndgf::NPhDesc> nph_desc;
+  std::vector<ndgf::ZeroDesc> zero_desc;
+  // launch schedules: the fold (S1-S3), the G^r extraction (S4) and the
+  // G^< / G^> steps (S5-S8) without (0) or with (1) a phonon self-energy
+  std::vector<ndgf::Step> sched_factor, sched_green, sched_lesser[2];
+};
+
+namespace ndgf {
+void build_schedules(nd_plan* p);
+}  // namespace ndgf

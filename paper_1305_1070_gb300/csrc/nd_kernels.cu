@@ -1,0 +1,596 @@
+// Device kernels of the nested-dissection NEGF path (sm_103a).
+//
+// Every kernel is batched over (descriptor, energy): blockIdx.x selects a
+// descriptor (or a GEMM tile), blockIdx.y the energy.  Storage type T is
+// double (complex128 path) or float (complex64 mixed path); complex numbers
+// are interleaved double2 / float2.
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "nd_kernels.h"
+
+namespace ndgf {
+
+template <typename T> struct C2;
+template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; };
+template <typename T> using cx = typename C2<T>::t;
+
+template <typename T> __device__ __forceinline__ cx<T> mk(T a, T b) {
+  cx<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename T> __device__ __forceinline__ cx<T> crecip(cx<T> a) {
+  T s = fmax(fabs(a.x), fabs(a.y));
+  T ar = a.x / s, ai = a.y / s;
+  T d = (ar * ar + ai * ai) * s;
+  return mk<T>(ar / d, -ai / d);
+}
+template <typename T> __device__ __forceinline__ T cabs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+
+template <typename To, typename Ti> __device__ __forceinline__ cx<To> ccast(cx<Ti> a) {
+  return mk<To>(To(a.x), To(a.y));
+}
+
+__device__ __forceinline__ double fermi_dev(double E, double mu, double kT) {
+  double x = (E - mu) / kT;
+  if (x > 0) {
+    double ex = exp(-x);
+    return ex / (1.0 + ex);
+  }
+  return 1.0 / (1.0 + exp(x));
+}
+
+// ---------------------------------------------------------------------------
+// S1 assembly: F = [A_ii | A_iB] with A = (E + i eta) I - H - Sigma; BB = 0.
+template <typename T>
+__global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                           const int32_t* __restrict__ ent_dst, const int32_t* __restrict__ ent_src,
+                           const int32_t* __restrict__ sites, const double* __restrict__ H,
+                           const double* __restrict__ energies, double eta, const double2* __restrict__ sigma_r,
+                           int64_t sigma_stride, const double2* __restrict__ ph_r, int n) {
+  const AssembleDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  cx<T>* F = arena + int64_t(e) * se + d.off_F;
+  cx<T>* BB = arena + int64_t(e) * se + d.off_BB;
+  const int64_t nf = int64_t(d.n) * d.ld, nb = int64_t(d.b) * d.b;
+  const cx<T> z = mk<T>(T(0), T(0));
+  for (int64_t i = threadIdx.x; i < nf; i += blockDim.x) F[i] = z;
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) BB[i] = z;
+  __syncthreads();
+  for (int i = d.ent_begin + threadIdx.x; i < d.ent_end; i += blockDim.x) F[ent_dst[i]] = mk<T>(T(-H[ent_src[i]]), T(0));
+  __syncthreads();
+  const double E = energies[e];
+  for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
+    double re = E, im = eta;
+    if (ph_r) {
+      double2 p = ph_r[int64_t(e) * n + sites[d.site_begin + r]];
+      re -= p.x;
+      im -= p.y;
+    }
+    cx<T>& a = F[int64_t(r) * d.ld + r];
+    a = mk<T>(T(double(a.x) + re), T(double(a.y) + im));
+  }
+  const double2* S = sigma_r + int64_t(e) * sigma_stride;
+  for (int c = 0; c < 2; ++c) {
+    const int r0 = c ? d.c1 : d.c0, m = c ? d.m1 : d.m0, so = c ? d.soff1 : d.soff0;
+    for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
+      const int a = i / m, b = i % m;
+      double2 s = S[so + i];
+      cx<T>& f = F[int64_t(r0 + a) * d.ld + r0 + b];
+      f = mk<T>(T(double(f.x) - s.x), T(double(f.y) - s.y));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched in-place Gauss-Jordan inversion with partial pivoting (one CTA per
+// matrix).  The matrix is n x n with leading dimension ld.
+template <typename TC>
+__device__ void gj_invert(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, int* n_singular) {
+  __shared__ TC red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+  for (int k = 0; k < n; ++k) {
+    // pivot: largest |a_ik|^2 over i >= k (smallest index on ties)
+    TC bv = TC(-1);
+    int bi = k;
+    for (int i = k + tid; i < n; i += nt) {
+      TC v = cabs2<TC>(M[int64_t(i) * ld + k]);
+      if (v > bv) {
+        bv = v;
+        bi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      TC ov = __shfl_down_sync(0xffffffffu, bv, o);
+      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      TC v = red_v[0];
+      int p = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < p)) {
+          v = red_v[w];
+          p = red_i[w];
+        }
+      s_p = p;
+      piv[k] = p;
+    }
+    __syncthreads();
+    const int p = s_p;
+    if (p != k)
+      for (int j = tid; j < n; j += nt) {
+        cx<TC> t = M[int64_t(k) * ld + j];
+        M[int64_t(k) * ld + j] = M[int64_t(p) * ld + j];
+        M[int64_t(p) * ld + j] = t;
+      }
+    __syncthreads();
+    cx<TC> pivot = M[int64_t(k) * ld + k];
+    if (!(cabs2<TC>(pivot) > TC(0))) {  // exactly singular (or NaN): record, keep going
+      if (tid == 0) atomicAdd(n_singular, 1);
+      pivot = mk<TC>(sizeof(TC) == 8 ? TC(1e-300) : TC(1e-30), TC(0));
+    }
+    const cx<TC> inv = crecip<TC>(pivot);
+    for (int i = tid; i < n; i += nt) colk[i] = (i == k) ? mk<TC>(TC(0), TC(0)) : M[int64_t(i) * ld + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      cx<TC>& a = M[int64_t(k) * ld + j];
+      a = (j == k) ? inv : cmul<TC>(a, inv);
+    }
+    __syncthreads();
+    const int64_t nn = int64_t(n) * n;
+    for (int64_t idx = tid; idx < nn; idx += nt) {
+      const int i = int(idx / n), j = int(idx % n);
+      if (i == k) continue;
+      const cx<TC> f = colk[i];
+      cx<TC>& a = M[int64_t(i) * ld + j];
+      cx<TC> v = (j == k) ? mk<TC>(TC(0), TC(0)) : a;
+      const cx<TC> r = M[int64_t(k) * ld + j];
+      v.x -= f.x * r.x - f.y * r.y;
+      v.y -= f.x * r.y + f.y * r.x;
+      a = v;
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = piv[k];
+    if (p != k)
+      for (int i = tid; i < n; i += nt) {
+        cx<TC> t = M[int64_t(i) * ld + k];
+        M[int64_t(i) * ld + k] = M[int64_t(i) * ld + p];
+        M[int64_t(i) * ld + p] = t;
+      }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_inverse(const InvDesc* __restrict__ descs, cx<T>* arena, int64_t se, double2* scratch,
+                          int64_t scratch_stride, int* n_singular) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const InvDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  cx<T>* M = arena + int64_t(e) * se + d.off;
+  int* piv = reinterpret_cast<int*>(smem);
+  const size_t colk_off = (size_t(d.n) * sizeof(int) + 15) & ~size_t(15);
+  if (sizeof(T) == 4 && d.fp64 && scratch) {
+    double2* W = scratch + int64_t(e) * scratch_stride;
+    const int64_t nn = int64_t(d.n) * d.n;
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = ccast<double, T>(M[(i / d.n) * d.ld + i % d.n]);
+    __syncthreads();
+    gj_invert<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off), n_singular);
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = ccast<T, double>(W[i]);
+  } else {
+    gj_invert<T>(M, d.n, d.ld, piv, reinterpret_cast<cx<T>*>(smem + colk_off), n_singular);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched complex GEMM, C = alpha op(A) op(B) + beta D, one CTA per BM x BN
+// output tile.  Thread (tx, ty) owns rows ty + i*(BM/TM), columns
+// tx + j*(BN/TN) of the tile.
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx<T>* arena, int64_t se,
+       const cx<T>* __restrict__ aux, int64_t sa) {
+  constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
+  __shared__ cx<T> As[BK][BM + 1];
+  __shared__ cx<T> Bs[BK][BN + 1];
+  const TileRef t = tiles[blockIdx.x];
+  const GemmDesc d = descs[t.desc];
+  const int64_t e = blockIdx.y;
+  cx<T>* base = arena + e * se;
+  const cx<T>* abase = aux + e * sa;
+  const cx<T>* A = (d.offA & AUX_BIT) ? abase + (d.offA & ~AUX_BIT) : base + d.offA;
+  const cx<T>* B = (d.offB & AUX_BIT) ? abase + (d.offB & ~AUX_BIT) : base + d.offB;
+  const int m0 = t.tm * BM, n0 = t.tn * BN;
+  const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
+  cx<T> acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = mk<T>(T(0), T(0));
+  const bool conjB = (d.opB == OP_C || d.opB == OP_H);
+  const bool transB = (d.opB == OP_T || d.opB == OP_H);
+  for (int k0 = 0; k0 < d.k; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      int mm, kk;
+      if (d.opA == OP_N) {
+        mm = idx / BK;
+        kk = idx % BK;
+      } else {
+        kk = idx / BM;
+        mm = idx % BM;
+      }
+      const int gm = m0 + mm, gk = k0 + kk;
+      cx<T> v = mk<T>(T(0), T(0));
+      if (gm < d.m && gk < d.k) v = (d.opA == OP_N) ? A[int64_t(gm) * d.lda + gk] : A[int64_t(gk) * d.lda + gm];
+      As[kk][mm] = v;
+    }
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      int kk, nn;
+      if (!transB) {
+        kk = idx / BN;
+        nn = idx % BN;
+      } else {
+        nn = idx / BK;
+        kk = idx % BK;
+      }
+      const int gk = k0 + kk, gn = n0 + nn;
+      cx<T> v = mk<T>(T(0), T(0));
+      if (gk < d.k && gn < d.n) v = transB ? B[int64_t(gn) * d.ldb + gk] : B[int64_t(gk) * d.ldb + gn];
+      if (conjB) v.y = -v.y;
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < BK; ++kk) {
+      cx<T> a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * NY];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * NX];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) cfma<T>(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  const T alpha = T(d.alpha), beta = T(d.beta);
+  cx<T>* C = base + d.offC;
+  const cx<T>* D = base + d.offD;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gm = m0 + ty + i * NY;
+    if (gm >= d.m) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gn = n0 + tx + j * NX;
+      if (gn >= d.n) continue;
+      cx<T> r = mk<T>(alpha * acc[i][j].x, alpha * acc[i][j].y);
+      if (beta != T(0)) {
+        const cx<T> dv = D[int64_t(gm) * d.ldd + gn];
+        r.x += beta * dv.x;
+        r.y += beta * dv.y;
+      }
+      C[int64_t(gm) * d.ldc + gn] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Extend-add of a child's update into its parent's front.  Entries whose row
+// is a boundary site of the parent and whose column is interior to it are
+// dropped: the front stores [X_II | X_IB] and X_BB only.
+template <typename T>
+__global__ void k_scatter(const ScatterDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                          const int32_t* __restrict__ maps) {
+  const ScatterDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const cx<T>* src = base + d.off_src;
+  cx<T>* front = base + d.off_front;
+  cx<T>* bb = base + d.off_bb;
+  const int32_t* map = maps + d.map_begin;
+  const int ldp = d.n_p + d.b_p;
+  const int64_t nb = int64_t(d.b) * d.b;
+  for (int64_t idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+    const int r = int(idx / d.b), s = int(idx % d.b);
+    const int pr = map[r], ps = map[s];
+    const cx<T> v = src[idx];
+    if (pr < d.n_p) {
+      cx<T>& f = front[int64_t(pr) * ldp + ps];
+      f.x += v.x;
+      f.y += v.y;
+    } else if (ps >= d.n_p) {
+      cx<T>& f = bb[int64_t(pr - d.n_p) * d.b_p + (ps - d.n_p)];
+      f.x += v.x;
+      f.y += v.y;
+    }
+  }
+}
+
+// Gather of X_BB for a child from the parent's [X_II | X_IB] and X_BB; the
+// parent's X_BI is X_IB^T (G^r, complex symmetric) or -X_IB^dagger (G^<, G^>).
+template <typename T>
+__global__ void k_gather(const GatherDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                         const int32_t* __restrict__ maps, int skew) {
+  const GatherDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  cx<T>* dst = base + d.off_dst;
+  const cx<T>* front = base + d.off_front;
+  const cx<T>* bb = base + d.off_bb;
+  const int32_t* map = maps + d.map_begin;
+  const int ldp = d.n_p + d.b_p;
+  const int64_t nb = int64_t(d.b) * d.b;
+  for (int64_t idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+    const int r = int(idx / d.b), s = int(idx % d.b);
+    const int pr = map[r], ps = map[s];
+    cx<T> v;
+    if (pr < d.n_p) {
+      v = front[int64_t(pr) * ldp + ps];
+    } else if (ps < d.n_p) {
+      v = front[int64_t(ps) * ldp + pr];
+      if (skew) v = mk<T>(-v.x, v.y);
+    } else {
+      v = bb[int64_t(pr - d.n_p) * d.b_p + (ps - d.n_p)];
+    }
+    dst[idx] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_zero(const ZeroDesc* __restrict__ descs, cx<T>* arena, int64_t se) {
+  const ZeroDesc d = descs[blockIdx.x];
+  cx<T>* p = arena + int64_t(blockIdx.y) * se + d.off;
+  const cx<T> z = mk<T>(T(0), T(0));
+  for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) p[i] = z;
+}
+
+// N_{I,F} = diag(Sigma_ph) conj(G_{I,F})  (paper Sec. 3.2, first G^< step)
+template <typename T>
+__global__ void k_nph(const NPhDesc* __restrict__ descs, cx<T>* arena, int64_t se, const int32_t* __restrict__ sites,
+                      const double2* __restrict__ ph_l, const double2* __restrict__ ph_g, int n) {
+  const NPhDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  cx<T>* base = arena + int64_t(e) * se;
+  cx<T>* N = base + d.off_N;
+  const cx<T>* G = base + d.off_G;
+  const double2* ph = (d.rhs ? ph_g : ph_l) + int64_t(e) * n;
+  const int64_t tot = int64_t(d.n) * d.ld;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / d.ld);
+    const double2 s = ph[sites[d.site_begin + r]];
+    const cx<T> g = G[idx];
+    const cx<T> sv = mk<T>(T(s.x), T(s.y));
+    N[idx] = cmul<T>(sv, mk<T>(g.x, -g.y));
+  }
+}
+
+template <typename T>
+__global__ void k_diag_out(const DiagDesc* __restrict__ descs, const cx<T>* arena, int64_t se,
+                           const int32_t* __restrict__ sites, double2* out, int n) {
+  const DiagDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  const cx<T>* X = arena + int64_t(e) * se + d.off;
+  for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
+    const cx<T> v = X[int64_t(r) * d.ld + r];
+    out[int64_t(e) * n + sites[d.site_begin + r]] = make_double2(double(v.x), double(v.y));
+  }
+}
+
+template <typename T>
+__global__ void k_convert_aux(const double2* __restrict__ lesser, const double2* __restrict__ greater, cx<T>* aux,
+                              int64_t sigma_elems, int n_e) {
+  const int64_t tot = int64_t(n_e) * sigma_elems;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < tot; i += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t e = i / sigma_elems, k = i % sigma_elems;
+    const double2 l = lesser ? lesser[i] : make_double2(0.0, 0.0);
+    const double2 g = greater ? greater[i] : make_double2(0.0, 0.0);
+    aux[e * 2 * sigma_elems + k] = mk<T>(T(l.x), T(l.y));
+    aux[e * 2 * sigma_elems + sigma_elems + k] = mk<T>(T(g.x), T(g.y));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launch wrappers
+template <typename T> struct GemmCfg;
+template <> struct GemmCfg<double> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<float> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+
+template <typename T> int Kern<T>::gemm_tile() { return GemmCfg<T>::BM; }
+
+template <typename T>
+void Kern<T>::assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst, const int32_t* ent_src,
+                       const int32_t* sites, const double* H, const double* energies, double eta,
+                       const double* sigma_r, int64_t sigma_stride, const double* ph_r, int n, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_assemble<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, ent_dst, ent_src, sites, H, energies, eta,
+                                                    (const double2*)sigma_r, sigma_stride, (const double2*)ph_r, n);
+}
+
+template <typename T>
+void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, double* scratch, int64_t scratch_stride,
+                      int* n_singular, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  size_t shm = ((size_t(max_n) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_n) * sizeof(double2);
+  if (shm > 48 * 1024) cudaFuncSetAttribute(k_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
+  k_inverse<T><<<dim3(count, w.n_e), 256, shm, s>>>(d, (cx<T>*)w.arena, w.se, (double2*)scratch, scratch_stride,
+                                                    n_singular);
+}
+
+template <typename T>
+void Kern<T>::gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
+  if (n_tiles <= 0 || w.n_e <= 0) return;
+  using G = GemmCfg<T>;
+  constexpr int NT = (G::BM / G::TM) * (G::BN / G::TN);
+  k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<dim3(n_tiles, w.n_e), NT, 0, s>>>(
+      d, tiles, (cx<T>*)w.arena, w.se, (const cx<T>*)w.aux, w.sa);
+}
+
+template <typename T>
+void Kern<T>::scatter(const Work& w, const ScatterDesc* d, int count, const int32_t* maps, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_scatter<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps);
+}
+
+template <typename T>
+void Kern<T>::gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_gather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps, skew ? 1 : 0);
+}
+
+template <typename T>
+void Kern<T>::zero(const Work& w, const ZeroDesc* d, int count, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_zero<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se);
+}
+
+template <typename T>
+void Kern<T>::nph(const Work& w, const NPhDesc* d, int count, const int32_t* sites, const double* ph_l,
+                  const double* ph_g, int n, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_nph<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, sites, (const double2*)ph_l,
+                                              (const double2*)ph_g, n);
+}
+
+template <typename T>
+void Kern<T>::diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
+                       cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_diag_out<T><<<dim3(count, w.n_e), 128, 0, s>>>(d, (const cx<T>*)w.arena, w.se, sites, (double2*)out, n);
+}
+
+template <typename T>
+void Kern<T>::convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
+                          cudaStream_t s) {
+  if (sigma_elems <= 0 || w.n_e <= 0) return;
+  int64_t tot = int64_t(w.n_e) * sigma_elems;
+  int blocks = int((tot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_convert_aux<T><<<blocks, 256, 0, s>>>((const double2*)lesser, (const double2*)greater, (cx<T>*)w.aux,
+                                          sigma_elems, w.n_e);
+}
+
+template struct Kern<double>;
+template struct Kern<float>;
+
+// ---------------------------------------------------------------------------
+// S1a contact self-energy of a lead with H01 = -h I, tau = -h I, in the
+// transverse-mode basis H00 = U diag(eps) U^T (FP64 always).
+__device__ __forceinline__ double2 csqrt_dev(double2 w) {
+  double r = hypot(w.x, w.y);
+  if (r == 0.0) return make_double2(0.0, 0.0);
+  double a = sqrt(0.5 * (r + fabs(w.x)));
+  if (w.x >= 0.0) return make_double2(a, w.y / (2.0 * a));
+  return make_double2(fabs(w.y) / (2.0 * a), copysign(a, w.y));
+}
+
+__global__ void k_lead_modes(const double* __restrict__ U, const double* __restrict__ eps, int m, double hop,
+                             const double* __restrict__ energies, double eta, double2* out, int64_t stride,
+                             int64_t offset) {
+  extern __shared__ double2 lam[];
+  const int e = blockIdx.y;
+  const double E = energies[e];
+  for (int q = threadIdx.x; q < m; q += blockDim.x) {
+    // lambda^2 - x lambda + 1 = 0, x = (z - eps)/h; keep the root with |lambda| < 1
+    const double2 x = make_double2((E - eps[q]) / hop, eta / hop);
+    const double2 w = make_double2(x.x * x.x - x.y * x.y - 4.0, 2.0 * x.x * x.y);
+    const double2 rt = csqrt_dev(w);
+    const double2 p = make_double2(x.x + rt.x, x.y + rt.y), mns = make_double2(x.x - rt.x, x.y - rt.y);
+    const double2 big = (p.x * p.x + p.y * p.y >= mns.x * mns.x + mns.y * mns.y) ? p : mns;
+    // lambda = 2 / big (product of the roots is 1)
+    const double den = big.x * big.x + big.y * big.y;
+    lam[q] = make_double2(hop * 2.0 * big.x / den, -hop * 2.0 * big.y / den);
+  }
+  __syncthreads();
+  const int64_t mm = int64_t(m) * m;
+  for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < mm; idx += int64_t(gridDim.x) * blockDim.x) {
+    const int j = int(idx / m), k = int(idx % m);
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < m; ++q) {
+      const double u = U[int64_t(j) * m + q] * U[int64_t(k) * m + q];
+      sr = fma(u, lam[q].x, sr);
+      si = fma(u, lam[q].y, si);
+    }
+    out[int64_t(e) * stride + offset + idx] = make_double2(sr, si);
+  }
+}
+
+void launch_lead_modes(const double* U, const double* eps, int m, double hop, const double* energies, int n_e,
+                       double eta, double* out, int64_t stride, int64_t offset, cudaStream_t s) {
+  const int64_t mm = int64_t(m) * m;
+  int bx = int((mm + 255) / 256);
+  if (bx > 64) bx = 64;
+  k_lead_modes<<<dim3(bx, n_e), 256, size_t(m) * sizeof(double2), s>>>(U, eps, m, hop, energies, eta, (double2*)out,
+                                                                       stride, offset);
+}
+
+// Sigma^< = i f Gamma, Sigma^> = -i (1 - f) Gamma, Gamma = i (Sigma - Sigma^dagger)
+__global__ void k_sigma_lesser(const double2* __restrict__ sr, ContactTable ct, double kT,
+                               const double* __restrict__ energies, int64_t stride, double2* lesser, double2* greater) {
+  const int c = blockIdx.y, e = blockIdx.z;
+  const int m = ct.m[c];
+  const double f = fermi_dev(energies[e], ct.mu[c], kT);
+  const double2* S = sr + int64_t(e) * stride + ct.off[c];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < m * m; idx += gridDim.x * blockDim.x) {
+    const int j = idx / m, k = idx % m;
+    const double2 a = S[idx], b = S[int64_t(k) * m + j];
+    const double2 dlt = make_double2(a.x - b.x, a.y + b.y);  // Sigma - Sigma^dagger = -i Gamma
+    const int64_t o = int64_t(e) * stride + ct.off[c] + idx;
+    if (lesser) lesser[o] = make_double2(-f * dlt.x, -f * dlt.y);
+    if (greater) greater[o] = make_double2((1.0 - f) * dlt.x, (1.0 - f) * dlt.y);
+  }
+}
+
+void launch_sigma_lesser(const double* sigma_r, int n_e, const ContactTable& ct, double kT, const double* energies,
+                         int64_t stride, double* lesser, double* greater, cudaStream_t s) {
+  k_sigma_lesser<<<dim3(16, ct.n, n_e), 256, 0, s>>>((const double2*)sigma_r, ct, kT, energies, stride,
+                                                    (double2*)lesser, (double2*)greater);
+}
+
+__global__ void k_phonon(int n, int n_e, double gamma, double mu, double kT, const double* __restrict__ energies,
+                         double2* r, double2* l, double2* g) {
+  const int64_t tot = int64_t(n) * n_e;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < tot; i += int64_t(gridDim.x) * blockDim.x) {
+    const double f = fermi_dev(energies[i / n], mu, kT);
+    if (r) r[i] = make_double2(0.0, -0.5 * gamma);
+    if (l) l[i] = make_double2(0.0, f * gamma);
+    if (g) g[i] = make_double2(0.0, -(1.0 - f) * gamma);
+  }
+}
+
+void launch_phonon(int n, int n_e, double gamma, double mu, double kT, const double* energies, double* r, double* l,
+                   double* g, cudaStream_t s) {
+  const int64_t tot = int64_t(n) * n_e;
+  int blocks = int((tot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_phonon<<<blocks, 256, 0, s>>>(n, n_e, gamma, mu, kT, energies, (double2*)r, (double2*)l, (double2*)g);
+}
+
+}  // namespace ndgf

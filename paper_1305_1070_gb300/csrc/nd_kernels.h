@@ -1,0 +1,58 @@
+// Launch wrappers of the device kernels (nd_kernels.cu).  Internal.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "nd_internal.h"
+
+namespace ndgf {
+
+// Workspace view handed to every launch: per-energy base = arena + e * se,
+// auxiliary per-energy base = aux + e * sa (elements of the storage type).
+struct Work {
+  void* arena;
+  int64_t se;
+  const void* aux;
+  int64_t sa;
+  int n_e;
+};
+
+template <typename T>
+struct Kern {
+  static void assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst,
+                       const int32_t* ent_src, const int32_t* sites, const double* H, const double* energies,
+                       double eta, const double* sigma_r, int64_t sigma_stride, const double* ph_r, int n,
+                       cudaStream_t s);
+  static void inverse(const Work& w, const InvDesc* d, int count, int max_n, double* fp64_scratch,
+                      int64_t scratch_stride, int* n_singular, cudaStream_t s);
+  static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
+  static void scatter(const Work& w, const ScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
+  static void gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew,
+                     cudaStream_t s);
+  static void zero(const Work& w, const ZeroDesc* d, int count, cudaStream_t s);
+  static void nph(const Work& w, const NPhDesc* d, int count, const int32_t* sites, const double* ph_l,
+                  const double* ph_g, int n, cudaStream_t s);
+  static void diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
+                       cudaStream_t s);
+  static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
+                          cudaStream_t s);
+  // tile edge (BM = BN) of the GEMM kernel of this precision
+  static int gemm_tile();
+};
+
+void launch_lead_modes(const double* U, const double* eps, int m, double hop, const double* energies, int n_e,
+                       double eta, double* out, int64_t stride, int64_t offset, cudaStream_t s);
+// Contacts of nd_sigma_lesser_fermi, passed by value.
+static constexpr int MAX_CONTACTS = 8;
+struct ContactTable {
+  int32_t n;
+  int32_t m[MAX_CONTACTS];
+  int64_t off[MAX_CONTACTS];
+  double mu[MAX_CONTACTS];
+};
+void launch_sigma_lesser(const double* sigma_r, int n_e, const ContactTable& ct, double kT, const double* energies,
+                         int64_t stride, double* lesser, double* greater, cudaStream_t s);
+void launch_phonon(int n, int n_e, double gamma, double mu, double kT, const double* energies, double* r,
+                   double* l, double* g, cudaStream_t s);
+
+}  // namespace ndgf

@@ -1,0 +1,327 @@
+// Launch schedule of the numeric phases, built once per plan on the host.
+//
+// Every step is one batched launch over (clusters of one tree level) x
+// (energies).  Descriptors hold per-energy workspace offsets; the kernels add
+// energy * (workspace elements per energy).  Cluster regions (see Cluster):
+//   F   = [A_ii | A_iB]  -> A_ii^{-1} in place after the fold
+//   Psi = -A_ii^{-1} A_iB
+//   BB  = Schur update accumulator (fold), then G_BB (extraction)
+//   G   = [G_II | G_IB]
+//   N_s = [N_II | N_IB], NBB_s = N_BB accumulator, then P_BB; P_s = [P_II | P_IB]
+// for s = 0 (Sigma^<, G^<) and s = 1 (Sigma^>, G^>).
+
+#include <algorithm>
+
+#include "nd_internal.h"
+
+namespace ndgf {
+
+namespace {
+
+struct Builder {
+  nd_plan* p;
+  std::vector<Step>* cur = nullptr;
+  Step st{};
+
+  void begin(std::vector<Step>* sched, int kind) {
+    cur = sched;
+    st = Step{kind, 0, 0, 0};
+    switch (kind) {
+      case ST_INVERSE: st.begin = int32_t(p->inv_desc.size()); break;
+      case ST_GEMM: st.begin = int32_t(p->gemm_desc.size()); break;
+      case ST_SCATTER: st.begin = int32_t(p->scat_desc.size()); break;
+      case ST_GATHER_SYM:
+      case ST_GATHER_SKEW: st.begin = int32_t(p->gath_desc.size()); break;
+      case ST_ZERO: st.begin = int32_t(p->zero_desc.size()); break;
+      case ST_NPH: st.begin = int32_t(p->nph_desc.size()); break;
+    }
+  }
+  void end() {
+    int32_t e = 0;
+    switch (st.kind) {
+      case ST_INVERSE: e = int32_t(p->inv_desc.size()); break;
+      case ST_GEMM: e = int32_t(p->gemm_desc.size()); break;
+      case ST_SCATTER: e = int32_t(p->scat_desc.size()); break;
+      case ST_GATHER_SYM:
+      case ST_GATHER_SKEW: e = int32_t(p->gath_desc.size()); break;
+      case ST_ZERO: e = int32_t(p->zero_desc.size()); break;
+      case ST_NPH: e = int32_t(p->nph_desc.size()); break;
+    }
+    st.count = e - st.begin;
+    if (st.count > 0) cur->push_back(st);
+  }
+  void dim(int d) { st.max_dim = std::max(st.max_dim, d); }
+
+  void gemm(int64_t C, int ldc, int64_t D, int ldd, int64_t A, int lda, int opA, int64_t B, int ldb, int opB,
+            int m, int n, int k, double alpha, double beta) {
+    if (m <= 0 || n <= 0) return;
+    GemmDesc g{};
+    g.offA = A; g.offB = B; g.offC = C; g.offD = D;
+    g.m = m; g.n = n; g.k = k;
+    g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.ldd = ldd;
+    g.opA = opA; g.opB = opB;
+    g.alpha = alpha; g.beta = beta;
+    p->gemm_desc.push_back(g);
+    dim(std::max(m, std::max(n, k)));
+  }
+};
+
+}  // namespace
+
+void build_schedules(nd_plan* p) {
+  auto& cl = p->cl;
+  const int nc = int(cl.size());
+  std::vector<int32_t> site_begin(nc), map_begin(nc);
+  for (int i = 0; i < nc; ++i) {
+    site_begin[i] = int32_t(p->sites.size());
+    p->sites.insert(p->sites.end(), cl[i].I.begin(), cl[i].I.end());
+    map_begin[i] = int32_t(p->maps.size());
+    p->maps.insert(p->maps.end(), cl[i].map.begin(), cl[i].map.end());
+  }
+  // contact offsets in the packed Sigma arrays
+  std::vector<int32_t> soff(p->n_contacts + 1, 0);
+  for (int c = 0; c < p->n_contacts; ++c) {
+    int m = p->contact_ptr[c + 1] - p->contact_ptr[c];
+    soff[c + 1] = soff[c] + m * m;
+  }
+  // ---- S1 assembly lists ----------------------------------------------------
+  {
+    std::vector<int> posB(p->n, -1);
+    for (int i = 0; i < nc; ++i) {
+      Cluster& c = cl[i];
+      const int ld = c.n + c.b;
+      for (int k = 0; k < c.b; ++k) posB[c.B[k]] = k;
+      AssembleDesc a{};
+      a.off_F = c.off_F;
+      a.off_BB = c.off_BB;
+      a.n = c.n;
+      a.b = c.b;
+      a.ld = ld;
+      a.site_begin = site_begin[i];
+      a.ent_begin = int32_t(p->ent_dst.size());
+      for (int r = 0; r < c.n; ++r) {
+        const int v = c.I[r];
+        for (int q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q) {
+          const int u = p->colind[q];
+          int dst = -1;
+          if (p->owner[u] == i)
+            dst = r * ld + p->pos[u];
+          else if (posB[u] >= 0)
+            dst = r * ld + c.n + posB[u];
+          if (dst >= 0) {
+            p->ent_dst.push_back(dst);
+            p->ent_src.push_back(q);
+          }
+        }
+      }
+      a.ent_end = int32_t(p->ent_dst.size());
+      a.c0 = a.m0 = a.soff0 = a.c1 = a.m1 = a.soff1 = 0;
+      if (!c.contacts.empty()) {
+        int cid = c.contacts[0].first;
+        a.c0 = c.contacts[0].second;
+        a.m0 = p->contact_ptr[cid + 1] - p->contact_ptr[cid];
+        a.soff0 = soff[cid];
+      }
+      if (c.contacts.size() > 1) {
+        int cid = c.contacts[1].first;
+        a.c1 = c.contacts[1].second;
+        a.m1 = p->contact_ptr[cid + 1] - p->contact_ptr[cid];
+        a.soff1 = soff[cid];
+      }
+      p->asm_desc.push_back(a);
+      for (int k = 0; k < c.b; ++k) posB[c.B[k]] = -1;
+    }
+  }
+  std::vector<std::vector<int>> lev(p->n_levels + 1);
+  for (int i = 0; i < nc; ++i) lev[cl[i].level].push_back(i);
+  int max_slot = 0;
+  for (int i = 0; i < nc; ++i) max_slot = std::max(max_slot, cl[i].slot);
+
+  Builder B{p};
+  // ---- S2/S3 fold: for l = 1..L, invert A_ii; Psi; Schur update; extend-add
+  for (int l = 1; l <= p->n_levels; ++l) {
+    B.begin(&p->sched_factor, ST_INVERSE);
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      p->inv_desc.push_back(InvDesc{c.off_F, c.n, c.n + c.b, i, c.b == 0 ? 1 : 0});
+      B.dim(c.n);
+    }
+    B.end();
+    B.begin(&p->sched_factor, ST_GEMM);  // Psi = -A_ii^{-1} A_iB
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0) continue;
+      const int ld = c.n + c.b;
+      B.gemm(c.off_Psi, c.b, c.off_Psi, c.b, c.off_F, ld, OP_N, c.off_F + c.n, ld, OP_N, c.n, c.b, c.n, -1.0, 0.0);
+    }
+    B.end();
+    B.begin(&p->sched_factor, ST_GEMM);  // U = A_BB-updates + A_iB^T Psi
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0) continue;
+      const int ld = c.n + c.b;
+      B.gemm(c.off_BB, c.b, c.off_BB, c.b, c.off_F + c.n, ld, OP_T, c.off_Psi, c.b, OP_N, c.b, c.b, c.n, 1.0, 1.0);
+    }
+    B.end();
+    for (int s = 0; s <= max_slot; ++s) {
+      B.begin(&p->sched_factor, ST_SCATTER);
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (c.b == 0 || c.slot != s) continue;
+        const Cluster& P = cl[c.parent];
+        p->scat_desc.push_back(ScatterDesc{c.off_BB, P.off_F, P.off_BB, c.b, P.n, P.b, map_begin[i]});
+        B.dim(c.b);
+      }
+      B.end();
+    }
+  }
+  // ---- S4 G^r extraction -----------------------------------------------------
+  B.begin(&p->sched_green, ST_GEMM);  // clusters without boundary: G_II = A_ii^{-1}
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = cl[i];
+    if (c.b != 0) continue;
+    B.gemm(c.off_G, c.n, c.off_F, c.n, 0, 1, OP_N, 0, 1, OP_N, c.n, c.n, 0, 0.0, 1.0);
+  }
+  B.end();
+  for (int l = p->n_levels; l >= 1; --l) {
+    B.begin(&p->sched_green, ST_GATHER_SYM);
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0) continue;
+      const Cluster& P = cl[c.parent];
+      p->gath_desc.push_back(GatherDesc{c.off_BB, P.off_G, P.off_BB, c.b, P.n, P.b, map_begin[i]});
+      B.dim(c.b);
+    }
+    B.end();
+    B.begin(&p->sched_green, ST_GEMM);  // G_IB = Psi G_BB
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0) continue;
+      const int ld = c.n + c.b;
+      B.gemm(c.off_G + c.n, ld, c.off_G + c.n, ld, c.off_Psi, c.b, OP_N, c.off_BB, c.b, OP_N, c.n, c.b, c.b, 1.0, 0.0);
+    }
+    B.end();
+    B.begin(&p->sched_green, ST_GEMM);  // G_II = A_ii^{-1} + Psi G_IB^T
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0) continue;
+      const int ld = c.n + c.b;
+      B.gemm(c.off_G, ld, c.off_F, ld, c.off_Psi, c.b, OP_N, c.off_G + c.n, ld, OP_T, c.n, c.n, c.b, 1.0, 1.0);
+    }
+    B.end();
+  }
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = cl[i];
+    p->diag_g.push_back(DiagDesc{c.off_G, c.n, c.n + c.b, site_begin[i]});
+    for (int s = 0; s < 2; ++s) p->diag_p[s].push_back(DiagDesc{c.off_P[s], c.n, c.n + c.b, site_begin[i]});
+  }
+  // ---- S5-S8 G^< and G^> -----------------------------------------------------
+  for (int v = 0; v < 2; ++v) {
+    auto* S = &p->sched_lesser[v];
+    auto active = [&](int i) { return v == 1 || cl[i].nactive; };
+    B.begin(S, ST_ZERO);
+    for (int i = 0; i < nc; ++i) {
+      const Cluster& c = cl[i];
+      const int64_t F = int64_t(c.n) * (c.n + c.b);
+      for (int s = 0; s < 2; ++s) {
+        if (active(i)) {
+          if (v == 0) p->zero_desc.push_back(ZeroDesc{c.off_N[s], F});
+          if (c.b) p->zero_desc.push_back(ZeroDesc{c.off_NBB[s], int64_t(c.b) * c.b});
+        } else if (c.b == 0) {
+          p->zero_desc.push_back(ZeroDesc{c.off_P[s], F});
+        }
+      }
+    }
+    B.end();
+    if (v == 1) {
+      B.begin(S, ST_NPH);  // N = Sigma_ph conj(G) on every cluster
+      for (int i = 0; i < nc; ++i) {
+        const Cluster& c = cl[i];
+        for (int s = 0; s < 2; ++s)
+          p->nph_desc.push_back(NPhDesc{c.off_N[s], c.off_G, c.n, c.n + c.b, site_begin[i], s});
+        B.dim(c.n + c.b);
+      }
+      B.end();
+    }
+    B.begin(S, ST_GEMM);  // N(contact rows) += Sigma^<_c conj(G(contact rows, :))
+    for (int i = 0; i < nc; ++i) {
+      const Cluster& c = cl[i];
+      const int ld = c.n + c.b;
+      for (auto& ct : c.contacts) {
+        const int m = p->contact_ptr[ct.first + 1] - p->contact_ptr[ct.first];
+        const int64_t row = int64_t(ct.second) * ld;
+        for (int s = 0; s < 2; ++s)
+          B.gemm(c.off_N[s] + row, ld, c.off_N[s] + row, ld, AUX_BIT | (int64_t(s) * p->sigma_elems + soff[ct.first]),
+                 m, OP_N, c.off_G + row, ld, OP_C, m, ld, m, 1.0, 1.0);
+      }
+    }
+    B.end();
+    for (int l = 1; l <= p->n_levels; ++l) {  // fold N: N_BB += Psi^T N_IB, extend-add
+      B.begin(S, ST_GEMM);
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (c.b == 0 || !active(i)) continue;
+        const int ld = c.n + c.b;
+        for (int s = 0; s < 2; ++s)
+          B.gemm(c.off_NBB[s], c.b, c.off_NBB[s], c.b, c.off_Psi, c.b, OP_T, c.off_N[s] + c.n, ld, OP_N, c.b, c.b,
+                 c.n, 1.0, 1.0);
+      }
+      B.end();
+      for (int sl = 0; sl <= max_slot; ++sl) {
+        B.begin(S, ST_SCATTER);
+        for (int i : lev[l]) {
+          const Cluster& c = cl[i];
+          if (c.b == 0 || !active(i) || c.slot != sl) continue;
+          const Cluster& P = cl[c.parent];
+          for (int s = 0; s < 2; ++s)
+            p->scat_desc.push_back(ScatterDesc{c.off_NBB[s], P.off_N[s], P.off_NBB[s], c.b, P.n, P.b, map_begin[i]});
+          B.dim(c.b);
+        }
+        B.end();
+      }
+    }
+    B.begin(S, ST_GEMM);  // P^(L-1) = G^(L-1) N^(L-1): P = A_ii^{-1} N
+    for (int i = 0; i < nc; ++i) {
+      const Cluster& c = cl[i];
+      if (!active(i)) continue;
+      const int ld = c.n + c.b;
+      for (int s = 0; s < 2; ++s)
+        B.gemm(c.off_P[s], ld, c.off_P[s], ld, c.off_F, ld, OP_N, c.off_N[s], ld, OP_N, c.n, ld, c.n, 1.0, 0.0);
+    }
+    B.end();
+    for (int l = p->n_levels; l >= 1; --l) {  // extract P
+      B.begin(S, ST_GATHER_SKEW);
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (c.b == 0) continue;
+        const Cluster& P = cl[c.parent];
+        for (int s = 0; s < 2; ++s)
+          p->gath_desc.push_back(GatherDesc{c.off_NBB[s], P.off_P[s], P.off_NBB[s], c.b, P.n, P.b, map_begin[i]});
+        B.dim(c.b);
+      }
+      B.end();
+      B.begin(S, ST_GEMM);  // P_IB = P_IB + Psi P_BB
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (c.b == 0) continue;
+        const int ld = c.n + c.b;
+        for (int s = 0; s < 2; ++s)
+          B.gemm(c.off_P[s] + c.n, ld, c.off_P[s] + c.n, ld, c.off_Psi, c.b, OP_N, c.off_NBB[s], c.b, OP_N, c.n, c.b,
+                 c.b, 1.0, active(i) ? 1.0 : 0.0);
+      }
+      B.end();
+      B.begin(S, ST_GEMM);  // P_II = P_II + Psi P_BI,  P_BI = -(P_IB)^dagger
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (c.b == 0) continue;
+        const int ld = c.n + c.b;
+        for (int s = 0; s < 2; ++s)
+          B.gemm(c.off_P[s], ld, c.off_P[s], ld, c.off_Psi, c.b, OP_N, c.off_P[s] + c.n, ld, OP_H, c.n, c.n, c.b,
+                 -1.0, active(i) ? 1.0 : 0.0);
+      }
+      B.end();
+    }
+  }
+}
+
+}  // namespace ndgf

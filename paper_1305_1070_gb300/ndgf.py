@@ -1,0 +1,265 @@
+"""ctypes binding of the C ABI in ``include/ndgf.h`` (argument marshalling only).
+
+Every function keeps the C name and raises ``NDError`` on a non-OK status.
+Array arguments may be torch tensors (CUDA or CPU) or numpy arrays (host);
+complex arrays are complex128 (interleaved re, im).  ``stream=None`` means
+torch's current CUDA stream.  The library is loaded from the in-tree build
+``_lib/libndgf.so``; there is no fallback when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+STATUS = {0: "ND_OK", 1: "ND_ERR_INVALID_ARG", 2: "ND_ERR_NOT_SYMMETRIC", 3: "ND_ERR_SINGULAR",
+          4: "ND_ERR_NOT_SKEW_HERMITIAN", 5: "ND_ERR_OOM", 6: "ND_ERR_CUDA", 7: "ND_ERR_TIMEOUT",
+          8: "ND_ERR_UNSUPPORTED"}
+ND_PREC_FP64 = 0
+ND_PREC_MIXED = 1
+
+EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
+           "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_fact_status",
+           "nd_lead_create", "nd_lead_sigma", "nd_lead_destroy", "nd_sigma_lesser_fermi", "nd_phonon_const",
+           "nd_last_error", "nd_version"]
+
+
+class NDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nd_graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("n_contacts", ctypes.c_int32), ("contact_ptr", ctypes.c_void_p), ("contact_idx", ctypes.c_void_p),
+                ("coord_dim", ctypes.c_int32), ("coords", ctypes.c_void_p)]
+
+
+class nd_opts(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+class nd_plan_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("n_clusters", ctypes.c_int32),
+                ("n_levels", ctypes.c_int32), ("max_n", ctypes.c_int32), ("max_b", ctypes.c_int32),
+                ("n_contacts", ctypes.c_int32), ("n_roots", ctypes.c_int32), ("flops_factor", ctypes.c_double),
+                ("flops_green_r", ctypes.c_double), ("flops_green_lesser", ctypes.c_double),
+                ("arena_bytes_fp64", ctypes.c_double), ("arena_bytes_fp32", ctypes.c_double)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def lib():
+    """Load the library (raises when it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"{_build.LIB} is missing: build it with paper_1305_1070_gb300.build.build()")
+        L = ctypes.CDLL(_build.LIB)
+        sig = {
+            "nd_analyze": ([ctypes.POINTER(nd_graph), ctypes.POINTER(nd_opts), ctypes.POINTER(_P)], _I32),
+            "nd_plan_query": ([_P, ctypes.POINTER(nd_plan_info)], _I32),
+            "nd_plan_tree": ([_P, _P, _P, _P, _P, _P], _I32),
+            "nd_plan_cluster_sites": ([_P, _I32, _P], _I32),
+            "nd_plan_destroy": ([_P], None),
+            "nd_fact_create": ([_P, _I32, _I32, ctypes.POINTER(_P)], _I32),
+            "nd_fact_destroy": ([_P], None),
+            "nd_factor": ([_P, _P, _P, _P, _P, _I32, _D, _P], _I32),
+            "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+            "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
+            "nd_lead_create": ([_I32, _I32, _P, _P, _P, ctypes.POINTER(_P)], _I32),
+            "nd_lead_sigma": ([_P, _P, _I32, _D, _P, _I64, _I64, _P], _I32),
+            "nd_lead_destroy": ([_P], None),
+            "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
+            "nd_phonon_const": ([_I32, _I32, _D, _D, _D, _P, _P, _P, _P, _P], _I32),
+            "nd_last_error": ([], ctypes.c_char_p),
+            "nd_version": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+def _check(st, name):
+    if st != 0:
+        raise NDError(st, f"{name}: {lib().nd_last_error().decode()}")
+
+
+def _ptr(x, keep):
+    """Raw pointer of a tensor / array (None -> NULL).  Arrays are kept alive
+    in ``keep`` for the duration of the call."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        keep.append(x)
+        return x.data_ptr()
+    a = np.ascontiguousarray(x)
+    keep.append(a)
+    return a.ctypes.data
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(lib(), self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan(_Handle):
+    _destroy = "nd_plan_destroy"
+
+
+class Fact(_Handle):
+    _destroy = "nd_fact_destroy"
+
+    def __init__(self, ptr, plan):
+        super().__init__(ptr)
+        self.plan = plan  # the plan must outlive the workspace
+
+
+class Lead(_Handle):
+    _destroy = "nd_lead_destroy"
+
+
+def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=None, leaf_size=0) -> Plan:
+    keep = []
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    g = nd_graph()
+    g.n = n
+    g.rowptr = _ptr(rp, keep)
+    g.colind = _ptr(ci, keep)
+    if contact_ptr is not None:
+        cp = np.ascontiguousarray(contact_ptr, dtype=np.int32)
+        cidx = np.ascontiguousarray(contact_idx, dtype=np.int32)
+        g.n_contacts = len(cp) - 1
+        g.contact_ptr = _ptr(cp, keep)
+        g.contact_idx = _ptr(cidx, keep)
+    if coords is not None:
+        co = np.ascontiguousarray(coords, dtype=np.float64)
+        g.coord_dim = co.shape[1]
+        g.coords = _ptr(co, keep)
+    o = nd_opts()
+    o.leaf_size = leaf_size
+    out = _P()
+    _check(lib().nd_analyze(ctypes.byref(g), ctypes.byref(o), ctypes.byref(out)), "nd_analyze")
+    return Plan(out.value)
+
+
+def nd_plan_query(plan: Plan) -> dict:
+    info = nd_plan_info()
+    _check(lib().nd_plan_query(plan.ptr, ctypes.byref(info)), "nd_plan_query")
+    return {f: getattr(info, f) for f, _ in nd_plan_info._fields_}
+
+
+def nd_plan_tree(plan: Plan) -> dict:
+    info = nd_plan_query(plan)
+    nc, n = info["n_clusters"], info["n"]
+    arr = {k: np.zeros(nc, dtype=np.int32) for k in ("level", "parent", "n_i", "b_i")}
+    arr["cluster_of_site"] = np.zeros(n, dtype=np.int32)
+    _check(lib().nd_plan_tree(plan.ptr, arr["level"].ctypes.data, arr["parent"].ctypes.data, arr["n_i"].ctypes.data,
+                              arr["b_i"].ctypes.data, arr["cluster_of_site"].ctypes.data), "nd_plan_tree")
+    return arr
+
+
+def nd_plan_cluster_sites(plan: Plan, c: int, n_i: int, b_i: int):
+    out = np.zeros(n_i + b_i, dtype=np.int32)
+    _check(lib().nd_plan_cluster_sites(plan.ptr, c, out.ctypes.data), "nd_plan_cluster_sites")
+    return out[:n_i], out[n_i:]
+
+
+def nd_fact_create(plan: Plan, max_ne: int, precision: int = ND_PREC_FP64) -> Fact:
+    out = _P()
+    _check(lib().nd_fact_create(plan.ptr, max_ne, precision, ctypes.byref(out)), "nd_fact_create")
+    return Fact(out.value, plan)
+
+
+def nd_factor(fact: Fact, H_values, sigma_r, sigma_ph_r, energies, n_e: int, eta: float, stream=None):
+    keep = []
+    _check(lib().nd_factor(fact.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), _ptr(sigma_ph_r, keep),
+                           _ptr(energies, keep), n_e, eta, _stream(stream)), "nd_factor")
+
+
+def nd_diag_green(fact: Fact, sigma_lesser, sigma_greater, ph_lesser, ph_greater, Gr, Gl, Gg, stream=None):
+    keep = []
+    _check(lib().nd_diag_green(fact.ptr, _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep), _ptr(ph_lesser, keep),
+                               _ptr(ph_greater, keep), _ptr(Gr, keep), _ptr(Gl, keep), _ptr(Gg, keep),
+                               _stream(stream)), "nd_diag_green")
+
+
+def nd_fact_status(fact: Fact) -> int:
+    n = _I32()
+    st = lib().nd_fact_status(fact.ptr, ctypes.byref(n))
+    if st not in (0, 3):
+        _check(st, "nd_fact_status")
+    return n.value
+
+
+def nd_lead_create(H00, H01, tau) -> Lead:
+    keep = []
+    H00 = np.ascontiguousarray(H00, dtype=np.float64)
+    m = H00.shape[0]
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    out = _P()
+    _check(lib().nd_lead_create(m, tau.shape[0], _ptr(H00, keep), _ptr(np.ascontiguousarray(H01, dtype=np.float64), keep),
+                                _ptr(tau, keep), ctypes.byref(out)), "nd_lead_create")
+    return Lead(out.value)
+
+
+def nd_lead_sigma(lead: Lead, energies, n_e: int, eta: float, sigma_out, stride: int, offset: int, stream=None):
+    keep = []
+    _check(lib().nd_lead_sigma(lead.ptr, _ptr(energies, keep), n_e, eta, _ptr(sigma_out, keep), stride, offset,
+                               _stream(stream)), "nd_lead_sigma")
+
+
+def nd_sigma_lesser_fermi(sigma_r, n_e, m_c, mu, kT, energies, sigma_lesser, sigma_greater, stream=None):
+    keep = []
+    mc = np.ascontiguousarray(m_c, dtype=np.int32)
+    muv = np.ascontiguousarray(mu, dtype=np.float64)
+    _check(lib().nd_sigma_lesser_fermi(_ptr(sigma_r, keep), n_e, len(mc), _ptr(mc, keep), _ptr(muv, keep), kT,
+                                       _ptr(energies, keep), _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep),
+                                       _stream(stream)), "nd_sigma_lesser_fermi")
+
+
+def nd_phonon_const(n, n_e, gamma, mu, kT, energies, ph_r, ph_lesser, ph_greater, stream=None):
+    keep = []
+    _check(lib().nd_phonon_const(n, n_e, gamma, mu, kT, _ptr(energies, keep), _ptr(ph_r, keep),
+                                 _ptr(ph_lesser, keep), _ptr(ph_greater, keep), _stream(stream)), "nd_phonon_const")
+
+
+def nd_version() -> str:
+    return lib().nd_version().decode()

@@ -1,0 +1,76 @@
+"""One pass of the GPU path for a device workload: contact self-energies (S1a),
+lesser/greater self-energies, assembly and fold (S1-S3), selected inversion for
+G^r, G^< and G^> (S4-S8), all through the C ABI of ``include/ndgf.h``.
+
+torch is used for device memory and streams only; every arithmetic step runs
+in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import ndgf
+
+
+class Solver:
+    def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
+                 leaf_size: int = 64, device: str = "cuda"):
+        self.dev, self.tr = dev, tr
+        self.device = torch.device(device)
+        self.n = dev.n
+        cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])]).astype(np.int32)
+        ci = np.concatenate(dev.contacts).astype(np.int32) if dev.contacts else np.zeros(0, np.int32)
+        self.plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, leaf_size)
+        self.info = ndgf.nd_plan_query(self.plan)
+        self.m_c = [len(c) for c in dev.contacts]
+        self.off = np.concatenate([[0], np.cumsum([m * m for m in self.m_c])]).astype(np.int64)
+        self.sigma_elems = int(self.off[-1])
+        self.max_ne = int(max_ne or tr.n_e)
+        self.precision = precision
+        self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision)
+        self.leads = [ndgf.nd_lead_create(l.H00, l.H01, l.tau) for l in dev.leads]
+        kw = dict(device=self.device)
+        self.H = torch.as_tensor(dev.values, dtype=torch.float64, **kw).contiguous()
+        self.E = torch.zeros(self.max_ne, dtype=torch.float64, **kw)
+        se = max(1, self.sigma_elems)
+        self.sig_r = torch.zeros(self.max_ne, se, dtype=torch.complex128, **kw)
+        self.sig_l = torch.zeros_like(self.sig_r)
+        self.sig_g = torch.zeros_like(self.sig_r)
+        self.ph = tr.gamma_ph > 0.0
+        if self.ph:
+            self.ph_r = torch.zeros(self.max_ne, self.n, dtype=torch.complex128, **kw)
+            self.ph_l = torch.zeros_like(self.ph_r)
+            self.ph_g = torch.zeros_like(self.ph_r)
+        else:
+            self.ph_r = self.ph_l = self.ph_g = None
+        self.Gr = torch.zeros(self.max_ne, self.n, dtype=torch.complex128, **kw)
+        self.Gl = torch.zeros_like(self.Gr)
+        self.Gg = torch.zeros_like(self.Gr)
+
+    def step(self, energies, lesser: bool = True):
+        """Diagonals of G^r, G^<, G^> (caller order) for the given energies."""
+        n_e = len(energies)
+        if n_e > self.max_ne:
+            raise ValueError("more energies than the workspace holds")
+        E = self.E[:n_e]
+        if isinstance(energies, torch.Tensor):
+            E.copy_(energies)
+        else:
+            E.copy_(torch.as_tensor(np.asarray(energies, dtype=np.float64)))
+        tr = self.tr
+        for c, lead in enumerate(self.leads):
+            ndgf.nd_lead_sigma(lead, E, n_e, tr.eta, self.sig_r, self.sigma_elems, int(self.off[c]))
+        if self.leads:
+            ndgf.nd_sigma_lesser_fermi(self.sig_r, n_e, self.m_c, list(tr.mu), tr.kT, E, self.sig_l, self.sig_g)
+        if self.ph:
+            mu_ph = tr.mu_ph if tr.mu_ph is not None else 0.5 * (tr.mu[0] + tr.mu[1])
+            ndgf.nd_phonon_const(self.n, n_e, tr.gamma_ph, mu_ph, tr.kT, E, self.ph_r, self.ph_l, self.ph_g)
+        ndgf.nd_factor(self.fact, self.H, self.sig_r if self.leads else None, self.ph_r, E, n_e, tr.eta)
+        ndgf.nd_diag_green(self.fact, self.sig_l if lesser else None, self.sig_g if lesser else None,
+                           self.ph_l if lesser else None, self.ph_g if lesser else None,
+                           self.Gr, self.Gl if lesser else None, self.Gg if lesser else None)
+        return self.Gr[:n_e], self.Gl[:n_e], self.Gg[:n_e]
+
+    def singular_pivots(self) -> int:
+        return ndgf.nd_fact_status(self.fact)

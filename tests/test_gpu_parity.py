@@ -1,0 +1,115 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle, element
+by element on diag G^r, G^<, G^> (paper Eq. (1)-(2)).
+
+Tolerance of the complex128 path: relative max error <= 1e-10 per energy,
+max_j |x_j - y_j| / max_j |y_j|.  Sizes span several tiles, ragged tails,
+single-cluster and one-site-leaf trees, phonons, host-pointer arguments, and
+the full 512 x 128 workload on sampled energies.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dense, observables, rgf  # noqa: E402
+from paper_1305_1070_gb300 import build, ndgf, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+
+
+def _gpu(dev, tr, precision=ndgf.ND_PREC_FP64, leaf=64, energies=None):
+    from paper_1305_1070_gb300.solver import Solver
+    E = tr.energies if energies is None else np.asarray(energies)
+    s = Solver(dev, tr, precision=precision, leaf_size=leaf, max_ne=len(E))
+    Gr, Gl, Gg = s.step(E)
+    torch.cuda.synchronize()
+    assert s.singular_pivots() == 0
+    return {"Gr": Gr.cpu().numpy(), "Gl": Gl.cpu().numpy(), "Gg": Gg.cpu().numpy()}
+
+
+def _compare(got, ref, tol):
+    worst = 0.0
+    for k in ("Gr", "Gl", "Gg"):
+        for e in range(ref[k].shape[0]):
+            err = observables.rel_err(got[k][e], ref[k][e])
+            worst = max(worst, err)
+            assert err <= tol, f"{k} energy {e}: rel err {err:.3e}"
+    return worst
+
+
+def test_superlattice_64x16_all_energies_fp64():
+    dev, tr = workloads.workload("superlattice_64x16")
+    ref = rgf.green_diag(dev, tr)
+    got = _gpu(dev, tr)
+    _compare(got, ref, TOL64)
+
+
+@pytest.mark.parametrize("L,W,leaf,dis", [(37, 11, 20, 0.05), (23, 7, 9, 0.0), (16, 3, 1, 0.02)])
+def test_ragged_trees_fp64(L, W, leaf, dis):
+    dev = workloads.superlattice(L, W, disorder=dis, seed=L * W)
+    tr = workloads.Transport(energies=np.array([0.0, 0.137, 0.42]))
+    _compare(_gpu(dev, tr, leaf=leaf), dense.green_diag(dev, tr), TOL64)
+
+
+def test_phonon_fp64():
+    dev = workloads.superlattice(24, 9, disorder=0.03, seed=4)
+    tr = workloads.Transport(energies=np.array([0.05, 0.31]), gamma_ph=5e-3, mu_ph=0.05)
+    _compare(_gpu(dev, tr, leaf=24), dense.green_diag(dev, tr), TOL64)
+
+
+def test_single_cluster_and_chain():
+    dev = workloads.chain(3, t=1.0)
+    tr = workloads.Transport(energies=np.array([-0.5, 0.3]), mu=(0.2, -0.1), kT=0.05)
+    _compare(_gpu(dev, tr, leaf=64), dense.green_diag(dev, tr), TOL64)
+    dev = workloads.chain(40, t=1.0, potential=np.linspace(0, 0.3, 40))
+    _compare(_gpu(dev, tr, leaf=3), dense.green_diag(dev, tr), TOL64)
+
+
+def test_host_pointers_match_device_pointers():
+    from paper_1305_1070_gb300.solver import Solver
+    dev = workloads.superlattice(20, 6, disorder=0.02, seed=8)
+    tr = workloads.Transport(energies=np.linspace(0.0, 0.5, 5))
+    s = Solver(dev, tr, leaf_size=16)
+    Gr_d, Gl_d, Gg_d = [x.clone() for x in s.step(tr.energies)]
+    # same call with host (numpy) inputs and outputs
+    sig_r = s.sig_r[:5].cpu().numpy()
+    sig_l = s.sig_l[:5].cpu().numpy()
+    sig_g = s.sig_g[:5].cpu().numpy()
+    H = dev.values.copy()
+    E = tr.energies.copy()
+    out = [np.zeros((5, dev.n), dtype=np.complex128) for _ in range(3)]
+    ndgf.nd_factor(s.fact, H, sig_r, None, E, 5, tr.eta)
+    ndgf.nd_diag_green(s.fact, sig_l, sig_g, None, None, out[0], out[1], out[2])
+    torch.cuda.synchronize()
+    for a, b in zip(out, (Gr_d, Gl_d, Gg_d)):
+        assert np.array_equal(a, b.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", [ndgf.ND_PREC_FP64, ndgf.ND_PREC_MIXED])
+def test_full_size_512x128_sampled_energies(precision):
+    dev, tr = workloads.workload("superlattice_512x128")
+    pick = np.array([0, 97, 255])
+    E = tr.energies[pick]
+    ref = rgf.green_diag(dev, tr, energies=E)
+    got = _gpu(dev, tr, precision=precision, energies=E)
+    tol = TOL64 if precision == ndgf.ND_PREC_FP64 else 5e-3
+    worst = _compare(got, ref, tol)
+    print(f"precision {precision}: worst rel err {worst:.3e}")
+
+
+def test_mixed_precision_64x16():
+    dev, tr = workloads.workload("superlattice_64x16")
+    ref = rgf.green_diag(dev, tr)
+    got = _gpu(dev, tr, precision=ndgf.ND_PREC_MIXED)
+    worst = _compare(got, ref, 1e-3)
+    dens_ref = observables.density(ref["Gl"], tr.energies)
+    dens = observables.density(got["Gl"], tr.energies)
+    print(f"mixed 64x16: worst diag rel err {worst:.3e}, density rel err {observables.rel_err(dens, dens_ref):.3e}")

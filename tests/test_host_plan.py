@@ -1,0 +1,139 @@
+"""Host-side checks of the C library (no GPU): it loads, exports every symbol
+of include/ndgf.h, and nd_analyze produces a valid nested-dissection tree
+(paper Sec. 3.2 partition rules) with the correct symbolic fold."""
+import os
+import re
+from collections import defaultdict
+
+import numpy as np
+import pytest
+
+from paper_1305_1070_gb300 import build, ndgf, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    build.build()
+
+
+def test_exports_match_header():
+    hdr = open(os.path.join(ROOT, "include", "ndgf.h")).read()
+    declared = set(re.findall(r"\b(nd_[a-z_]+)\s*\(", hdr))
+    lib = ndgf.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(ndgf.EXPORTS)
+
+
+def _plan(dev, leaf):
+    cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])])
+    ci = np.concatenate(dev.contacts)
+    plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, leaf)
+    info = ndgf.nd_plan_query(plan)
+    tree = ndgf.nd_plan_tree(plan)
+    sets = [ndgf.nd_plan_cluster_sites(plan, c, tree["n_i"][c], tree["b_i"][c]) for c in range(info["n_clusters"])]
+    return plan, info, tree, sets
+
+
+def _ancestors(parent, i):
+    out = []
+    p = parent[i]
+    while p >= 0:
+        out.append(p)
+        p = parent[p]
+    return out
+
+
+def _check_tree(dev, leaf):
+    plan, info, tree, sets = _plan(dev, leaf)
+    parent, level, owner = tree["parent"], tree["level"], tree["cluster_of_site"]
+    nc = info["n_clusters"]
+    # partition of the sites
+    allI = np.concatenate([s[0] for s in sets])
+    assert sorted(allI.tolist()) == list(range(dev.n))
+    for c in range(nc):
+        assert (owner[sets[c][0]] == c).all()
+    # postorder, levels
+    for c in range(nc):
+        if parent[c] >= 0:
+            assert parent[c] > c and level[parent[c]] > level[c]
+    anc = [set(_ancestors(parent, c)) for c in range(nc)]
+    # every coupling is between a cluster and one of its ancestors (no coupling
+    # between clusters that are not on one root path, in particular on one level)
+    for r in range(dev.n):
+        for p in range(dev.rowptr[r], dev.rowptr[r + 1]):
+            a, b = owner[r], owner[dev.colind[p]]
+            assert a == b or a in anc[b] or b in anc[a]
+    # contact sets inside one cluster, leaves
+    for c_sites in dev.contacts:
+        assert len(set(owner[c_sites].tolist())) == 1
+    # symbolic fold: simulate block elimination on the boolean pattern
+    A = [set() for _ in range(dev.n)]
+    for r in range(dev.n):
+        A[r].update(dev.colind[dev.rowptr[r]:dev.rowptr[r + 1]].tolist())
+    for idx in dev.contacts:
+        for u in idx:
+            A[u].update(idx.tolist())
+    for c in range(nc):  # postorder = elimination order
+        I = set(sets[c][0].tolist())
+        nb = set()
+        for u in I:
+            nb |= A[u]
+        nb -= I
+        elim = {v for v in nb if owner[v] < c}  # folded already: must be descendants
+        assert all(c in anc[owner[v]] for v in elim)
+        nb -= elim
+        assert nb == set(sets[c][1].tolist()), f"boundary of cluster {c}"
+        for u in nb:  # fill among the boundary
+            A[u] |= nb
+    return info, tree
+
+
+@pytest.mark.parametrize("L,W,leaf", [(64, 16, 64), (37, 11, 20), (20, 20, 16), (9, 6, 8), (5, 2, 4), (16, 3, 1)])
+def test_superlattice_tree_valid(L, W, leaf):
+    info, tree = _check_tree(workloads.superlattice(L, W), leaf)
+    assert info["n_roots"] == 1
+    assert info["max_n"] <= max(leaf, W) or info["max_n"] <= max(L, W)
+
+
+def test_cnt_tree_valid():
+    _check_tree(workloads.cnt_zigzag(6), 40)
+
+
+def test_chain_and_single_cluster():
+    info, tree = _check_tree(workloads.chain(12), 4)
+    info, tree = _check_tree(workloads.chain(3), 64)
+    assert info["n_clusters"] == 1 and tree["b_i"][0] == 0
+
+
+def test_no_coordinates_bfs_bisection():
+    dev = workloads.superlattice(24, 8)
+    dev.coords = None
+    _check_tree(dev, 16)
+
+
+def test_rejects_asymmetric_and_out_of_range():
+    rp = np.array([0, 2, 3, 4])
+    ci = np.array([0, 1, 1, 2])  # (0,1) present but (1,0) missing
+    with pytest.raises(ndgf.NDError) as e:
+        ndgf.nd_analyze(3, rp, ci)
+    assert e.value.status == 2
+    with pytest.raises(ndgf.NDError) as e:
+        ndgf.nd_analyze(3, np.array([0, 1, 2, 3]), np.array([0, 1, 7]))
+    assert e.value.status == 1
+    with pytest.raises(ndgf.NDError) as e:  # a site in two contacts
+        dev = workloads.superlattice(4, 2)
+        ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, [0, 2, 4], [0, 1, 1, 2])
+    assert e.value.status == 1
+
+
+def test_flop_model_scaling():
+    # O(W^2 L) for fixed W (paper Sec. 4.2.1): doubling L doubles the count
+    f = []
+    for L in (128, 256, 512):
+        dev = workloads.superlattice(L, 32)
+        _, info, _, _ = _plan(dev, 64)
+        f.append(info["flops_factor"] + info["flops_green_r"])
+    assert 1.7 < f[1] / f[0] < 2.3 and 1.7 < f[2] / f[1] < 2.3
