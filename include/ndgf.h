@@ -54,6 +54,12 @@ typedef enum {
 
 typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1 } nd_precision;
 
+/* nd_fact_create flags.  ND_FACT_PHONON: reserve the G^< workspace of every
+ * cluster so that nd_diag_green accepts a phonon Sigma^< / Sigma^> (without it
+ * only the clusters on the path from a contact to the root carry that
+ * workspace). */
+#define ND_FACT_PHONON 1
+
 /* Sparsity pattern of H plus the contact site sets (host arrays).
  * rowptr[n+1], colind[nnz]: CSR pattern, 0-based, must be structurally
  * symmetric; the diagonal may be present or absent.  Contact c owns sites
@@ -118,9 +124,10 @@ void nd_plan_destroy(nd_plan* plan);
 /* ---- numeric workspace -----------------------------------------------------
  * Allocates device memory for up to max_ne energies at the given precision:
  * ND_PREC_FP64 = complex128 throughout; ND_PREC_MIXED = complex64 cluster
- * blocks and products with complex128 root inversion.  The plan must outlive
- * the handle.  Errors: ND_ERR_OOM, ND_ERR_CUDA, ND_ERR_INVALID_ARG. */
-nd_status nd_fact_create(const nd_plan* plan, int32_t max_ne, int32_t precision, nd_fact** out);
+ * blocks and products with complex128 root inversion.  flags: ND_FACT_*.
+ * The plan must outlive the handle.  Errors: ND_ERR_OOM, ND_ERR_CUDA,
+ * ND_ERR_INVALID_ARG. */
+nd_status nd_fact_create(const nd_plan* plan, int32_t max_ne, int32_t precision, int32_t flags, nd_fact** out);
 void nd_fact_destroy(nd_fact* fact);
 
 /* ---- S1 + S2 + S3: assemble and fold (paper Sec. 3.2, "folding", root) -----

@@ -68,6 +68,14 @@ struct nd_fact {
   DiagDesc *d_diag_g = nullptr, *d_diag_p[2] = {nullptr, nullptr};
   NPhDesc* d_nph = nullptr;
   ZeroDesc* d_zero = nullptr;
+  AncGatherDesc* d_anc = nullptr;
+  RowScatterDesc* d_rows = nullptr;
+  ColGatherDesc* d_colg = nullptr;
+  int32_t *d_site_ids = nullptr, *d_cmaps = nullptr, *d_owner = nullptr, *d_pos = nullptr;
+  int32_t *d_cl_n = nullptr, *d_cl_A = nullptr, *d_cl_ldG = nullptr;
+  int64_t *d_cl_offG = nullptr, *d_cl_offGX[2] = {nullptr, nullptr};
+  int flags = 0;
+  int64_t se = 0;  // workspace elements per energy
   TileRef* d_tiles = nullptr;
   // tile range of every GEMM step: index = step index in its schedule
   std::vector<std::pair<int, int>> tr_factor, tr_green, tr_lesser[2];
@@ -138,8 +146,10 @@ nd_status stage_in(const double* src, double* staging, size_t bytes, cudaStream_
 
 template <typename T>
 nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::vector<std::pair<int, int>>& tr,
-                       const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s) {
+                       const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s, int variant = 0) {
   const nd_plan* p = f->plan;
+  const AncTables at{f->d_site_ids, f->d_owner, f->d_pos, f->d_cl_n, f->d_cl_A, f->d_cl_ldG, f->d_cl_offG,
+                     f->d_cl_offGX[variant]};
   for (size_t si = 0; si < sched.size(); ++si) {
     const Step& st = sched[si];
     switch (st.kind) {
@@ -163,6 +173,15 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
       case ST_NPH:
         Kern<T>::nph(w, f->d_nph + st.begin, st.count, f->d_sites, ph_l, ph_g, p->n, s);
         break;
+      case ST_GATHER_ANC:
+        Kern<T>::gather_anc(w, f->d_anc + st.begin, st.count, at, s);
+        break;
+      case ST_SCATTER_ROWS:
+        Kern<T>::scatter_rows(w, f->d_rows + st.begin, st.count, f->d_maps, s);
+        break;
+      case ST_COLGATHER:
+        Kern<T>::colgather(w, f->d_colg + st.begin, st.count, f->d_cmaps, s);
+        break;
     }
   }
   ND_CUDA(cudaGetLastError());
@@ -171,7 +190,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
 
 }  // namespace
 
-extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t precision, nd_fact** out) {
+extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t precision, int32_t flags,
+                                    nd_fact** out) {
   if (!p || !out || max_ne <= 0) return fail(ND_ERR_INVALID_ARG, "nd_fact_create: bad argument");
   if (precision != ND_PREC_FP64 && precision != ND_PREC_MIXED)
     return fail(ND_ERR_INVALID_ARG, "nd_fact_create: unknown precision");
@@ -184,6 +204,8 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   f->precision = precision;
   f->max_ne = max_ne;
   f->esize = precision == ND_PREC_FP64 ? 16 : 8;
+  f->flags = flags;
+  f->se = p->arena_elems + ((flags & ND_FACT_PHONON) ? std::max(p->ext_elems[0], p->ext_elems[1]) : p->ext_elems[0]);
   nd_status st;
 #define TRY(x)          \
   do {                  \
@@ -193,7 +215,7 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
       return st;        \
     }                   \
   } while (0)
-  TRY(dalloc(f, &f->arena, size_t(p->arena_elems) * f->esize * max_ne));
+  TRY(dalloc(f, &f->arena, size_t(f->se) * f->esize * max_ne));
   TRY(dalloc(f, &f->aux, size_t(std::max<int64_t>(1, 2 * p->sigma_elems)) * f->esize * max_ne));
   if (precision == ND_PREC_MIXED) {
     int64_t rmax = 0;
@@ -218,6 +240,19 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dupload(f, p->diag_p[1], &f->d_diag_p[1]));
   TRY(dupload(f, p->nph_desc, &f->d_nph));
   TRY(dupload(f, p->zero_desc, &f->d_zero));
+  TRY(dupload(f, p->anc_desc, &f->d_anc));
+  TRY(dupload(f, p->rows_desc, &f->d_rows));
+  TRY(dupload(f, p->colg_desc, &f->d_colg));
+  TRY(dupload(f, p->site_ids, &f->d_site_ids));
+  TRY(dupload(f, p->cmaps, &f->d_cmaps));
+  TRY(dupload(f, p->owner, &f->d_owner));
+  TRY(dupload(f, p->pos, &f->d_pos));
+  TRY(dupload(f, p->cl_n, &f->d_cl_n));
+  TRY(dupload(f, p->cl_A, &f->d_cl_A));
+  TRY(dupload(f, p->cl_ldG, &f->d_cl_ldG));
+  TRY(dupload(f, p->cl_offG, &f->d_cl_offG));
+  TRY(dupload(f, p->cl_offGX[0], &f->d_cl_offGX[0]));
+  TRY(dupload(f, p->cl_offGX[1], &f->d_cl_offGX[1]));
   {
     const int tile = precision == ND_PREC_FP64 ? Kern<double>::gemm_tile() : Kern<float>::gemm_tile();
     std::vector<TileRef> tiles;
@@ -265,7 +300,7 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
   if ((st = stage_in(energies, f->st_E, size_t(n_e) * 8, s, &E)) != ND_OK) return st;
   f->n_e = n_e;
   ND_CUDA(cudaMemsetAsync(f->d_status, 0, sizeof(int), s));
-  Work w{f->arena, p->arena_elems, f->aux, 2 * p->sigma_elems, n_e};
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, n_e};
   const int nc = int(p->cl.size());
   if (f->precision == ND_PREC_FP64) {
     Kern<double>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph,
@@ -281,7 +316,7 @@ template <typename T>
 static nd_status diag_green_t(nd_fact* f, const double* sl, const double* sg, const double* pl, const double* pg,
                               double* outs[3], cudaStream_t s) {
   const nd_plan* p = f->plan;
-  Work w{f->arena, p->arena_elems, f->aux, 2 * p->sigma_elems, f->n_e};
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
   const int nc = int(p->cl.size());
   nd_status st = run_schedule<T>(f, p->sched_green, f->tr_green, w, nullptr, nullptr, s);
   if (st != ND_OK) return st;
@@ -289,7 +324,7 @@ static nd_status diag_green_t(nd_fact* f, const double* sl, const double* sg, co
   if (outs[1] || outs[2]) {
     Kern<T>::convert_aux(w, sl, sg, p->sigma_elems, s);
     const int v = (pl || pg) ? 1 : 0;
-    st = run_schedule<T>(f, p->sched_lesser[v], f->tr_lesser[v], w, pl, pg, s);
+    st = run_schedule<T>(f, p->sched_lesser[v], f->tr_lesser[v], w, pl, pg, s, v);
     if (st != ND_OK) return st;
     if (outs[1]) Kern<T>::diag_out(w, f->d_diag_p[0], nc, f->d_sites, outs[1], p->n, s);
     if (outs[2]) Kern<T>::diag_out(w, f->d_diag_p[1], nc, f->d_sites, outs[2], p->n, s);
@@ -307,6 +342,8 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
     return fail(ND_ERR_INVALID_ARG, "nd_diag_green: G^< / G^> requested without Sigma^< / Sigma^>");
   if ((ph_lesser == nullptr) != (ph_greater == nullptr))
     return fail(ND_ERR_INVALID_ARG, "nd_diag_green: pass both phonon Sigma^< and Sigma^> or neither");
+  if (ph_lesser && !(f->flags & ND_FACT_PHONON))
+    return fail(ND_ERR_INVALID_ARG, "nd_diag_green: phonon Sigma^< needs a workspace created with ND_FACT_PHONON");
   const nd_plan* p = f->plan;
   cudaStream_t s = (cudaStream_t)stream;
   const int n_e = f->n_e;

@@ -28,14 +28,24 @@ struct Cluster {
   std::vector<std::pair<int, int>> contacts; // (contact id, first row in I)
   std::vector<int> children;
   bool nactive = false; // the subtree holds a contact (N of Sec. 3.2 nonzero without phonons)
+  int A = 0;            // number of sites of all ancestors (columns of the extended blocks)
   // per-energy workspace regions, offsets in complex elements
   int64_t off_F = 0;    // n x (n+b): [A_ii | A_iB] folded front; A_ii^{-1} after the fold
   int64_t off_Psi = 0;  // n x b   : Psi_i = -A_ii^{-1} A_iB
   int64_t off_BB = 0;   // b x b   : Schur update accumulator, then G_BB
   int64_t off_G = 0;    // n x (n+b): [G_II | G_IB]
-  int64_t off_N[2] = {0, 0};   // n x (n+b): [N_II | N_IB] for Sigma^< (0) and Sigma^> (1)
-  int64_t off_NBB[2] = {0, 0}; // b x b: N_BB accumulator, then P_BB
+  int64_t off_PBB[2] = {0, 0}; // b x b: P_BB for Sigma^< (0) and Sigma^> (1)
   int64_t off_P[2] = {0, 0};   // n x (n+b): [P_II | P_IB]
+  // G^< workspace of clusters whose row block of N is nonzero, per variant
+  // (0: contacts only, 1: every cluster), -1 when the cluster has none.
+  // Columns run over Y_i = I_i followed by all ancestor sites (nearest first).
+  struct Ext {
+    int64_t off_GX = -1;       // n x A      : G_{I_i, anc(i)}
+    int64_t off_GBA = -1;      // b x A      : G_{B_i, anc(i)} (gathered)
+    int64_t off_NX[2] = {-1, -1}; // n x (n+A): N_{I_i, Y_i}
+    int64_t off_NB[2] = {-1, -1}; // b x A    : fold accumulator N_{B_i, anc(i)}
+    int64_t off_PX[2] = {-1, -1}; // n x (n+A): A_ii^{-1} N_{I_i, Y_i}
+  } ext[2];
 };
 
 // ---- device descriptors (plain structs, copied to the GPU) -----------------
@@ -93,11 +103,36 @@ struct DiagDesc {
   int32_t site_begin;
 };
 
-struct NPhDesc {     // N_{I,F} = diag(ph) conj(G_{I,F}) for one cluster and one side
-  int64_t off_N, off_G;
-  int32_t n, ld;
+struct NPhDesc {     // N_{I,Y} = diag(ph) conj([G_II | G_{I,anc}]) for one cluster and one side
+  int64_t off_NX, off_G, off_GX;
+  int32_t n, ldG, A;  // N is n x (n + A); G front has leading dimension ldG
   int32_t site_begin;
   int32_t rhs;        // 0: Sigma^<_ph, 1: Sigma^>_ph
+};
+
+// G_{B_i, anc(i)}: entry (r, j) is G between B_i[r] and the j-th ancestor site,
+// read from the G_II block or the extended block of the lower of the two
+// owning clusters (G^r is complex symmetric).
+struct AncGatherDesc {
+  int64_t off_dst;   // b x A
+  int32_t b, A;
+  int32_t bsite_begin;   // B_i sites in the site-id array
+  int32_t anc_begin;     // ancestor sites in the site-id array
+};
+
+// Rows of a child's fold update C (b x A_c, columns = Y_parent) into the
+// parent's N (rows in I_p) or its accumulator (rows in B_p, columns anc(p)).
+struct RowScatterDesc {
+  int64_t off_src, off_nx, off_nb;
+  int32_t b, A_c, n_p, A_p;
+  int32_t map_begin;
+};
+
+// P_{I,F}[:, j] = PX[:, cmap[j]] (columns I_i then B_i picked out of Y_i).
+struct ColGatherDesc {
+  int64_t off_P, off_PX;
+  int32_t n, b, A;
+  int32_t cmap_begin;
 };
 
 struct ZeroDesc {
@@ -114,6 +149,9 @@ enum StepKind : int32_t {
   ST_GATHER_SKEW = 4,
   ST_ZERO = 5,
   ST_NPH = 6,
+  ST_GATHER_ANC = 7,
+  ST_SCATTER_ROWS = 8,
+  ST_COLGATHER = 9,
 };
 
 struct Step {
@@ -134,7 +172,8 @@ struct nd_plan {
   std::vector<ndgf::Cluster> cl;  // postorder
   int32_t n_levels = 0, n_roots = 0, max_n = 0, max_b = 0;
   std::vector<int32_t> owner, pos; // owning cluster and position in its I, per site
-  int64_t arena_elems = 0;         // complex elements per energy
+  int64_t arena_elems = 0;         // complex elements per energy (base regions)
+  int64_t ext_elems[2] = {0, 0};   // extra elements of the G^< blocks, per variant
   int64_t sigma_elems = 0;         // sum_c m_c^2
   double flops_factor = 0, flops_green_r = 0, flops_green_lesser = 0;
 
@@ -151,6 +190,14 @@ struct nd_plan {
   std::vector<ndgf::DiagDesc> diag_g, diag_p[2];
   std::vector<ndgf::NPhDesc> nph_desc;
   std::vector<ndgf::ZeroDesc> zero_desc;
+  std::vector<ndgf::AncGatherDesc> anc_desc;
+  std::vector<ndgf::RowScatterDesc> rows_desc;
+  std::vector<ndgf::ColGatherDesc> colg_desc;
+  std::vector<int32_t> site_ids;   // B lists and ancestor lists (caller ids)
+  std::vector<int32_t> cmaps;      // column maps of ColGatherDesc
+  // per-cluster tables for the G lookup of AncGatherDesc (variant v = 0, 1)
+  std::vector<int32_t> cl_n, cl_A, cl_ldG;
+  std::vector<int64_t> cl_offG, cl_offGX[2];
   // launch schedules: the fold (S1-S3), the G^r extraction (S4) and the
   // G^< / G^> steps (S5-S8) without (0) or with (1) a phonon self-energy
   std::vector<ndgf::Step> sched_factor, sched_green, sched_lesser[2];

@@ -84,6 +84,7 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
     cx<T>& a = F[int64_t(r) * d.ld + r];
     a = mk<T>(T(double(a.x) + re), T(double(a.y) + im));
   }
+  __syncthreads();  // the contact blocks below update the same diagonal entries
   const double2* S = sigma_r + int64_t(e) * sigma_stride;
   for (int c = 0; c < 2; ++c) {
     const int r0 = c ? d.c1 : d.c0, m = c ? d.m1 : d.m0, so = c ? d.soff1 : d.soff0;
@@ -372,23 +373,99 @@ __global__ void k_zero(const ZeroDesc* __restrict__ descs, cx<T>* arena, int64_t
   for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) p[i] = z;
 }
 
-// N_{I,F} = diag(Sigma_ph) conj(G_{I,F})  (paper Sec. 3.2, first G^< step)
+// N_{I,Y} = diag(Sigma_ph) conj([G_II | G_{I,anc}])  (paper Sec. 3.2, first G^< step)
 template <typename T>
 __global__ void k_nph(const NPhDesc* __restrict__ descs, cx<T>* arena, int64_t se, const int32_t* __restrict__ sites,
                       const double2* __restrict__ ph_l, const double2* __restrict__ ph_g, int n) {
   const NPhDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   cx<T>* base = arena + int64_t(e) * se;
-  cx<T>* N = base + d.off_N;
+  cx<T>* N = base + d.off_NX;
   const cx<T>* G = base + d.off_G;
+  const cx<T>* GX = base + d.off_GX;
   const double2* ph = (d.rhs ? ph_g : ph_l) + int64_t(e) * n;
-  const int64_t tot = int64_t(d.n) * d.ld;
+  const int w = d.n + d.A;
+  const int64_t tot = int64_t(d.n) * w;
   for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int r = int(idx / d.ld);
+    const int r = int(idx / w), j = int(idx % w);
     const double2 s = ph[sites[d.site_begin + r]];
-    const cx<T> g = G[idx];
-    const cx<T> sv = mk<T>(T(s.x), T(s.y));
-    N[idx] = cmul<T>(sv, mk<T>(g.x, -g.y));
+    const cx<T> g = j < d.n ? G[int64_t(r) * d.ldG + j] : GX[int64_t(r) * d.A + (j - d.n)];
+    N[idx] = cmul<T>(mk<T>(T(s.x), T(s.y)), mk<T>(g.x, -g.y));
+  }
+}
+
+// G_{B_i, anc(i)} from the G_II and G_{I,anc} blocks of the ancestors: the
+// entry between sites x and y is stored by the lower of their two clusters
+// (G^r is complex symmetric); the column of a site y (owner o) inside the
+// ancestor columns of cluster q is A_q - n_o - A_o + pos(y).
+template <typename T>
+__global__ void k_gather_anc(const AncGatherDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                             const int32_t* __restrict__ site_ids, const int32_t* __restrict__ owner,
+                             const int32_t* __restrict__ pos, const int32_t* __restrict__ cl_n,
+                             const int32_t* __restrict__ cl_A, const int32_t* __restrict__ cl_ldG,
+                             const int64_t* __restrict__ cl_offG, const int64_t* __restrict__ cl_offGX) {
+  const AncGatherDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  cx<T>* dst = base + d.off_dst;
+  const int64_t tot = int64_t(d.b) * d.A;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / d.A), j = int(idx % d.A);
+    const int x = site_ids[d.bsite_begin + r], y = site_ids[d.anc_begin + j];
+    const int qx = owner[x], qy = owner[y];
+    int64_t src;
+    if (qx == qy)
+      src = cl_offG[qx] + int64_t(pos[x]) * cl_ldG[qx] + pos[y];
+    else if (qx < qy)
+      src = cl_offGX[qx] + int64_t(pos[x]) * cl_A[qx] + (cl_A[qx] - cl_n[qy] - cl_A[qy] + pos[y]);
+    else
+      src = cl_offGX[qy] + int64_t(pos[y]) * cl_A[qy] + (cl_A[qy] - cl_n[qx] - cl_A[qx] + pos[x]);
+    dst[idx] = base[src];
+  }
+}
+
+// Rows of a child's N fold update into its parent: rows of I_p go to the
+// parent's N_{I_p, Y_p} (same columns), rows of B_p to its accumulator
+// N_{B_p, anc(p)} (columns of I_p there are dead lower blocks and dropped).
+template <typename T>
+__global__ void k_scatter_rows(const RowScatterDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                               const int32_t* __restrict__ maps) {
+  const RowScatterDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const cx<T>* src = base + d.off_src;
+  cx<T>* nx = base + d.off_nx;
+  cx<T>* nb = base + d.off_nb;
+  const int32_t* map = maps + d.map_begin;
+  const int64_t tot = int64_t(d.b) * d.A_c;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / d.A_c), j = int(idx % d.A_c);
+    const int pr = map[r];
+    const cx<T> v = src[idx];
+    if (pr < d.n_p) {
+      cx<T>& f = nx[int64_t(pr) * d.A_c + j];
+      f.x += v.x;
+      f.y += v.y;
+    } else if (j >= d.n_p) {
+      cx<T>& f = nb[int64_t(pr - d.n_p) * d.A_p + (j - d.n_p)];
+      f.x += v.x;
+      f.y += v.y;
+    }
+  }
+}
+
+// [P_II | P_IB] = columns I_i and B_i of A_ii^{-1} N_{I,Y}.
+template <typename T>
+__global__ void k_colgather(const ColGatherDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                            const int32_t* __restrict__ cmaps) {
+  const ColGatherDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  cx<T>* P = base + d.off_P;
+  const cx<T>* PX = base + d.off_PX;
+  const int w = d.n + d.b, wx = d.n + d.A;
+  const int64_t tot = int64_t(d.n) * w;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / w), j = int(idx % w);
+    const int col = j < d.n ? j : cmaps[d.cmap_begin + j - d.n];
+    P[idx] = PX[int64_t(r) * wx + col];
   }
 }
 
@@ -477,6 +554,25 @@ void Kern<T>::nph(const Work& w, const NPhDesc* d, int count, const int32_t* sit
   if (count <= 0 || w.n_e <= 0) return;
   k_nph<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, sites, (const double2*)ph_l,
                                               (const double2*)ph_g, n);
+}
+
+template <typename T>
+void Kern<T>::gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_gather_anc<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, t.site_ids, t.owner, t.pos, t.cl_n,
+                                                     t.cl_A, t.cl_ldG, t.cl_offG, t.cl_offGX);
+}
+
+template <typename T>
+void Kern<T>::scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_scatter_rows<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps);
+}
+
+template <typename T>
+void Kern<T>::colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_colgather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, cmaps);
 }
 
 template <typename T>

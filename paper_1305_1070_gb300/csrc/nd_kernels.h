@@ -17,6 +17,12 @@ struct Work {
   int n_e;
 };
 
+// Per-site and per-cluster tables read by the ancestor gather.
+struct AncTables {
+  const int32_t *site_ids, *owner, *pos, *cl_n, *cl_A, *cl_ldG;
+  const int64_t *cl_offG, *cl_offGX;
+};
+
 template <typename T>
 struct Kern {
   static void assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst,
@@ -32,6 +38,9 @@ struct Kern {
   static void zero(const Work& w, const ZeroDesc* d, int count, cudaStream_t s);
   static void nph(const Work& w, const NPhDesc* d, int count, const int32_t* sites, const double* ph_l,
                   const double* ph_g, int n, cudaStream_t s);
+  static void gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, cudaStream_t s);
+  static void scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
+  static void colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, cudaStream_t s);
   static void diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
                        cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,

@@ -267,7 +267,14 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
     for (int r = 0; r < n; ++r)
       for (int p = g->rowptr[r]; p < g->rowptr[r + 1]; ++p)
         if (g->colind[p] != r) d.adj[fill[r]++] = g->colind[p];
-    for (int r = 0; r < n; ++r) std::sort(d.adj.begin() + d.aptr[r], d.adj.begin() + d.aptr[r + 1]);
+    for (int r = 0; r < n; ++r) {
+      std::sort(d.adj.begin() + d.aptr[r], d.adj.begin() + d.aptr[r + 1]);
+      for (int p = d.aptr[r] + 1; p < d.aptr[r + 1]; ++p)
+        if (d.adj[p] == d.adj[p - 1]) {
+          delete plan;
+          return fail(ND_ERR_INVALID_ARG, "nd_analyze: duplicate entry in row " + std::to_string(r));
+        }
+    }
     for (int r = 0; r < n; ++r)
       for (int p = d.aptr[r]; p < d.aptr[r + 1]; ++p) {
         int c = d.adj[p];
@@ -462,6 +469,10 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
     }
   }
   // ---- levels, sizes, workspace layout, flop model --------------------------
+  for (int i = nn - 1; i >= 0; --i) {  // parents come after children in postorder
+    Cluster& c = cl[i];
+    c.A = c.parent >= 0 ? cl[c.parent].A + cl[c.parent].n : 0;
+  }
   int64_t off = 0;
   double ff = 0, fg = 0, fl = 0;
   for (int i = 0; i < nn; ++i) {
@@ -476,20 +487,38 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
     c.off_BB = off; off = align16(off + b * b);
     c.off_G = off; off = align16(off + F);
     for (int s = 0; s < 2; ++s) {
-      c.off_N[s] = off; off = align16(off + F);
-      c.off_NBB[s] = off; off = align16(off + b * b);
+      c.off_PBB[s] = off; off = align16(off + b * b);
       c.off_P[s] = off; off = align16(off + F);
     }
-    const double dn = double(nI), db = double(b);
+    const double dn = double(nI), db = double(b), dA = double(c.A);
     ff += 8.0 * (dn * dn * dn + dn * dn * db + dn * db * db);
     fg += 8.0 * (dn * db * db + dn * dn * db);
     double lesser = 2.0 * (dn * db * db + dn * dn * db);  // P extraction, both sides
-    if (c.nactive) lesser += 2.0 * (dn * db * db + dn * dn * (dn + db));  // N fold + P^(L-1)
+    if (c.nactive) lesser += dn * db * dA + 2.0 * (db * dn * dA + dn * dn * (dn + dA));  // G_{I,anc}, N fold, P^(L-1)
     for (auto& ct : c.contacts) {
       double m = double(plan->contact_ptr[ct.first + 1] - plan->contact_ptr[ct.first]);
-      lesser += 2.0 * m * m * (dn + db);  // N = Sigma^< conj(G)
+      lesser += 2.0 * m * m * (dn + dA);  // N = Sigma^< conj(G)
     }
     fl += 8.0 * lesser;
+  }
+  // G^< blocks over ancestor columns: variant 0 = clusters whose subtree holds
+  // a contact, variant 1 = every cluster (a phonon self-energy on all sites)
+  for (int v = 0; v < 2; ++v) {
+    int64_t eo = off;
+    for (int i = 0; i < nn; ++i) {
+      Cluster& c = cl[i];
+      if (v == 0 && !c.nactive) continue;
+      const int64_t nI = c.n, b = c.b, A = c.A, W = nI * (nI + A);
+      auto& x = c.ext[v];
+      x.off_GX = eo; eo = align16(eo + nI * A);
+      x.off_GBA = eo; eo = align16(eo + b * A);
+      for (int s = 0; s < 2; ++s) {
+        x.off_NX[s] = eo; eo = align16(eo + W);
+        x.off_NB[s] = eo; eo = align16(eo + b * A);
+        x.off_PX[s] = eo; eo = align16(eo + W);
+      }
+    }
+    plan->ext_elems[v] = eo - off;
   }
   plan->arena_elems = off;
   plan->flops_factor = ff;
@@ -514,8 +543,8 @@ extern "C" nd_status nd_plan_query(const nd_plan* p, nd_plan_info* out) {
   out->flops_factor = p->flops_factor;
   out->flops_green_r = p->flops_green_r;
   out->flops_green_lesser = p->flops_green_lesser;
-  out->arena_bytes_fp64 = double(p->arena_elems) * 16.0;
-  out->arena_bytes_fp32 = double(p->arena_elems) * 8.0;
+  out->arena_bytes_fp64 = double(p->arena_elems + p->ext_elems[0]) * 16.0;
+  out->arena_bytes_fp32 = double(p->arena_elems + p->ext_elems[0]) * 8.0;
   return ND_OK;
 }
 

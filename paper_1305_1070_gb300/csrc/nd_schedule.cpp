@@ -7,8 +7,9 @@
 //   Psi = -A_ii^{-1} A_iB
 //   BB  = Schur update accumulator (fold), then G_BB (extraction)
 //   G   = [G_II | G_IB]
-//   N_s = [N_II | N_IB], NBB_s = N_BB accumulator, then P_BB; P_s = [P_II | P_IB]
-// for s = 0 (Sigma^<, G^<) and s = 1 (Sigma^>, G^>).
+//   P_s = [P_II | P_IB], PBB_s = P_BB, for s = 0 (Sigma^<, G^<) and s = 1 (Sigma^>, G^>)
+//   and, on clusters whose N row block is nonzero, the ancestor-column blocks
+//   GX = G_{I,anc}, NX_s = N_{I, I+anc}, NB_s = N_{B,anc}, PX_s = A_ii^{-1} NX_s.
 
 #include <algorithm>
 
@@ -34,6 +35,9 @@ struct Builder {
       case ST_GATHER_SKEW: st.begin = int32_t(p->gath_desc.size()); break;
       case ST_ZERO: st.begin = int32_t(p->zero_desc.size()); break;
       case ST_NPH: st.begin = int32_t(p->nph_desc.size()); break;
+      case ST_GATHER_ANC: st.begin = int32_t(p->anc_desc.size()); break;
+      case ST_SCATTER_ROWS: st.begin = int32_t(p->rows_desc.size()); break;
+      case ST_COLGATHER: st.begin = int32_t(p->colg_desc.size()); break;
     }
   }
   void end() {
@@ -46,6 +50,9 @@ struct Builder {
       case ST_GATHER_SKEW: e = int32_t(p->gath_desc.size()); break;
       case ST_ZERO: e = int32_t(p->zero_desc.size()); break;
       case ST_NPH: e = int32_t(p->nph_desc.size()); break;
+      case ST_GATHER_ANC: e = int32_t(p->anc_desc.size()); break;
+      case ST_SCATTER_ROWS: e = int32_t(p->rows_desc.size()); break;
+      case ST_COLGATHER: e = int32_t(p->colg_desc.size()); break;
     }
     st.count = e - st.begin;
     if (st.count > 0) cur->push_back(st);
@@ -216,77 +223,136 @@ void build_schedules(nd_plan* p) {
     for (int s = 0; s < 2; ++s) p->diag_p[s].push_back(DiagDesc{c.off_P[s], c.n, c.n + c.b, site_begin[i]});
   }
   // ---- S5-S8 G^< and G^> -----------------------------------------------------
+  // Paper Sec. 3.2: N = Sigma^< (G^(0))^dagger uses G^(0)_{ij} for every
+  // ancestor cluster j of i, so a cluster whose row block of N is nonzero
+  // carries N over I_i and all ancestor sites (Y_i); its fold update moves
+  // up row by row.  The P extraction only needs [P_II | P_IB] and P_BB.
+  std::vector<int32_t> bsite_begin(nc), anc_begin(nc), cmap_begin(nc);
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = cl[i];
+    bsite_begin[i] = int32_t(p->site_ids.size());
+    p->site_ids.insert(p->site_ids.end(), c.B.begin(), c.B.end());
+    anc_begin[i] = int32_t(p->site_ids.size());
+    for (int a = c.parent; a >= 0; a = cl[a].parent) p->site_ids.insert(p->site_ids.end(), cl[a].I.begin(), cl[a].I.end());
+    cmap_begin[i] = int32_t(p->cmaps.size());
+    for (int k = 0; k < c.b; ++k) {
+      const int u = c.B[k], o = p->owner[u];
+      p->cmaps.push_back(c.n + c.A - cl[o].n - cl[o].A + p->pos[u]);
+    }
+    p->cl_n.push_back(c.n);
+    p->cl_A.push_back(c.A);
+    p->cl_ldG.push_back(c.n + c.b);
+    p->cl_offG.push_back(c.off_G);
+    p->cl_offGX[0].push_back(c.ext[0].off_GX);
+    p->cl_offGX[1].push_back(c.ext[1].off_GX);
+  }
   for (int v = 0; v < 2; ++v) {
     auto* S = &p->sched_lesser[v];
     auto active = [&](int i) { return v == 1 || cl[i].nactive; };
     B.begin(S, ST_ZERO);
     for (int i = 0; i < nc; ++i) {
       const Cluster& c = cl[i];
-      const int64_t F = int64_t(c.n) * (c.n + c.b);
+      const auto& x = c.ext[v];
       for (int s = 0; s < 2; ++s) {
         if (active(i)) {
-          if (v == 0) p->zero_desc.push_back(ZeroDesc{c.off_N[s], F});
-          if (c.b) p->zero_desc.push_back(ZeroDesc{c.off_NBB[s], int64_t(c.b) * c.b});
+          if (v == 0) p->zero_desc.push_back(ZeroDesc{x.off_NX[s], int64_t(c.n) * (c.n + c.A)});
+          if (c.b && c.A) p->zero_desc.push_back(ZeroDesc{x.off_NB[s], int64_t(c.b) * c.A});
         } else if (c.b == 0) {
-          p->zero_desc.push_back(ZeroDesc{c.off_P[s], F});
+          p->zero_desc.push_back(ZeroDesc{c.off_P[s], int64_t(c.n) * c.n});
         }
       }
     }
     B.end();
-    if (v == 1) {
-      B.begin(S, ST_NPH);  // N = Sigma_ph conj(G) on every cluster
-      for (int i = 0; i < nc; ++i) {
+    for (int l = p->n_levels; l >= 1; --l) {  // G_{I,anc} = Psi G_{B,anc}, top down
+      B.begin(S, ST_GATHER_ANC);
+      for (int i : lev[l]) {
         const Cluster& c = cl[i];
-        for (int s = 0; s < 2; ++s)
-          p->nph_desc.push_back(NPhDesc{c.off_N[s], c.off_G, c.n, c.n + c.b, site_begin[i], s});
-        B.dim(c.n + c.b);
+        if (!active(i) || c.b == 0 || c.A == 0) continue;
+        p->anc_desc.push_back(AncGatherDesc{c.ext[v].off_GBA, c.b, c.A, bsite_begin[i], anc_begin[i]});
+        B.dim(c.b);
+      }
+      B.end();
+      B.begin(S, ST_GEMM);
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (!active(i) || c.b == 0 || c.A == 0) continue;
+        B.gemm(c.ext[v].off_GX, c.A, c.ext[v].off_GX, c.A, c.off_Psi, c.b, OP_N, c.ext[v].off_GBA, c.A, OP_N, c.n, c.A,
+               c.b, 1.0, 0.0);
       }
       B.end();
     }
-    B.begin(S, ST_GEMM);  // N(contact rows) += Sigma^<_c conj(G(contact rows, :))
+    if (v == 1) {
+      B.begin(S, ST_NPH);  // N = Sigma_ph conj(G_{I,Y}) on every cluster
+      for (int i = 0; i < nc; ++i) {
+        const Cluster& c = cl[i];
+        for (int s = 0; s < 2; ++s)
+          p->nph_desc.push_back(NPhDesc{c.ext[v].off_NX[s], c.off_G, c.ext[v].off_GX, c.n, c.n + c.b, c.A,
+                                        site_begin[i], s});
+        B.dim(c.n + c.A);
+      }
+      B.end();
+    }
+    B.begin(S, ST_GEMM);  // N(contact rows) += Sigma^<_c conj(G(contact rows, Y))
     for (int i = 0; i < nc; ++i) {
       const Cluster& c = cl[i];
-      const int ld = c.n + c.b;
+      const auto& x = c.ext[v];
+      const int ldN = c.n + c.A, ldG = c.n + c.b;
       for (auto& ct : c.contacts) {
         const int m = p->contact_ptr[ct.first + 1] - p->contact_ptr[ct.first];
-        const int64_t row = int64_t(ct.second) * ld;
-        for (int s = 0; s < 2; ++s)
-          B.gemm(c.off_N[s] + row, ld, c.off_N[s] + row, ld, AUX_BIT | (int64_t(s) * p->sigma_elems + soff[ct.first]),
-                 m, OP_N, c.off_G + row, ld, OP_C, m, ld, m, 1.0, 1.0);
+        const int64_t r0 = ct.second;
+        for (int s = 0; s < 2; ++s) {
+          const int64_t sig = AUX_BIT | (int64_t(s) * p->sigma_elems + soff[ct.first]);
+          B.gemm(x.off_NX[s] + r0 * ldN, ldN, x.off_NX[s] + r0 * ldN, ldN, sig, m, OP_N, c.off_G + r0 * ldG, ldG, OP_C,
+                 m, c.n, m, 1.0, 1.0);
+          if (c.A)
+            B.gemm(x.off_NX[s] + r0 * ldN + c.n, ldN, x.off_NX[s] + r0 * ldN + c.n, ldN, sig, m, OP_N,
+                   x.off_GX + r0 * c.A, c.A, OP_C, m, c.A, m, 1.0, 1.0);
+        }
       }
     }
     B.end();
-    for (int l = 1; l <= p->n_levels; ++l) {  // fold N: N_BB += Psi^T N_IB, extend-add
+    for (int l = 1; l <= p->n_levels; ++l) {  // fold N: N_{B,anc} += Psi^T N_{I,anc}, rows to the parent
       B.begin(S, ST_GEMM);
       for (int i : lev[l]) {
         const Cluster& c = cl[i];
         if (c.b == 0 || !active(i)) continue;
-        const int ld = c.n + c.b;
+        const auto& x = c.ext[v];
         for (int s = 0; s < 2; ++s)
-          B.gemm(c.off_NBB[s], c.b, c.off_NBB[s], c.b, c.off_Psi, c.b, OP_T, c.off_N[s] + c.n, ld, OP_N, c.b, c.b,
-                 c.n, 1.0, 1.0);
+          B.gemm(x.off_NB[s], c.A, x.off_NB[s], c.A, c.off_Psi, c.b, OP_T, x.off_NX[s] + c.n, c.n + c.A, OP_N, c.b,
+                 c.A, c.n, 1.0, 1.0);
       }
       B.end();
       for (int sl = 0; sl <= max_slot; ++sl) {
-        B.begin(S, ST_SCATTER);
+        B.begin(S, ST_SCATTER_ROWS);
         for (int i : lev[l]) {
           const Cluster& c = cl[i];
           if (c.b == 0 || !active(i) || c.slot != sl) continue;
           const Cluster& P = cl[c.parent];
           for (int s = 0; s < 2; ++s)
-            p->scat_desc.push_back(ScatterDesc{c.off_NBB[s], P.off_N[s], P.off_NBB[s], c.b, P.n, P.b, map_begin[i]});
+            p->rows_desc.push_back(RowScatterDesc{c.ext[v].off_NB[s], P.ext[v].off_NX[s], P.ext[v].off_NB[s], c.b, c.A,
+                                                  P.n, P.A, map_begin[i]});
           B.dim(c.b);
         }
         B.end();
       }
     }
-    B.begin(S, ST_GEMM);  // P^(L-1) = G^(L-1) N^(L-1): P = A_ii^{-1} N
+    B.begin(S, ST_GEMM);  // P^(L-1) rows: A_ii^{-1} N_{I,Y}
     for (int i = 0; i < nc; ++i) {
       const Cluster& c = cl[i];
       if (!active(i)) continue;
-      const int ld = c.n + c.b;
+      const int ldN = c.n + c.A;
       for (int s = 0; s < 2; ++s)
-        B.gemm(c.off_P[s], ld, c.off_P[s], ld, c.off_F, ld, OP_N, c.off_N[s], ld, OP_N, c.n, ld, c.n, 1.0, 0.0);
+        B.gemm(c.ext[v].off_PX[s], ldN, c.ext[v].off_PX[s], ldN, c.off_F, c.n + c.b, OP_N, c.ext[v].off_NX[s], ldN,
+               OP_N, c.n, ldN, c.n, 1.0, 0.0);
+    }
+    B.end();
+    B.begin(S, ST_COLGATHER);  // [P_II | P_IB] = columns I_i, B_i of it
+    for (int i = 0; i < nc; ++i) {
+      const Cluster& c = cl[i];
+      if (!active(i)) continue;
+      for (int s = 0; s < 2; ++s)
+        p->colg_desc.push_back(ColGatherDesc{c.off_P[s], c.ext[v].off_PX[s], c.n, c.b, c.A, cmap_begin[i]});
+      B.dim(c.n + c.b);
     }
     B.end();
     for (int l = p->n_levels; l >= 1; --l) {  // extract P
@@ -296,7 +362,7 @@ void build_schedules(nd_plan* p) {
         if (c.b == 0) continue;
         const Cluster& P = cl[c.parent];
         for (int s = 0; s < 2; ++s)
-          p->gath_desc.push_back(GatherDesc{c.off_NBB[s], P.off_P[s], P.off_NBB[s], c.b, P.n, P.b, map_begin[i]});
+          p->gath_desc.push_back(GatherDesc{c.off_PBB[s], P.off_P[s], P.off_PBB[s], c.b, P.n, P.b, map_begin[i]});
         B.dim(c.b);
       }
       B.end();
@@ -306,7 +372,7 @@ void build_schedules(nd_plan* p) {
         if (c.b == 0) continue;
         const int ld = c.n + c.b;
         for (int s = 0; s < 2; ++s)
-          B.gemm(c.off_P[s] + c.n, ld, c.off_P[s] + c.n, ld, c.off_Psi, c.b, OP_N, c.off_NBB[s], c.b, OP_N, c.n, c.b,
+          B.gemm(c.off_P[s] + c.n, ld, c.off_P[s] + c.n, ld, c.off_Psi, c.b, OP_N, c.off_PBB[s], c.b, OP_N, c.n, c.b,
                  c.b, 1.0, active(i) ? 1.0 : 0.0);
       }
       B.end();

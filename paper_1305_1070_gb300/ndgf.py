@@ -20,6 +20,7 @@ STATUS = {0: "ND_OK", 1: "ND_ERR_INVALID_ARG", 2: "ND_ERR_NOT_SYMMETRIC", 3: "ND
           8: "ND_ERR_UNSUPPORTED"}
 ND_PREC_FP64 = 0
 ND_PREC_MIXED = 1
+ND_FACT_PHONON = 1
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_fact_status",
@@ -71,7 +72,7 @@ def lib():
             "nd_plan_tree": ([_P, _P, _P, _P, _P, _P], _I32),
             "nd_plan_cluster_sites": ([_P, _I32, _P], _I32),
             "nd_plan_destroy": ([_P], None),
-            "nd_fact_create": ([_P, _I32, _I32, ctypes.POINTER(_P)], _I32),
+            "nd_fact_create": ([_P, _I32, _I32, _I32, ctypes.POINTER(_P)], _I32),
             "nd_fact_destroy": ([_P], None),
             "nd_factor": ([_P, _P, _P, _P, _P, _I32, _D, _P], _I32),
             "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
@@ -202,9 +203,9 @@ def nd_plan_cluster_sites(plan: Plan, c: int, n_i: int, b_i: int):
     return out[:n_i], out[n_i:]
 
 
-def nd_fact_create(plan: Plan, max_ne: int, precision: int = ND_PREC_FP64) -> Fact:
+def nd_fact_create(plan: Plan, max_ne: int, precision: int = ND_PREC_FP64, flags: int = 0) -> Fact:
     out = _P()
-    _check(lib().nd_fact_create(plan.ptr, max_ne, precision, ctypes.byref(out)), "nd_fact_create")
+    _check(lib().nd_fact_create(plan.ptr, max_ne, precision, flags, ctypes.byref(out)), "nd_fact_create")
     return Fact(out.value, plan)
 
 

@@ -28,7 +28,8 @@ class Solver:
         self.sigma_elems = int(self.off[-1])
         self.max_ne = int(max_ne or tr.n_e)
         self.precision = precision
-        self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision)
+        self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision,
+                                        ndgf.ND_FACT_PHONON if tr.gamma_ph > 0.0 else 0)
         self.leads = [ndgf.nd_lead_create(l.H00, l.H01, l.tau) for l in dev.leads]
         kw = dict(device=self.device)
         self.H = torch.as_tensor(dev.values, dtype=torch.float64, **kw).contiguous()
