@@ -1,0 +1,347 @@
+"""Benchmark: energy points/sec for diag G^r, G^< (and G^>) by nested dissection.
+
+Workload: the 512 (transport) x 128 effective-mass superlattice, 65,536 sites,
+256 energies in [0, 0.5] eV, onsite disorder +-0.02 eV, dense contact
+self-energies from the semi-infinite leads, Fermi levels 0.1 / 0.0 eV at 300 K,
+eta = 1e-6 eV.  One step = the whole hot path over the 256-energy batch:
+contact self-energies (S1a), lesser/greater self-energies, assembly and fold
+(S1-S3), selected inversion of G^r, G^<, G^> (S4-S8), the FP64 residual
+certificate (S9) and the density epilogue (S10).
+
+Paths: "fp32x2" = cluster blocks and products in FP32-pair ("double-float")
+arithmetic on the FP32 pipe with complex128 root inversion, with a second
+nested-dissection tree for energies whose fold growth max|Psi| exceeds 10;
+"fp64" = complex128 throughout on one tree (the plain ND path); "fp32" = plain
+complex64 (reported, gated).
+The reported value is the fp32x2 path when its energy-integrated density
+matches the FP64 path to <= 1e-6 relative error, else the FP64 path.  Inputs
+(the per-energy workspace, ~100 GB per step) are far larger than L2, so no
+explicit flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "superlattice_512x128"
+METRIC = "energy points/sec for diag G^r,G^< (mixed vs FP64 ND, same GB300, rel err ≤1e-6)"
+UNIT = "energies/s"
+GATE = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--chunk-mixed", type=int, default=128)
+    ap.add_argument("--chunk-fp64", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
+    ap.add_argument("--growth-max", type=float, default=10.0, help="growth above which the second tree runs")
+    ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm): the block RGF of oracle/, timed
+# in a child process with every host core available to BLAS.
+
+def cpu_worker(n_energies: int) -> None:
+    import numpy as np
+    from oracle import rgf
+    from paper_1305_1070_gb300 import workloads
+    dev, tr = workloads.workload(WORKLOAD)
+    pick = np.linspace(0, tr.n_e - 1, n_energies).round().astype(int)
+    solver = rgf.RGF(dev, tr)
+    t0 = time.perf_counter()
+    for e in pick:
+        solver.solve(float(tr.energies[e]))
+    dt = time.perf_counter() - t0
+    print(json.dumps({"energies": int(n_energies), "seconds": dt}))
+
+
+def run_cpu_oracle(n_energies: int) -> dict:
+    cores = os.cpu_count() or 1
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(cores), OMP_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_energies)], env=env,
+                       capture_output=True, text=True, check=True)
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["cores"] = cores
+    return out
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) > 8 for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def main_ours(a) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1070_gb300 import ndgf, workloads
+    from paper_1305_1070_gb300.solver import RobustSolver, Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev, tr = workloads.workload(WORKLOAD)
+    n_e = tr.n_e
+    E_all = torch.as_tensor(tr.energies, device="cuda")
+    w = np.zeros(n_e)
+    d = np.diff(tr.energies)
+    w[:-1] += 0.5 * d
+    w[1:] += 0.5 * d
+    weights = torch.as_tensor(w, device="cuda")
+    scale = 2.0 / (2.0 * np.pi)
+
+    n = dev.n
+    Gr = torch.zeros(n_e, n, dtype=torch.complex128, device="cuda")
+    Gl = torch.zeros_like(Gr)
+    Gg = torch.zeros_like(Gr)
+    dens = torch.zeros(n, dtype=torch.float64, device="cuda")
+    cert_max = {}
+
+    redo = {}
+
+    def make_step(solver, chunk, name):
+        def step():
+            cmax = torch.zeros(8, dtype=torch.float64, device="cuda")
+            nredo = 0
+            for c0 in range(0, n_e, chunk):
+                m = min(chunk, n_e - c0)
+                if isinstance(solver, RobustSolver):
+                    cert = solver.step(E_all[c0:c0 + m], Gr[c0:c0 + m], Gl[c0:c0 + m], Gg[c0:c0 + m])
+                    nredo += solver.last_redo
+                else:
+                    r, l, g = solver.step(E_all[c0:c0 + m])
+                    Gr[c0:c0 + m], Gl[c0:c0 + m], Gg[c0:c0 + m] = r, l, g
+                    cert = solver.certificate(m)
+                cmax = torch.maximum(cmax, cert.amax(dim=0))
+            ndgf.nd_density(Gl, weights, n_e, n, scale, 0, dens)
+            cert_max[name] = cmax
+            redo[name] = nredo
+        return step
+
+    def timed(step, K, W):
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(K):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / K
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    def rel(x, y):
+        return float((x - y).abs().max() / y.abs().max())
+
+    paths, results, solvers = {}, {}, {}
+    clk = Clocks(local)
+    for name, prec, chunk in (("fp64_nd", ndgf.ND_PREC_FP64, a.chunk_fp64),
+                              ("fp32x2", ndgf.ND_PREC_FP32X2, a.chunk_fp64),
+                              ("fp32", ndgf.ND_PREC_MIXED, a.chunk_mixed)):
+        if name == "fp32x2":
+            solver = RobustSolver(dev, tr, precision=prec, max_ne=chunk, growth_max=a.growth_max)
+        else:
+            solver = Solver(dev, tr, precision=prec, max_ne=chunk)
+        step = make_step(solver, chunk, name)
+        W = a.warmup if name == "fp32x2" else min(a.warmup, 1)
+        ms = timed(step, a.steps, W)
+        results[name] = (dens.clone(), Gl[:, ::97].clone())
+        c = cert_max[name].tolist()
+        paths[name] = {"energies_per_s": round(n_e * world / (ms * 1e-3), 3), "ms_per_step": round(ms, 3),
+                       "certificate_max": {"resid_r": c[0], "resid_lesser": c[2], "max_Gr": c[1], "max_Gl": c[3],
+                                           "growth_max_psi": c[4]},
+                       "second_tree_energies": redo.get(name, 0)}
+        solvers[name] = (solver, step, ms)
+        if name != "fp32x2":
+            del solver
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    d64, g64 = results["fp64_nd"]
+    for name in ("fp32x2", "fp32"):
+        paths[name]["density_rel_err_vs_fp64"] = rel(results[name][0], d64)
+        paths[name]["diag_Gl_rel_err_vs_fp64_sampled"] = float(
+            ((results[name][1] - g64).abs().amax(dim=1) / g64.abs().amax(dim=1)).max())
+        paths[name]["gate_1e-6"] = paths[name]["density_rel_err_vs_fp64"] <= GATE
+    gate = paths["fp32x2"]["gate_1e-6"]
+    head = "fp32x2" if gate else "fp64_nd"
+    paths["speedup_fp32x2_over_fp64"] = round(solvers["fp64_nd"][2] / solvers["fp32x2"][2], 3)
+    ms_headline = solvers[head][2]
+
+    # live roofline of the dominant kernel (one extra profiled step per path)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: one FFMA per CUDA core per clock
+    fp64_peak = 1.25  # TFLOP/s: GB300 FP64 rate (nominal)
+    prof = {}
+    for name in ("fp64_nd", "fp32x2"):
+        solver, step, _ = solvers[name]
+        ndgf.nd_profile(solver.fact, True)
+        step()
+        torch.cuda.synchronize()
+        prof[name] = ndgf.nd_profile(solver.fact, False)
+
+    def dominant(pr, peak, label, flop_factor=1.0, note=""):
+        tot = sum(p["ms"] for p in pr) or 1.0
+        top = max(pr, key=lambda p: p["ms"])
+        ach = top["flops"] / (top["ms"] * 1e-3) / 1e12 if top["ms"] > 0 else 0.0
+        out = {"kernel": f"{label}:{top['name']}", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
+               "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+               "share": round(top["ms"] / tot, 4), "launches": top["launches"],
+               "ms_per_launch": round(top["ms"] / max(1, top["launches"]), 4)}
+        if note:
+            out["note"] = note
+        return out
+
+    roof = {"fp64_nd": dominant(prof["fp64_nd"], fp64_peak, "complex128"),
+            # one complex multiply-add in FP32 pairs is about 48 FP32 operations
+            "fp32x2": dominant(prof["fp32x2"], fp32_peak / 12.0, "complex-fp32x2",
+                               note="achieved in useful complex flops (8 per complex multiply-add); peak = FP32 rate / 12 "
+                                    "(48 FP32 operations per complex multiply-add in FP32 pairs)")}
+    roofline = roof[head]
+    launches_per_step = sum(p["launches"] for p in prof[head])
+
+    # end to end through the public API with host buffers (pinned)
+    solver, step, _ = solvers[head]
+    H_host = torch.as_tensor(dev.values).pin_memory()
+    E_host = torch.as_tensor(tr.energies).pin_memory()
+    out_host = [torch.empty(n_e, n, dtype=torch.complex128).pin_memory() for _ in range(3)]
+    dens_host = torch.empty(n, dtype=torch.float64).pin_memory()
+
+    def step_e2e():
+        if isinstance(solver, RobustSolver):
+            solver.set_H(H_host)
+        else:
+            solver.H.copy_(H_host, non_blocking=True)
+        E_all.copy_(E_host, non_blocking=True)
+        step()
+        for dst, src in zip(out_host, (Gr, Gl, Gg)):
+            dst.copy_(src, non_blocking=True)
+        dens_host.copy_(dens, non_blocking=True)
+
+    ms_e2e = timed(step_e2e, a.steps, 1)
+    h2d = H_host.numel() * 8 + E_host.numel() * 8
+    d2h = 3 * n_e * n * 16 + n * 8
+    info = solver.info
+
+    if rank == 0:
+        cpu = run_cpu_oracle(a.cpu_sample)
+        cpu_val = cpu["energies"] / cpu["seconds"]
+        line = {
+            "metric": METRIC, "value": round(n_e * world / (ms_headline * 1e-3), 3), "unit": UNIT,
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_headline, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32x2 (c64 pairs) + f64 root" if gate else "c128",
+            "data": "synthetic (seeded superlattice, PCG64 seed 1306)",
+            "config": {"workload": WORKLOAD, "sites": n, "energies_per_gpu": n_e, "clusters": info["n_clusters"],
+                       "levels": info["n_levels"], "leaf_size": 64, "eta": tr.eta, "path": head,
+                       "l2": "inputs larger than L2 (~100-200 GB workspace per step)"},
+            "paths": paths,
+            "roofline": roofline,
+            "roofline_other": roof["fp64_nd" if head == "fp32x2" else "fp32x2"],
+            "kernel_profile": prof,
+            "flops_per_energy": {"factor": info["flops_factor"], "green_r": info["flops_green_r"],
+                                 "green_lesser": info["flops_green_lesser"]},
+            "gpu_launches": launches_per_step * a.steps,
+            "clocks": clocks,
+            "e2e": {"value": round(n_e * world / (ms_e2e * 1e-3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "cpu_baseline": {"value": round(cpu_val, 4), "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
+                             "sample": f"block RGF (oracle/rgf.py), {cpu['energies']} of the 256 energies, "
+                                       f"{cpu['seconds']:.1f} s"},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main_reference(a) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(1, a.cpu_sample // 3)
+    for _ in range(a.warmup):
+        run_cpu_oracle(per_step)
+    tot_e, tot_s = 0, 0.0
+    for _ in range(a.steps):
+        r = run_cpu_oracle(per_step)
+        tot_e += r["energies"]
+        tot_s += r["seconds"]
+        cores = r["cores"]
+    val = tot_e / tot_s
+    line = {"metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": round(1e3 * tot_s / a.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded superlattice)",
+            "config": {"workload": WORKLOAD, "energies_per_step": per_step}, "impl": "reference",
+            "cpu_baseline": {"value": round(val, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"block RGF (oracle/rgf.py), {per_step} energies per step"},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker)
+    elif args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)

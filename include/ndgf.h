@@ -52,7 +52,11 @@ typedef enum {
   ND_ERR_UNSUPPORTED = 8         /* valid request this build does not handle    */
 } nd_status;
 
-typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1 } nd_precision;
+/* Arithmetic of the cluster blocks and products: complex128; complex64
+ * (FP32, with complex128 root inversion); or complex numbers whose parts are
+ * unevaluated sums of two FP32 numbers ("double-float", ~48-bit significand,
+ * computed on the FP32 pipe with error-free transforms, complex128 root). */
+typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_precision;
 
 /* nd_fact_create flags.  ND_FACT_PHONON: reserve the G^< workspace of every
  * cluster so that nd_diag_green accepts a phonon Sigma^< / Sigma^> (without it
@@ -80,10 +84,13 @@ typedef struct nd_graph {
 
 /* Options of nd_analyze.  leaf_size: maximal number of sites of a leaf
  * cluster (0 = default 64); a contact set is never split, so a contact leaf
- * may be larger. */
+ * may be larger.  split_permille: position of each cut as a quantile of the
+ * sites' keys, in 1/1000 (0 = default 500, the median); other values give a
+ * different tree over the same graph. */
 typedef struct nd_opts {
   int32_t leaf_size;
-  int32_t reserved[7];
+  int32_t split_permille;
+  int32_t reserved[6];
 } nd_opts;
 
 typedef struct nd_plan nd_plan; /* symbolic analysis (host + device copy)      */
@@ -122,9 +129,8 @@ nd_status nd_plan_cluster_sites(const nd_plan* plan, int32_t c, int32_t* sites);
 void nd_plan_destroy(nd_plan* plan);
 
 /* ---- numeric workspace -----------------------------------------------------
- * Allocates device memory for up to max_ne energies at the given precision:
- * ND_PREC_FP64 = complex128 throughout; ND_PREC_MIXED = complex64 cluster
- * blocks and products with complex128 root inversion.  flags: ND_FACT_*.
+ * Allocates device memory for up to max_ne energies at the given precision
+ * (nd_precision).  flags: ND_FACT_*.
  * The plan must outlive the handle.  Errors: ND_ERR_OOM, ND_ERR_CUDA,
  * ND_ERR_INVALID_ARG. */
 nd_status nd_fact_create(const nd_plan* plan, int32_t max_ne, int32_t precision, int32_t flags, nd_fact** out);
@@ -157,6 +163,44 @@ nd_status nd_factor(nd_fact* fact, const double* H_values, const double* sigma_r
 nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double* sigma_greater,
                         const double* ph_lesser, const double* ph_greater, double* Gr, double* Gl,
                         double* Gg, void* stream);
+
+/* ---- S9: accuracy certificate ---------------------------------------------
+ * For the last nd_factor + nd_diag_green of the handle, in FP64 from the
+ * stored selected entries, per energy e and over all sites j:
+ *   cert[e][0] = max_j |(A G^r)_jj - 1|,           cert[e][1] = max_j |G^r_jj|,
+ *   cert[e][2] = max_j |(A G^<)_jj - (Sigma^< G^a)_jj|, cert[e][3] = max_j |G^<_jj|
+ * (paper Eq. (1): A G^r = I and A G^< = Sigma^< (G^r)^dagger; every nonzero
+ * A_jk has its G_kj among the entries the selected inversion stores, Sec. 3.2).
+ *   cert[e][4] = max over clusters of max |Psi_i| (Psi_i = -A_ii^{-1} A_iB), the
+ *                growth of the fold: the extraction multiplies rounding errors
+ *                of G_BB by Psi_i, so large values flag energies whose diagonal
+ *                carries amplified rounding;   cert[e][5..7] = 0 (reserved).
+ * Entries 2 and 3 are 0 when G^< was not computed.  cert: [n_e][8] doubles,
+ * host or device.  Stream ordered after the nd_diag_green call. */
+nd_status nd_certificate(nd_fact* fact, double* cert, void* stream);
+
+/* ---- S10: density epilogue --------------------------------------------------
+ * out[j] = (accumulate ? out[j] : 0) + scale * sum_e weights[e] Im X[e][j],
+ * X = diag G^< ([n_e][n] complex, caller order).  With trapezoid weights and
+ * scale = 2/(2 pi) this is the spin-degenerate electron density per site
+ * (paper Sec. 1: the diagonal of G^< is the electron density per unit energy).
+ * All arrays are device pointers. */
+nd_status nd_density(const double* Gl, const double* weights, int32_t n_e, int32_t n, double scale,
+                     int32_t accumulate, double* out, void* stream);
+
+/* ---- launch profiling ------------------------------------------------------
+ * While enabled, every launch of the fold / extraction schedules on the
+ * handle's stream is bracketed by CUDA events.  nd_profile(f, enable, stats,
+ * max, &count) synchronises the device, writes per-kernel-kind totals of the
+ * launches recorded since the previous call (launch count, milliseconds,
+ * algorithmic flops: 8 per complex multiply-add, n^3 complex multiply-adds per
+ * n x n inverse), clears them and sets the enable state. */
+typedef struct nd_kernel_stats {
+  char name[24];
+  int32_t launches;
+  double ms, flops, bytes;
+} nd_kernel_stats;
+nd_status nd_profile(nd_fact* fact, int32_t enable, nd_kernel_stats* stats, int32_t max_stats, int32_t* n_stats);
 
 /* Status of the last factor/diag call (synchronises the handle's stream):
  * n_singular = number of (energy, cluster) pivots that were exactly zero;

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "nd_arith.cuh"
 #include "nd_internal.h"
 #include "nd_kernels.h"
 
@@ -46,6 +47,41 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
+namespace {
+// Per-kind launch timing with CUDA events on the launching stream.
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void clear() {
+    for (auto& r : recs) {
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    recs.clear();
+  }
+  ~Profiler() {
+    clear();
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+}  // namespace
+
 struct nd_fact {
   const nd_plan* plan = nullptr;
   int precision = ND_PREC_FP64;
@@ -76,6 +112,17 @@ struct nd_fact {
   int64_t *d_cl_offG = nullptr, *d_cl_offGX[2] = {nullptr, nullptr};
   int flags = 0;
   int64_t se = 0;  // workspace elements per energy
+  // inputs of the last nd_factor / nd_diag_green (staged copies) for nd_certificate
+  double eta = 0.0;
+  const double *cur_H = nullptr, *cur_sr = nullptr, *cur_ph = nullptr, *cur_E = nullptr;
+  const double *cur_sl = nullptr, *cur_pl = nullptr;
+  bool have_lesser = false;
+  double* d_cert = nullptr;
+  int32_t *d_cert_ptr = nullptr, *d_cert_terms = nullptr, *d_cl_ldG2 = nullptr;
+  int64_t* d_cl_offP0 = nullptr;
+  ZeroDesc* d_psi = nullptr;
+  Profiler prof;
+  std::vector<double> step_flops_factor, step_flops_green, step_flops_lesser[2];  // per step, per energy
   TileRef* d_tiles = nullptr;
   // tile range of every GEMM step: index = step index in its schedule
   std::vector<std::pair<int, int>> tr_factor, tr_green, tr_lesser[2];
@@ -128,30 +175,37 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
   }
 }
 
-// Stage a per-energy input: device pointers pass through; host data is
-// copied to the staging buffer on the stream.
+// Copy a per-energy input (host or device memory) into the handle's buffer on
+// the stream; the handle keeps it for the certificate of the same call.
 nd_status stage_in(const double* src, double* staging, size_t bytes, cudaStream_t s, const double** out) {
   if (!src) {
     *out = nullptr;
     return ND_OK;
   }
-  if (is_device_ptr(src)) {
-    *out = src;
-    return ND_OK;
-  }
-  ND_CUDA(cudaMemcpyAsync(staging, src, bytes, cudaMemcpyHostToDevice, s));
+  ND_CUDA(cudaMemcpyAsync(staging, src, bytes, is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          s));
   *out = staging;
   return ND_OK;
 }
 
 template <typename T>
 nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::vector<std::pair<int, int>>& tr,
-                       const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s, int variant = 0) {
+                       const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s, int variant = 0,
+                       const std::vector<double>* step_flops = nullptr) {
   const nd_plan* p = f->plan;
   const AncTables at{f->d_site_ids, f->d_owner, f->d_pos, f->d_cl_n, f->d_cl_A, f->d_cl_ldG, f->d_cl_offG,
                      f->d_cl_offGX[variant]};
   for (size_t si = 0; si < sched.size(); ++si) {
     const Step& st = sched[si];
+    Profiler::Rec rec{};
+    if (f->prof.on) {
+      rec.kind = st.kind;
+      rec.a = f->prof.get();
+      rec.b = f->prof.get();
+      rec.flops = step_flops ? (*step_flops)[si] * w.n_e : 0.0;
+      rec.bytes = 0.0;
+      cudaEventRecord(rec.a, s);
+    }
     switch (st.kind) {
       case ST_INVERSE:
         Kern<T>::inverse(w, f->d_inv + st.begin, st.count, st.max_dim, f->root_scratch, f->root_stride, f->d_status,
@@ -183,9 +237,35 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
         Kern<T>::colgather(w, f->d_colg + st.begin, st.count, f->d_cmaps, s);
         break;
     }
+    if (f->prof.on) {
+      cudaEventRecord(rec.b, s);
+      f->prof.recs.push_back(rec);
+    }
   }
   ND_CUDA(cudaGetLastError());
   return ND_OK;
+}
+
+// Algorithmic flops per energy of every step (8 per complex multiply-add for
+// GEMMs, n^3 complex multiply-adds per inverse); 0 for data movement steps.
+std::vector<double> step_flops(const nd_plan* p, const std::vector<Step>& sched) {
+  std::vector<double> out(sched.size(), 0.0);
+  for (size_t si = 0; si < sched.size(); ++si) {
+    const Step& st = sched[si];
+    double f = 0.0;
+    if (st.kind == ST_GEMM)
+      for (int k = st.begin; k < st.begin + st.count; ++k) {
+        const GemmDesc& g = p->gemm_desc[k];
+        f += 8.0 * double(g.m) * g.n * g.k;
+      }
+    if (st.kind == ST_INVERSE)
+      for (int k = st.begin; k < st.begin + st.count; ++k) {
+        const double n = p->inv_desc[k].n;
+        f += 8.0 * n * n * n;
+      }
+    out[si] = f;
+  }
+  return out;
 }
 
 }  // namespace
@@ -193,7 +273,7 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
 extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t precision, int32_t flags,
                                     nd_fact** out) {
   if (!p || !out || max_ne <= 0) return fail(ND_ERR_INVALID_ARG, "nd_fact_create: bad argument");
-  if (precision != ND_PREC_FP64 && precision != ND_PREC_MIXED)
+  if (precision != ND_PREC_FP64 && precision != ND_PREC_MIXED && precision != ND_PREC_FP32X2)
     return fail(ND_ERR_INVALID_ARG, "nd_fact_create: unknown precision");
   if (p->max_n > 8192) return fail(ND_ERR_UNSUPPORTED, "nd_fact_create: cluster larger than 8192 sites");
   for (const auto& c : p->cl)
@@ -203,7 +283,7 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   f->plan = p;
   f->precision = precision;
   f->max_ne = max_ne;
-  f->esize = precision == ND_PREC_FP64 ? 16 : 8;
+  f->esize = precision == ND_PREC_MIXED ? 8 : 16;
   f->flags = flags;
   f->se = p->arena_elems + ((flags & ND_FACT_PHONON) ? std::max(p->ext_elems[0], p->ext_elems[1]) : p->ext_elems[0]);
   nd_status st;
@@ -217,7 +297,7 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   } while (0)
   TRY(dalloc(f, &f->arena, size_t(f->se) * f->esize * max_ne));
   TRY(dalloc(f, &f->aux, size_t(std::max<int64_t>(1, 2 * p->sigma_elems)) * f->esize * max_ne));
-  if (precision == ND_PREC_MIXED) {
+  if (precision != ND_PREC_FP64) {
     int64_t rmax = 0;
     for (const auto& c : p->cl)
       if (c.b == 0) rmax = std::max<int64_t>(rmax, int64_t(c.n) * c.n);
@@ -253,8 +333,19 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dupload(f, p->cl_offG, &f->d_cl_offG));
   TRY(dupload(f, p->cl_offGX[0], &f->d_cl_offGX[0]));
   TRY(dupload(f, p->cl_offGX[1], &f->d_cl_offGX[1]));
+  TRY(dupload(f, p->cl_offP[0], &f->d_cl_offP0));
+  TRY(dupload(f, p->cert_ptr, &f->d_cert_ptr));
+  TRY(dupload(f, p->cert_terms, &f->d_cert_terms));
+  TRY(dalloc(f, (void**)&f->d_cert, size_t(max_ne) * 8 * sizeof(double)));
+  TRY(dupload(f, p->psi_desc, &f->d_psi));
+  f->step_flops_factor = step_flops(p, p->sched_factor);
+  f->step_flops_green = step_flops(p, p->sched_green);
+  f->step_flops_lesser[0] = step_flops(p, p->sched_lesser[0]);
+  f->step_flops_lesser[1] = step_flops(p, p->sched_lesser[1]);
   {
-    const int tile = precision == ND_PREC_FP64 ? Kern<double>::gemm_tile() : Kern<float>::gemm_tile();
+    const int tile = precision == ND_PREC_FP64 ? Kern<double>::gemm_tile()
+                     : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile()
+                                                  : Kern<DF>::gemm_tile();
     std::vector<TileRef> tiles;
     build_tiles(p->sched_factor, p->gemm_desc, tile, tiles, f->tr_factor);
     build_tiles(p->sched_green, p->gemm_desc, tile, tiles, f->tr_green);
@@ -284,6 +375,14 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
 
 extern "C" void nd_fact_destroy(nd_fact* f) { delete f; }
 
+template <typename T>
+static nd_status factor_t(nd_fact* f, const Work& w, const double* H, const double* E, double eta, const double* sr,
+                          const double* ph, int nc, cudaStream_t s) {
+  const nd_plan* p = f->plan;
+  Kern<T>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph, p->n, s);
+  return run_schedule<T>(f, p->sched_factor, f->tr_factor, w, nullptr, nullptr, s, 0, &f->step_flops_factor);
+}
+
 extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double* sigma_r, const double* sigma_ph_r,
                                const double* energies, int32_t n_e, double eta, void* stream) {
   if (!f || !H_values || !energies) return fail(ND_ERR_INVALID_ARG, "nd_factor: NULL argument");
@@ -299,17 +398,18 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
   if ((st = stage_in(sigma_ph_r, f->st_ph, size_t(n_e) * p->n * 16, s, &ph)) != ND_OK) return st;
   if ((st = stage_in(energies, f->st_E, size_t(n_e) * 8, s, &E)) != ND_OK) return st;
   f->n_e = n_e;
+  f->eta = eta;
+  f->cur_H = H;
+  f->cur_sr = sr;
+  f->cur_ph = ph;
+  f->cur_E = E;
+  f->have_lesser = false;
   ND_CUDA(cudaMemsetAsync(f->d_status, 0, sizeof(int), s));
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, n_e};
   const int nc = int(p->cl.size());
-  if (f->precision == ND_PREC_FP64) {
-    Kern<double>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph,
-                           p->n, s);
-    return run_schedule<double>(f, p->sched_factor, f->tr_factor, w, nullptr, nullptr, s);
-  }
-  Kern<float>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph,
-                        p->n, s);
-  return run_schedule<float>(f, p->sched_factor, f->tr_factor, w, nullptr, nullptr, s);
+  if (f->precision == ND_PREC_FP64) return factor_t<double>(f, w, H, E, eta, sr, ph, nc, s);
+  if (f->precision == ND_PREC_MIXED) return factor_t<float>(f, w, H, E, eta, sr, ph, nc, s);
+  return factor_t<DF>(f, w, H, E, eta, sr, ph, nc, s);
 }
 
 template <typename T>
@@ -318,13 +418,13 @@ static nd_status diag_green_t(nd_fact* f, const double* sl, const double* sg, co
   const nd_plan* p = f->plan;
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
   const int nc = int(p->cl.size());
-  nd_status st = run_schedule<T>(f, p->sched_green, f->tr_green, w, nullptr, nullptr, s);
+  nd_status st = run_schedule<T>(f, p->sched_green, f->tr_green, w, nullptr, nullptr, s, 0, &f->step_flops_green);
   if (st != ND_OK) return st;
   if (outs[0]) Kern<T>::diag_out(w, f->d_diag_g, nc, f->d_sites, outs[0], p->n, s);
   if (outs[1] || outs[2]) {
     Kern<T>::convert_aux(w, sl, sg, p->sigma_elems, s);
     const int v = (pl || pg) ? 1 : 0;
-    st = run_schedule<T>(f, p->sched_lesser[v], f->tr_lesser[v], w, pl, pg, s, v);
+    st = run_schedule<T>(f, p->sched_lesser[v], f->tr_lesser[v], w, pl, pg, s, v, &f->step_flops_lesser[v]);
     if (st != ND_OK) return st;
     if (outs[1]) Kern<T>::diag_out(w, f->d_diag_p[0], nc, f->d_sites, outs[1], p->n, s);
     if (outs[2]) Kern<T>::diag_out(w, f->d_diag_p[1], nc, f->d_sites, outs[2], p->n, s);
@@ -360,11 +460,98 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
     host[k] = user[k] && !is_device_ptr(user[k]);
     dev[k] = host[k] ? f->st_out[k] : user[k];
   }
-  st = f->precision == ND_PREC_FP64 ? diag_green_t<double>(f, sl, sg, pl, pg, dev, s)
-                                    : diag_green_t<float>(f, sl, sg, pl, pg, dev, s);
+  st = f->precision == ND_PREC_FP64    ? diag_green_t<double>(f, sl, sg, pl, pg, dev, s)
+       : f->precision == ND_PREC_MIXED ? diag_green_t<float>(f, sl, sg, pl, pg, dev, s)
+                                       : diag_green_t<DF>(f, sl, sg, pl, pg, dev, s);
   if (st != ND_OK) return st;
+  f->have_lesser = (Gl || Gg);
+  f->cur_sl = sl;
+  f->cur_pl = pl;
   for (int k = 0; k < 3; ++k)
     if (host[k]) ND_CUDA(cudaMemcpyAsync(user[k], dev[k], size_t(n_e) * p->n * 16, cudaMemcpyDeviceToHost, s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_certificate(nd_fact* f, double* cert, void* stream) {
+  if (!f || !cert) return fail(ND_ERR_INVALID_ARG, "nd_certificate: NULL argument");
+  if (f->n_e <= 0) return fail(ND_ERR_INVALID_ARG, "nd_certificate: call nd_factor and nd_diag_green first");
+  const nd_plan* p = f->plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = size_t(f->n_e) * 8 * sizeof(double);
+  ND_CUDA(cudaMemsetAsync(f->d_cert, 0, bytes, s));
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
+  CertArgs a{};
+  a.n = p->n;
+  a.cptr = f->d_cert_ptr;
+  a.terms = f->d_cert_terms;
+  a.owner = f->d_owner;
+  a.pos = f->d_pos;
+  a.ldG = f->d_cl_ldG;
+  a.offG = f->d_cl_offG;
+  a.offP = f->d_cl_offP0;
+  a.H = f->cur_H;
+  a.sr = f->cur_sr;
+  a.sl = f->cur_sl;
+  a.ph_r = f->cur_ph;
+  a.ph_l = f->cur_pl;
+  a.energies = f->cur_E;
+  a.sstride = p->sigma_elems;
+  a.eta = f->eta;
+  a.lesser = f->have_lesser ? 1 : 0;
+  a.cert = f->d_cert;
+  a.psi = f->d_psi;
+  a.n_psi = int(p->psi_desc.size());
+  if (f->precision == ND_PREC_FP64)
+    Kern<double>::certificate(w, a, s);
+  else if (f->precision == ND_PREC_MIXED)
+    Kern<float>::certificate(w, a, s);
+  else
+    Kern<DF>::certificate(w, a, s);
+  ND_CUDA(cudaGetLastError());
+  ND_CUDA(cudaMemcpyAsync(cert, f->d_cert, bytes, is_device_ptr(cert) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_profile(nd_fact* f, int32_t enable, nd_kernel_stats* stats, int32_t max_stats,
+                                int32_t* n_stats) {
+  if (!f) return fail(ND_ERR_INVALID_ARG, "nd_profile: NULL handle");
+  int cnt = 0;
+  if (stats && max_stats > 0) {
+    ND_CUDA(cudaDeviceSynchronize());
+    static const char* names[] = {"inverse", "gemm", "scatter", "gather_sym", "gather_skew",
+                                  "zero", "nph", "gather_anc", "scatter_rows", "colgather"};
+    const int nk = int(sizeof(names) / sizeof(names[0]));
+    std::vector<nd_kernel_stats> acc(nk);
+    for (int k = 0; k < nk; ++k) {
+      std::memset(&acc[k], 0, sizeof(nd_kernel_stats));
+      std::strncpy(acc[k].name, names[k], sizeof(acc[k].name) - 1);
+    }
+    for (auto& r : f->prof.recs) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      if (r.kind < 0 || r.kind >= nk) continue;
+      acc[r.kind].launches += 1;
+      acc[r.kind].ms += ms;
+      acc[r.kind].flops += r.flops;
+      acc[r.kind].bytes += r.bytes;
+    }
+    for (int k = 0; k < nk && cnt < max_stats; ++k)
+      if (acc[k].launches > 0) stats[cnt++] = acc[k];
+  }
+  if (n_stats) *n_stats = cnt;
+  f->prof.clear();
+  f->prof.on = enable != 0;
+  return ND_OK;
+}
+
+extern "C" nd_status nd_density(const double* Gl, const double* weights, int32_t n_e, int32_t n, double scale,
+                                int32_t accumulate, double* out, void* stream) {
+  if (!Gl || !weights || !out || n_e <= 0 || n <= 0) return fail(ND_ERR_INVALID_ARG, "nd_density: bad argument");
+  if (!is_device_ptr(Gl) || !is_device_ptr(weights) || !is_device_ptr(out))
+    return fail(ND_ERR_INVALID_ARG, "nd_density: arrays must be device pointers");
+  launch_density(Gl, weights, n_e, n, scale, accumulate, out, (cudaStream_t)stream);
+  ND_CUDA(cudaGetLastError());
   return ND_OK;
 }
 

@@ -197,7 +197,14 @@ struct nd_plan {
   std::vector<int32_t> cmaps;      // column maps of ColGatherDesc
   // per-cluster tables for the G lookup of AncGatherDesc (variant v = 0, 1)
   std::vector<int32_t> cl_n, cl_A, cl_ldG;
-  std::vector<int64_t> cl_offG, cl_offGX[2];
+  std::vector<int64_t> cl_offG, cl_offGX[2], cl_offP[2];
+  // residual certificate: for site j, terms [cert_ptr[j], cert_ptr[j+1]) of
+  // sum_k A_jk X_kj, each {cluster, element index in its [X_II | X_IB] front,
+  // coefficient source (CSR index >= 0, or -1 - packed Sigma index), flag 1 when
+  // the stored element is X_jk with k an ancestor site (X^< needs -conj)}
+  std::vector<ndgf::ZeroDesc> psi_desc;  // Psi regions (growth indicator)
+  std::vector<int32_t> cert_ptr;
+  std::vector<int32_t> cert_terms;  // 4 ints per term
   // launch schedules: the fold (S1-S3), the G^r extraction (S4) and the
   // G^< / G^> steps (S5-S8) without (0) or with (1) a phonon self-energy
   std::vector<ndgf::Step> sched_factor, sched_green, sched_lesser[2];

@@ -9,41 +9,14 @@
 
 #include <cstdint>
 
+#include <type_traits>
+
+#include "nd_arith.cuh"
 #include "nd_kernels.h"
 
 namespace ndgf {
 
-template <typename T> struct C2;
-template <> struct C2<double> { using t = double2; };
-template <> struct C2<float> { using t = float2; };
-template <typename T> using cx = typename C2<T>::t;
-
-template <typename T> __device__ __forceinline__ cx<T> mk(T a, T b) {
-  cx<T> r;
-  r.x = a;
-  r.y = b;
-  return r;
-}
-template <typename T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-template <typename T> __device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(a.y, b.x, acc.y);
-}
-template <typename T> __device__ __forceinline__ cx<T> crecip(cx<T> a) {
-  T s = fmax(fabs(a.x), fabs(a.y));
-  T ar = a.x / s, ai = a.y / s;
-  T d = (ar * ar + ai * ai) * s;
-  return mk<T>(ar / d, -ai / d);
-}
-template <typename T> __device__ __forceinline__ T cabs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
-
-template <typename To, typename Ti> __device__ __forceinline__ cx<To> ccast(cx<Ti> a) {
-  return mk<To>(To(a.x), To(a.y));
-}
+template <typename T> using O = Ops<T>;
 
 __device__ __forceinline__ double fermi_dev(double E, double mu, double kT) {
   double x = (E - mu) / kT;
@@ -67,22 +40,23 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
   cx<T>* F = arena + int64_t(e) * se + d.off_F;
   cx<T>* BB = arena + int64_t(e) * se + d.off_BB;
   const int64_t nf = int64_t(d.n) * d.ld, nb = int64_t(d.b) * d.b;
-  const cx<T> z = mk<T>(T(0), T(0));
-  for (int64_t i = threadIdx.x; i < nf; i += blockDim.x) F[i] = z;
-  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) BB[i] = z;
+  for (int64_t i = threadIdx.x; i < nf; i += blockDim.x) F[i] = O<T>::zero();
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) BB[i] = O<T>::zero();
   __syncthreads();
-  for (int i = d.ent_begin + threadIdx.x; i < d.ent_end; i += blockDim.x) F[ent_dst[i]] = mk<T>(T(-H[ent_src[i]]), T(0));
+  for (int i = d.ent_begin + threadIdx.x; i < d.ent_end; i += blockDim.x)
+    F[ent_dst[i]] = O<T>::from_d2(make_double2(-H[ent_src[i]], 0.0));
   __syncthreads();
   const double E = energies[e];
   for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
-    double re = E, im = eta;
+    double2 z = make_double2(E, eta);
     if (ph_r) {
-      double2 p = ph_r[int64_t(e) * n + sites[d.site_begin + r]];
-      re -= p.x;
-      im -= p.y;
+      const double2 p = ph_r[int64_t(e) * n + sites[d.site_begin + r]];
+      z.x -= p.x;
+      z.y -= p.y;
     }
     cx<T>& a = F[int64_t(r) * d.ld + r];
-    a = mk<T>(T(double(a.x) + re), T(double(a.y) + im));
+    const double2 av = O<T>::to_d2(a);
+    a = O<T>::from_d2(make_double2(av.x + z.x, av.y + z.y));
   }
   __syncthreads();  // the contact blocks below update the same diagonal entries
   const double2* S = sigma_r + int64_t(e) * sigma_stride;
@@ -90,9 +64,10 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
     const int r0 = c ? d.c1 : d.c0, m = c ? d.m1 : d.m0, so = c ? d.soff1 : d.soff0;
     for (int i = threadIdx.x; i < m * m; i += blockDim.x) {
       const int a = i / m, b = i % m;
-      double2 s = S[so + i];
+      const double2 sv = S[so + i];
       cx<T>& f = F[int64_t(r0 + a) * d.ld + r0 + b];
-      f = mk<T>(T(double(f.x) - s.x), T(double(f.y) - s.y));
+      const double2 fv = O<T>::to_d2(f);
+      f = O<T>::from_d2(make_double2(fv.x - sv.x, fv.y - sv.y));
     }
   }
 }
@@ -102,25 +77,26 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
 // matrix).  The matrix is n x n with leading dimension ld.
 template <typename TC>
 __device__ void gj_invert(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, int* n_singular) {
-  __shared__ TC red_v[32];
+  using R = typename O<TC>::R;
+  __shared__ R red_v[32];
   __shared__ int red_i[32];
   __shared__ int s_p;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
   for (int k = 0; k < n; ++k) {
     // pivot: largest |a_ik|^2 over i >= k (smallest index on ties)
-    TC bv = TC(-1);
+    R bv = R(-1);
     int bi = k;
     for (int i = k + tid; i < n; i += nt) {
-      TC v = cabs2<TC>(M[int64_t(i) * ld + k]);
+      const R v = O<TC>::mag2(M[int64_t(i) * ld + k]);
       if (v > bv) {
         bv = v;
         bi = i;
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      TC ov = __shfl_down_sync(0xffffffffu, bv, o);
-      int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      const R ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
       if (ov > bv || (ov == bv && oi < bi)) {
         bv = ov;
         bi = oi;
@@ -132,7 +108,7 @@ __device__ void gj_invert(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, int*
     }
     __syncthreads();
     if (tid == 0) {
-      TC v = red_v[0];
+      R v = red_v[0];
       int p = red_i[0];
       for (int w = 1; w < nw; ++w)
         if (red_v[w] > v || (red_v[w] == v && red_i[w] < p)) {
@@ -146,35 +122,31 @@ __device__ void gj_invert(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, int*
     const int p = s_p;
     if (p != k)
       for (int j = tid; j < n; j += nt) {
-        cx<TC> t = M[int64_t(k) * ld + j];
+        const cx<TC> t = M[int64_t(k) * ld + j];
         M[int64_t(k) * ld + j] = M[int64_t(p) * ld + j];
         M[int64_t(p) * ld + j] = t;
       }
     __syncthreads();
     cx<TC> pivot = M[int64_t(k) * ld + k];
-    if (!(cabs2<TC>(pivot) > TC(0))) {  // exactly singular (or NaN): record, keep going
+    if (!(O<TC>::mag2(pivot) > R(0))) {  // exactly singular (or NaN): record, keep going
       if (tid == 0) atomicAdd(n_singular, 1);
-      pivot = mk<TC>(sizeof(TC) == 8 ? TC(1e-300) : TC(1e-30), TC(0));
+      pivot = O<TC>::from_d2(make_double2(std::is_same<TC, double>::value ? 1e-300 : 1e-30, 0.0));
     }
-    const cx<TC> inv = crecip<TC>(pivot);
-    for (int i = tid; i < n; i += nt) colk[i] = (i == k) ? mk<TC>(TC(0), TC(0)) : M[int64_t(i) * ld + k];
+    const cx<TC> inv = O<TC>::recip(pivot);
+    for (int i = tid; i < n; i += nt) colk[i] = (i == k) ? O<TC>::zero() : M[int64_t(i) * ld + k];
     __syncthreads();
     for (int j = tid; j < n; j += nt) {
       cx<TC>& a = M[int64_t(k) * ld + j];
-      a = (j == k) ? inv : cmul<TC>(a, inv);
+      a = (j == k) ? inv : O<TC>::mul(a, inv);
     }
     __syncthreads();
     const int64_t nn = int64_t(n) * n;
     for (int64_t idx = tid; idx < nn; idx += nt) {
       const int i = int(idx / n), j = int(idx % n);
       if (i == k) continue;
-      const cx<TC> f = colk[i];
       cx<TC>& a = M[int64_t(i) * ld + j];
-      cx<TC> v = (j == k) ? mk<TC>(TC(0), TC(0)) : a;
-      const cx<TC> r = M[int64_t(k) * ld + j];
-      v.x -= f.x * r.x - f.y * r.y;
-      v.y -= f.x * r.y + f.y * r.x;
-      a = v;
+      const cx<TC> v = (j == k) ? O<TC>::zero() : a;
+      a = O<TC>::sub(v, O<TC>::mul(colk[i], M[int64_t(k) * ld + j]));
     }
     __syncthreads();
   }
@@ -182,7 +154,7 @@ __device__ void gj_invert(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, int*
     const int p = piv[k];
     if (p != k)
       for (int i = tid; i < n; i += nt) {
-        cx<TC> t = M[int64_t(i) * ld + k];
+        const cx<TC> t = M[int64_t(i) * ld + k];
         M[int64_t(i) * ld + k] = M[int64_t(i) * ld + p];
         M[int64_t(i) * ld + p] = t;
       }
@@ -199,13 +171,13 @@ __global__ void k_inverse(const InvDesc* __restrict__ descs, cx<T>* arena, int64
   cx<T>* M = arena + int64_t(e) * se + d.off;
   int* piv = reinterpret_cast<int*>(smem);
   const size_t colk_off = (size_t(d.n) * sizeof(int) + 15) & ~size_t(15);
-  if (sizeof(T) == 4 && d.fp64 && scratch) {
+  if (!std::is_same<T, double>::value && d.fp64 && scratch) {  // root block in complex128
     double2* W = scratch + int64_t(e) * scratch_stride;
     const int64_t nn = int64_t(d.n) * d.n;
-    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = ccast<double, T>(M[(i / d.n) * d.ld + i % d.n]);
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = O<T>::to_d2(M[(i / d.n) * d.ld + i % d.n]);
     __syncthreads();
     gj_invert<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off), n_singular);
-    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = ccast<T, double>(W[i]);
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = O<T>::from_d2(W[i]);
   } else {
     gj_invert<T>(M, d.n, d.ld, piv, reinterpret_cast<cx<T>*>(smem + colk_off), n_singular);
   }
@@ -231,11 +203,11 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
   const cx<T>* B = (d.offB & AUX_BIT) ? abase + (d.offB & ~AUX_BIT) : base + d.offB;
   const int m0 = t.tm * BM, n0 = t.tn * BN;
   const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
-  cx<T> acc[TM][TN];
+  typename O<T>::Acc acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = mk<T>(T(0), T(0));
+    for (int j = 0; j < TN; ++j) acc[i][j] = O<T>::acc_zero();
   const bool conjB = (d.opB == OP_C || d.opB == OP_H);
   const bool transB = (d.opB == OP_T || d.opB == OP_H);
   for (int k0 = 0; k0 < d.k; k0 += BK) {
@@ -249,7 +221,7 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
         mm = idx % BM;
       }
       const int gm = m0 + mm, gk = k0 + kk;
-      cx<T> v = mk<T>(T(0), T(0));
+      cx<T> v = O<T>::zero();
       if (gm < d.m && gk < d.k) v = (d.opA == OP_N) ? A[int64_t(gm) * d.lda + gk] : A[int64_t(gk) * d.lda + gm];
       As[kk][mm] = v;
     }
@@ -263,10 +235,9 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
         kk = idx % BK;
       }
       const int gk = k0 + kk, gn = n0 + nn;
-      cx<T> v = mk<T>(T(0), T(0));
+      cx<T> v = O<T>::zero();
       if (gk < d.k && gn < d.n) v = transB ? B[int64_t(gn) * d.ldb + gk] : B[int64_t(gk) * d.ldb + gn];
-      if (conjB) v.y = -v.y;
-      Bs[kk][nn] = v;
+      Bs[kk][nn] = conjB ? O<T>::conj(v) : v;
     }
     __syncthreads();
 #pragma unroll 4
@@ -279,11 +250,10 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) cfma<T>(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) O<T>::acc_fma(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
-  const T alpha = T(d.alpha), beta = T(d.beta);
   cx<T>* C = base + d.offC;
   const cx<T>* D = base + d.offD;
 #pragma unroll
@@ -294,11 +264,14 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
     for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + j * NX;
       if (gn >= d.n) continue;
-      cx<T> r = mk<T>(alpha * acc[i][j].x, alpha * acc[i][j].y);
-      if (beta != T(0)) {
+      cx<T> r = O<T>::acc_get(acc[i][j]);
+      if (d.alpha == -1.0)
+        r = O<T>::neg(r);
+      else if (d.alpha != 1.0)
+        r = O<T>::scale(r, d.alpha);
+      if (d.beta != 0.0) {
         const cx<T> dv = D[int64_t(gm) * d.ldd + gn];
-        r.x += beta * dv.x;
-        r.y += beta * dv.y;
+        r = O<T>::add(r, d.beta == 1.0 ? dv : O<T>::scale(dv, d.beta));
       }
       C[int64_t(gm) * d.ldc + gn] = r;
     }
@@ -326,12 +299,10 @@ __global__ void k_scatter(const ScatterDesc* __restrict__ descs, cx<T>* arena, i
     const cx<T> v = src[idx];
     if (pr < d.n_p) {
       cx<T>& f = front[int64_t(pr) * ldp + ps];
-      f.x += v.x;
-      f.y += v.y;
+      f = O<T>::add(f, v);
     } else if (ps >= d.n_p) {
       cx<T>& f = bb[int64_t(pr - d.n_p) * d.b_p + (ps - d.n_p)];
-      f.x += v.x;
-      f.y += v.y;
+      f = O<T>::add(f, v);
     }
   }
 }
@@ -357,7 +328,7 @@ __global__ void k_gather(const GatherDesc* __restrict__ descs, cx<T>* arena, int
       v = front[int64_t(pr) * ldp + ps];
     } else if (ps < d.n_p) {
       v = front[int64_t(ps) * ldp + pr];
-      if (skew) v = mk<T>(-v.x, v.y);
+      if (skew) v = O<T>::neg(O<T>::conj(v));
     } else {
       v = bb[int64_t(pr - d.n_p) * d.b_p + (ps - d.n_p)];
     }
@@ -369,7 +340,7 @@ template <typename T>
 __global__ void k_zero(const ZeroDesc* __restrict__ descs, cx<T>* arena, int64_t se) {
   const ZeroDesc d = descs[blockIdx.x];
   cx<T>* p = arena + int64_t(blockIdx.y) * se + d.off;
-  const cx<T> z = mk<T>(T(0), T(0));
+  const cx<T> z = O<T>::zero();
   for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) p[i] = z;
 }
 
@@ -390,7 +361,7 @@ __global__ void k_nph(const NPhDesc* __restrict__ descs, cx<T>* arena, int64_t s
     const int r = int(idx / w), j = int(idx % w);
     const double2 s = ph[sites[d.site_begin + r]];
     const cx<T> g = j < d.n ? G[int64_t(r) * d.ldG + j] : GX[int64_t(r) * d.A + (j - d.n)];
-    N[idx] = cmul<T>(mk<T>(T(s.x), T(s.y)), mk<T>(g.x, -g.y));
+    N[idx] = O<T>::mul(O<T>::from_d2(s), O<T>::conj(g));
   }
 }
 
@@ -442,12 +413,10 @@ __global__ void k_scatter_rows(const RowScatterDesc* __restrict__ descs, cx<T>* 
     const cx<T> v = src[idx];
     if (pr < d.n_p) {
       cx<T>& f = nx[int64_t(pr) * d.A_c + j];
-      f.x += v.x;
-      f.y += v.y;
+      f = O<T>::add(f, v);
     } else if (j >= d.n_p) {
       cx<T>& f = nb[int64_t(pr - d.n_p) * d.A_p + (j - d.n_p)];
-      f.x += v.x;
-      f.y += v.y;
+      f = O<T>::add(f, v);
     }
   }
 }
@@ -476,8 +445,7 @@ __global__ void k_diag_out(const DiagDesc* __restrict__ descs, const cx<T>* aren
   const int e = blockIdx.y;
   const cx<T>* X = arena + int64_t(e) * se + d.off;
   for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
-    const cx<T> v = X[int64_t(r) * d.ld + r];
-    out[int64_t(e) * n + sites[d.site_begin + r]] = make_double2(double(v.x), double(v.y));
+    out[int64_t(e) * n + sites[d.site_begin + r]] = O<T>::to_d2(X[int64_t(r) * d.ld + r]);
   }
 }
 
@@ -489,8 +457,118 @@ __global__ void k_convert_aux(const double2* __restrict__ lesser, const double2*
     const int64_t e = i / sigma_elems, k = i % sigma_elems;
     const double2 l = lesser ? lesser[i] : make_double2(0.0, 0.0);
     const double2 g = greater ? greater[i] : make_double2(0.0, 0.0);
-    aux[e * 2 * sigma_elems + k] = mk<T>(T(l.x), T(l.y));
-    aux[e * 2 * sigma_elems + sigma_elems + k] = mk<T>(T(g.x), T(g.y));
+    aux[e * 2 * sigma_elems + k] = O<T>::from_d2(l);
+    aux[e * 2 * sigma_elems + sigma_elems + k] = O<T>::from_d2(g);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// S9 certificate: for every site j, in FP64 from the stored selected entries,
+//   r_j  = sum_k A_jk G_kj - 1
+//   r<_j = sum_k A_jk G<_kj - (Sigma^< G^a)_jj
+// with A = (E + i eta - Sigma_ph) I - H - Sigma_contact.  Every nonzero A_jk
+// pairs with a stored entry of G^(0) (paper Sec. 3.2: the stored entries
+// cover the fill pattern).  Per energy: max |r|, max |G_jj|, max |r<|, max |G<_jj|.
+__device__ __forceinline__ void atomic_max_pos(double* a, double v) {
+  atomicMax(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
+}
+
+template <typename T>
+__global__ void k_certificate(int n, const int32_t* __restrict__ cptr, const int4* __restrict__ terms,
+                              const int32_t* __restrict__ owner, const int32_t* __restrict__ pos,
+                              const int64_t* __restrict__ offG, const int64_t* __restrict__ offP,
+                              const int32_t* __restrict__ ldG, const cx<T>* arena, int64_t se,
+                              const double* __restrict__ H, const double2* __restrict__ sr,
+                              const double2* __restrict__ sl, int64_t sstride, const double2* __restrict__ ph_r,
+                              const double2* __restrict__ ph_l, const double* __restrict__ energies, double eta,
+                              int lesser, double* cert) {
+  const int e = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (j < n) {
+    const cx<T>* base = arena + int64_t(e) * se;
+    const int c = owner[j], r = pos[j];
+    const int64_t dj = int64_t(r) * ldG[c] + r;
+    const double2 gjj = O<T>::to_d2(base[offG[c] + dj]);
+    double2 pjj = make_double2(0.0, 0.0);
+    if (lesser) pjj = O<T>::to_d2(base[offP[c] + dj]);
+    double2 d = make_double2(energies[e], eta);
+    if (ph_r) {
+      const double2 q = ph_r[int64_t(e) * n + j];
+      d.x -= q.x;
+      d.y -= q.y;
+    }
+    double2 rr = make_double2(d.x * gjj.x - d.y * gjj.y - 1.0, d.x * gjj.y + d.y * gjj.x);
+    double2 rl = make_double2(d.x * pjj.x - d.y * pjj.y, d.x * pjj.y + d.y * pjj.x);
+    double2 rhs = make_double2(0.0, 0.0);
+    if (lesser && ph_l) {  // ph^<_j conj(G_jj)
+      const double2 q = ph_l[int64_t(e) * n + j];
+      rhs.x += q.x * gjj.x + q.y * gjj.y;
+      rhs.y += q.y * gjj.x - q.x * gjj.y;
+    }
+    for (int t = cptr[j]; t < cptr[j + 1]; ++t) {
+      const int4 tm = terms[t];
+      const double2 g = O<T>::to_d2(base[offG[tm.x] + tm.y]);
+      double2 a;  // -A_jk
+      if (tm.z >= 0) {
+        a = make_double2(H[tm.z], 0.0);
+      } else {
+        a = sr[int64_t(e) * sstride + (-1 - tm.z)];
+        if (lesser && sl) {  // Sigma^<_jk conj(G_jk)
+          const double2 q = sl[int64_t(e) * sstride + (-1 - tm.z)];
+          rhs.x += q.x * g.x + q.y * g.y;
+          rhs.y += q.y * g.x - q.x * g.y;
+        }
+      }
+      rr.x -= a.x * g.x - a.y * g.y;
+      rr.y -= a.x * g.y + a.y * g.x;
+      if (lesser) {
+        double2 pv = O<T>::to_d2(base[offP[tm.x] + tm.y]);
+        if (tm.w) pv = make_double2(-pv.x, pv.y);  // G<_kj = -conj(G<_jk)
+        rl.x -= a.x * pv.x - a.y * pv.y;
+        rl.y -= a.x * pv.y + a.y * pv.x;
+      }
+    }
+    rl.x -= rhs.x;
+    rl.y -= rhs.y;
+    v[0] = hypot(rr.x, rr.y);
+    v[1] = hypot(gjj.x, gjj.y);
+    v[2] = hypot(rl.x, rl.y);
+    v[3] = hypot(pjj.x, pjj.y);
+  }
+  __shared__ double red[4][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k = 0; k < 4; ++k) {
+    double x = v[k];
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if (lane == 0) red[k][warp] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) x = fmax(x, red[threadIdx.x][w]);
+    atomic_max_pos(cert + int64_t(e) * 8 + threadIdx.x, x);
+  }
+}
+
+// Growth indicator: out[e * 8 + 4] = max over the listed regions of max |x|.
+template <typename T>
+__global__ void k_absmax(const ZeroDesc* __restrict__ descs, const cx<T>* arena, int64_t se, double* cert) {
+  const ZeroDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  const cx<T>* p = arena + int64_t(e) * se + d.off;
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) {
+    const double2 v = O<T>::to_d2(p[i]);
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    atomic_max_pos(cert + int64_t(e) * 8 + 4, m);
   }
 }
 
@@ -499,6 +577,7 @@ __global__ void k_convert_aux(const double2* __restrict__ lesser, const double2*
 template <typename T> struct GemmCfg;
 template <> struct GemmCfg<double> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
 template <> struct GemmCfg<float> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+template <> struct GemmCfg<DF> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
 
 template <typename T> int Kern<T>::gemm_tile() { return GemmCfg<T>::BM; }
 
@@ -593,8 +672,38 @@ void Kern<T>::convert_aux(const Work& w, const double* lesser, const double* gre
                                           sigma_elems, w.n_e);
 }
 
+template <typename T>
+void Kern<T>::certificate(const Work& w, const CertArgs& a, cudaStream_t s) {
+  if (w.n_e <= 0 || a.n <= 0) return;
+  if (a.n_psi > 0)
+    k_absmax<T><<<dim3(a.n_psi, w.n_e), 256, 0, s>>>(a.psi, (const cx<T>*)w.arena, w.se, a.cert);
+  k_certificate<T><<<dim3((a.n + 255) / 256, w.n_e), 256, 0, s>>>(
+      a.n, a.cptr, (const int4*)a.terms, a.owner, a.pos, a.offG, a.offP, a.ldG, (const cx<T>*)w.arena, w.se, a.H,
+      (const double2*)a.sr, (const double2*)a.sl, a.sstride, (const double2*)a.ph_r, (const double2*)a.ph_l,
+      a.energies, a.eta, a.lesser, a.cert);
+}
+
 template struct Kern<double>;
 template struct Kern<float>;
+template struct Kern<DF>;
+
+// ---------------------------------------------------------------------------
+// S10 density: out_j (+)= scale * sum_e w_e Im X[e][j]   (X = diag G^<, caller order)
+__global__ void k_density(const double2* __restrict__ X, const double* __restrict__ w, int n_e, int n, double scale,
+                          int accumulate, double* out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int e = 0; e < n_e; ++e) acc = fma(w[e], X[int64_t(e) * n + j].y, acc);
+    out[j] = (accumulate ? out[j] : 0.0) + scale * acc;
+  }
+}
+
+void launch_density(const double* X, const double* w, int n_e, int n, double scale, int accumulate, double* out,
+                    cudaStream_t s) {
+  int blocks = (n + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_density<<<blocks, 256, 0, s>>>((const double2*)X, w, n_e, n, scale, accumulate, out);
+}
 
 // ---------------------------------------------------------------------------
 // S1a contact self-energy of a lead with H01 = -h I, tau = -h I, in the

@@ -23,6 +23,19 @@ struct AncTables {
   const int64_t *cl_offG, *cl_offGX;
 };
 
+struct CertArgs {
+  int n;
+  const int32_t *cptr, *terms, *owner, *pos, *ldG;
+  const int64_t *offG, *offP;
+  const double *H, *sr, *sl, *ph_r, *ph_l, *energies;
+  int64_t sstride;
+  double eta;
+  int lesser;
+  double* cert;  // [n_e][8]
+  const ZeroDesc* psi;
+  int n_psi;
+};
+
 template <typename T>
 struct Kern {
   static void assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst,
@@ -41,6 +54,7 @@ struct Kern {
   static void gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, cudaStream_t s);
   static void scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
   static void colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, cudaStream_t s);
+  static void certificate(const Work& w, const CertArgs& a, cudaStream_t s);
   static void diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
                        cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
@@ -61,6 +75,8 @@ struct ContactTable {
 };
 void launch_sigma_lesser(const double* sigma_r, int n_e, const ContactTable& ct, double kT, const double* energies,
                          int64_t stride, double* lesser, double* greater, cudaStream_t s);
+void launch_density(const double* X, const double* w, int n_e, int n, double scale, int accumulate, double* out,
+                    cudaStream_t s);
 void launch_phonon(int n, int n_e, double gamma, double mu, double kT, const double* energies, double* r,
                    double* l, double* g, cudaStream_t s);
 

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <exception>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -45,6 +46,7 @@ struct Dissector {
   std::vector<std::vector<int>> groups;     // sites of each contact
   std::vector<std::vector<double>> gcent;   // group centroid per axis
   int leaf = 64;
+  int split = 500;  // cut position as a quantile of the keys, per mille
   std::vector<Node> nodes;
   std::vector<int> mark;
   int tag = 0;
@@ -143,7 +145,7 @@ struct Dissector {
     keys(D, key);
     std::vector<double> sk = key;
     std::sort(sk.begin(), sk.end());
-    double c = sk[sk.size() / 2];
+    double c = sk[std::min(sk.size() - 1, size_t(double(sk.size()) * split / 1000.0))];
     if (!(c > sk[0])) {
       auto it = std::upper_bound(sk.begin(), sk.end(), sk[0]);
       if (it == sk.end()) {  // cannot be split
@@ -252,6 +254,11 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
   Dissector d;
   d.n = n;
   d.leaf = (opts && opts->leaf_size > 0) ? opts->leaf_size : 64;
+  d.split = (opts && opts->split_permille > 0) ? opts->split_permille : 500;
+  if (d.split < 100 || d.split > 900) {
+    delete plan;
+    return fail(ND_ERR_INVALID_ARG, "nd_analyze: split_permille must be in 100..900");
+  }
   d.dim = g->coord_dim;
   d.coords = g->coords;
   d.mark.assign(n, 0);
@@ -524,7 +531,12 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
   plan->flops_factor = ff;
   plan->flops_green_r = fg;
   plan->flops_green_lesser = fl;
-  build_schedules(plan);
+  try {
+    build_schedules(plan);
+  } catch (const std::exception& ex) {
+    delete plan;
+    return fail(ND_ERR_INVALID_ARG, std::string("nd_analyze: internal error building the schedule: ") + ex.what());
+  }
   *out = plan;
   return ND_OK;
 }

@@ -12,6 +12,7 @@
 //   GX = G_{I,anc}, NX_s = N_{I, I+anc}, NB_s = N_{B,anc}, PX_s = A_ii^{-1} NX_s.
 
 #include <algorithm>
+#include <unordered_map>
 
 #include "nd_internal.h"
 
@@ -245,6 +246,58 @@ void build_schedules(nd_plan* p) {
     p->cl_offG.push_back(c.off_G);
     p->cl_offGX[0].push_back(c.ext[0].off_GX);
     p->cl_offGX[1].push_back(c.ext[1].off_GX);
+    p->cl_offP[0].push_back(c.off_P[0]);
+    p->cl_offP[1].push_back(c.off_P[1]);
+  }
+  // ---- S9 certificate term lists --------------------------------------------
+  for (int i = 0; i < nc; ++i)
+    if (cl[i].b) p->psi_desc.push_back(ZeroDesc{cl[i].off_Psi, int64_t(cl[i].n) * cl[i].b});
+  {
+    std::unordered_map<int64_t, int32_t> posB;  // (cluster, site) -> index in B
+    for (int i = 0; i < nc; ++i)
+      for (int k = 0; k < cl[i].b; ++k) posB[int64_t(i) * p->n + cl[i].B[k]] = k;
+    // where X_jk (or X_kj) is stored for a coupled pair j, k
+    auto locate = [&](int j, int k, int32_t* cl_out, int32_t* idx_out, int32_t* anc_out) {
+      const int cj = p->owner[j], ck = p->owner[k];
+      if (cj == ck) {  // X_kj in the I x I block
+        *cl_out = cj;
+        *idx_out = p->pos[k] * (cl[cj].n + cl[cj].b) + p->pos[j];
+        *anc_out = 0;
+      } else if (ck > cj) {  // k is an ancestor site of j: X_jk in j's I x B block
+        *cl_out = cj;
+        *idx_out = p->pos[j] * (cl[cj].n + cl[cj].b) + cl[cj].n + posB.at(int64_t(cj) * p->n + k);
+        *anc_out = 1;
+      } else {  // j is an ancestor site of k: X_kj in k's I x B block
+        *cl_out = ck;
+        *idx_out = p->pos[k] * (cl[ck].n + cl[ck].b) + cl[ck].n + posB.at(int64_t(ck) * p->n + j);
+        *anc_out = 0;
+      }
+    };
+    std::vector<int32_t> contact_of(p->n, -1), cpos(p->n, -1);
+    for (int c = 0; c < p->n_contacts; ++c)
+      for (int q = p->contact_ptr[c]; q < p->contact_ptr[c + 1]; ++q) {
+        contact_of[p->contact_idx[q]] = c;
+        cpos[p->contact_idx[q]] = q - p->contact_ptr[c];
+      }
+    p->cert_ptr.assign(1, 0);
+    for (int j = 0; j < p->n; ++j) {
+      for (int q = p->rowptr[j]; q < p->rowptr[j + 1]; ++q) {
+        int32_t c, idx, anc;
+        locate(j, p->colind[q], &c, &idx, &anc);
+        p->cert_terms.insert(p->cert_terms.end(), {c, idx, q, anc});
+      }
+      const int ct = contact_of[j];
+      if (ct >= 0) {
+        const int m = p->contact_ptr[ct + 1] - p->contact_ptr[ct];
+        for (int q = p->contact_ptr[ct]; q < p->contact_ptr[ct + 1]; ++q) {
+          int32_t c, idx, anc;
+          locate(j, p->contact_idx[q], &c, &idx, &anc);
+          const int32_t sidx = soff[ct] + cpos[j] * m + (q - p->contact_ptr[ct]);
+          p->cert_terms.insert(p->cert_terms.end(), {c, idx, -1 - sidx, anc});
+        }
+      }
+      p->cert_ptr.push_back(int32_t(p->cert_terms.size() / 4));
+    }
   }
   for (int v = 0; v < 2; ++v) {
     auto* S = &p->sched_lesser[v];

@@ -20,10 +20,12 @@ STATUS = {0: "ND_OK", 1: "ND_ERR_INVALID_ARG", 2: "ND_ERR_NOT_SYMMETRIC", 3: "ND
           8: "ND_ERR_UNSUPPORTED"}
 ND_PREC_FP64 = 0
 ND_PREC_MIXED = 1
+ND_PREC_FP32X2 = 2
 ND_FACT_PHONON = 1
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
-           "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_fact_status",
+           "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
+           "nd_density", "nd_profile",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_destroy", "nd_sigma_lesser_fermi", "nd_phonon_const",
            "nd_last_error", "nd_version"]
 
@@ -41,7 +43,12 @@ class nd_graph(ctypes.Structure):
 
 
 class nd_opts(ctypes.Structure):
-    _fields_ = [("leaf_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+    _fields_ = [("leaf_size", ctypes.c_int32), ("split_permille", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+class nd_kernel_stats(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
 class nd_plan_info(ctypes.Structure):
@@ -77,6 +84,9 @@ def lib():
             "nd_factor": ([_P, _P, _P, _P, _P, _I32, _D, _P], _I32),
             "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
             "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
+            "nd_certificate": ([_P, _P, _P], _I32),
+            "nd_density": ([_P, _P, _I32, _I32, _D, _I32, _P, _P], _I32),
+            "nd_profile": ([_P, _I32, _P, _I32, ctypes.POINTER(_I32)], _I32),
             "nd_lead_create": ([_I32, _I32, _P, _P, _P, ctypes.POINTER(_P)], _I32),
             "nd_lead_sigma": ([_P, _P, _I32, _D, _P, _I64, _I64, _P], _I32),
             "nd_lead_destroy": ([_P], None),
@@ -156,7 +166,8 @@ class Lead(_Handle):
     _destroy = "nd_lead_destroy"
 
 
-def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=None, leaf_size=0) -> Plan:
+def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=None, leaf_size=0,
+               split_permille=0) -> Plan:
     keep = []
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(colind, dtype=np.int32)
@@ -176,6 +187,7 @@ def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=Non
         g.coords = _ptr(co, keep)
     o = nd_opts()
     o.leaf_size = leaf_size
+    o.split_permille = split_permille
     out = _P()
     _check(lib().nd_analyze(ctypes.byref(g), ctypes.byref(o), ctypes.byref(out)), "nd_analyze")
     return Plan(out.value)
@@ -220,6 +232,27 @@ def nd_diag_green(fact: Fact, sigma_lesser, sigma_greater, ph_lesser, ph_greater
     _check(lib().nd_diag_green(fact.ptr, _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep), _ptr(ph_lesser, keep),
                                _ptr(ph_greater, keep), _ptr(Gr, keep), _ptr(Gl, keep), _ptr(Gg, keep),
                                _stream(stream)), "nd_diag_green")
+
+
+def nd_certificate(fact: Fact, cert, stream=None):
+    keep = []
+    _check(lib().nd_certificate(fact.ptr, _ptr(cert, keep), _stream(stream)), "nd_certificate")
+
+
+def nd_density(Gl, weights, n_e, n, scale, accumulate, out, stream=None):
+    keep = []
+    _check(lib().nd_density(_ptr(Gl, keep), _ptr(weights, keep), n_e, n, scale, int(accumulate), _ptr(out, keep),
+                            _stream(stream)), "nd_density")
+
+
+def nd_profile(fact: Fact, enable: bool) -> list:
+    """Returns per-kernel-kind stats recorded since the previous call and sets
+    the enable state."""
+    arr = (nd_kernel_stats * 16)()
+    cnt = _I32()
+    _check(lib().nd_profile(fact.ptr, int(enable), arr, 16, ctypes.byref(cnt)), "nd_profile")
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops,
+             "bytes": arr[i].bytes} for i in range(cnt.value)]
 
 
 def nd_fact_status(fact: Fact) -> int:
