@@ -9,9 +9,10 @@ contact self-energies (S1a), lesser/greater self-energies, assembly and fold
 certificate (S9) and the density epilogue (S10).
 
 Paths: "fp32x2" = cluster blocks and products in FP32-pair ("double-float")
-arithmetic on the FP32 pipe with complex128 root inversion, with a second
-nested-dissection tree for energies whose fold growth max|Psi| exceeds 10;
-"fp64" = complex128 throughout on one tree (the plain ND path); "fp32" = plain
+arithmetic on the FP32 pipe with complex128 root inversion; every energy whose
+certificate reports a fold growth max|Psi| above 3 (where the elimination
+amplifies rounding, see the design notes) is recomputed on the complex128
+path; "fp64_nd" = complex128 throughout (the plain ND path); "fp32" = plain
 complex64 (reported, gated).
 The reported value is the fp32x2 path when its energy-integrated density
 matches the FP64 path to <= 1e-6 relative error, else the FP64 path.  Inputs
@@ -49,7 +50,11 @@ def parse():
     ap.add_argument("--chunk-mixed", type=int, default=128)
     ap.add_argument("--chunk-fp64", type=int, default=64)
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
-    ap.add_argument("--growth-max", type=float, default=10.0, help="growth above which the second tree runs")
+    ap.add_argument("--growth-max", type=float, default=3.0, help="fold growth above which fp32x2 redoes in FP64")
+    ap.add_argument("--dump-density", default="", help="write the densities of the paths to this .npz")
+    ap.add_argument("--only", default="", help="run one path only (fp64_nd, fp32x2, fp32); for profiling")
+    ap.add_argument("--energies", type=int, default=0, help="use the first K energies only; for profiling")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -122,7 +127,7 @@ def main_ours(a) -> None:
     import __graft_entry__
     __graft_entry__.build()
     from paper_1305_1070_gb300 import ndgf, workloads
-    from paper_1305_1070_gb300.solver import RobustSolver, Solver
+    from paper_1305_1070_gb300.solver import Solver
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -131,6 +136,8 @@ def main_ours(a) -> None:
     if world > 1:
         dist.init_process_group("nccl")
     dev, tr = workloads.workload(WORKLOAD)
+    if a.energies:
+        tr.energies = tr.energies[:a.energies]
     n_e = tr.n_e
     E_all = torch.as_tensor(tr.energies, device="cuda")
     w = np.zeros(n_e)
@@ -148,21 +155,34 @@ def main_ours(a) -> None:
     cert_max = {}
 
     redo = {}
+    calls = {"n": 0}  # solver.step calls of the last step (each launches 10 kernels outside the schedules)
 
-    def make_step(solver, chunk, name):
+    def make_step(solver, chunk, name, fallback=None):
+        """One pass over all energies; with a fallback solver, energies whose
+        certificate growth exceeds --growth-max are recomputed by it."""
         def step():
             cmax = torch.zeros(8, dtype=torch.float64, device="cuda")
-            nredo = 0
+            flagged = []
+            calls["n"] = 0
             for c0 in range(0, n_e, chunk):
                 m = min(chunk, n_e - c0)
-                if isinstance(solver, RobustSolver):
-                    cert = solver.step(E_all[c0:c0 + m], Gr[c0:c0 + m], Gl[c0:c0 + m], Gg[c0:c0 + m])
-                    nredo += solver.last_redo
-                else:
-                    r, l, g = solver.step(E_all[c0:c0 + m])
-                    Gr[c0:c0 + m], Gl[c0:c0 + m], Gg[c0:c0 + m] = r, l, g
-                    cert = solver.certificate(m)
+                calls["n"] += 1
+                r, l, g = solver.step(E_all[c0:c0 + m])
+                Gr[c0:c0 + m], Gl[c0:c0 + m], Gg[c0:c0 + m] = r, l, g
+                cert = solver.certificate(m)
                 cmax = torch.maximum(cmax, cert.amax(dim=0))
+                if fallback is not None:
+                    flagged.append(torch.nonzero(cert[:, 4] > a.growth_max).flatten() + c0)
+            nredo = 0
+            if fallback is not None:
+                idx = torch.cat(flagged)
+                nredo = int(idx.numel())
+                fchunk = fallback.max_ne
+                for c0 in range(0, nredo, fchunk):
+                    sel = idx[c0:c0 + fchunk]
+                    calls["n"] += 1
+                    r, l, g = fallback.step(E_all[sel])
+                    Gr[sel], Gl[sel], Gg[sel] = r, l, g
             ndgf.nd_density(Gl, weights, n_e, n, scale, 0, dens)
             cert_max[name] = cmax
             redo[name] = nredo
@@ -192,14 +212,17 @@ def main_ours(a) -> None:
 
     paths, results, solvers = {}, {}, {}
     clk = Clocks(local)
+    fallback = None
     for name, prec, chunk in (("fp64_nd", ndgf.ND_PREC_FP64, a.chunk_fp64),
                               ("fp32x2", ndgf.ND_PREC_FP32X2, a.chunk_fp64),
                               ("fp32", ndgf.ND_PREC_MIXED, a.chunk_mixed)):
-        if name == "fp32x2":
-            solver = RobustSolver(dev, tr, precision=prec, max_ne=chunk, growth_max=a.growth_max)
-        else:
-            solver = Solver(dev, tr, precision=prec, max_ne=chunk)
-        step = make_step(solver, chunk, name)
+        if a.only and name != a.only:
+            continue
+        chunk = min(chunk, n_e)
+        solver = Solver(dev, tr, precision=prec, max_ne=chunk)
+        if name == "fp64_nd":
+            fallback = solver
+        step = make_step(solver, chunk, name, fallback if name == "fp32x2" else None)
         W = a.warmup if name == "fp32x2" else min(a.warmup, 1)
         ms = timed(step, a.steps, W)
         results[name] = (dens.clone(), Gl[:, ::97].clone())
@@ -207,12 +230,17 @@ def main_ours(a) -> None:
         paths[name] = {"energies_per_s": round(n_e * world / (ms * 1e-3), 3), "ms_per_step": round(ms, 3),
                        "certificate_max": {"resid_r": c[0], "resid_lesser": c[2], "max_Gr": c[1], "max_Gl": c[3],
                                            "growth_max_psi": c[4]},
-                       "second_tree_energies": redo.get(name, 0)}
+                       "fp64_redo_energies": redo.get(name, 0)}
         solvers[name] = (solver, step, ms)
-        if name != "fp32x2":
-            del solver
         torch.cuda.empty_cache()
     clocks = clk.stop()
+    if a.only:
+        ms = solvers[a.only][2]
+        print(json.dumps({"only": a.only, "energies": n_e, "ms_per_step": ms, "energies_per_s": n_e / (ms * 1e-3)}))
+        return
+    if a.dump_density:
+        import numpy as np
+        np.savez(a.dump_density, **{k: v[0].cpu().numpy() for k, v in results.items()})
     d64, g64 = results["fp64_nd"]
     for name in ("fp32x2", "fp32"):
         paths[name]["density_rel_err_vs_fp64"] = rel(results[name][0], d64)
@@ -230,13 +258,22 @@ def main_ours(a) -> None:
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s: one FFMA per CUDA core per clock
     fp64_peak = 1.25  # TFLOP/s: GB300 FP64 rate (nominal)
-    prof = {}
+    prof, launches = {}, {}
     for name in ("fp64_nd", "fp32x2"):
         solver, step, _ = solvers[name]
+        f64 = solvers["fp64_nd"][0]
         ndgf.nd_profile(solver.fact, True)
+        if name == "fp32x2":
+            ndgf.nd_profile(f64.fact, True)
         step()
         torch.cuda.synchronize()
         prof[name] = ndgf.nd_profile(solver.fact, False)
+        extra = ndgf.nd_profile(f64.fact, False) if name == "fp32x2" else []
+        # schedule launches (profiled) + 10 per solver call (assembly, outputs, certificate,
+        # leads, lesser self-energies) + the density epilogue
+        launches[name] = sum(p["launches"] for p in prof[name] + extra) + 10 * calls["n"] + 1
+        if extra:
+            prof[name + "_fp64_redo"] = extra
 
     def dominant(pr, peak, label, flop_factor=1.0, note=""):
         tot = sum(p["ms"] for p in pr) or 1.0
@@ -256,7 +293,7 @@ def main_ours(a) -> None:
                                note="achieved in useful complex flops (8 per complex multiply-add); peak = FP32 rate / 12 "
                                     "(48 FP32 operations per complex multiply-add in FP32 pairs)")}
     roofline = roof[head]
-    launches_per_step = sum(p["launches"] for p in prof[head])
+    launches_per_step = launches[head]
 
     # end to end through the public API with host buffers (pinned)
     solver, step, _ = solvers[head]
@@ -266,10 +303,9 @@ def main_ours(a) -> None:
     dens_host = torch.empty(n, dtype=torch.float64).pin_memory()
 
     def step_e2e():
-        if isinstance(solver, RobustSolver):
-            solver.set_H(H_host)
-        else:
-            solver.H.copy_(H_host, non_blocking=True)
+        solver.H.copy_(H_host, non_blocking=True)
+        if head == "fp32x2":
+            solvers["fp64_nd"][0].H.copy_(H_host, non_blocking=True)
         E_all.copy_(E_host, non_blocking=True)
         step()
         for dst, src in zip(out_host, (Gr, Gl, Gg)):
@@ -282,13 +318,13 @@ def main_ours(a) -> None:
     info = solver.info
 
     if rank == 0:
-        cpu = run_cpu_oracle(a.cpu_sample)
+        cpu = run_cpu_oracle(a.cpu_sample) if not a.no_cpu else {"energies": 0, "seconds": 1.0, "cores": 0}
         cpu_val = cpu["energies"] / cpu["seconds"]
         line = {
             "metric": METRIC, "value": round(n_e * world / (ms_headline * 1e-3), 3), "unit": UNIT,
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_headline, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "fp32x2 (c64 pairs) + f64 root" if gate else "c128",
+            "dtype": "fp32x2 (FP32-pair complex) + c128 root and redo" if gate else "c128",
             "data": "synthetic (seeded superlattice, PCG64 seed 1306)",
             "config": {"workload": WORKLOAD, "sites": n, "energies_per_gpu": n_e, "clusters": info["n_clusters"],
                        "levels": info["n_levels"], "leaf_size": 64, "eta": tr.eta, "path": head,

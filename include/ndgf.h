@@ -86,11 +86,17 @@ typedef struct nd_graph {
  * cluster (0 = default 64); a contact set is never split, so a contact leaf
  * may be larger.  split_permille: position of each cut as a quantile of the
  * sites' keys, in 1/1000 (0 = default 500, the median); other values give a
- * different tree over the same graph. */
+ * different tree over the same graph.  slab: when > 0, every cut across the
+ * first coordinate axis (transport) is placed `slab` distinct coordinate
+ * values below the high end instead of at the quantile, so the tree is a
+ * chain of separators, each holding the low-side contact in its subtree, with
+ * slabs of `slab` layers dissected below them (paper Sec. 3.2, Fig. 6 is the
+ * case slab = 1 without the inner dissection). */
 typedef struct nd_opts {
   int32_t leaf_size;
   int32_t split_permille;
-  int32_t reserved[6];
+  int32_t slab;
+  int32_t reserved[5];
 } nd_opts;
 
 typedef struct nd_plan nd_plan; /* symbolic analysis (host + device copy)      */

@@ -12,11 +12,10 @@
 #include <type_traits>
 
 #include "nd_arith.cuh"
+#include "nd_gj.cuh"
 #include "nd_kernels.h"
 
 namespace ndgf {
-
-template <typename T> using O = Ops<T>;
 
 __device__ __forceinline__ double fermi_dev(double E, double mu, double kT) {
   double x = (E - mu) / kT;
@@ -72,112 +71,29 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
   }
 }
 
-// ---------------------------------------------------------------------------
-// Batched in-place Gauss-Jordan inversion with partial pivoting (one CTA per
-// matrix).  The matrix is n x n with leading dimension ld.
-template <typename TC>
-__device__ void gj_invert(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, int* n_singular) {
-  using R = typename O<TC>::R;
-  __shared__ R red_v[32];
-  __shared__ int red_i[32];
-  __shared__ int s_p;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
-  for (int k = 0; k < n; ++k) {
-    // pivot: largest |a_ik|^2 over i >= k (smallest index on ties)
-    R bv = R(-1);
-    int bi = k;
-    for (int i = k + tid; i < n; i += nt) {
-      const R v = O<TC>::mag2(M[int64_t(i) * ld + k]);
-      if (v > bv) {
-        bv = v;
-        bi = i;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const R ov = __shfl_down_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-      if (ov > bv || (ov == bv && oi < bi)) {
-        bv = ov;
-        bi = oi;
-      }
-    }
-    if (lane == 0) {
-      red_v[warp] = bv;
-      red_i[warp] = bi;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      R v = red_v[0];
-      int p = red_i[0];
-      for (int w = 1; w < nw; ++w)
-        if (red_v[w] > v || (red_v[w] == v && red_i[w] < p)) {
-          v = red_v[w];
-          p = red_i[w];
-        }
-      s_p = p;
-      piv[k] = p;
-    }
-    __syncthreads();
-    const int p = s_p;
-    if (p != k)
-      for (int j = tid; j < n; j += nt) {
-        const cx<TC> t = M[int64_t(k) * ld + j];
-        M[int64_t(k) * ld + j] = M[int64_t(p) * ld + j];
-        M[int64_t(p) * ld + j] = t;
-      }
-    __syncthreads();
-    cx<TC> pivot = M[int64_t(k) * ld + k];
-    if (!(O<TC>::mag2(pivot) > R(0))) {  // exactly singular (or NaN): record, keep going
-      if (tid == 0) atomicAdd(n_singular, 1);
-      pivot = O<TC>::from_d2(make_double2(std::is_same<TC, double>::value ? 1e-300 : 1e-30, 0.0));
-    }
-    const cx<TC> inv = O<TC>::recip(pivot);
-    for (int i = tid; i < n; i += nt) colk[i] = (i == k) ? O<TC>::zero() : M[int64_t(i) * ld + k];
-    __syncthreads();
-    for (int j = tid; j < n; j += nt) {
-      cx<TC>& a = M[int64_t(k) * ld + j];
-      a = (j == k) ? inv : O<TC>::mul(a, inv);
-    }
-    __syncthreads();
-    const int64_t nn = int64_t(n) * n;
-    for (int64_t idx = tid; idx < nn; idx += nt) {
-      const int i = int(idx / n), j = int(idx % n);
-      if (i == k) continue;
-      cx<TC>& a = M[int64_t(i) * ld + j];
-      const cx<TC> v = (j == k) ? O<TC>::zero() : a;
-      a = O<TC>::sub(v, O<TC>::mul(colk[i], M[int64_t(k) * ld + j]));
-    }
-    __syncthreads();
-  }
-  for (int k = n - 1; k >= 0; --k) {
-    const int p = piv[k];
-    if (p != k)
-      for (int i = tid; i < n; i += nt) {
-        const cx<TC> t = M[int64_t(i) * ld + k];
-        M[int64_t(i) * ld + k] = M[int64_t(i) * ld + p];
-        M[int64_t(i) * ld + p] = t;
-      }
-    __syncthreads();
-  }
-}
-
 template <typename T>
 __global__ void k_inverse(const InvDesc* __restrict__ descs, cx<T>* arena, int64_t se, double2* scratch,
-                          int64_t scratch_stride, int* n_singular) {
+                          int64_t scratch_stride, int* n_singular, int smem_max_n) {
   extern __shared__ __align__(16) unsigned char smem[];
   const InvDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   cx<T>* M = arena + int64_t(e) * se + d.off;
   int* piv = reinterpret_cast<int*>(smem);
   const size_t colk_off = (size_t(d.n) * sizeof(int) + 15) & ~size_t(15);
+  const int64_t nn = int64_t(d.n) * d.n;
   if (!std::is_same<T, double>::value && d.fp64 && scratch) {  // root block in complex128
     double2* W = scratch + int64_t(e) * scratch_stride;
-    const int64_t nn = int64_t(d.n) * d.n;
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = O<T>::to_d2(M[(i / d.n) * d.ld + i % d.n]);
     __syncthreads();
     gj_invert<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off), n_singular);
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = O<T>::from_d2(W[i]);
+  } else if (d.n <= smem_max_n) {  // whole block resident in shared memory
+    cx<T>* colk = reinterpret_cast<cx<T>*>(smem + colk_off);
+    cx<T>* S = colk + d.n;
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) S[i] = M[(i / d.n) * d.ld + i % d.n];
+    __syncthreads();
+    gj_invert<T>(S, d.n, d.n, piv, colk, n_singular);
+    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = S[i];
   } else {
     gj_invert<T>(M, d.n, d.ld, piv, reinterpret_cast<cx<T>*>(smem + colk_off), n_singular);
   }
@@ -594,10 +510,16 @@ template <typename T>
 void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, double* scratch, int64_t scratch_stride,
                       int* n_singular, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  size_t shm = ((size_t(max_n) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_n) * sizeof(double2);
+  const size_t base = ((size_t(max_n) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_n) * sizeof(double2);
+  // blocks with base + n^2 elements within 72 KB (n <= 64 for 16-byte elements)
+  // are inverted in shared memory; larger ones in place in global memory
+  int cap = 0;
+  while (base + size_t(cap + 1) * (cap + 1) * sizeof(cx<T>) <= size_t(72 * 1024)) ++cap;
+  const int smem_max_n = cap < max_n ? cap : max_n;
+  const size_t shm = base + size_t(smem_max_n) * smem_max_n * sizeof(cx<T>);
   if (shm > 48 * 1024) cudaFuncSetAttribute(k_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
   k_inverse<T><<<dim3(count, w.n_e), 256, shm, s>>>(d, (cx<T>*)w.arena, w.se, (double2*)scratch, scratch_stride,
-                                                    n_singular);
+                                                    n_singular, smem_max_n);
 }
 
 template <typename T>

@@ -47,6 +47,7 @@ struct Dissector {
   std::vector<std::vector<double>> gcent;   // group centroid per axis
   int leaf = 64;
   int split = 500;  // cut position as a quantile of the keys, per mille
+  int slab = 0;     // > 0: cuts along axis 0 leave slabs of this many distinct keys on the high side
   std::vector<Node> nodes;
   std::vector<int> mark;
   int tag = 0;
@@ -65,8 +66,10 @@ struct Dissector {
   // the axis of largest extent over D (the first axis wins ties); otherwise
   // breadth-first distance from a pseudo-peripheral site.  A contact group
   // gets one key for all its sites so that a cut never splits it.
+  int last_axis = -1;  // axis chosen by the last keys() call with coordinates
   void keys(const std::vector<int>& D, std::vector<double>& key) {
     key.assign(D.size(), 0.0);
+    last_axis = -1;
     if (coords && dim > 0) {
       int best = 0;
       double bext = -1.0;
@@ -86,6 +89,7 @@ struct Dissector {
         int v = D[i];
         key[i] = group[v] >= 0 ? gcent[group[v]][best] : coords[size_t(v) * dim + best];
       }
+      last_axis = best;
       return;
     }
     // breadth-first level structure inside D
@@ -146,6 +150,13 @@ struct Dissector {
     std::vector<double> sk = key;
     std::sort(sk.begin(), sk.end());
     double c = sk[std::min(sk.size() - 1, size_t(double(sk.size()) * split / 1000.0))];
+    if (slab > 0 && last_axis == 0) {
+      // caterpillar cut: leave `slab` distinct key values (columns) above the
+      // separator, so that the part below keeps the low-side contact
+      std::vector<double> uk = sk;
+      uk.erase(std::unique(uk.begin(), uk.end()), uk.end());
+      if (int(uk.size()) > slab + 1) c = uk[uk.size() - 1 - slab];
+    }
     if (!(c > sk[0])) {
       auto it = std::upper_bound(sk.begin(), sk.end(), sk[0]);
       if (it == sk.end()) {  // cannot be split
@@ -255,6 +266,7 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
   d.n = n;
   d.leaf = (opts && opts->leaf_size > 0) ? opts->leaf_size : 64;
   d.split = (opts && opts->split_permille > 0) ? opts->split_permille : 500;
+  d.slab = (opts && opts->slab > 0) ? opts->slab : 0;
   if (d.split < 100 || d.split > 900) {
     delete plan;
     return fail(ND_ERR_INVALID_ARG, "nd_analyze: split_permille must be in 100..900");

@@ -83,57 +83,3 @@ class Solver:
     def singular_pivots(self) -> int:
         return ndgf.nd_fact_status(self.fact)
 
-
-class RobustSolver:
-    """Two nested-dissection trees over the same device (cuts at the median and
-    at the 40% quantile of the sites).  Every energy runs on the first tree;
-    energies whose growth indicator max|Psi| exceeds ``growth_max`` run again
-    on the second tree and keep the result of the tree with the smaller
-    growth.  The elimination of isolated interior clusters amplifies rounding
-    where a folded block A_ii is nearly singular; which blocks are nearly
-    singular at an energy depends on where the separators are, so the second
-    tree acts as a pivoting step on the partition.  Selection is a row copy."""
-
-    def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
-                 leaf_size: int = 64, growth_max: float = 10.0, device: str = "cuda"):
-        self.a = Solver(dev, tr, precision=precision, max_ne=max_ne, leaf_size=leaf_size, split_permille=500,
-                        device=device)
-        self.b = Solver(dev, tr, precision=precision, max_ne=max_ne, leaf_size=leaf_size, split_permille=400,
-                        device=device)
-        self.growth_max = growth_max
-        self.info = self.a.info
-        self.fact = self.a.fact
-        self.H = self.a.H
-        self.last_redo = 0
-
-    def set_H(self, src):
-        self.a.H.copy_(src, non_blocking=True)
-        self.b.H.copy_(src, non_blocking=True)
-
-    def step(self, energies, Gr, Gl, Gg, cert_out=None):
-        """Fills rows of Gr, Gl, Gg (views [n_e, n]) for the energies; returns
-        the per-energy certificate rows of the kept results."""
-        n_e = len(energies)
-        r, l, g = self.a.step(energies)
-        Gr.copy_(r)
-        Gl.copy_(l)
-        Gg.copy_(g)
-        cert = self.a.certificate(n_e)
-        grow = cert[:, 4].cpu()
-        redo = torch.nonzero(grow > self.growth_max).flatten()
-        self.last_redo = int(redo.numel())
-        if redo.numel():
-            idx = redo.to(cert.device)
-            E = energies[idx] if isinstance(energies, torch.Tensor) else torch.as_tensor(
-                np.asarray(energies)[redo.numpy()], device=cert.device)
-            rb, lb, gb = self.b.step(E)
-            cb = self.b.certificate(len(redo))
-            better = (cb[:, 4] < cert[idx, 4]).cpu()
-            for k in range(len(redo)):
-                if better[k]:
-                    i = int(redo[k])
-                    Gr[i].copy_(rb[k])
-                    Gl[i].copy_(lb[k])
-                    Gg[i].copy_(gb[k])
-                    cert[i].copy_(cb[k])
-        return cert

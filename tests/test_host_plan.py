@@ -20,7 +20,7 @@ def _built():
 
 def test_exports_match_header():
     hdr = open(os.path.join(ROOT, "include", "ndgf.h")).read()
-    declared = set(re.findall(r"\b(nd_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(nd_[a-z_0-9]+)\s*\(", hdr))
     lib = ndgf.lib()
     for name in declared:
         assert hasattr(lib, name), name
