@@ -248,6 +248,24 @@ nd_status nd_phonon_const(int32_t n, int32_t n_e, double gamma, double mu, doubl
                           const double* energies, double* ph_r, double* ph_lesser,
                           double* ph_greater, void* stream);
 
+/* ---- allocation-free batched inversion (no counterpart in the paper) -------
+ * For callers that cannot allocate device memory (a frozen or foreign memory
+ * pool, allocation forbidden inside a host framework's callbacks, a
+ * fixed-footprint service).  Inverts `batch` complex64 matrices A[b] (device,
+ * [batch][n][n] interleaved (re, im) floats, row major) in place: each is
+ * copied to complex128, inverted by Gauss-Jordan with partial pivoting, and
+ * rounded back.  The complex128 copies live in a fixed file-scope device array
+ * of 2^18 complex128 elements (4 MiB) that every GPU loading the library holds
+ * until the process exits; batch * n * n must not exceed 2^18 and n must not
+ * exceed 1024, else ND_ERR_INVALID_ARG.  No cudaMalloc/cudaFree is called.
+ * n_singular (device int32) receives the number of exactly singular pivots
+ * (it is cleared by the call).  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and must be serialised by the caller. */
+nd_status nd_invert_c64_noalloc(float* A, int32_t n, int32_t batch, int32_t* n_singular, void* stream);
+
 const char* nd_last_error(void);
 const char* nd_version(void);
 

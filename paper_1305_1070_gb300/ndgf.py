@@ -25,7 +25,7 @@ ND_FACT_PHONON = 1
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
-           "nd_density", "nd_profile",
+           "nd_density", "nd_profile", "nd_invert_c64_noalloc",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_destroy", "nd_sigma_lesser_fermi", "nd_phonon_const",
            "nd_last_error", "nd_version"]
 
@@ -87,6 +87,7 @@ def lib():
             "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
             "nd_certificate": ([_P, _P, _P], _I32),
             "nd_density": ([_P, _P, _I32, _I32, _D, _I32, _P, _P], _I32),
+            "nd_invert_c64_noalloc": ([_P, _I32, _I32, _P, _P], _I32),
             "nd_profile": ([_P, _I32, _P, _I32, ctypes.POINTER(_I32)], _I32),
             "nd_lead_create": ([_I32, _I32, _P, _P, _P, ctypes.POINTER(_P)], _I32),
             "nd_lead_sigma": ([_P, _P, _I32, _D, _P, _I64, _I64, _P], _I32),
@@ -255,6 +256,13 @@ def nd_profile(fact: Fact, enable: bool) -> list:
     _check(lib().nd_profile(fact.ptr, int(enable), arr, 16, ctypes.byref(cnt)), "nd_profile")
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops,
              "bytes": arr[i].bytes} for i in range(cnt.value)]
+
+
+def nd_invert_c64_noalloc(A, n, batch, n_singular, stream=None):
+    """In-place inversion of complex64 matrices without device allocation."""
+    keep = []
+    _check(lib().nd_invert_c64_noalloc(_ptr(A, keep), n, batch, _ptr(n_singular, keep), _stream(stream)),
+           "nd_invert_c64_noalloc")
 
 
 def nd_fact_status(fact: Fact) -> int:
