@@ -221,8 +221,13 @@ nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
  *     z = E + i eta.   All three arrays are host, row major.
  * When H01 = -h I and tau = -h I the lead is diagonalised once on the host
  * (transverse modes) and Sigma^r = U diag(h lambda_n) U^T with lambda_n the
- * decaying root of lambda^2 - ((z - eps_n)/h) lambda + 1 = 0; otherwise
- * Lopez-Sancho decimation is used (FP64 on the device). */
+ * decaying root of lambda^2 - ((z - eps_n)/h) lambda + 1 = 0.  Any other lead
+ * uses the renormalisation-decimation of Lopez Sancho, Lopez Sancho and Rubio
+ * (J. Phys. F 15, 851 (1985)) on the device in complex128, one CTA per
+ * energy, at most 100 doubling steps, stopping when the effective couplings
+ * fall below 1e-14 * max(1, |H00|, |H01|).  The lead copies H00, H01, tau;
+ * the caller keeps ownership of its arrays.  Errors: ND_ERR_INVALID_ARG,
+ * ND_ERR_NOT_SYMMETRIC (H00), ND_ERR_OOM. */
 nd_status nd_lead_create(int32_t m, int32_t m_c, const double* H00, const double* H01,
                          const double* tau, nd_lead** out);
 /* Writes Sigma^r of every energy into sigma_out (device, complex): block of
@@ -230,6 +235,13 @@ nd_status nd_lead_create(int32_t m, int32_t m_c, const double* H00, const double
  * energies: device [n_e]. */
 nd_status nd_lead_sigma(nd_lead* lead, const double* energies, int32_t n_e, double eta,
                         double* sigma_out, int64_t stride, int64_t offset, void* stream);
+/* Decimation leads only: number of energies that had not converged within the
+ * step limit and number of exactly singular pivots met, accumulated over the
+ * nd_lead_sigma calls since the previous nd_lead_status (then reset).
+ * Synchronises the stream of the last nd_lead_sigma call.  Returns
+ * ND_ERR_SINGULAR when either count is non-zero; always ND_OK and zeros for a
+ * transverse-mode lead. */
+nd_status nd_lead_status(nd_lead* lead, int32_t* n_unconverged, int32_t* n_singular);
 void nd_lead_destroy(nd_lead* lead);
 
 /* Lesser/greater contact self-energies from the retarded ones (device arrays,

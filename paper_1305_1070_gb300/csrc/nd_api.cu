@@ -615,12 +615,26 @@ struct nd_lead {
   int m = 0, m_c = 0;
   bool modes = false;
   double hop = 0.0;
-  double *d_U = nullptr, *d_eps = nullptr;
+  double *d_U = nullptr, *d_eps = nullptr;  // transverse modes (uniform lead)
+  // decimation (general lead): H00, H01, tau on the device, workspace grown on demand
+  double *d_H00 = nullptr, *d_H01 = nullptr, *d_tau = nullptr, *d_work = nullptr;
+  int* d_status = nullptr;  // [0] energies not converged, [1] singular pivots
+  double scale = 1.0;
+  int64_t work_energies = 0;
+  cudaStream_t last_stream = nullptr;
   ~nd_lead() {
     cudaFree(d_U);
     cudaFree(d_eps);
+    cudaFree(d_H00);
+    cudaFree(d_H01);
+    cudaFree(d_tau);
+    cudaFree(d_work);
+    cudaFree(d_status);
   }
 };
+
+constexpr int LEAD_MAX_ITER = 100;
+constexpr double LEAD_TOL = 1e-14;
 
 extern "C" nd_status nd_lead_create(int32_t m, int32_t m_c, const double* H00, const double* H01, const double* tau,
                                     nd_lead** out) {
@@ -639,11 +653,21 @@ extern "C" nd_status nd_lead_create(int32_t m, int32_t m_c, const double* H00, c
       uniform = std::fabs(H01[size_t(i) * m + j] - want) <= 1e-14 * std::fabs(h) &&
                 std::fabs(tau[size_t(i) * m + j] - want) <= 1e-14 * std::fabs(h);
     }
-  if (!uniform)
-    return fail(ND_ERR_UNSUPPORTED, "nd_lead_create: only leads with H01 = tau = -h I are supported by this build");
   auto L = new nd_lead();
   L->m = m;
   L->m_c = m_c;
+  if (!uniform) {
+    std::vector<double> h00(H00, H00 + size_t(m) * m), h01(H01, H01 + size_t(m) * m), t(tau, tau + size_t(m_c) * m);
+    for (double v : h00) L->scale = std::max(L->scale, std::fabs(v));
+    for (double v : h01) L->scale = std::max(L->scale, std::fabs(v));
+    if (upload(h00, &L->d_H00) != ND_OK || upload(h01, &L->d_H01) != ND_OK || upload(t, &L->d_tau) != ND_OK ||
+        cudaMalloc(&L->d_status, 2 * sizeof(int)) != cudaSuccess || cudaMemset(L->d_status, 0, 2 * sizeof(int)) != cudaSuccess) {
+      delete L;
+      return fail(ND_ERR_OOM, "nd_lead_create: device allocation failed");
+    }
+    *out = L;
+    return ND_OK;
+  }
   L->modes = true;
   L->hop = h;
   std::vector<double> A(H00, H00 + size_t(m) * m), V;
@@ -663,10 +687,42 @@ extern "C" nd_status nd_lead_sigma(nd_lead* L, const double* energies, int32_t n
   if (!L || !energies || !sigma_out || n_e <= 0) return fail(ND_ERR_INVALID_ARG, "nd_lead_sigma: bad argument");
   if (!is_device_ptr(energies) || !is_device_ptr(sigma_out))
     return fail(ND_ERR_INVALID_ARG, "nd_lead_sigma: energies and sigma_out must be device pointers");
-  launch_lead_modes(L->d_U, L->d_eps, L->m, L->hop, energies, n_e, eta, sigma_out, stride, offset,
-                    (cudaStream_t)stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  L->last_stream = st;
+  if (L->modes) {
+    launch_lead_modes(L->d_U, L->d_eps, L->m, L->hop, energies, n_e, eta, sigma_out, stride, offset, st);
+  } else {
+    if (n_e > L->work_energies) {
+      cudaFree(L->d_work);
+      L->d_work = nullptr;
+      L->work_energies = 0;
+      const size_t bytes = lead_decimation_work_elems(L->m, L->m_c) * size_t(n_e) * sizeof(double2);
+      if (cudaMalloc(&L->d_work, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ND_ERR_OOM, "nd_lead_sigma: cannot allocate the decimation workspace");
+      }
+      L->work_energies = n_e;
+    }
+    launch_lead_decimation(L->d_H00, L->d_H01, L->d_tau, L->m, L->m_c, energies, n_e, eta, L->scale, LEAD_TOL,
+                           LEAD_MAX_ITER, sigma_out, stride, offset, L->d_work, L->d_status, st);
+  }
   ND_CUDA(cudaGetLastError());
   return ND_OK;
+}
+
+extern "C" nd_status nd_lead_status(nd_lead* L, int32_t* n_unconverged, int32_t* n_singular) {
+  if (!L || !n_unconverged || !n_singular) return fail(ND_ERR_INVALID_ARG, "nd_lead_status: bad argument");
+  *n_unconverged = 0;
+  *n_singular = 0;
+  if (L->modes) return ND_OK;
+  int h[2] = {0, 0};
+  ND_CUDA(cudaStreamSynchronize(L->last_stream));
+  ND_CUDA(cudaMemcpy(h, L->d_status, sizeof(h), cudaMemcpyDeviceToHost));
+  ND_CUDA(cudaMemset(L->d_status, 0, sizeof(h)));
+  *n_unconverged = h[0];
+  *n_singular = h[1];
+  return (h[0] || h[1]) ? fail(ND_ERR_SINGULAR, "nd_lead_status: decimation did not converge or met a zero pivot")
+                        : ND_OK;
 }
 
 extern "C" void nd_lead_destroy(nd_lead* L) { delete L; }

@@ -108,8 +108,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx<T>* arena, int64_t se,
        const cx<T>* __restrict__ aux, int64_t sa) {
   constexpr int NX = BN / TN, NY = BM / TM, NT = NX * NY;
-  __shared__ cx<T> As[BK][BM + 1];
-  __shared__ cx<T> Bs[BK][BN + 1];
+  constexpr int LA = (BM * BK + NT - 1) / NT, LB = (BK * BN + NT - 1) / NT;  // staged loads per thread
+  // two shared buffers: the next k-tile is fetched into registers while the
+  // current one is used, then stored to the other buffer (one barrier per step)
+  __shared__ cx<T> As[2][BK][BM + 1];
+  __shared__ cx<T> Bs[2][BK][BN + 1];
   const TileRef t = tiles[blockIdx.x];
   const GemmDesc d = descs[t.desc];
   const int64_t e = blockIdx.y;
@@ -119,55 +122,79 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
   const cx<T>* B = (d.offB & AUX_BIT) ? abase + (d.offB & ~AUX_BIT) : base + d.offB;
   const int m0 = t.tm * BM, n0 = t.tn * BN;
   const int tid = threadIdx.x, tx = tid % NX, ty = tid / NX;
+  const bool conjB = (d.opB == OP_C || d.opB == OP_H);
+  const bool transB = (d.opB == OP_T || d.opB == OP_H);
+  const bool transA = (d.opA != OP_N);
+  cx<T> ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int idx = tid + l * NT;
+      cx<T> v = O<T>::zero();
+      if (idx < BM * BK) {
+        const int mm = transA ? idx % BM : idx / BK, kk = transA ? idx / BM : idx % BK;
+        const int gm = m0 + mm, gk = k0 + kk;
+        if (gm < d.m && gk < d.k) v = transA ? A[int64_t(gk) * d.lda + gm] : A[int64_t(gm) * d.lda + gk];
+      }
+      ra[l] = v;
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int idx = tid + l * NT;
+      cx<T> v = O<T>::zero();
+      if (idx < BK * BN) {
+        const int kk = transB ? idx % BK : idx / BN, nn = transB ? idx / BK : idx % BN;
+        const int gk = k0 + kk, gn = n0 + nn;
+        if (gk < d.k && gn < d.n) v = transB ? B[int64_t(gn) * d.ldb + gk] : B[int64_t(gk) * d.ldb + gn];
+      }
+      rb[l] = conjB ? O<T>::conj(v) : v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int l = 0; l < LA; ++l) {
+      const int idx = tid + l * NT;
+      if (idx < BM * BK) {
+        const int mm = transA ? idx % BM : idx / BK, kk = transA ? idx / BM : idx % BK;
+        As[buf][kk][mm] = ra[l];
+      }
+    }
+#pragma unroll
+    for (int l = 0; l < LB; ++l) {
+      const int idx = tid + l * NT;
+      if (idx < BK * BN) {
+        const int kk = transB ? idx % BK : idx / BN, nn = transB ? idx / BK : idx % BN;
+        Bs[buf][kk][nn] = rb[l];
+      }
+    }
+  };
   typename O<T>::Acc acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = O<T>::acc_zero();
-  const bool conjB = (d.opB == OP_C || d.opB == OP_H);
-  const bool transB = (d.opB == OP_T || d.opB == OP_H);
-  for (int k0 = 0; k0 < d.k; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += NT) {
-      int mm, kk;
-      if (d.opA == OP_N) {
-        mm = idx / BK;
-        kk = idx % BK;
-      } else {
-        kk = idx / BM;
-        mm = idx % BM;
-      }
-      const int gm = m0 + mm, gk = k0 + kk;
-      cx<T> v = O<T>::zero();
-      if (gm < d.m && gk < d.k) v = (d.opA == OP_N) ? A[int64_t(gm) * d.lda + gk] : A[int64_t(gk) * d.lda + gm];
-      As[kk][mm] = v;
-    }
-    for (int idx = tid; idx < BK * BN; idx += NT) {
-      int kk, nn;
-      if (!transB) {
-        kk = idx / BN;
-        nn = idx % BN;
-      } else {
-        nn = idx / BK;
-        kk = idx % BK;
-      }
-      const int gk = k0 + kk, gn = n0 + nn;
-      cx<T> v = O<T>::zero();
-      if (gk < d.k && gn < d.n) v = transB ? B[int64_t(gn) * d.ldb + gk] : B[int64_t(gk) * d.ldb + gn];
-      Bs[kk][nn] = conjB ? O<T>::conj(v) : v;
-    }
-    __syncthreads();
+  const int nk = (d.k + BK - 1) / BK;
+  if (nk > 0) {
+    fetch(0);
+    store(0);
+  }
+  __syncthreads();
+  for (int kt = 0; kt < nk; ++kt) {
+    const int cur = kt & 1;
+    if (kt + 1 < nk) fetch((kt + 1) * BK);
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       cx<T> a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + i * NY];
+      for (int i = 0; i < TM; ++i) a[i] = As[cur][kk][ty + i * NY];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + j * NX];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[cur][kk][tx + j * NX];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) O<T>::acc_fma(acc[i][j], a[i], b[j]);
     }
+    if (kt + 1 < nk) store(cur ^ 1);
     __syncthreads();
   }
   cx<T>* C = base + d.offC;
@@ -676,6 +703,137 @@ void launch_lead_modes(const double* U, const double* eps, int m, double hop, co
   if (bx > 64) bx = 64;
   k_lead_modes<<<dim3(bx, n_e), 256, size_t(m) * sizeof(double2), s>>>(U, eps, m, hop, energies, eta, (double2*)out,
                                                                        stride, offset);
+}
+
+// ---------------------------------------------------------------------------
+// S1a for a general lead: renormalisation-decimation of Lopez Sancho, Lopez
+// Sancho and Rubio (J. Phys. F 15, 851 (1985)) in complex128, one CTA per
+// energy.  Layers 1, 2, ... of the lead have on-site block H00 and hopping H01
+// from a layer to the next; every step eliminates every other remaining layer,
+// doubling the reach of the effective couplings a (outwards) and b (inwards):
+//   g = (z - e)^{-1};  e_s += a g b;  e += a g b + b g a;  a <- a g a;  b <- b g b
+// with e_s = e = H00, a = H01, b = H01^T at the start.  The loop ends when
+// every |a_ij|, |b_ij| < tol * scale (scale = max(1, max|H00|, max|H01|)) or
+// after max_iter steps (counted in status[0]); then g_s = (z - e_s)^{-1} and
+// Sigma = tau g_s tau^T.  Singular pivots of the inversions go to status[1].
+
+// C = A B, all m x m row major, CTA-wide; ends with a barrier.
+__device__ void cta_matmul(double2* __restrict__ C, const double2* __restrict__ A, const double2* __restrict__ B,
+                           int rows, int inner, int cols, bool transB) {
+  for (int idx = threadIdx.x; idx < rows * cols; idx += blockDim.x) {
+    const int i = idx / cols, j = idx % cols;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < inner; ++k) {
+      const double2 a = A[i * inner + k], b = transB ? B[j * inner + k] : B[k * cols + j];
+      re = fma(a.x, b.x, re);
+      re = fma(-a.y, b.y, re);
+      im = fma(a.x, b.y, im);
+      im = fma(a.y, b.x, im);
+    }
+    C[idx] = make_double2(re, im);
+  }
+  __syncthreads();
+}
+
+__global__ void k_lead_decimation(const double* __restrict__ H00, const double* __restrict__ H01,
+                                  const double* __restrict__ tau, int m, int m_c,
+                                  const double* __restrict__ energies, double eta, double scale, double tol,
+                                  int max_iter, double2* __restrict__ out, int64_t stride, int64_t offset,
+                                  double2* __restrict__ work, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_big;
+  const int e = blockIdx.x;
+  const int mm = m * m, mx = m_c > m ? m_c : m;
+  double2* es = work + int64_t(e) * (5 * mm + 2 * mx * m);  // e_s
+  double2* ep = es + mm;                     // e
+  double2* al = ep + mm;                     // a
+  double2* be = al + mm;                     // b
+  double2* g = be + mm;                      // (z - e)^{-1}, then products
+  double2* ag = g + mm;                      // a g
+  double2* bg = ag + mx * m;                 // b g
+  int* piv = reinterpret_cast<int*>(smem);
+  double2* colk = reinterpret_cast<double2*>(smem + ((size_t(m) * sizeof(int) + 15) & ~size_t(15)));
+  const double E = energies[e];
+  const double lim = tol * scale;
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+    const int r = i / m, c = i % m;
+    es[i] = ep[i] = make_double2(H00[i], 0.0);
+    al[i] = make_double2(H01[i], 0.0);
+    be[i] = make_double2(H01[c * m + r], 0.0);
+  }
+  __syncthreads();
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+      const int r = i / m, c = i % m;
+      g[i] = make_double2((r == c ? E : 0.0) - ep[i].x, (r == c ? eta : 0.0) - ep[i].y);
+    }
+    __syncthreads();
+    gj_invert<double>(g, m, m, piv, colk, status + 1);
+    __syncthreads();
+    cta_matmul(ag, al, g, m, m, m, false);
+    cta_matmul(bg, be, g, m, m, m, false);
+    cta_matmul(g, ag, be, m, m, m, false);  // a g b
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+      es[i] = make_double2(es[i].x + g[i].x, es[i].y + g[i].y);
+      ep[i] = make_double2(ep[i].x + g[i].x, ep[i].y + g[i].y);
+    }
+    __syncthreads();
+    cta_matmul(g, bg, al, m, m, m, false);  // b g a
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) ep[i] = make_double2(ep[i].x + g[i].x, ep[i].y + g[i].y);
+    __syncthreads();
+    cta_matmul(g, ag, al, m, m, m, false);  // a g a
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) al[i] = g[i];
+    __syncthreads();
+    cta_matmul(g, bg, be, m, m, m, false);  // b g b
+    if (threadIdx.x == 0) s_big = 0;
+    __syncthreads();
+    bool big = false;
+    for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+      be[i] = g[i];
+      big = big || fabs(g[i].x) >= lim || fabs(g[i].y) >= lim || fabs(al[i].x) >= lim || fabs(al[i].y) >= lim;
+    }
+    if (big) s_big = 1;
+    __syncthreads();
+    const bool done = (s_big == 0);
+    __syncthreads();
+    if (done) break;
+  }
+  if (it == max_iter && threadIdx.x == 0) atomicAdd(status, 1);
+  for (int i = threadIdx.x; i < mm; i += blockDim.x) {
+    const int r = i / m, c = i % m;
+    g[i] = make_double2((r == c ? E : 0.0) - es[i].x, (r == c ? eta : 0.0) - es[i].y);
+  }
+  __syncthreads();
+  gj_invert<double>(g, m, m, piv, colk, status + 1);
+  __syncthreads();
+  // tau (m_c x m, real) into ag as complex, then Sigma = (tau g_s) tau^T
+  for (int i = threadIdx.x; i < m_c * m; i += blockDim.x) ag[i] = make_double2(tau[i], 0.0);
+  __syncthreads();
+  cta_matmul(bg, ag, g, m_c, m, m, false);  // tau g_s, m_c x m
+  double2* o = out + int64_t(e) * stride + offset;
+  for (int idx = threadIdx.x; idx < m_c * m_c; idx += blockDim.x) {
+    const int i = idx / m_c, j = idx % m_c;
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < m; ++k) {
+      const double t = tau[j * m + k];
+      re = fma(bg[i * m + k].x, t, re);
+      im = fma(bg[i * m + k].y, t, im);
+    }
+    o[idx] = make_double2(re, im);
+  }
+}
+
+size_t lead_decimation_work_elems(int m, int m_c) {
+  return size_t(5) * m * m + size_t(2) * (m_c > m ? m_c : m) * m;
+}
+
+void launch_lead_decimation(const double* H00, const double* H01, const double* tau, int m, int m_c,
+                            const double* energies, int n_e, double eta, double scale, double tol, int max_iter,
+                            double* out, int64_t stride, int64_t offset, double* work, int* status, cudaStream_t s) {
+  const size_t shm = ((size_t(m) * sizeof(int) + 15) & ~size_t(15)) + size_t(m) * sizeof(double2);
+  k_lead_decimation<<<n_e, 256, shm, s>>>(H00, H01, tau, m, m_c, energies, eta, scale, tol, max_iter, (double2*)out,
+                                          stride, offset, (double2*)work, status);
 }
 
 // Sigma^< = i f Gamma, Sigma^> = -i (1 - f) Gamma, Gamma = i (Sigma - Sigma^dagger)

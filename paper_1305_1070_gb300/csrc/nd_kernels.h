@@ -63,6 +63,11 @@ struct Kern {
   static int gemm_tile();
 };
 
+// Per-energy complex128 workspace of launch_lead_decimation, in elements.
+size_t lead_decimation_work_elems(int m, int m_c);
+void launch_lead_decimation(const double* H00, const double* H01, const double* tau, int m, int m_c,
+                            const double* energies, int n_e, double eta, double scale, double tol, int max_iter,
+                            double* out, int64_t stride, int64_t offset, double* work, int* status, cudaStream_t s);
 void launch_lead_modes(const double* U, const double* eps, int m, double hop, const double* energies, int n_e,
                        double eta, double* out, int64_t stride, int64_t offset, cudaStream_t s);
 // Contacts of nd_sigma_lesser_fermi, passed by value.

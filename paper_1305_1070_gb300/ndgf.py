@@ -26,7 +26,7 @@ ND_FACT_PHONON = 1
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
-           "nd_lead_create", "nd_lead_sigma", "nd_lead_destroy", "nd_sigma_lesser_fermi", "nd_phonon_const",
+           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_sigma_lesser_fermi", "nd_phonon_const",
            "nd_last_error", "nd_version"]
 
 
@@ -91,6 +91,7 @@ def lib():
             "nd_profile": ([_P, _I32, _P, _I32, ctypes.POINTER(_I32)], _I32),
             "nd_lead_create": ([_I32, _I32, _P, _P, _P, ctypes.POINTER(_P)], _I32),
             "nd_lead_sigma": ([_P, _P, _I32, _D, _P, _I64, _I64, _P], _I32),
+            "nd_lead_status": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], _I32),
             "nd_lead_destroy": ([_P], None),
             "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
             "nd_phonon_const": ([_I32, _I32, _D, _D, _D, _P, _P, _P, _P, _P], _I32),
@@ -288,6 +289,15 @@ def nd_lead_sigma(lead: Lead, energies, n_e: int, eta: float, sigma_out, stride:
     keep = []
     _check(lib().nd_lead_sigma(lead.ptr, _ptr(energies, keep), n_e, eta, _ptr(sigma_out, keep), stride, offset,
                                _stream(stream)), "nd_lead_sigma")
+
+
+def nd_lead_status(lead: Lead):
+    """(n_unconverged, n_singular) of the decimation since the previous call."""
+    a, b = _I32(), _I32()
+    st = lib().nd_lead_status(lead.ptr, ctypes.byref(a), ctypes.byref(b))
+    if st not in (0, 3):
+        _check(st, "nd_lead_status")
+    return a.value, b.value
 
 
 def nd_sigma_lesser_fermi(sigma_r, n_e, m_c, mu, kT, energies, sigma_lesser, sigma_greater, stream=None):

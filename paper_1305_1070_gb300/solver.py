@@ -83,3 +83,7 @@ class Solver:
     def singular_pivots(self) -> int:
         return ndgf.nd_fact_status(self.fact)
 
+    def lead_status(self):
+        """Per lead (n_unconverged, n_singular) of the decimation since the last query."""
+        return [ndgf.nd_lead_status(lead) for lead in self.leads]
+

@@ -1,0 +1,107 @@
+"""Contact self-energies of general leads (renormalisation-decimation on the
+device, paper Sec. 2) and the (10,0) nanotube workload end to end.
+
+Pins of the device decimation:
+* a uniform lead written with a two-column principal layer (so that its
+  hopping is not a multiple of the identity) must give the transverse-mode
+  closed form of the one-column lead;
+* the nanotube lead must match the oracle's decimation.
+Then the nanotube device (four-ring cells, phonon broadening, disorder) is
+compared element by element with the dense oracle, complex128 at 1e-10 and
+FP32 pairs at 1e-9 relative max error per energy.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dense, leads, observables  # noqa: E402
+from paper_1305_1070_gb300 import build, ndgf, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-10
+TOL_X2 = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+
+
+def _sigma(H00, H01, tau, E, eta):
+    lead = ndgf.nd_lead_create(H00, H01, tau)
+    m_c = tau.shape[0]
+    Ed = torch.as_tensor(np.asarray(E, dtype=np.float64), device="cuda")
+    out = torch.zeros(len(E), m_c * m_c, dtype=torch.complex128, device="cuda")
+    ndgf.nd_lead_sigma(lead, Ed, len(E), eta, out, m_c * m_c, 0)
+    torch.cuda.synchronize()
+    status = ndgf.nd_lead_status(lead)
+    return out.cpu().numpy().reshape(len(E), m_c, m_c), status
+
+
+def test_two_column_layer_matches_mode_closed_form():
+    dev = workloads.superlattice(8, 12)
+    lead = dev.leads[1]
+    m = lead.H00.shape[0]
+    H00 = np.block([[lead.H00, lead.H01], [lead.H01.T, lead.H00]])
+    H01 = np.zeros((2 * m, 2 * m))
+    H01[m:, :m] = lead.H01
+    tau = np.hstack([lead.tau, np.zeros((m, m))])
+    E = np.array([0.0, 0.05, 0.21, 0.37, 0.5])
+    eta = 1e-6
+    got, status = _sigma(H00, H01, tau, E, eta)
+    assert status == (0, 0)
+    for e, En in enumerate(E):
+        ref = leads.self_energy(lead, En, eta, method="modes")
+        err = observables.rel_err(got[e].ravel(), ref.ravel())
+        assert err <= 1e-10, f"E={En}: {err:.3e}"
+
+
+def test_nanotube_lead_matches_oracle_decimation():
+    dev = workloads.cnt_zigzag(3)
+    E = np.linspace(-1.0, 1.0, 7)
+    for lead in dev.leads:
+        got, status = _sigma(lead.H00, lead.H01, lead.tau, E, 1e-6)
+        assert status == (0, 0)
+        for e, En in enumerate(E):
+            ref = leads.self_energy(lead, En, 1e-6, method="decimation")
+            err = observables.rel_err(got[e].ravel(), ref.ravel())
+            assert err <= 1e-10, f"E={En}: {err:.3e}"
+
+
+def _nanotube(precision, leaf, gamma_ph):
+    from paper_1305_1070_gb300.solver import Solver
+    dev = workloads.cnt_zigzag(6, disorder=0.1, seed=1307)
+    tr = workloads.Transport(energies=np.array([-0.93, -0.41, 0.02, 0.37, 0.88]), gamma_ph=gamma_ph, mu_ph=0.05)
+    s = Solver(dev, tr, precision=precision, leaf_size=leaf)
+    Gr, Gl, Gg = s.step(tr.energies)
+    torch.cuda.synchronize()
+    assert s.singular_pivots() == 0
+    assert all(st == (0, 0) for st in s.lead_status())
+    got = {"Gr": Gr.cpu().numpy(), "Gl": Gl.cpu().numpy(), "Gg": Gg.cpu().numpy()}
+    ref = dense.green_diag(dev, tr)
+    worst = 0.0
+    for k in ("Gr", "Gl", "Gg"):
+        for e in range(len(tr.energies)):
+            err = observables.rel_err(got[k][e], ref[k][e])
+            worst = max(worst, err)
+    return worst
+
+
+@pytest.mark.parametrize("leaf", [40, 15])
+def test_nanotube_phonon_fp64(leaf):
+    worst = _nanotube(ndgf.ND_PREC_FP64, leaf, 5e-3)
+    assert worst <= TOL64, worst
+
+
+def test_nanotube_ballistic_fp64():
+    worst = _nanotube(ndgf.ND_PREC_FP64, 40, 0.0)
+    assert worst <= TOL64, worst
+
+
+def test_nanotube_phonon_fp32x2():
+    worst = _nanotube(ndgf.ND_PREC_FP32X2, 40, 5e-3)
+    print(f"nanotube fp32x2 worst rel err {worst:.3e}")
+    assert worst <= TOL_X2, worst
