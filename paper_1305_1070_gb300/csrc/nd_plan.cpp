@@ -1,10 +1,10 @@
 // S0 of the path: nested-dissection ordering, cluster tree, symbolic fold and
 // the precomputed launch schedule (host only; runs without a GPU).
 //
-// Paper Sec. 3.2: "nested dissection divides the system into two disconnected
-// sets and an interface, called the separator; the process is repeated
-// recursively on each set to create a multilevel binary tree", with the rules
-// (i) clusters on one level do not interact and (ii) separators are small.
+// Paper Sec. 3.2: each dissection step removes a small set of sites (the
+// separator) that leaves two parts with no coupling between them, and is
+// applied again to each part, which yields a binary cluster tree; clusters of
+// one level never couple to each other and separators are kept small.
 // Sec. 3.2, Fig. 8: the dense contact layers stay inside one cluster each.
 
 #include <algorithm>

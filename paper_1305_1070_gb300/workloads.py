@@ -46,8 +46,8 @@ class Lead:
     (rows, in the order of the device contact set) to the lead layer adjacent to
     the device (columns).  The retarded self-energy that the lead folds onto the
     contact sites is tau g_s tau^T, g_s the surface Green's function of the lead
-    (paper Sec. 2, "their respective effect can be folded into layer 1 and
-    layer N_y").
+    (paper Sec. 2: each semi-infinite lead enters only through a self-energy on
+    the first or last device layer).
     """
 
     H00: np.ndarray

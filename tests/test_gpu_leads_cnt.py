@@ -60,8 +60,11 @@ def test_two_column_layer_matches_mode_closed_form():
 
 
 def test_nanotube_lead_matches_oracle_decimation():
+    # E = 0 is left out: there the semi-infinite zigzag tube has edge states,
+    # Sigma has a pole regularised only by eta, and its value is determined
+    # only to about (unit roundoff) / eta^2 relative.
     dev = workloads.cnt_zigzag(3)
-    E = np.linspace(-1.0, 1.0, 7)
+    E = np.linspace(-1.0, 1.0, 8)
     for lead in dev.leads:
         got, status = _sigma(lead.H00, lead.H01, lead.tau, E, 1e-6)
         assert status == (0, 0)
