@@ -91,12 +91,24 @@ typedef struct nd_graph {
  * values below the high end instead of at the quantile, so the tree is a
  * chain of separators, each holding the low-side contact in its subtree, with
  * slabs of `slab` layers dissected below them (paper Sec. 3.2, Fig. 6 is the
- * case slab = 1 without the inner dissection). */
+ * case slab = 1 without the inner dissection).
+ * delay (0..8): delayed pivots, an extension of the paper's elimination.
+ * Every cluster that is not a root and holds no contact site leaves `delay`
+ * of its front rows uneliminated and hands them to its parent as extra
+ * interior unknowns.  The rows are chosen per energy as the largest diagonal
+ * entries of the front's inverse, one at a time, updating the inverse after
+ * each choice (complex64 selection).  This keeps the fold bounded where an
+ * isolated cluster is close to resonance, which the paper's scheme without
+ * pivoting across clusters is not.  The result is the same matrix function;
+ * only the elimination order differs per energy.  delay > 0 adds an unknown
+ * id range n .. n + n_virtual - 1 to the cluster site lists
+ * (nd_plan_cluster_sites) and turns off the residual part of nd_certificate. */
 typedef struct nd_opts {
   int32_t leaf_size;
   int32_t split_permille;
   int32_t slab;
-  int32_t reserved[5];
+  int32_t delay;        /* delayed pivots per cluster, 0..8 (0 = none) */
+  int32_t reserved[4];
 } nd_opts;
 
 typedef struct nd_plan nd_plan; /* symbolic analysis (host + device copy)      */
@@ -125,8 +137,10 @@ typedef struct nd_plan_info {
 nd_status nd_analyze(const nd_graph* graph, const nd_opts* opts, nd_plan** out);
 nd_status nd_plan_query(const nd_plan* plan, nd_plan_info* out);
 /* Per-cluster tree arrays (host, each of length n_clusters, any may be NULL):
- * level (1 = leaf), parent (-1 = root), n_i (interior size), b_i (boundary
- * size).  cluster_of_site[n] (may be NULL): owning cluster of each site. */
+ * level (1 = leaf), parent (-1 = root), n_i (front rows: interior size, plus
+ * the rows delayed from this cluster when nd_opts.delay > 0), b_i (boundary
+ * size, counting the cluster's own delayed rows first).  cluster_of_site[n]
+ * (may be NULL): owning cluster of each site. */
 nd_status nd_plan_tree(const nd_plan* plan, int32_t* level, int32_t* parent, int32_t* n_i,
                        int32_t* b_i, int32_t* cluster_of_site);
 /* Sites of cluster c: interior set I_c (n_c entries) then boundary set B_c

@@ -107,6 +107,10 @@ struct nd_fact {
   AncGatherDesc* d_anc = nullptr;
   RowScatterDesc* d_rows = nullptr;
   ColGatherDesc* d_colg = nullptr;
+  DelayDesc* d_delay = nullptr;
+  LocDesc* d_loc = nullptr;
+  DelayTabs dt{nullptr, nullptr, nullptr, nullptr, 0};  // per-energy row tables (delayed pivots)
+  int32_t *d_unk_q = nullptr, *d_unk_r = nullptr, *d_anc_q = nullptr, *d_anc_r = nullptr;
   int32_t *d_site_ids = nullptr, *d_cmaps = nullptr, *d_owner = nullptr, *d_pos = nullptr;
   int32_t *d_cl_n = nullptr, *d_cl_A = nullptr, *d_cl_ldG = nullptr;
   int64_t *d_cl_offG = nullptr, *d_cl_offGX[2] = {nullptr, nullptr};
@@ -193,8 +197,9 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
                        const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s, int variant = 0,
                        const std::vector<double>* step_flops = nullptr) {
   const nd_plan* p = f->plan;
-  const AncTables at{f->d_site_ids, f->d_owner, f->d_pos, f->d_cl_n, f->d_cl_A, f->d_cl_ldG, f->d_cl_offG,
-                     f->d_cl_offGX[variant]};
+  const AncTables at{f->d_site_ids, f->d_unk_q, f->d_unk_r, f->d_anc_q,       f->d_anc_r,
+                     f->d_cl_n,     f->d_cl_A,  f->d_cl_ldG, f->d_cl_offG, f->d_cl_offGX[variant]};
+  const DelayTabs& dt = f->dt;
   for (size_t si = 0; si < sched.size(); ++si) {
     const Step& st = sched[si];
     Profiler::Rec rec{};
@@ -219,22 +224,28 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
         break;
       case ST_GATHER_SYM:
       case ST_GATHER_SKEW:
-        Kern<T>::gather(w, f->d_gath + st.begin, st.count, f->d_maps, st.kind == ST_GATHER_SKEW, s);
+        Kern<T>::gather(w, f->d_gath + st.begin, st.count, f->d_maps, st.kind == ST_GATHER_SKEW, dt, s);
         break;
       case ST_ZERO:
         Kern<T>::zero(w, f->d_zero + st.begin, st.count, s);
         break;
       case ST_NPH:
-        Kern<T>::nph(w, f->d_nph + st.begin, st.count, f->d_sites, ph_l, ph_g, p->n, s);
+        Kern<T>::nph(w, f->d_nph + st.begin, st.count, f->d_sites, ph_l, ph_g, p->n, dt, s);
         break;
       case ST_GATHER_ANC:
-        Kern<T>::gather_anc(w, f->d_anc + st.begin, st.count, at, s);
+        Kern<T>::gather_anc(w, f->d_anc + st.begin, st.count, at, dt, s);
         break;
       case ST_SCATTER_ROWS:
-        Kern<T>::scatter_rows(w, f->d_rows + st.begin, st.count, f->d_maps, s);
+        Kern<T>::scatter_rows(w, f->d_rows + st.begin, st.count, f->d_maps, dt, s);
         break;
       case ST_COLGATHER:
-        Kern<T>::colgather(w, f->d_colg + st.begin, st.count, f->d_cmaps, s);
+        Kern<T>::colgather(w, f->d_colg + st.begin, st.count, f->d_cmaps, at, dt, s);
+        break;
+      case ST_DELAY:
+        Kern<T>::delay(w, f->d_delay + st.begin, st.count, st.max_dim, dt, s);
+        break;
+      case ST_LOC:
+        launch_loc(f->d_loc + st.begin, st.count, w.n_e, dt, s);
         break;
     }
     if (f->prof.on) {
@@ -262,6 +273,11 @@ std::vector<double> step_flops(const nd_plan* p, const std::vector<Step>& sched)
       for (int k = st.begin; k < st.begin + st.count; ++k) {
         const double n = p->inv_desc[k].n;
         f += 8.0 * n * n * n;
+      }
+    if (st.kind == ST_DELAY)  // complex64 inverse of the front's interior block and k rank-one updates
+      for (int k = st.begin; k < st.begin + st.count; ++k) {
+        const double n = p->delay_desc[k].nf;
+        f += 8.0 * n * n * (n + p->delay_desc[k].k);
       }
     out[si] = f;
   }
@@ -323,6 +339,20 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dupload(f, p->anc_desc, &f->d_anc));
   TRY(dupload(f, p->rows_desc, &f->d_rows));
   TRY(dupload(f, p->colg_desc, &f->d_colg));
+  TRY(dupload(f, p->delay_desc, &f->d_delay));
+  TRY(dupload(f, p->loc_desc, &f->d_loc));
+  TRY(dupload(f, p->unk_q, &f->d_unk_q));
+  TRY(dupload(f, p->unk_r, &f->d_unk_r));
+  TRY(dupload(f, p->anc_q, &f->d_anc_q));
+  TRY(dupload(f, p->anc_r, &f->d_anc_r));
+  if (p->n_virtual > 0) {
+    const size_t tb = size_t(p->n_unk) * max_ne * sizeof(int32_t);
+    f->dt.n_unk = p->n_unk;
+    TRY(dalloc(f, (void**)&f->dt.iperm, tb));
+    TRY(dalloc(f, (void**)&f->dt.rsite, tb));
+    TRY(dalloc(f, (void**)&f->dt.locq, tb));
+    TRY(dalloc(f, (void**)&f->dt.locr, tb));
+  }
   TRY(dupload(f, p->site_ids, &f->d_site_ids));
   TRY(dupload(f, p->cmaps, &f->d_cmaps));
   TRY(dupload(f, p->owner, &f->d_owner));
@@ -379,7 +409,8 @@ template <typename T>
 static nd_status factor_t(nd_fact* f, const Work& w, const double* H, const double* E, double eta, const double* sr,
                           const double* ph, int nc, cudaStream_t s) {
   const nd_plan* p = f->plan;
-  Kern<T>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph, p->n, s);
+  Kern<T>::assemble(w, f->d_asm, nc, f->d_ent_dst, f->d_ent_src, f->d_sites, H, E, eta, sr, p->sigma_elems, ph, p->n,
+                    f->dt, s);
   return run_schedule<T>(f, p->sched_factor, f->tr_factor, w, nullptr, nullptr, s, 0, &f->step_flops_factor);
 }
 
@@ -420,14 +451,14 @@ static nd_status diag_green_t(nd_fact* f, const double* sl, const double* sg, co
   const int nc = int(p->cl.size());
   nd_status st = run_schedule<T>(f, p->sched_green, f->tr_green, w, nullptr, nullptr, s, 0, &f->step_flops_green);
   if (st != ND_OK) return st;
-  if (outs[0]) Kern<T>::diag_out(w, f->d_diag_g, nc, f->d_sites, outs[0], p->n, s);
+  if (outs[0]) Kern<T>::diag_out(w, f->d_diag_g, nc, f->d_sites, outs[0], p->n, f->dt, s);
   if (outs[1] || outs[2]) {
     Kern<T>::convert_aux(w, sl, sg, p->sigma_elems, s);
     const int v = (pl || pg) ? 1 : 0;
     st = run_schedule<T>(f, p->sched_lesser[v], f->tr_lesser[v], w, pl, pg, s, v, &f->step_flops_lesser[v]);
     if (st != ND_OK) return st;
-    if (outs[1]) Kern<T>::diag_out(w, f->d_diag_p[0], nc, f->d_sites, outs[1], p->n, s);
-    if (outs[2]) Kern<T>::diag_out(w, f->d_diag_p[1], nc, f->d_sites, outs[2], p->n, s);
+    if (outs[1]) Kern<T>::diag_out(w, f->d_diag_p[0], nc, f->d_sites, outs[1], p->n, f->dt, s);
+    if (outs[2]) Kern<T>::diag_out(w, f->d_diag_p[1], nc, f->d_sites, outs[2], p->n, f->dt, s);
   }
   ND_CUDA(cudaGetLastError());
   return ND_OK;
@@ -482,7 +513,7 @@ extern "C" nd_status nd_certificate(nd_fact* f, double* cert, void* stream) {
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
   CertArgs a{};
   a.n = p->n;
-  a.cptr = f->d_cert_ptr;
+  a.cptr = p->n_virtual > 0 ? nullptr : f->d_cert_ptr;
   a.terms = f->d_cert_terms;
   a.owner = f->d_owner;
   a.pos = f->d_pos;
@@ -519,8 +550,8 @@ extern "C" nd_status nd_profile(nd_fact* f, int32_t enable, nd_kernel_stats* sta
   int cnt = 0;
   if (stats && max_stats > 0) {
     ND_CUDA(cudaDeviceSynchronize());
-    static const char* names[] = {"inverse", "gemm", "scatter", "gather_sym", "gather_skew",
-                                  "zero", "nph", "gather_anc", "scatter_rows", "colgather"};
+    static const char* names[] = {"inverse",    "gemm",         "scatter",   "gather_sym", "gather_skew", "zero",
+                                  "nph",        "gather_anc",   "scatter_rows", "colgather", "delay",     "loc"};
     const int nk = int(sizeof(names) / sizeof(names[0]));
     std::vector<nd_kernel_stats> acc(nk);
     for (int k = 0; k < nk; ++k) {

@@ -21,19 +21,26 @@ struct Cluster {
   int parent = -1;    // -1 = root
   int slot = 0;       // index of this cluster among its parent's children
   int first_desc = 0; // postorder index of the first cluster of its subtree
-  int n = 0, b = 0;   // |I_i|, |B_i|
-  std::vector<int> I; // interior sites (caller order ids); contact sites first
-  std::vector<int> B; // boundary sites: ancestor sites coupled to I_i after folding
+  int n = 0, b = 0;   // rows eliminated here, size of the boundary B_i
+  // Delayed pivots (nd_opts.delay): k rows of the front are not eliminated
+  // here but passed on to the parent, where they are the k "virtual" unknowns
+  // starting at front row dslot.  Which k rows are delayed is decided per
+  // energy (k_delay); the front then holds the eliminated rows first.  The
+  // front has n + k rows: n_own own sites, then the children's virtual rows.
+  int k = 0, n_own = 0, dslot = -1;
+  int nf() const { return n + k; }
+  std::vector<int> I; // front rows: own sites (caller ids, contact sites first), then virtual ids (>= n_sites)
+  std::vector<int> B; // boundary: own virtual ids (k, in the parent), then ancestor sites coupled after folding
   std::vector<int> map; // B[k] -> position in the parent's front [I_p ; B_p]
   std::vector<std::pair<int, int>> contacts; // (contact id, first row in I)
   std::vector<int> children;
   bool nactive = false; // the subtree holds a contact (N of Sec. 3.2 nonzero without phonons)
   int A = 0;            // number of sites of all ancestors (columns of the extended blocks)
   // per-energy workspace regions, offsets in complex elements
-  int64_t off_F = 0;    // n x (n+b): [A_ii | A_iB] folded front; A_ii^{-1} after the fold
+  int64_t off_F = 0;    // (n+k) x (n+b): [A_ii | A_iB] folded front; A_ii^{-1} after the fold
   int64_t off_Psi = 0;  // n x b   : Psi_i = -A_ii^{-1} A_iB
   int64_t off_BB = 0;   // b x b   : Schur update accumulator, then G_BB
-  int64_t off_G = 0;    // n x (n+b): [G_II | G_IB]
+  int64_t off_G = 0;    // n x (n+b): [G_II | G_IB]; (n+k) x (n+b) scratch of k_delay during the fold
   int64_t off_PBB[2] = {0, 0}; // b x b: P_BB for Sigma^< (0) and Sigma^> (1)
   int64_t off_P[2] = {0, 0};   // n x (n+b): [P_II | P_IB]
   // G^< workspace of clusters whose row block of N is nonzero, per variant
@@ -51,7 +58,8 @@ struct Cluster {
 // ---- device descriptors (plain structs, copied to the GPU) -----------------
 struct AssembleDesc {
   int64_t off_F, off_BB;
-  int32_t n, b, ld;          // ld = n + b
+  int32_t n, b, ld;          // n = front rows, b = boundary, ld = row length of F
+  int32_t n_own;             // rows with a site of their own (the rest are virtual)
   int32_t ent_begin, ent_end; // range in the assembly entry list
   int32_t site_begin;        // range [site_begin, site_begin+n) of the site list
   int32_t c0, m0, soff0;     // first contact: row offset, size, offset in packed Sigma (elements)
@@ -82,10 +90,11 @@ static constexpr int64_t AUX_BIT = int64_t(1) << 62;
 // (rows in I_p -> front [n_p x (n_p+b_p)], rows and columns in B_p -> BB).
 struct ScatterDesc {
   int64_t off_src;   // child's b x b block
-  int64_t off_front; // parent's n_p x (n_p + b_p) front
+  int64_t off_front; // parent's front, rows of length n_p + b_p
   int64_t off_bb;    // parent's b_p x b_p block
   int32_t b, n_p, b_p;
   int32_t map_begin; // child's map in the map array
+  int32_t k_p;       // parent's delayed rows: front rows are map positions < n_p + k_p
 };
 
 // Gather of a child's G_BB (or P_BB) from its parent's front.
@@ -95,6 +104,7 @@ struct GatherDesc {
   int64_t off_bb;    // parent's X_BB
   int32_t b, n_p, b_p;
   int32_t map_begin;
+  int32_t k_p, sb_p; // parent's delayed rows and first unknown (per-energy row order)
 };
 
 struct DiagDesc {
@@ -116,8 +126,8 @@ struct NPhDesc {     // N_{I,Y} = diag(ph) conj([G_II | G_{I,anc}]) for one clus
 struct AncGatherDesc {
   int64_t off_dst;   // b x A
   int32_t b, A;
-  int32_t bsite_begin;   // B_i sites in the site-id array
-  int32_t anc_begin;     // ancestor sites in the site-id array
+  int32_t bsite_begin;   // B_i unknowns in the unknown-id array
+  int32_t anc_begin;     // ancestor columns (cluster, row) in the anc arrays
 };
 
 // Rows of a child's fold update C (b x A_c, columns = Y_parent) into the
@@ -126,6 +136,24 @@ struct RowScatterDesc {
   int64_t off_src, off_nx, off_nb;
   int32_t b, A_c, n_p, A_p;
   int32_t map_begin;
+  int32_t k_p, sb_p; // parent's delayed rows and first unknown (per-energy row order)
+};
+
+// Delayed-pivot selection of one cluster (k_delay): front F with nf = n + k
+// rows of length ld, boundary accumulator BB (bb x bb, bb = b), scratch S in
+// the G region; unknowns [sb, sb + nf) of the cluster, the parent's virtual
+// rows of this cluster start at unknown sb_p + dslot.
+struct DelayDesc {
+  int64_t off_F, off_BB, off_S;
+  int32_t nf, k, ld, bb;
+  int32_t sb, sb_p, dslot;
+};
+
+// Final position of every front row after the delayed pivots (k_loc).
+struct LocDesc {
+  int32_t sb, nf, n;  // first unknown, front rows, rows eliminated here
+  int32_t cluster;
+  int32_t sb_p, dslot; // parent's first unknown and this cluster's virtual rows there
 };
 
 // P_{I,F}[:, j] = PX[:, cmap[j]] (columns I_i then B_i picked out of Y_i).
@@ -133,6 +161,7 @@ struct ColGatherDesc {
   int64_t off_P, off_PX;
   int32_t n, b, A;
   int32_t cmap_begin;
+  int32_t bsite_begin;   // B_i unknowns (used with per-energy positions)
 };
 
 struct ZeroDesc {
@@ -152,6 +181,8 @@ enum StepKind : int32_t {
   ST_GATHER_ANC = 7,
   ST_SCATTER_ROWS = 8,
   ST_COLGATHER = 9,
+  ST_DELAY = 10,
+  ST_LOC = 11,
 };
 
 struct Step {
@@ -171,14 +202,18 @@ struct nd_plan {
   std::vector<int32_t> contact_ptr, contact_idx;
   std::vector<ndgf::Cluster> cl;  // postorder
   int32_t n_levels = 0, n_roots = 0, max_n = 0, max_b = 0;
-  std::vector<int32_t> owner, pos; // owning cluster and position in its I, per site
+  std::vector<int32_t> owner, pos; // owning cluster and front row, per site and per virtual id
+  int32_t delay = 0;               // nd_opts.delay
+  int32_t n_virtual = 0;           // virtual unknowns (delayed rows), ids n .. n + n_virtual - 1
+  int64_t n_unk = 0;               // front rows of all clusters (n + n_virtual)
   int64_t arena_elems = 0;         // complex elements per energy (base regions)
   int64_t ext_elems[2] = {0, 0};   // extra elements of the G^< blocks, per variant
   int64_t sigma_elems = 0;         // sum_c m_c^2
   double flops_factor = 0, flops_green_r = 0, flops_green_lesser = 0;
 
   // device-independent descriptor tables (uploaded by nd_fact_create)
-  std::vector<int32_t> sites;        // concatenated I lists (caller ids)
+  std::vector<int32_t> sites;        // concatenated front-row lists (caller ids; virtual ids >= n)
+  std::vector<int32_t> unk_q, unk_r; // per unknown: cluster and front row (static order)
   std::vector<int32_t> maps;         // concatenated child maps
   std::vector<int32_t> ent_dst;      // assembly: destination offset within off_F region
   std::vector<int32_t> ent_src;      // assembly: CSR value index
@@ -193,7 +228,10 @@ struct nd_plan {
   std::vector<ndgf::AncGatherDesc> anc_desc;
   std::vector<ndgf::RowScatterDesc> rows_desc;
   std::vector<ndgf::ColGatherDesc> colg_desc;
-  std::vector<int32_t> site_ids;   // B lists and ancestor lists (caller ids)
+  std::vector<ndgf::DelayDesc> delay_desc;
+  std::vector<ndgf::LocDesc> loc_desc;
+  std::vector<int32_t> site_ids;   // B lists as unknown ids (sb of the owner + front row)
+  std::vector<int32_t> anc_q, anc_r; // ancestor columns: (cluster, eliminated row)
   std::vector<int32_t> cmaps;      // column maps of ColGatherDesc
   // per-cluster tables for the G lookup of AncGatherDesc (variant v = 0, 1)
   std::vector<int32_t> cl_n, cl_A, cl_ldG;

@@ -33,7 +33,7 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
                            const int32_t* __restrict__ ent_dst, const int32_t* __restrict__ ent_src,
                            const int32_t* __restrict__ sites, const double* __restrict__ H,
                            const double* __restrict__ energies, double eta, const double2* __restrict__ sigma_r,
-                           int64_t sigma_stride, const double2* __restrict__ ph_r, int n) {
+                           int64_t sigma_stride, const double2* __restrict__ ph_r, int n, DelayTabs dt) {
   const AssembleDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   cx<T>* F = arena + int64_t(e) * se + d.off_F;
@@ -45,8 +45,13 @@ __global__ void k_assemble(const AssembleDesc* __restrict__ descs, cx<T>* arena,
   for (int i = d.ent_begin + threadIdx.x; i < d.ent_end; i += blockDim.x)
     F[ent_dst[i]] = O<T>::from_d2(make_double2(-H[ent_src[i]], 0.0));
   __syncthreads();
+  if (dt.iperm) {  // static row order and sites; virtual rows get their site from the child
+    for (int r = threadIdx.x; r < d.n; r += blockDim.x) dt.iperm[int64_t(e) * dt.n_unk + d.site_begin + r] = r;
+    for (int r = threadIdx.x; r < d.n_own; r += blockDim.x)
+      dt.rsite[int64_t(e) * dt.n_unk + d.site_begin + r] = sites[d.site_begin + r];
+  }
   const double E = energies[e];
-  for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
+  for (int r = threadIdx.x; r < d.n_own; r += blockDim.x) {
     double2 z = make_double2(E, eta);
     if (ph_r) {
       const double2 p = ph_r[int64_t(e) * n + sites[d.site_begin + r]];
@@ -222,6 +227,172 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Delayed pivots (an extension of the paper's fold; paper Sec. 3.2 eliminates
+// every interior row of a cluster at the cluster).  The k rows of the front
+// that are handed to the parent are chosen on X = (interior block)^{-1},
+// computed in complex64: repeatedly the row j with the largest |X_jj|, after
+// which X is replaced by the inverse of the block without row and column j,
+// X <- X - X[:, j] X[j, :] / X_jj.  A large X_jj means that eliminating the
+// other rows first leaves a small pivot 1 / X_jj for row j, so the chosen rows
+// are the near-singular directions of the block.  The front is then reordered
+// (eliminated rows first, in their previous order, then the chosen rows), the
+// per-energy row tables follow, and the chosen rows' own couplings
+// [A_DD | A_DB] go to the boundary accumulator, whose first k rows and columns
+// are the parent's virtual rows of this cluster.  One CTA per (cluster, energy).
+template <typename T>
+__global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64_t se, DelayTabs dt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_sel, s_nsing;
+  const DelayDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  const int nf = d.nf, k = d.k, m = nf - k, ld = d.ld, bb = d.bb;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+  cx<T>* base = arena + int64_t(e) * se;
+  cx<T>* F = base + d.off_F;
+  cx<T>* BB = base + d.off_BB;
+  cx<T>* S = base + d.off_S;
+  float2* X = reinterpret_cast<float2*>(S);  // nf x nf complex64 inside the nf x ld scratch
+  const size_t o1 = (size_t(nf) * sizeof(int) + 15) & ~size_t(15);
+  int* piv = reinterpret_cast<int*>(smem);
+  float2* colk = reinterpret_cast<float2*>(smem + o1);
+  int* perm = reinterpret_cast<int*>(smem + o1 + size_t(nf) * sizeof(float2));
+  int* rs = perm + nf;
+  int* alive = rs + nf;
+  const int64_t nn = int64_t(nf) * nf;
+  for (int64_t i = tid; i < nn; i += nt) {
+    const double2 v = O<T>::to_d2(F[(i / nf) * ld + (i % nf)]);
+    X[i] = make_float2(float(v.x), float(v.y));
+  }
+  for (int i = tid; i < nf; i += nt) alive[i] = 1;
+  if (tid == 0) s_nsing = 0;
+  __syncthreads();
+  gj_invert<float>(X, nf, nf, piv, colk, &s_nsing);
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    float bv = -1.f;
+    int bi = nf;
+    for (int j = tid; j < nf; j += nt)
+      if (alive[j]) {
+        const float2 x = X[int64_t(j) * nf + j];
+        const float v = x.x * x.x + x.y * x.y;
+        if (v > bv) {  // j increases along a thread's loop: ties keep the smaller index
+          bv = v;
+          bi = j;
+        }
+      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ov > bv || (ov == bv && oi < bi)) {
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_i[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float v = red_v[0];
+      int p = red_i[0];
+      for (int w = 1; w < nw; ++w)
+        if (red_v[w] > v || (red_v[w] == v && red_i[w] < p)) {
+          v = red_v[w];
+          p = red_i[w];
+        }
+      if (p >= nf)  // no comparable value (NaN): take the first remaining row
+        for (p = 0; p < nf && !alive[p]; ++p) {
+        }
+      s_sel = p;
+      alive[p] = 0;
+      perm[m + t] = p;
+    }
+    __syncthreads();
+    const int j = s_sel;
+    const float2 pj = X[int64_t(j) * nf + j];
+    const float den = pj.x * pj.x + pj.y * pj.y;
+    if (den > 0.f) {
+      const float2 inv = make_float2(pj.x / den, -pj.y / den);
+      for (int64_t i = tid; i < nn; i += nt) {
+        const int a = int(i / nf), b = int(i % nf);
+        if (!alive[a] || !alive[b]) continue;
+        const float2 xa = X[int64_t(a) * nf + j], xb = X[int64_t(j) * nf + b];
+        const float2 q = make_float2(xa.x * inv.x - xa.y * inv.y, xa.x * inv.y + xa.y * inv.x);
+        X[i] = make_float2(X[i].x - (q.x * xb.x - q.y * xb.y), X[i].y - (q.x * xb.y + q.y * xb.x));
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int q = 0;
+    for (int j = 0; j < nf; ++j)
+      if (alive[j]) perm[q++] = j;
+  }
+  __syncthreads();
+  int32_t* ip = dt.iperm + int64_t(e) * dt.n_unk + d.sb;
+  int32_t* rsite = dt.rsite + int64_t(e) * dt.n_unk + d.sb;
+  for (int r = tid; r < nf; r += nt) {
+    ip[perm[r]] = r;
+    rs[r] = rsite[perm[r]];
+  }
+  __syncthreads();
+  for (int r = tid; r < nf; r += nt) rsite[r] = rs[r];
+  for (int j = tid; j < k; j += nt) dt.rsite[int64_t(e) * dt.n_unk + d.sb_p + d.dslot + j] = rs[m + j];
+  const int64_t nfl = int64_t(nf) * ld;
+  for (int64_t i = tid; i < nfl; i += nt) {
+    const int r = int(i / ld), c = int(i % ld);
+    S[i] = F[int64_t(perm[r]) * ld + (c < nf ? perm[c] : c)];
+  }
+  __syncthreads();
+  for (int64_t i = tid; i < nfl; i += nt) F[i] = S[i];
+  __syncthreads();
+  for (int i = tid; i < k * bb; i += nt) {
+    const int a = i / bb, c = i % bb;
+    BB[int64_t(a) * bb + c] = F[int64_t(m + a) * ld + m + c];
+  }
+  for (int i = tid; i < (bb - k) * k; i += nt) {
+    const int a = i / k, c = i % k;
+    BB[int64_t(k + a) * bb + c] = F[int64_t(m + c) * ld + m + k + a];
+  }
+}
+
+// Final cluster and row of every front row of one cluster (top down: a
+// delayed row takes the final position of the parent's virtual row).
+__global__ void k_loc(const LocDesc* __restrict__ descs, DelayTabs dt) {
+  const LocDesc d = descs[blockIdx.x];
+  const int64_t eb = int64_t(blockIdx.y) * dt.n_unk;
+  for (int s = threadIdx.x; s < d.nf; s += blockDim.x) {
+    const int r = dt.iperm[eb + d.sb + s];
+    int q = d.cluster, row = r;
+    if (r >= d.n) {
+      const int64_t u = eb + d.sb_p + d.dslot + (r - d.n);
+      q = dt.locq[u];
+      row = dt.locr[u];
+    }
+    dt.locq[eb + d.sb + s] = q;
+    dt.locr[eb + d.sb + s] = row;
+  }
+}
+
+__global__ void k_cert_off(double* cert, int n_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_e * 4) cert[(i / 4) * 8 + (i % 4)] = -1.0;
+}
+
+void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s) {
+  if (count <= 0 || n_e <= 0) return;
+  k_loc<<<dim3(count, n_e), 128, 0, s>>>(d, dt);
+}
+
+void launch_cert_off(double* cert, int n_e, cudaStream_t s) {
+  if (n_e <= 0) return;
+  k_cert_off<<<(n_e * 4 + 127) / 128, 128, 0, s>>>(cert, n_e);
+}
+
 // Extend-add of a child's update into its parent's front.  Entries whose row
 // is a boundary site of the parent and whose column is interior to it are
 // dropped: the front stores [X_II | X_IB] and X_BB only.
@@ -234,16 +405,16 @@ __global__ void k_scatter(const ScatterDesc* __restrict__ descs, cx<T>* arena, i
   cx<T>* front = base + d.off_front;
   cx<T>* bb = base + d.off_bb;
   const int32_t* map = maps + d.map_begin;
-  const int ldp = d.n_p + d.b_p;
+  const int ldp = d.n_p + d.b_p, nfp = d.n_p + d.k_p;  // front rows of the parent: positions < nfp
   const int64_t nb = int64_t(d.b) * d.b;
   for (int64_t idx = threadIdx.x; idx < nb; idx += blockDim.x) {
     const int r = int(idx / d.b), s = int(idx % d.b);
     const int pr = map[r], ps = map[s];
     const cx<T> v = src[idx];
-    if (pr < d.n_p) {
+    if (pr < nfp) {
       cx<T>& f = front[int64_t(pr) * ldp + ps];
       f = O<T>::add(f, v);
-    } else if (ps >= d.n_p) {
+    } else if (ps >= nfp) {
       cx<T>& f = bb[int64_t(pr - d.n_p) * d.b_p + (ps - d.n_p)];
       f = O<T>::add(f, v);
     }
@@ -252,11 +423,15 @@ __global__ void k_scatter(const ScatterDesc* __restrict__ descs, cx<T>* arena, i
 
 // Gather of X_BB for a child from the parent's [X_II | X_IB] and X_BB; the
 // parent's X_BI is X_IB^T (G^r, complex symmetric) or -X_IB^dagger (G^<, G^>).
+// With delayed pivots the parent's rows are in its per-energy order: a static
+// front position is translated through the parent's iperm first.
 template <typename T>
 __global__ void k_gather(const GatherDesc* __restrict__ descs, cx<T>* arena, int64_t se,
-                         const int32_t* __restrict__ maps, int skew) {
+                         const int32_t* __restrict__ maps, int skew, DelayTabs dt) {
   const GatherDesc d = descs[blockIdx.x];
   cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const int32_t* ip = dt.iperm ? dt.iperm + int64_t(blockIdx.y) * dt.n_unk + d.sb_p : nullptr;
+  const int nfp = d.n_p + d.k_p;
   cx<T>* dst = base + d.off_dst;
   const cx<T>* front = base + d.off_front;
   const cx<T>* bb = base + d.off_bb;
@@ -265,7 +440,11 @@ __global__ void k_gather(const GatherDesc* __restrict__ descs, cx<T>* arena, int
   const int64_t nb = int64_t(d.b) * d.b;
   for (int64_t idx = threadIdx.x; idx < nb; idx += blockDim.x) {
     const int r = int(idx / d.b), s = int(idx % d.b);
-    const int pr = map[r], ps = map[s];
+    int pr = map[r], ps = map[s];
+    if (ip) {
+      if (pr < nfp) pr = ip[pr];
+      if (ps < nfp) ps = ip[ps];
+    }
     cx<T> v;
     if (pr < d.n_p) {
       v = front[int64_t(pr) * ldp + ps];
@@ -290,7 +469,7 @@ __global__ void k_zero(const ZeroDesc* __restrict__ descs, cx<T>* arena, int64_t
 // N_{I,Y} = diag(Sigma_ph) conj([G_II | G_{I,anc}])  (paper Sec. 3.2, first G^< step)
 template <typename T>
 __global__ void k_nph(const NPhDesc* __restrict__ descs, cx<T>* arena, int64_t se, const int32_t* __restrict__ sites,
-                      const double2* __restrict__ ph_l, const double2* __restrict__ ph_g, int n) {
+                      const double2* __restrict__ ph_l, const double2* __restrict__ ph_g, int n, DelayTabs dt) {
   const NPhDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   cx<T>* base = arena + int64_t(e) * se;
@@ -302,37 +481,47 @@ __global__ void k_nph(const NPhDesc* __restrict__ descs, cx<T>* arena, int64_t s
   const int64_t tot = int64_t(d.n) * w;
   for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int r = int(idx / w), j = int(idx % w);
-    const double2 s = ph[sites[d.site_begin + r]];
+    const int site = dt.rsite ? dt.rsite[int64_t(e) * dt.n_unk + d.site_begin + r] : sites[d.site_begin + r];
+    const double2 s = ph[site];
     const cx<T> g = j < d.n ? G[int64_t(r) * d.ldG + j] : GX[int64_t(r) * d.A + (j - d.n)];
     N[idx] = O<T>::mul(O<T>::from_d2(s), O<T>::conj(g));
   }
 }
 
 // G_{B_i, anc(i)} from the G_II and G_{I,anc} blocks of the ancestors: the
-// entry between sites x and y is stored by the lower of their two clusters
-// (G^r is complex symmetric); the column of a site y (owner o) inside the
-// ancestor columns of cluster q is A_q - n_o - A_o + pos(y).
+// entry between unknowns x and y is stored by the lower of the two clusters
+// that eliminate them (G^r is complex symmetric); the column of an unknown
+// eliminated as row p of cluster o inside the ancestor columns of cluster q
+// is A_q - n_o - A_o + p.  Ancestor column j is row anc_r[j] of cluster
+// anc_q[j]; a boundary unknown's cluster and row are static, or per energy
+// with delayed pivots.
 template <typename T>
-__global__ void k_gather_anc(const AncGatherDesc* __restrict__ descs, cx<T>* arena, int64_t se,
-                             const int32_t* __restrict__ site_ids, const int32_t* __restrict__ owner,
-                             const int32_t* __restrict__ pos, const int32_t* __restrict__ cl_n,
-                             const int32_t* __restrict__ cl_A, const int32_t* __restrict__ cl_ldG,
-                             const int64_t* __restrict__ cl_offG, const int64_t* __restrict__ cl_offGX) {
+__global__ void k_gather_anc(const AncGatherDesc* __restrict__ descs, cx<T>* arena, int64_t se, AncTables t,
+                             DelayTabs dt) {
   const AncGatherDesc d = descs[blockIdx.x];
-  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const int e = blockIdx.y;
+  cx<T>* base = arena + int64_t(e) * se;
   cx<T>* dst = base + d.off_dst;
   const int64_t tot = int64_t(d.b) * d.A;
   for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int r = int(idx / d.A), j = int(idx % d.A);
-    const int x = site_ids[d.bsite_begin + r], y = site_ids[d.anc_begin + j];
-    const int qx = owner[x], qy = owner[y];
+    const int u = t.site_ids[d.bsite_begin + r];
+    int qx, px;
+    if (dt.locq) {
+      qx = dt.locq[int64_t(e) * dt.n_unk + u];
+      px = dt.locr[int64_t(e) * dt.n_unk + u];
+    } else {
+      qx = t.unk_q[u];
+      px = t.unk_r[u];
+    }
+    const int qy = t.anc_q[d.anc_begin + j], py = t.anc_r[d.anc_begin + j];
     int64_t src;
     if (qx == qy)
-      src = cl_offG[qx] + int64_t(pos[x]) * cl_ldG[qx] + pos[y];
+      src = t.cl_offG[qx] + int64_t(px) * t.cl_ldG[qx] + py;
     else if (qx < qy)
-      src = cl_offGX[qx] + int64_t(pos[x]) * cl_A[qx] + (cl_A[qx] - cl_n[qy] - cl_A[qy] + pos[y]);
+      src = t.cl_offGX[qx] + int64_t(px) * t.cl_A[qx] + (t.cl_A[qx] - t.cl_n[qy] - t.cl_A[qy] + py);
     else
-      src = cl_offGX[qy] + int64_t(pos[y]) * cl_A[qy] + (cl_A[qy] - cl_n[qx] - cl_A[qx] + pos[x]);
+      src = t.cl_offGX[qy] + int64_t(py) * t.cl_A[qy] + (t.cl_A[qy] - t.cl_n[qx] - t.cl_A[qx] + px);
     dst[idx] = base[src];
   }
 }
@@ -342,9 +531,11 @@ __global__ void k_gather_anc(const AncGatherDesc* __restrict__ descs, cx<T>* are
 // N_{B_p, anc(p)} (columns of I_p there are dead lower blocks and dropped).
 template <typename T>
 __global__ void k_scatter_rows(const RowScatterDesc* __restrict__ descs, cx<T>* arena, int64_t se,
-                               const int32_t* __restrict__ maps) {
+                               const int32_t* __restrict__ maps, DelayTabs dt) {
   const RowScatterDesc d = descs[blockIdx.x];
   cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const int32_t* ip = dt.iperm ? dt.iperm + int64_t(blockIdx.y) * dt.n_unk + d.sb_p : nullptr;
+  const int nfp = d.n_p + d.k_p;
   const cx<T>* src = base + d.off_src;
   cx<T>* nx = base + d.off_nx;
   cx<T>* nb = base + d.off_nb;
@@ -352,7 +543,8 @@ __global__ void k_scatter_rows(const RowScatterDesc* __restrict__ descs, cx<T>* 
   const int64_t tot = int64_t(d.b) * d.A_c;
   for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int r = int(idx / d.A_c), j = int(idx % d.A_c);
-    const int pr = map[r];
+    int pr = map[r];
+    if (ip && pr < nfp) pr = ip[pr];
     const cx<T> v = src[idx];
     if (pr < d.n_p) {
       cx<T>& f = nx[int64_t(pr) * d.A_c + j];
@@ -367,28 +559,39 @@ __global__ void k_scatter_rows(const RowScatterDesc* __restrict__ descs, cx<T>* 
 // [P_II | P_IB] = columns I_i and B_i of A_ii^{-1} N_{I,Y}.
 template <typename T>
 __global__ void k_colgather(const ColGatherDesc* __restrict__ descs, cx<T>* arena, int64_t se,
-                            const int32_t* __restrict__ cmaps) {
+                            const int32_t* __restrict__ cmaps, AncTables t, DelayTabs dt) {
   const ColGatherDesc d = descs[blockIdx.x];
-  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const int e = blockIdx.y;
+  cx<T>* base = arena + int64_t(e) * se;
   cx<T>* P = base + d.off_P;
   const cx<T>* PX = base + d.off_PX;
   const int w = d.n + d.b, wx = d.n + d.A;
   const int64_t tot = int64_t(d.n) * w;
   for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int r = int(idx / w), j = int(idx % w);
-    const int col = j < d.n ? j : cmaps[d.cmap_begin + j - d.n];
+    int col = j;
+    if (j >= d.n) {
+      if (dt.locq) {  // boundary unknown: eliminated as row p of ancestor q
+        const int u = t.site_ids[d.bsite_begin + j - d.n];
+        const int q = dt.locq[int64_t(e) * dt.n_unk + u], pq = dt.locr[int64_t(e) * dt.n_unk + u];
+        col = d.n + d.A - t.cl_n[q] - t.cl_A[q] + pq;
+      } else {
+        col = cmaps[d.cmap_begin + j - d.n];
+      }
+    }
     P[idx] = PX[int64_t(r) * wx + col];
   }
 }
 
 template <typename T>
 __global__ void k_diag_out(const DiagDesc* __restrict__ descs, const cx<T>* arena, int64_t se,
-                           const int32_t* __restrict__ sites, double2* out, int n) {
+                           const int32_t* __restrict__ sites, double2* out, int n, DelayTabs dt) {
   const DiagDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   const cx<T>* X = arena + int64_t(e) * se + d.off;
   for (int r = threadIdx.x; r < d.n; r += blockDim.x) {
-    out[int64_t(e) * n + sites[d.site_begin + r]] = O<T>::to_d2(X[int64_t(r) * d.ld + r]);
+    const int site = dt.rsite ? dt.rsite[int64_t(e) * dt.n_unk + d.site_begin + r] : sites[d.site_begin + r];
+    out[int64_t(e) * n + site] = O<T>::to_d2(X[int64_t(r) * d.ld + r]);
   }
 }
 
@@ -527,10 +730,20 @@ template <typename T> int Kern<T>::gemm_tile() { return GemmCfg<T>::BM; }
 template <typename T>
 void Kern<T>::assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst, const int32_t* ent_src,
                        const int32_t* sites, const double* H, const double* energies, double eta,
-                       const double* sigma_r, int64_t sigma_stride, const double* ph_r, int n, cudaStream_t s) {
+                       const double* sigma_r, int64_t sigma_stride, const double* ph_r, int n,
+                       const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
   k_assemble<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, ent_dst, ent_src, sites, H, energies, eta,
-                                                    (const double2*)sigma_r, sigma_stride, (const double2*)ph_r, n);
+                                                    (const double2*)sigma_r, sigma_stride, (const double2*)ph_r, n, dt);
+}
+
+template <typename T>
+void Kern<T>::delay(const Work& w, const DelayDesc* d, int count, int max_nf, const DelayTabs& dt, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  const size_t shm = ((size_t(max_nf) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_nf) * sizeof(float2) +
+                     size_t(3) * max_nf * sizeof(int);
+  if (shm > 48 * 1024) cudaFuncSetAttribute(k_delay<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
+  k_delay<T><<<dim3(count, w.n_e), 256, shm, s>>>(d, (cx<T>*)w.arena, w.se, dt);
 }
 
 template <typename T>
@@ -565,9 +778,10 @@ void Kern<T>::scatter(const Work& w, const ScatterDesc* d, int count, const int3
 }
 
 template <typename T>
-void Kern<T>::gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew, cudaStream_t s) {
+void Kern<T>::gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew,
+                     const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  k_gather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps, skew ? 1 : 0);
+  k_gather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps, skew ? 1 : 0, dt);
 }
 
 template <typename T>
@@ -578,36 +792,38 @@ void Kern<T>::zero(const Work& w, const ZeroDesc* d, int count, cudaStream_t s) 
 
 template <typename T>
 void Kern<T>::nph(const Work& w, const NPhDesc* d, int count, const int32_t* sites, const double* ph_l,
-                  const double* ph_g, int n, cudaStream_t s) {
+                  const double* ph_g, int n, const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
   k_nph<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, sites, (const double2*)ph_l,
-                                              (const double2*)ph_g, n);
+                                              (const double2*)ph_g, n, dt);
 }
 
 template <typename T>
-void Kern<T>::gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, cudaStream_t s) {
+void Kern<T>::gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, const DelayTabs& dt,
+                         cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  k_gather_anc<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, t.site_ids, t.owner, t.pos, t.cl_n,
-                                                     t.cl_A, t.cl_ldG, t.cl_offG, t.cl_offGX);
+  k_gather_anc<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, t, dt);
 }
 
 template <typename T>
-void Kern<T>::scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps, cudaStream_t s) {
+void Kern<T>::scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps,
+                           const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  k_scatter_rows<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps);
+  k_scatter_rows<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps, dt);
 }
 
 template <typename T>
-void Kern<T>::colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, cudaStream_t s) {
+void Kern<T>::colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, const AncTables& t,
+                        const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  k_colgather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, cmaps);
+  k_colgather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, cmaps, t, dt);
 }
 
 template <typename T>
 void Kern<T>::diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
-                       cudaStream_t s) {
+                       const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  k_diag_out<T><<<dim3(count, w.n_e), 128, 0, s>>>(d, (const cx<T>*)w.arena, w.se, sites, (double2*)out, n);
+  k_diag_out<T><<<dim3(count, w.n_e), 128, 0, s>>>(d, (const cx<T>*)w.arena, w.se, sites, (double2*)out, n, dt);
 }
 
 template <typename T>
@@ -626,6 +842,10 @@ void Kern<T>::certificate(const Work& w, const CertArgs& a, cudaStream_t s) {
   if (w.n_e <= 0 || a.n <= 0) return;
   if (a.n_psi > 0)
     k_absmax<T><<<dim3(a.n_psi, w.n_e), 256, 0, s>>>(a.psi, (const cx<T>*)w.arena, w.se, a.cert);
+  if (!a.cptr) {  // no residual terms (delayed pivots): entries 0..3 = -1
+    launch_cert_off(a.cert, w.n_e, s);
+    return;
+  }
   k_certificate<T><<<dim3((a.n + 255) / 256, w.n_e), 256, 0, s>>>(
       a.n, a.cptr, (const int4*)a.terms, a.owner, a.pos, a.offG, a.offP, a.ldG, (const cx<T>*)w.arena, w.se, a.H,
       (const double2*)a.sr, (const double2*)a.sl, a.sstride, (const double2*)a.ph_r, (const double2*)a.ph_l,

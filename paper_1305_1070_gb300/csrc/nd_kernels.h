@@ -17,9 +17,20 @@ struct Work {
   int n_e;
 };
 
-// Per-site and per-cluster tables read by the ancestor gather.
+// Per-energy row tables of the delayed pivots, [n_e][n_unk] each (all NULL
+// when the plan has no delayed rows: then every front row keeps its static
+// position and site).
+//   iperm: position of each static front row in its cluster's reordered front
+//   rsite: caller site of each row of a cluster's front in its current order
+//   locq, locr: cluster and eliminated row where each unknown ends up
+struct DelayTabs {
+  int32_t *iperm, *rsite, *locq, *locr;
+  int64_t n_unk;
+};
+
+// Per-unknown and per-cluster tables read by the ancestor gather.
 struct AncTables {
-  const int32_t *site_ids, *owner, *pos, *cl_n, *cl_A, *cl_ldG;
+  const int32_t *site_ids, *unk_q, *unk_r, *anc_q, *anc_r, *cl_n, *cl_A, *cl_ldG;
   const int64_t *cl_offG, *cl_offGX;
 };
 
@@ -41,27 +52,36 @@ struct Kern {
   static void assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst,
                        const int32_t* ent_src, const int32_t* sites, const double* H, const double* energies,
                        double eta, const double* sigma_r, int64_t sigma_stride, const double* ph_r, int n,
-                       cudaStream_t s);
+                       const DelayTabs& dt, cudaStream_t s);
+  static void delay(const Work& w, const DelayDesc* d, int count, int max_nf, const DelayTabs& dt, cudaStream_t s);
   static void inverse(const Work& w, const InvDesc* d, int count, int max_n, double* fp64_scratch,
                       int64_t scratch_stride, int* n_singular, cudaStream_t s);
   static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
   static void scatter(const Work& w, const ScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
   static void gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew,
-                     cudaStream_t s);
+                     const DelayTabs& dt, cudaStream_t s);
   static void zero(const Work& w, const ZeroDesc* d, int count, cudaStream_t s);
   static void nph(const Work& w, const NPhDesc* d, int count, const int32_t* sites, const double* ph_l,
-                  const double* ph_g, int n, cudaStream_t s);
-  static void gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, cudaStream_t s);
-  static void scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
-  static void colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, cudaStream_t s);
+                  const double* ph_g, int n, const DelayTabs& dt, cudaStream_t s);
+  static void gather_anc(const Work& w, const AncGatherDesc* d, int count, const AncTables& t, const DelayTabs& dt,
+                         cudaStream_t s);
+  static void scatter_rows(const Work& w, const RowScatterDesc* d, int count, const int32_t* maps,
+                           const DelayTabs& dt, cudaStream_t s);
+  static void colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, const AncTables& t,
+                        const DelayTabs& dt, cudaStream_t s);
   static void certificate(const Work& w, const CertArgs& a, cudaStream_t s);
   static void diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
-                       cudaStream_t s);
+                       const DelayTabs& dt, cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
                           cudaStream_t s);
   // tile edge (BM = BN) of the GEMM kernel of this precision
   static int gemm_tile();
 };
+
+// Final positions of the unknowns after the delayed pivots (one tree level).
+void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s);
+// Certificate entries 0..3 set to -1 (no residual terms with delayed pivots).
+void launch_cert_off(double* cert, int n_e, cudaStream_t s);
 
 // Per-energy complex128 workspace of launch_lead_decimation, in elements.
 size_t lead_decimation_work_elems(int m, int m_c);

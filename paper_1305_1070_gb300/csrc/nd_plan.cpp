@@ -267,6 +267,11 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
   d.leaf = (opts && opts->leaf_size > 0) ? opts->leaf_size : 64;
   d.split = (opts && opts->split_permille > 0) ? opts->split_permille : 500;
   d.slab = (opts && opts->slab > 0) ? opts->slab : 0;
+  plan->delay = opts ? opts->delay : 0;
+  if (plan->delay < 0 || plan->delay > 8) {
+    delete plan;
+    return fail(ND_ERR_INVALID_ARG, "nd_analyze: delay must be in 0..8");
+  }
   if (d.split < 100 || d.split > 900) {
     delete plan;
     return fail(ND_ERR_INVALID_ARG, "nd_analyze: split_permille must be in 100..900");
@@ -403,6 +408,7 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
     }
     c.I = I;
     c.n = int(I.size());
+    c.n_own = c.n;
     for (int k = 0; k < c.n; ++k) {
       plan->owner[I[k]] = i;
       plan->pos[I[k]] = k;
@@ -462,8 +468,39 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
         return fail(ND_ERR_INVALID_ARG, "nd_analyze: internal error (root with boundary)");
       }
     }
-    // maps into the parent's front [I_p ; B_p]
-    std::vector<int> posB(n, -1);
+    // Delayed pivots: in postorder (children first), every eligible cluster
+    // hands k of its front rows to its parent as virtual unknowns (ids n, n+1,
+    // ...), appended to the parent's front rows and put first in its own
+    // boundary.  They couple only to the cluster's boundary, which lies in
+    // the parent's front, so the boundary sets above stay valid.
+    if (plan->delay > 0) {
+      int nv = 0;
+      for (int i = 0; i < nn; ++i) {
+        Cluster& c = cl[i];
+        const int nfr = int(c.I.size());
+        const int k = (c.parent >= 0 && c.contacts.empty() && c.b > 0 && nfr >= 2) ? std::min(plan->delay, nfr - 1) : 0;
+        c.k = k;
+        c.n = nfr - k;
+        if (k == 0) continue;
+        Cluster& P = cl[c.parent];
+        c.dslot = int(P.I.size());
+        std::vector<int> Bn;
+        for (int j = 0; j < k; ++j) {
+          const int v = n + nv++;
+          plan->owner.push_back(c.parent);
+          plan->pos.push_back(int(P.I.size()));
+          P.I.push_back(v);
+          Bn.push_back(v);
+        }
+        Bn.insert(Bn.end(), c.B.begin(), c.B.end());
+        c.B = std::move(Bn);
+        c.b = int(c.B.size());
+      }
+      plan->n_virtual = nv;
+    }
+    // maps into the parent's front: front rows [0, n_p + k_p) in their static
+    // order, then the parent's boundary entries (positions n_p + index in B_p)
+    std::vector<int> posB(n + plan->n_virtual, -1);
     for (int p = 0; p < nn; ++p) {
       Cluster& P = cl[p];
       for (int k = 0; k < P.b; ++k) posB[P.B[k]] = k;
@@ -475,7 +512,7 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
           int m;
           if (plan->owner[u] == p) {
             m = plan->pos[u];
-          } else if (posB[u] >= 0 && P.B[posB[u]] == u) {
+          } else if (posB[u] >= P.k && P.B[posB[u]] == u) {
             m = P.n + posB[u];
           } else {
             delete plan;
@@ -496,15 +533,15 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
   double ff = 0, fg = 0, fl = 0;
   for (int i = 0; i < nn; ++i) {
     Cluster& c = cl[i];
-    const int64_t nI = c.n, b = c.b, F = nI * (nI + b);
+    const int64_t nI = c.n, b = c.b, F = nI * (nI + b), Ff = int64_t(c.nf()) * (nI + b);
     plan->n_levels = std::max(plan->n_levels, c.level);
-    plan->max_n = std::max(plan->max_n, c.n);
+    plan->max_n = std::max(plan->max_n, c.nf());
     plan->max_b = std::max(plan->max_b, c.b);
     if (c.parent < 0) plan->n_roots++;
-    c.off_F = off; off = align16(off + F);
+    c.off_F = off; off = align16(off + Ff);
     c.off_Psi = off; off = align16(off + nI * b);
     c.off_BB = off; off = align16(off + b * b);
-    c.off_G = off; off = align16(off + F);
+    c.off_G = off; off = align16(off + Ff);
     for (int s = 0; s < 2; ++s) {
       c.off_PBB[s] = off; off = align16(off + b * b);
       c.off_P[s] = off; off = align16(off + F);
@@ -578,7 +615,7 @@ extern "C" nd_status nd_plan_tree(const nd_plan* p, int32_t* level, int32_t* par
   for (size_t i = 0; i < p->cl.size(); ++i) {
     if (level) level[i] = p->cl[i].level;
     if (parent) parent[i] = p->cl[i].parent;
-    if (n_i) n_i[i] = p->cl[i].n;
+    if (n_i) n_i[i] = p->cl[i].nf();
     if (b_i) b_i[i] = p->cl[i].b;
   }
   if (cluster_of_site)
@@ -591,7 +628,7 @@ extern "C" nd_status nd_plan_cluster_sites(const nd_plan* p, int32_t c, int32_t*
   if (c < 0 || c >= int32_t(p->cl.size())) return fail(ND_ERR_INVALID_ARG, "nd_plan_cluster_sites: bad cluster");
   const Cluster& C = p->cl[c];
   std::copy(C.I.begin(), C.I.end(), sites);
-  std::copy(C.B.begin(), C.B.end(), sites + C.n);
+  std::copy(C.B.begin(), C.B.end(), sites + C.nf());
   return ND_OK;
 }
 

@@ -39,6 +39,8 @@ struct Builder {
       case ST_GATHER_ANC: st.begin = int32_t(p->anc_desc.size()); break;
       case ST_SCATTER_ROWS: st.begin = int32_t(p->rows_desc.size()); break;
       case ST_COLGATHER: st.begin = int32_t(p->colg_desc.size()); break;
+      case ST_DELAY: st.begin = int32_t(p->delay_desc.size()); break;
+      case ST_LOC: st.begin = int32_t(p->loc_desc.size()); break;
     }
   }
   void end() {
@@ -54,6 +56,8 @@ struct Builder {
       case ST_GATHER_ANC: e = int32_t(p->anc_desc.size()); break;
       case ST_SCATTER_ROWS: e = int32_t(p->rows_desc.size()); break;
       case ST_COLGATHER: e = int32_t(p->colg_desc.size()); break;
+      case ST_DELAY: e = int32_t(p->delay_desc.size()); break;
+      case ST_LOC: e = int32_t(p->loc_desc.size()); break;
     }
     st.count = e - st.begin;
     if (st.count > 0) cur->push_back(st);
@@ -80,12 +84,19 @@ void build_schedules(nd_plan* p) {
   auto& cl = p->cl;
   const int nc = int(cl.size());
   std::vector<int32_t> site_begin(nc), map_begin(nc);
+  p->unk_q.clear();
+  p->unk_r.clear();
   for (int i = 0; i < nc; ++i) {
     site_begin[i] = int32_t(p->sites.size());
     p->sites.insert(p->sites.end(), cl[i].I.begin(), cl[i].I.end());
+    for (int r = 0; r < cl[i].nf(); ++r) {
+      p->unk_q.push_back(i);
+      p->unk_r.push_back(r);
+    }
     map_begin[i] = int32_t(p->maps.size());
     p->maps.insert(p->maps.end(), cl[i].map.begin(), cl[i].map.end());
   }
+  p->n_unk = int64_t(p->sites.size());
   // contact offsets in the packed Sigma arrays
   std::vector<int32_t> soff(p->n_contacts + 1, 0);
   for (int c = 0; c < p->n_contacts; ++c) {
@@ -94,7 +105,7 @@ void build_schedules(nd_plan* p) {
   }
   // ---- S1 assembly lists ----------------------------------------------------
   {
-    std::vector<int> posB(p->n, -1);
+    std::vector<int> posB(p->n + p->n_virtual, -1);
     for (int i = 0; i < nc; ++i) {
       Cluster& c = cl[i];
       const int ld = c.n + c.b;
@@ -102,12 +113,13 @@ void build_schedules(nd_plan* p) {
       AssembleDesc a{};
       a.off_F = c.off_F;
       a.off_BB = c.off_BB;
-      a.n = c.n;
+      a.n = c.nf();
+      a.n_own = c.n_own;
       a.b = c.b;
       a.ld = ld;
       a.site_begin = site_begin[i];
       a.ent_begin = int32_t(p->ent_dst.size());
-      for (int r = 0; r < c.n; ++r) {
+      for (int r = 0; r < c.n_own; ++r) {
         const int v = c.I[r];
         for (int q = p->rowptr[v]; q < p->rowptr[v + 1]; ++q) {
           const int u = p->colind[q];
@@ -148,6 +160,15 @@ void build_schedules(nd_plan* p) {
   Builder B{p};
   // ---- S2/S3 fold: for l = 1..L, invert A_ii; Psi; Schur update; extend-add
   for (int l = 1; l <= p->n_levels; ++l) {
+    B.begin(&p->sched_factor, ST_DELAY);  // delayed pivots: choose, reorder the front
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.k == 0) continue;
+      p->delay_desc.push_back(DelayDesc{c.off_F, c.off_BB, c.off_G, c.nf(), c.k, c.n + c.b, c.b, site_begin[i],
+                                        site_begin[c.parent], c.dslot});
+      B.dim(c.nf());
+    }
+    B.end();
     B.begin(&p->sched_factor, ST_INVERSE);
     for (int i : lev[l]) {
       const Cluster& c = cl[i];
@@ -177,12 +198,25 @@ void build_schedules(nd_plan* p) {
         const Cluster& c = cl[i];
         if (c.b == 0 || c.slot != s) continue;
         const Cluster& P = cl[c.parent];
-        p->scat_desc.push_back(ScatterDesc{c.off_BB, P.off_F, P.off_BB, c.b, P.n, P.b, map_begin[i]});
+        p->scat_desc.push_back(ScatterDesc{c.off_BB, P.off_F, P.off_BB, c.b, P.n, P.b, map_begin[i], P.k});
         B.dim(c.b);
       }
       B.end();
     }
   }
+  // final position of every front row once all delayed pivots are chosen
+  // (top down: a delayed row ends where its parent's virtual row ends)
+  if (p->n_virtual > 0)
+    for (int l = p->n_levels; l >= 1; --l) {
+      B.begin(&p->sched_factor, ST_LOC);
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        p->loc_desc.push_back(LocDesc{site_begin[i], c.nf(), c.n, i, c.parent >= 0 ? site_begin[c.parent] : -1,
+                                      c.dslot});
+        B.dim(c.nf());
+      }
+      B.end();
+    }
   // ---- S4 G^r extraction -----------------------------------------------------
   B.begin(&p->sched_green, ST_GEMM);  // clusters without boundary: G_II = A_ii^{-1}
   for (int i = 0; i < nc; ++i) {
@@ -197,7 +231,8 @@ void build_schedules(nd_plan* p) {
       const Cluster& c = cl[i];
       if (c.b == 0) continue;
       const Cluster& P = cl[c.parent];
-      p->gath_desc.push_back(GatherDesc{c.off_BB, P.off_G, P.off_BB, c.b, P.n, P.b, map_begin[i]});
+      p->gath_desc.push_back(GatherDesc{c.off_BB, P.off_G, P.off_BB, c.b, P.n, P.b, map_begin[i], P.k,
+                                        site_begin[c.parent]});
       B.dim(c.b);
     }
     B.end();
@@ -232,9 +267,13 @@ void build_schedules(nd_plan* p) {
   for (int i = 0; i < nc; ++i) {
     const Cluster& c = cl[i];
     bsite_begin[i] = int32_t(p->site_ids.size());
-    p->site_ids.insert(p->site_ids.end(), c.B.begin(), c.B.end());
-    anc_begin[i] = int32_t(p->site_ids.size());
-    for (int a = c.parent; a >= 0; a = cl[a].parent) p->site_ids.insert(p->site_ids.end(), cl[a].I.begin(), cl[a].I.end());
+    for (int u : c.B) p->site_ids.push_back(site_begin[p->owner[u]] + p->pos[u]);
+    anc_begin[i] = int32_t(p->anc_q.size());
+    for (int a = c.parent; a >= 0; a = cl[a].parent)
+      for (int r = 0; r < cl[a].n; ++r) {
+        p->anc_q.push_back(a);
+        p->anc_r.push_back(r);
+      }
     cmap_begin[i] = int32_t(p->cmaps.size());
     for (int k = 0; k < c.b; ++k) {
       const int u = c.B[k], o = p->owner[u];
@@ -252,7 +291,7 @@ void build_schedules(nd_plan* p) {
   // ---- S9 certificate term lists --------------------------------------------
   for (int i = 0; i < nc; ++i)
     if (cl[i].b) p->psi_desc.push_back(ZeroDesc{cl[i].off_Psi, int64_t(cl[i].n) * cl[i].b});
-  {
+  if (p->n_virtual == 0) {  // with delayed pivots the positions are per energy: no residual terms
     std::unordered_map<int64_t, int32_t> posB;  // (cluster, site) -> index in B
     for (int i = 0; i < nc; ++i)
       for (int k = 0; k < cl[i].b; ++k) posB[int64_t(i) * p->n + cl[i].B[k]] = k;
@@ -383,7 +422,7 @@ void build_schedules(nd_plan* p) {
           const Cluster& P = cl[c.parent];
           for (int s = 0; s < 2; ++s)
             p->rows_desc.push_back(RowScatterDesc{c.ext[v].off_NB[s], P.ext[v].off_NX[s], P.ext[v].off_NB[s], c.b, c.A,
-                                                  P.n, P.A, map_begin[i]});
+                                                  P.n, P.A, map_begin[i], P.k, site_begin[c.parent]});
           B.dim(c.b);
         }
         B.end();
@@ -404,7 +443,8 @@ void build_schedules(nd_plan* p) {
       const Cluster& c = cl[i];
       if (!active(i)) continue;
       for (int s = 0; s < 2; ++s)
-        p->colg_desc.push_back(ColGatherDesc{c.off_P[s], c.ext[v].off_PX[s], c.n, c.b, c.A, cmap_begin[i]});
+        p->colg_desc.push_back(ColGatherDesc{c.off_P[s], c.ext[v].off_PX[s], c.n, c.b, c.A, cmap_begin[i],
+                                             bsite_begin[i]});
       B.dim(c.n + c.b);
     }
     B.end();
@@ -415,7 +455,8 @@ void build_schedules(nd_plan* p) {
         if (c.b == 0) continue;
         const Cluster& P = cl[c.parent];
         for (int s = 0; s < 2; ++s)
-          p->gath_desc.push_back(GatherDesc{c.off_PBB[s], P.off_P[s], P.off_PBB[s], c.b, P.n, P.b, map_begin[i]});
+          p->gath_desc.push_back(GatherDesc{c.off_PBB[s], P.off_P[s], P.off_PBB[s], c.b, P.n, P.b, map_begin[i], P.k,
+                                            site_begin[c.parent]});
         B.dim(c.b);
       }
       B.end();

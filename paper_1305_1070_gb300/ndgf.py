@@ -44,7 +44,7 @@ class nd_graph(ctypes.Structure):
 
 class nd_opts(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int32), ("split_permille", ctypes.c_int32), ("slab", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("delay", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class nd_kernel_stats(ctypes.Structure):
@@ -170,7 +170,7 @@ class Lead(_Handle):
 
 
 def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=None, leaf_size=0,
-               split_permille=0, slab=0) -> Plan:
+               split_permille=0, slab=0, delay=0) -> Plan:
     keep = []
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(colind, dtype=np.int32)
@@ -192,6 +192,7 @@ def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=Non
     o.leaf_size = leaf_size
     o.split_permille = split_permille
     o.slab = slab
+    o.delay = delay
     out = _P()
     _check(lib().nd_analyze(ctypes.byref(g), ctypes.byref(o), ctypes.byref(out)), "nd_analyze")
     return Plan(out.value)

@@ -15,13 +15,14 @@ from . import ndgf
 
 class Solver:
     def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
-                 leaf_size: int = 64, split_permille: int = 0, device: str = "cuda"):
+                 leaf_size: int = 64, split_permille: int = 0, delay: int = 0, device: str = "cuda"):
         self.dev, self.tr = dev, tr
         self.device = torch.device(device)
         self.n = dev.n
         cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])]).astype(np.int32)
         ci = np.concatenate(dev.contacts).astype(np.int32) if dev.contacts else np.zeros(0, np.int32)
-        self.plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, leaf_size, split_permille)
+        self.plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, leaf_size, split_permille,
+                                    delay=delay)
         self.info = ndgf.nd_plan_query(self.plan)
         self.m_c = [len(c) for c in dev.contacts]
         self.off = np.concatenate([[0], np.cumsum([m * m for m in self.m_c])]).astype(np.int64)

@@ -137,3 +137,56 @@ def test_flop_model_scaling():
         _, info, _, _ = _plan(dev, 64)
         f.append(info["flops_factor"] + info["flops_green_r"])
     assert 1.7 < f[1] / f[0] < 2.3 and 1.7 < f[2] / f[1] < 2.3
+
+
+def _plan_sets(dev, leaf, delay):
+    cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])]).astype(np.int32)
+    ci = np.concatenate(dev.contacts).astype(np.int32)
+    plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, leaf, 0, delay=delay)
+    tree = ndgf.nd_plan_tree(plan)
+    nc = len(tree["level"])
+    sets = [ndgf.nd_plan_cluster_sites(plan, c, tree["n_i"][c], tree["b_i"][c]) for c in range(nc)]
+    return tree, sets
+
+
+@pytest.mark.parametrize("L,W,leaf,delay", [(64, 16, 64, 2), (37, 11, 20, 3), (16, 3, 1, 1), (20, 20, 16, 8)])
+def test_delayed_pivot_structure(L, W, leaf, delay):
+    """Delayed rows are virtual unknowns (ids >= n): each sits in exactly one
+    front (the parent's) and first in exactly one boundary (its cluster's);
+    the rest of every boundary equals the plain plan's, and every boundary
+    entry lies in the parent's front or boundary (the extend-add target)."""
+    dev = workloads.superlattice(L, W, disorder=0.02, seed=L)
+    t0, s0 = _plan_sets(dev, leaf, 0)
+    t1, s1 = _plan_sets(dev, leaf, delay)
+    parent = t1["parent"]
+    assert (parent == t0["parent"]).all()
+    front = {}
+    for c, (I, B) in enumerate(s1):
+        for v in I.tolist():
+            assert v not in front
+            front[v] = c
+    assert sorted(v for v in front if v < dev.n) == list(range(dev.n))
+    virtual = sorted(v for v in front if v >= dev.n)
+    assert virtual == list(range(dev.n, dev.n + len(virtual))) and len(virtual) > 0
+    seen = {}
+    for c, (I, B) in enumerate(s1):
+        nv = int((B >= dev.n).sum())
+        assert (B[:nv] >= dev.n).all() and (B[nv:] < dev.n).all()
+        assert nv <= delay and (nv == 0 or parent[c] >= 0)
+        assert B[nv:].tolist() == s0[c][1].tolist()
+        assert sorted(I[I < dev.n].tolist()) == sorted(s0[c][0].tolist())
+        for v in B[:nv].tolist():
+            assert v not in seen and front[v] == parent[c]
+            seen[v] = c
+        if parent[c] >= 0:
+            Ip, Bp = s1[parent[c]]
+            assert set(B.tolist()) <= set(Ip.tolist()) | set(Bp.tolist())
+        else:
+            assert len(B) == 0
+    assert sorted(seen) == virtual
+
+
+def test_delay_out_of_range_rejected():
+    dev = workloads.superlattice(8, 4)
+    with pytest.raises(RuntimeError):
+        _plan_sets(dev, 8, 9)
