@@ -8,16 +8,19 @@ contact self-energies (S1a), lesser/greater self-energies, assembly and fold
 (S1-S3), selected inversion of G^r, G^<, G^> (S4-S8), the FP64 residual
 certificate (S9) and the density epilogue (S10).
 
-Paths: "fp32x2" = cluster blocks and products in FP32-pair ("double-float")
-arithmetic on the FP32 pipe with complex128 root inversion; every energy whose
-certificate reports a fold growth max|Psi| above 3 (where the elimination
-amplifies rounding, see the design notes) is recomputed on the complex128
-path; "fp64_nd" = complex128 throughout (the plain ND path); "fp32" = plain
-complex64 (reported, gated).
+Paths, all with delayed pivots across clusters (--delay, default 2 rows per
+cluster), which keep the fold growth below ~2 at every energy:
+"fp32x2" = cluster blocks and products in FP32-pair ("double-float")
+arithmetic on the FP32 pipe with complex128 root inversion; an energy whose
+certificate still reports a fold growth max|Psi| above 3 would be recomputed
+on the complex128 path; "fp64_nd" = complex128 throughout; "fp32" = plain
+complex64 (reported, gated).  "fp64_nd_plain" = complex128 with the paper's
+elimination (no delayed pivots), timed once for reference.
 The reported value is the fp32x2 path when its energy-integrated density
-matches the FP64 path to <= 1e-6 relative error, else the FP64 path.  Inputs
-(the per-energy workspace, ~100 GB per step) are far larger than L2, so no
-explicit flush is needed.
+matches the FP64 path to <= 1e-6 relative error, else the FP64 path.  Every
+path's diagonals are also compared with the CPU oracle (block RGF) at the
+energies of the CPU baseline sample.  Inputs (the per-energy workspace,
+~100 GB per step) are far larger than L2, so no explicit flush is needed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -51,11 +54,15 @@ def parse():
     ap.add_argument("--chunk-fp64", type=int, default=64)
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
     ap.add_argument("--growth-max", type=float, default=3.0, help="fold growth above which fp32x2 redoes in FP64")
+    ap.add_argument("--delay", type=int, default=2, help="delayed pivots per cluster (0 = the paper's elimination)")
+    ap.add_argument("--no-plain", action="store_true", help="skip the reference timing without delayed pivots")
+    ap.add_argument("--tile", default="auto", choices=["auto", "large", "small"], help="GEMM tile size per launch")
     ap.add_argument("--dump-density", default="", help="write the densities of the paths to this .npz")
     ap.add_argument("--only", default="", help="run one path only (fp64_nd, fp32x2, fp32); for profiling")
     ap.add_argument("--energies", type=int, default=0, help="use the first K energies only; for profiling")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-save", default="", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -63,25 +70,35 @@ def parse():
 # CPU oracle (baseline leg and reference arm): the block RGF of oracle/, timed
 # in a child process with every host core available to BLAS.
 
-def cpu_worker(n_energies: int) -> None:
+def oracle_pick(n_e: int, n_energies: int):
+    import numpy as np
+    return np.linspace(0, n_e - 1, n_energies).round().astype(int)
+
+
+def cpu_worker(n_energies: int, save: str) -> None:
     import numpy as np
     from oracle import rgf
     from paper_1305_1070_gb300 import workloads
     dev, tr = workloads.workload(WORKLOAD)
-    pick = np.linspace(0, tr.n_e - 1, n_energies).round().astype(int)
+    pick = oracle_pick(tr.n_e, n_energies)
     solver = rgf.RGF(dev, tr)
+    res = []
     t0 = time.perf_counter()
     for e in pick:
-        solver.solve(float(tr.energies[e]))
+        res.append(solver.solve(float(tr.energies[e])))
     dt = time.perf_counter() - t0
+    if save:
+        np.savez(save, pick=pick, Gr=np.stack([r["Gr"] for r in res]), Gl=np.stack([r["Gl"] for r in res]))
     print(json.dumps({"energies": int(n_energies), "seconds": dt}))
 
 
-def run_cpu_oracle(n_energies: int) -> dict:
+def run_cpu_oracle(n_energies: int, save: str = "") -> dict:
     cores = os.cpu_count() or 1
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(cores), OMP_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_energies)], env=env,
-                       capture_output=True, text=True, check=True)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_energies)]
+    if save:
+        cmd += ["--cpu-save", save]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
     out = json.loads(r.stdout.strip().splitlines()[-1])
     out["cores"] = cores
     return out
@@ -211,27 +228,37 @@ def main_ours(a) -> None:
         return float((x - y).abs().max() / y.abs().max())
 
     paths, results, solvers = {}, {}, {}
+    pick = torch.as_tensor(oracle_pick(n_e, a.cpu_sample), device="cuda")
     clk = Clocks(local)
     fallback = None
-    for name, prec, chunk in (("fp64_nd", ndgf.ND_PREC_FP64, a.chunk_fp64),
-                              ("fp32x2", ndgf.ND_PREC_FP32X2, a.chunk_fp64),
-                              ("fp32", ndgf.ND_PREC_MIXED, a.chunk_mixed)):
+    runs = [("fp64_nd", ndgf.ND_PREC_FP64, a.chunk_fp64, a.delay), ("fp32x2", ndgf.ND_PREC_FP32X2, a.chunk_fp64, a.delay),
+            ("fp32", ndgf.ND_PREC_MIXED, a.chunk_mixed, a.delay)]
+    if not a.no_plain and a.delay > 0:
+        runs.append(("fp64_nd_plain", ndgf.ND_PREC_FP64, a.chunk_fp64, 0))
+    for name, prec, chunk, delay in runs:
         if a.only and name != a.only:
             continue
         chunk = min(chunk, n_e)
-        solver = Solver(dev, tr, precision=prec, max_ne=chunk)
+        solver = Solver(dev, tr, precision=prec, max_ne=chunk, delay=delay, tile=a.tile)
         if name == "fp64_nd":
             fallback = solver
         step = make_step(solver, chunk, name, fallback if name == "fp32x2" else None)
-        W = a.warmup if name == "fp32x2" else min(a.warmup, 1)
-        ms = timed(step, a.steps, W)
-        results[name] = (dens.clone(), Gl[:, ::97].clone())
+        if name == "fp64_nd_plain":  # reference only: one warm-up, one timed step
+            ms = timed(step, 1, 1)
+        else:
+            ms = timed(step, a.steps, a.warmup if name == "fp32x2" else min(a.warmup, 1))
+        results[name] = (dens.clone(), Gl[:, ::97].clone(), Gr[pick].clone(), Gl[pick].clone())
         c = cert_max[name].tolist()
         paths[name] = {"energies_per_s": round(n_e * world / (ms * 1e-3), 3), "ms_per_step": round(ms, 3),
+                       "delay": delay,
                        "certificate_max": {"resid_r": c[0], "resid_lesser": c[2], "max_Gr": c[1], "max_Gl": c[3],
                                            "growth_max_psi": c[4]},
                        "fp64_redo_energies": redo.get(name, 0)}
-        solvers[name] = (solver, step, ms)
+        if name in ("fp64_nd", "fp32x2"):
+            solvers[name] = (solver, step, ms)
+        else:
+            solvers[name] = (None, None, ms)
+            del solver, step
         torch.cuda.empty_cache()
     clocks = clk.stop()
     if a.only:
@@ -241,7 +268,9 @@ def main_ours(a) -> None:
     if a.dump_density:
         import numpy as np
         np.savez(a.dump_density, **{k: v[0].cpu().numpy() for k, v in results.items()})
-    d64, g64 = results["fp64_nd"]
+    d64, g64 = results["fp64_nd"][:2]
+    if "fp64_nd_plain" in results:
+        paths["fp64_nd_plain"]["density_rel_err_vs_fp64"] = rel(results["fp64_nd_plain"][0], d64)
     for name in ("fp32x2", "fp32"):
         paths[name]["density_rel_err_vs_fp64"] = rel(results[name][0], d64)
         paths[name]["diag_Gl_rel_err_vs_fp64_sampled"] = float(
@@ -318,16 +347,29 @@ def main_ours(a) -> None:
     info = solver.info
 
     if rank == 0:
-        cpu = run_cpu_oracle(a.cpu_sample) if not a.no_cpu else {"energies": 0, "seconds": 1.0, "cores": 0}
+        save = os.path.join(tempfile.gettempdir(), f"ndgf_oracle_{os.getpid()}.npz")
+        cpu = run_cpu_oracle(a.cpu_sample, save) if not a.no_cpu else {"energies": 0, "seconds": 1.0, "cores": 0}
         cpu_val = cpu["energies"] / cpu["seconds"]
+        if not a.no_cpu:  # every path against the oracle at the sampled energies, all sites
+            ref = np.load(save)
+            os.unlink(save)
+            for name, r in results.items():
+                errs = []
+                for q, (got, want) in enumerate(((r[2], ref["Gr"]), (r[3], ref["Gl"]))):
+                    g = got.cpu().numpy()
+                    errs.append([float(np.abs(g[i] - want[i]).max() / np.abs(want[i]).max()) for i in range(len(want))])
+                paths[name]["diag_rel_err_vs_oracle"] = {"energy_index": ref["pick"].tolist(), "Gr": errs[0],
+                                                         "Gl": errs[1], "max": max(max(errs[0]), max(errs[1]))}
         line = {
             "metric": METRIC, "value": round(n_e * world / (ms_headline * 1e-3), 3), "unit": UNIT,
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_headline, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "fp32x2 (FP32-pair complex) + c128 root and redo" if gate else "c128",
+            "dtype": ("fp32x2 (FP32-pair complex) + c128 root" + (" and redo" if paths["fp32x2"]["fp64_redo_energies"] else ""))
+            if gate else "c128",
             "data": "synthetic (seeded superlattice, PCG64 seed 1306)",
             "config": {"workload": WORKLOAD, "sites": n, "energies_per_gpu": n_e, "clusters": info["n_clusters"],
                        "levels": info["n_levels"], "leaf_size": 64, "eta": tr.eta, "path": head,
+                       "delayed_pivots_per_cluster": a.delay,
                        "l2": "inputs larger than L2 (~100-200 GB workspace per step)"},
             "paths": paths,
             "roofline": roofline,
@@ -376,7 +418,7 @@ def main_reference(a) -> None:
 if __name__ == "__main__":
     args = parse()
     if args.cpu_worker:
-        cpu_worker(args.cpu_worker)
+        cpu_worker(args.cpu_worker, args.cpu_save)
     elif args.impl == "reference":
         main_reference(args)
     else:

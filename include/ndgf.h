@@ -63,6 +63,13 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
  * only the clusters on the path from a contact to the root carry that
  * workspace). */
 #define ND_FACT_PHONON 1
+/* GEMM tile size of the batched Schur products.  By default every launch
+ * (one tree level of one product) takes the large or the small tile,
+ * whichever covers its matrices with less padded work, the small tile being
+ * charged a fixed per-flop overhead; these flags force one size
+ * (complex128 / FP32 pairs: 32x32 or 16x16; complex64: 64x64 or 32x32). */
+#define ND_FACT_TILE_LARGE 2
+#define ND_FACT_TILE_SMALL 4
 
 /* Sparsity pattern of H plus the contact site sets (host arrays).
  * rowptr[n+1], colind[nnz]: CSR pattern, 0-based, must be structurally

@@ -129,7 +129,7 @@ struct nd_fact {
   std::vector<double> step_flops_factor, step_flops_green, step_flops_lesser[2];  // per step, per energy
   TileRef* d_tiles = nullptr;
   // tile range of every GEMM step: index = step index in its schedule
-  std::vector<std::pair<int, int>> tr_factor, tr_green, tr_lesser[2];
+  std::vector<TileRange> tr_factor, tr_green, tr_lesser[2];
   // staging buffers for host inputs / outputs
   double *st_H = nullptr, *st_sr = nullptr, *st_ph = nullptr, *st_E = nullptr;
   double *st_sl = nullptr, *st_sg = nullptr, *st_pl = nullptr, *st_pg = nullptr;
@@ -162,12 +162,32 @@ nd_status dupload(nd_fact* f, const std::vector<V>& h, V** d) {
   return st;
 }
 
-void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile,
-                 std::vector<TileRef>& tiles, std::vector<std::pair<int, int>>& ranges) {
-  ranges.assign(sched.size(), {0, 0});
+// Tile lists of the GEMM steps.  Each step takes the large or the small tile:
+// forced by the workspace flags, else the one with less padded work
+// sum(tiles * tile area * k), the small tile's work weighted by small_cost
+// (its lower reuse per loaded element; measured on the 512 x 128 workload:
+// complex128 ran fastest with the small tile on every step, FP32 pairs with
+// this per-step choice).
+double small_tile_cost(int precision) { return precision == ND_PREC_FP64 ? 0.9 : 1.15; }
+
+void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
+                 double small_cost, std::vector<TileRef>& tiles, std::vector<TileRange>& ranges) {
+  ranges.assign(sched.size(), TileRange{0, 0, 0});
+  auto work = [&](const Step& s, int tile) {
+    double w = 0.0;
+    for (int k = s.begin; k < s.begin + s.count; ++k) {
+      const GemmDesc& g = gd[k];
+      w += double((g.m + tile - 1) / tile) * ((g.n + tile - 1) / tile) * tile * tile * std::max(1, g.k);
+    }
+    return w;
+  };
   for (size_t si = 0; si < sched.size(); ++si) {
     const Step& s = sched[si];
     if (s.kind != ST_GEMM) continue;
+    bool small = small_cost * work(s, tile_s) < work(s, tile_l);
+    if (flags & ND_FACT_TILE_LARGE) small = false;
+    if (flags & ND_FACT_TILE_SMALL) small = true;
+    const int tile = small ? tile_s : tile_l;
     int b = int(tiles.size());
     for (int k = s.begin; k < s.begin + s.count; ++k) {
       const GemmDesc& g = gd[k];
@@ -175,7 +195,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
     }
-    ranges[si] = {b, int(tiles.size()) - b};
+    ranges[si] = TileRange{b, int(tiles.size()) - b, small ? 1 : 0};
   }
 }
 
@@ -193,7 +213,7 @@ nd_status stage_in(const double* src, double* staging, size_t bytes, cudaStream_
 }
 
 template <typename T>
-nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::vector<std::pair<int, int>>& tr,
+nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::vector<TileRange>& tr,
                        const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s, int variant = 0,
                        const std::vector<double>* step_flops = nullptr) {
   const nd_plan* p = f->plan;
@@ -217,7 +237,7 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
                          s);
         break;
       case ST_GEMM:
-        Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].second, s);
+        Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, tr[si].small != 0, s);
         break;
       case ST_SCATTER:
         Kern<T>::scatter(w, f->d_scat + st.begin, st.count, f->d_maps, s);
@@ -373,14 +393,18 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   f->step_flops_lesser[0] = step_flops(p, p->sched_lesser[0]);
   f->step_flops_lesser[1] = step_flops(p, p->sched_lesser[1]);
   {
-    const int tile = precision == ND_PREC_FP64 ? Kern<double>::gemm_tile()
-                     : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile()
-                                                  : Kern<DF>::gemm_tile();
+    auto tile_of = [&](bool small) {
+      return precision == ND_PREC_FP64    ? Kern<double>::gemm_tile(small)
+             : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile(small)
+                                          : Kern<DF>::gemm_tile(small);
+    };
+    const int tl = tile_of(false), ts = tile_of(true);
     std::vector<TileRef> tiles;
-    build_tiles(p->sched_factor, p->gemm_desc, tile, tiles, f->tr_factor);
-    build_tiles(p->sched_green, p->gemm_desc, tile, tiles, f->tr_green);
-    build_tiles(p->sched_lesser[0], p->gemm_desc, tile, tiles, f->tr_lesser[0]);
-    build_tiles(p->sched_lesser[1], p->gemm_desc, tile, tiles, f->tr_lesser[1]);
+    const double sc = small_tile_cost(precision);
+    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_factor);
+    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_green);
+    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_lesser[0]);
+    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_lesser[1]);
     TRY(dupload(f, tiles, &f->d_tiles));
   }
   const size_t ne = size_t(max_ne), n = size_t(p->n), se = size_t(p->sigma_elems);

@@ -192,6 +192,7 @@ struct Step {
 };
 
 struct TileRef { int32_t desc, tm, tn, pad; };
+struct TileRange { int32_t first, count, small; };  // tiles of one GEMM step and its tile size
 
 }  // namespace ndgf
 

@@ -241,7 +241,7 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
 // [A_DD | A_DB] go to the boundary accumulator, whose first k rows and columns
 // are the parent's virtual rows of this cluster.  One CTA per (cluster, energy).
 template <typename T>
-__global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64_t se, DelayTabs dt) {
+__global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64_t se, DelayTabs dt, int x_smem) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float red_v[32];
   __shared__ int red_i[32];
@@ -254,13 +254,16 @@ __global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64
   cx<T>* F = base + d.off_F;
   cx<T>* BB = base + d.off_BB;
   cx<T>* S = base + d.off_S;
-  float2* X = reinterpret_cast<float2*>(S);  // nf x nf complex64 inside the nf x ld scratch
   const size_t o1 = (size_t(nf) * sizeof(int) + 15) & ~size_t(15);
   int* piv = reinterpret_cast<int*>(smem);
   float2* colk = reinterpret_cast<float2*>(smem + o1);
   int* perm = reinterpret_cast<int*>(smem + o1 + size_t(nf) * sizeof(float2));
   int* rs = perm + nf;
   int* alive = rs + nf;
+  // nf x nf complex64 working inverse: in shared memory when the launch
+  // reserved room for it (behind the index arrays), else in the nf x ld scratch
+  const size_t o2 = (o1 + size_t(nf) * sizeof(float2) + size_t(3) * nf * sizeof(int) + 15) & ~size_t(15);
+  float2* X = x_smem ? reinterpret_cast<float2*>(smem + o2) : reinterpret_cast<float2*>(S);
   const int64_t nn = int64_t(nf) * nf;
   for (int64_t i = tid; i < nn; i += nt) {
     const double2 v = O<T>::to_d2(F[(i / nf) * ld + (i % nf)]);
@@ -720,12 +723,21 @@ __global__ void k_absmax(const ZeroDesc* __restrict__ descs, const cx<T>* arena,
 
 // ---------------------------------------------------------------------------
 // Host launch wrappers
-template <typename T> struct GemmCfg;
-template <> struct GemmCfg<double> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
-template <> struct GemmCfg<float> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
-template <> struct GemmCfg<DF> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+// Large and small GEMM tiles per precision.  The FP64 pipe (and the FP32 pipe
+// under the 48-operation FP32-pair multiply-add) is slow enough that one or
+// four outputs per thread keep it busy; the small tile wastes less on the
+// ragged 10-60 row blocks of the lower tree levels.
+template <typename T, bool SMALL> struct GemmCfg;
+template <> struct GemmCfg<double, false> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<double, true> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1; };
+template <> struct GemmCfg<float, false> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+template <> struct GemmCfg<float, true> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<DF, false> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<DF, true> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1; };
 
-template <typename T> int Kern<T>::gemm_tile() { return GemmCfg<T>::BM; }
+template <typename T> int Kern<T>::gemm_tile(bool small) {
+  return small ? GemmCfg<T, true>::BM : GemmCfg<T, false>::BM;
+}
 
 template <typename T>
 void Kern<T>::assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst, const int32_t* ent_src,
@@ -740,10 +752,13 @@ void Kern<T>::assemble(const Work& w, const AssembleDesc* d, int count, const in
 template <typename T>
 void Kern<T>::delay(const Work& w, const DelayDesc* d, int count, int max_nf, const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  const size_t shm = ((size_t(max_nf) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_nf) * sizeof(float2) +
-                     size_t(3) * max_nf * sizeof(int);
+  const size_t base = (((size_t(max_nf) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_nf) * sizeof(float2) +
+                       size_t(3) * max_nf * sizeof(int) + 15) & ~size_t(15);
+  const size_t xs = size_t(max_nf) * max_nf * sizeof(float2);
+  const int x_smem = base + xs <= size_t(200 * 1024) ? 1 : 0;  // up to nf = 158
+  const size_t shm = base + (x_smem ? xs : 0);
   if (shm > 48 * 1024) cudaFuncSetAttribute(k_delay<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
-  k_delay<T><<<dim3(count, w.n_e), 256, shm, s>>>(d, (cx<T>*)w.arena, w.se, dt);
+  k_delay<T><<<dim3(count, w.n_e), 256, shm, s>>>(d, (cx<T>*)w.arena, w.se, dt, x_smem);
 }
 
 template <typename T>
@@ -762,13 +777,21 @@ void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, dou
                                                     n_singular, smem_max_n);
 }
 
-template <typename T>
-void Kern<T>::gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
-  if (n_tiles <= 0 || w.n_e <= 0) return;
-  using G = GemmCfg<T>;
+template <typename T, bool SMALL>
+static void launch_gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
+  using G = GemmCfg<T, SMALL>;
   constexpr int NT = (G::BM / G::TM) * (G::BN / G::TN);
   k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<dim3(n_tiles, w.n_e), NT, 0, s>>>(
       d, tiles, (cx<T>*)w.arena, w.se, (const cx<T>*)w.aux, w.sa);
+}
+
+template <typename T>
+void Kern<T>::gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, bool small, cudaStream_t s) {
+  if (n_tiles <= 0 || w.n_e <= 0) return;
+  if (small)
+    launch_gemm<T, true>(w, d, tiles, n_tiles, s);
+  else
+    launch_gemm<T, false>(w, d, tiles, n_tiles, s);
 }
 
 template <typename T>

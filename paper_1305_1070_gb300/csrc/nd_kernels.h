@@ -56,7 +56,7 @@ struct Kern {
   static void delay(const Work& w, const DelayDesc* d, int count, int max_nf, const DelayTabs& dt, cudaStream_t s);
   static void inverse(const Work& w, const InvDesc* d, int count, int max_n, double* fp64_scratch,
                       int64_t scratch_stride, int* n_singular, cudaStream_t s);
-  static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
+  static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, bool small, cudaStream_t s);
   static void scatter(const Work& w, const ScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
   static void gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew,
                      const DelayTabs& dt, cudaStream_t s);
@@ -74,8 +74,8 @@ struct Kern {
                        const DelayTabs& dt, cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
                           cudaStream_t s);
-  // tile edge (BM = BN) of the GEMM kernel of this precision
-  static int gemm_tile();
+  // tile edge (BM = BN) of the large and the small GEMM configuration
+  static int gemm_tile(bool small);
 };
 
 // Final positions of the unknowns after the delayed pivots (one tree level).

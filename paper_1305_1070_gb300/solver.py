@@ -15,7 +15,8 @@ from . import ndgf
 
 class Solver:
     def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
-                 leaf_size: int = 64, split_permille: int = 0, delay: int = 0, device: str = "cuda"):
+                 leaf_size: int = 64, split_permille: int = 0, delay: int = 0, tile: str = "auto",
+                 device: str = "cuda"):
         self.dev, self.tr = dev, tr
         self.device = torch.device(device)
         self.n = dev.n
@@ -29,8 +30,9 @@ class Solver:
         self.sigma_elems = int(self.off[-1])
         self.max_ne = int(max_ne or tr.n_e)
         self.precision = precision
-        self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision,
-                                        ndgf.ND_FACT_PHONON if tr.gamma_ph > 0.0 else 0)
+        flags = ndgf.ND_FACT_PHONON if tr.gamma_ph > 0.0 else 0
+        flags |= {"auto": 0, "large": ndgf.ND_FACT_TILE_LARGE, "small": ndgf.ND_FACT_TILE_SMALL}[tile]
+        self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision, flags)
         self.leads = [ndgf.nd_lead_create(l.H00, l.H01, l.tau) for l in dev.leads]
         kw = dict(device=self.device)
         self.H = torch.as_tensor(dev.values, dtype=torch.float64, **kw).contiguous()
