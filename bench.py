@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--growth-max", type=float, default=3.0, help="fold growth above which fp32x2 redoes in FP64")
     ap.add_argument("--delay", type=int, default=2, help="delayed pivots per cluster (0 = the paper's elimination)")
     ap.add_argument("--no-plain", action="store_true", help="skip the reference timing without delayed pivots")
-    ap.add_argument("--tile", default="auto", choices=["auto", "large", "small"], help="GEMM tile size per launch")
+    ap.add_argument("--tile", default="auto", choices=["auto", "large", "small", "tc", "alu"],
+                    help="GEMM kernel per launch: auto, a forced ALU tile size, tensor cores (FP32 pairs) or never")
     ap.add_argument("--dump-density", default="", help="write the densities of the paths to this .npz")
     ap.add_argument("--only", default="", help="run one path only (fp64_nd, fp32x2, fp32); for profiling")
     ap.add_argument("--energies", type=int, default=0, help="use the first K energies only; for profiling")

@@ -70,6 +70,14 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
  * (complex128 / FP32 pairs: 32x32 or 16x16; complex64: 64x64 or 32x32). */
 #define ND_FACT_TILE_LARGE 2
 #define ND_FACT_TILE_SMALL 4
+/* FP32-pair precision only: the Schur products may instead run on the tensor
+ * cores, as exact products of 8-bit digits of a 46-bit fixed-point form of
+ * each row and column (BF16 in, FP32 accumulate; same accuracy class).  By
+ * default a launch takes them when the padded work, weighted by their lower
+ * cost per flop, is smallest; ND_FACT_GEMM_TC forces them for every GEMM
+ * launch, ND_FACT_GEMM_ALU never uses them. */
+#define ND_FACT_GEMM_TC 8
+#define ND_FACT_GEMM_ALU 16
 
 /* Sparsity pattern of H plus the contact site sets (host arrays).
  * rowptr[n+1], colind[nnz]: CSR pattern, 0-based, must be structurally

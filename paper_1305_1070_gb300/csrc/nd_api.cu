@@ -169,9 +169,15 @@ nd_status dupload(nd_fact* f, const std::vector<V>& h, V** d) {
 // complex128 ran fastest with the small tile on every step, FP32 pairs with
 // this per-step choice).
 double small_tile_cost(int precision) { return precision == ND_PREC_FP64 ? 0.9 : 1.15; }
+// FP32 pairs: padded work of the tensor-core kernel relative to the large ALU
+// tile.  Measured equal on the 512 x 128 workload (GEMM time per step with
+// every launch forced: 1209.6 ms tensor cores, 1206.7 ms 32 x 32 FP32 pipe):
+// the digit split, redone by every tile, costs as much as the products saved,
+// so the default choice never prefers it.
+constexpr double TC_COST = 1.0;
 
 void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
-                 double small_cost, std::vector<TileRef>& tiles, std::vector<TileRange>& ranges) {
+                 double small_cost, int tile_tc, std::vector<TileRef>& tiles, std::vector<TileRange>& ranges) {
   ranges.assign(sched.size(), TileRange{0, 0, 0});
   auto work = [&](const Step& s, int tile) {
     double w = 0.0;
@@ -187,7 +193,12 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
     bool small = small_cost * work(s, tile_s) < work(s, tile_l);
     if (flags & ND_FACT_TILE_LARGE) small = false;
     if (flags & ND_FACT_TILE_SMALL) small = true;
-    const int tile = small ? tile_s : tile_l;
+    bool tc = false;
+    if (tile_tc > 0 && !(flags & ND_FACT_GEMM_ALU)) {
+      tc = TC_COST * work(s, tile_tc) < std::min(work(s, tile_l), small_cost * work(s, tile_s));
+      if (flags & ND_FACT_GEMM_TC) tc = true;
+    }
+    const int tile = tc ? tile_tc : small ? tile_s : tile_l;
     int b = int(tiles.size());
     for (int k = s.begin; k < s.begin + s.count; ++k) {
       const GemmDesc& g = gd[k];
@@ -195,7 +206,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
     }
-    ranges[si] = TileRange{b, int(tiles.size()) - b, small ? 1 : 0};
+    ranges[si] = TileRange{b, int(tiles.size()) - b, tc ? 2 : small ? 1 : 0};
   }
 }
 
@@ -237,7 +248,10 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
                          s);
         break;
       case ST_GEMM:
-        Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, tr[si].small != 0, s);
+        if (tr[si].kind == 2)
+          launch_gemm_tc(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
+        else
+          Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, tr[si].kind == 1, s);
         break;
       case ST_SCATTER:
         Kern<T>::scatter(w, f->d_scat + st.begin, st.count, f->d_maps, s);
@@ -401,10 +415,11 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
     const int tl = tile_of(false), ts = tile_of(true);
     std::vector<TileRef> tiles;
     const double sc = small_tile_cost(precision);
-    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_factor);
-    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_green);
-    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_lesser[0]);
-    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, tiles, f->tr_lesser[1]);
+    const int ttc = precision == ND_PREC_FP32X2 ? gemm_tc_tile() : 0;
+    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_factor);
+    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_green);
+    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_lesser[0]);
+    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_lesser[1]);
     TRY(dupload(f, tiles, &f->d_tiles));
   }
   const size_t ne = size_t(max_ne), n = size_t(p->n), se = size_t(p->sigma_elems);

@@ -53,6 +53,25 @@ template <> struct Ops<double> {
     c.y = fma(a.y, b.x, c.y);
   }
   static __device__ __forceinline__ C acc_get(const Acc& c) { return make_double2(c.x, c.y); }
+  // a -= c r, the update of Gauss-Jordan elimination (gj_invert2)
+  static __device__ __forceinline__ C norm(C a) { return a; }
+  static __device__ __forceinline__ void sub_mul(C& a, C c, C r) {
+    a.x = fma(-c.x, r.x, a.x);
+    a.x = fma(c.y, r.y, a.x);
+    a.y = fma(-c.x, r.y, a.y);
+    a.y = fma(-c.y, r.x, a.y);
+  }
+  // 3-multiplication complex products (see Ops<DF>::Acc3)
+  using S = double;
+  struct Acc3 { double p1, p2, p3; };
+  static __device__ __forceinline__ S sum(C a) { return a.x + a.y; }
+  static __device__ __forceinline__ Acc3 acc3_zero() { return Acc3{0.0, 0.0, 0.0}; }
+  static __device__ __forceinline__ void acc3_fma(Acc3& c, C a, S as, C b, S bs) {
+    c.p1 = fma(a.x, b.x, c.p1);
+    c.p2 = fma(a.y, b.y, c.p2);
+    c.p3 = fma(as, bs, c.p3);
+  }
+  static __device__ __forceinline__ C acc3_get(const Acc3& c) { return make_double2(c.p1 - c.p2, (c.p3 - c.p1) - c.p2); }
 };
 
 template <> struct Ops<float> {
@@ -82,6 +101,23 @@ template <> struct Ops<float> {
     c.y = fmaf(a.y, b.x, c.y);
   }
   static __device__ __forceinline__ C acc_get(const Acc& c) { return make_float2(c.x, c.y); }
+  static __device__ __forceinline__ C norm(C a) { return a; }
+  static __device__ __forceinline__ void sub_mul(C& a, C c, C r) {
+    a.x = fmaf(-c.x, r.x, a.x);
+    a.x = fmaf(c.y, r.y, a.x);
+    a.y = fmaf(-c.x, r.y, a.y);
+    a.y = fmaf(-c.y, r.x, a.y);
+  }
+  using S = float;
+  struct Acc3 { float p1, p2, p3; };
+  static __device__ __forceinline__ S sum(C a) { return a.x + a.y; }
+  static __device__ __forceinline__ Acc3 acc3_zero() { return Acc3{0.f, 0.f, 0.f}; }
+  static __device__ __forceinline__ void acc3_fma(Acc3& c, C a, S as, C b, S bs) {
+    c.p1 = fmaf(a.x, b.x, c.p1);
+    c.p2 = fmaf(a.y, b.y, c.p2);
+    c.p3 = fmaf(as, bs, c.p3);
+  }
+  static __device__ __forceinline__ C acc3_get(const Acc3& c) { return make_float2(c.p1 - c.p2, (c.p3 - c.p1) - c.p2); }
 };
 
 // ---- double-float reals ----------------------------------------------------
@@ -188,6 +224,47 @@ template <> struct Ops<DF> {
     two_sum(c.rh, c.rl, r.h, r.l);
     two_sum(c.ih, c.il, i.h, i.l);
     return mk(r, i);
+  }
+  // Elements updated by sub_mul are kept as unnormalised pairs (h, l), like
+  // the accumulator above; norm() brings one back to a double-float before it
+  // is used as a factor.
+  static __device__ __forceinline__ C norm(C a) {
+    f2 r, i;
+    two_sum(a.x, a.y, r.h, r.l);
+    two_sum(a.z, a.w, i.h, i.l);
+    return mk(r, i);
+  }
+  static __device__ __forceinline__ void sub_mul(C& a, C c, C r) {  // a -= c r, c and r normalised
+    acc_term(a.x, a.y, re(c), re(r), -1.f);
+    acc_term(a.x, a.y, im(c), im(r), 1.f);
+    acc_term(a.z, a.w, re(c), im(r), -1.f);
+    acc_term(a.z, a.w, im(c), re(r), -1.f);
+  }
+  // 3-multiplication complex multiply-add (Gauss's trick; Higham, "Accuracy
+  // and Stability of Numerical Algorithms", 2nd ed., Sec. 23.2.4):
+  //   P1 += Re a Re b,  P2 += Im a Im b,  P3 += (Re a + Im a)(Re b + Im b),
+  //   Re = P1 - P2,     Im = P3 - P1 - P2.
+  // The sums Re + Im are formed once per staged element, so a multiply-add
+  // costs three lazy double-float terms (36 FP32 operations) instead of four.
+  // The error bound is normwise: |error| <~ eps (|Re a| + |Im a|)(|Re b| + |Im b|).
+  using S = float2;  // double-float real (h, l)
+  struct Acc3 { float h1, l1, h2, l2, h3, l3; };
+  static __device__ __forceinline__ S sum(C a) {
+    const f2 r = dd_add(re(a), im(a));
+    return make_float2(r.h, r.l);
+  }
+  static __device__ __forceinline__ Acc3 acc3_zero() { return Acc3{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; }
+  static __device__ __forceinline__ void acc3_fma(Acc3& c, C a, S as, C b, S bs) {
+    acc_term(c.h1, c.l1, re(a), re(b), 1.f);
+    acc_term(c.h2, c.l2, im(a), im(b), 1.f);
+    acc_term(c.h3, c.l3, f2{as.x, as.y}, f2{bs.x, bs.y}, 1.f);
+  }
+  static __device__ __forceinline__ C acc3_get(const Acc3& c) {
+    f2 p1, p2, p3;
+    two_sum(c.h1, c.l1, p1.h, p1.l);
+    two_sum(c.h2, c.l2, p2.h, p2.l);
+    two_sum(c.h3, c.l3, p3.h, p3.l);
+    return mk(dd_sub(p1, p2), dd_sub(dd_sub(p3, p1), p2));
   }
 };
 

@@ -192,7 +192,8 @@ struct Step {
 };
 
 struct TileRef { int32_t desc, tm, tn, pad; };
-struct TileRange { int32_t first, count, small; };  // tiles of one GEMM step and its tile size
+// tiles of one GEMM step and its kernel: 0 large tile, 1 small tile, 2 tensor cores
+struct TileRange { int32_t first, count, kind; };
 
 }  // namespace ndgf
 

@@ -83,24 +83,30 @@ __global__ void k_inverse(const InvDesc* __restrict__ descs, cx<T>* arena, int64
   const InvDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   cx<T>* M = arena + int64_t(e) * se + d.off;
+  // shared memory: piv (n ints), colk and R (n elements of up to 16 bytes
+  // each), then the block itself when it fits
   int* piv = reinterpret_cast<int*>(smem);
   const size_t colk_off = (size_t(d.n) * sizeof(int) + 15) & ~size_t(15);
+  const size_t r_off = colk_off + size_t(d.n) * sizeof(double2);
   const int64_t nn = int64_t(d.n) * d.n;
   if (!std::is_same<T, double>::value && d.fp64 && scratch) {  // root block in complex128
     double2* W = scratch + int64_t(e) * scratch_stride;
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = O<T>::to_d2(M[(i / d.n) * d.ld + i % d.n]);
     __syncthreads();
-    gj_invert<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off), n_singular);
+    gj_invert2<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off),
+                       reinterpret_cast<double2*>(smem + r_off), n_singular);
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = O<T>::from_d2(W[i]);
   } else if (d.n <= smem_max_n) {  // whole block resident in shared memory
     cx<T>* colk = reinterpret_cast<cx<T>*>(smem + colk_off);
-    cx<T>* S = colk + d.n;
+    cx<T>* R = reinterpret_cast<cx<T>*>(smem + r_off);
+    cx<T>* S = reinterpret_cast<cx<T>*>(smem + r_off + size_t(d.n) * sizeof(double2));
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) S[i] = M[(i / d.n) * d.ld + i % d.n];
     __syncthreads();
-    gj_invert<T>(S, d.n, d.n, piv, colk, n_singular);
+    gj_invert2<T>(S, d.n, d.n, piv, colk, R, n_singular);
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = S[i];
   } else {
-    gj_invert<T>(M, d.n, d.ld, piv, reinterpret_cast<cx<T>*>(smem + colk_off), n_singular);
+    gj_invert2<T>(M, d.n, d.ld, piv, reinterpret_cast<cx<T>*>(smem + colk_off),
+                  reinterpret_cast<cx<T>*>(smem + r_off), n_singular);
   }
 }
 
@@ -116,8 +122,15 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
   constexpr int LA = (BM * BK + NT - 1) / NT, LB = (BK * BN + NT - 1) / NT;  // staged loads per thread
   // two shared buffers: the next k-tile is fetched into registers while the
   // current one is used, then stored to the other buffer (one barrier per step)
-  __shared__ cx<T> As[2][BK][BM + 1];
-  __shared__ cx<T> Bs[2][BK][BN + 1];
+  // staged tiles plus Re + Im of every element (3-multiplication products),
+  // in dynamic shared memory (gemm_smem_bytes)
+  using S = typename O<T>::S;
+  extern __shared__ __align__(16) unsigned char gsm[];
+  auto As = reinterpret_cast<cx<T>(*)[BK][BM + 1]>(gsm);
+  auto Bs = reinterpret_cast<cx<T>(*)[BK][BN + 1]>(gsm + sizeof(cx<T>) * 2 * BK * (BM + 1));
+  auto Ass = reinterpret_cast<S(*)[BK][BM + 1]>(gsm + sizeof(cx<T>) * 2 * BK * (BM + 1 + BN + 1));
+  auto Bss = reinterpret_cast<S(*)[BK][BN + 1]>(gsm + sizeof(cx<T>) * 2 * BK * (BM + 1 + BN + 1) +
+                                                sizeof(S) * 2 * BK * (BM + 1));
   const TileRef t = tiles[blockIdx.x];
   const GemmDesc d = descs[t.desc];
   const int64_t e = blockIdx.y;
@@ -162,6 +175,7 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
       if (idx < BM * BK) {
         const int mm = transA ? idx % BM : idx / BK, kk = transA ? idx / BM : idx % BK;
         As[buf][kk][mm] = ra[l];
+        Ass[buf][kk][mm] = O<T>::sum(ra[l]);
       }
     }
 #pragma unroll
@@ -170,14 +184,15 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
       if (idx < BK * BN) {
         const int kk = transB ? idx % BK : idx / BN, nn = transB ? idx / BK : idx % BN;
         Bs[buf][kk][nn] = rb[l];
+        Bss[buf][kk][nn] = O<T>::sum(rb[l]);
       }
     }
   };
-  typename O<T>::Acc acc[TM][TN];
+  typename O<T>::Acc3 acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = O<T>::acc_zero();
+    for (int j = 0; j < TN; ++j) acc[i][j] = O<T>::acc3_zero();
   const int nk = (d.k + BK - 1) / BK;
   if (nk > 0) {
     fetch(0);
@@ -190,14 +205,21 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
 #pragma unroll 4
     for (int kk = 0; kk < BK; ++kk) {
       cx<T> a[TM], b[TN];
+      S as[TM], bs[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[cur][kk][ty + i * NY];
+      for (int i = 0; i < TM; ++i) {
+        a[i] = As[cur][kk][ty + i * NY];
+        as[i] = Ass[cur][kk][ty + i * NY];
+      }
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[cur][kk][tx + j * NX];
+      for (int j = 0; j < TN; ++j) {
+        b[j] = Bs[cur][kk][tx + j * NX];
+        bs[j] = Bss[cur][kk][tx + j * NX];
+      }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TN; ++j) O<T>::acc_fma(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) O<T>::acc3_fma(acc[i][j], a[i], as[i], b[j], bs[j]);
     }
     if (kt + 1 < nk) store(cur ^ 1);
     __syncthreads();
@@ -212,7 +234,7 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
     for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + j * NX;
       if (gn >= d.n) continue;
-      cx<T> r = O<T>::acc_get(acc[i][j]);
+      cx<T> r = O<T>::acc3_get(acc[i][j]);
       if (d.alpha == -1.0)
         r = O<T>::neg(r);
       else if (d.alpha != 1.0)
@@ -261,8 +283,11 @@ __global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64
   int* rs = perm + nf;
   int* alive = rs + nf;
   // nf x nf complex64 working inverse: in shared memory when the launch
-  // reserved room for it (behind the index arrays), else in the nf x ld scratch
-  const size_t o2 = (o1 + size_t(nf) * sizeof(float2) + size_t(3) * nf * sizeof(int) + 15) & ~size_t(15);
+  // reserved room for it (behind the index arrays and the row buffer R), else
+  // in the nf x ld scratch
+  const size_t oR = (o1 + size_t(nf) * sizeof(float2) + size_t(3) * nf * sizeof(int) + 15) & ~size_t(15);
+  float2* Rrow = reinterpret_cast<float2*>(smem + oR);
+  const size_t o2 = oR + size_t(nf) * sizeof(float2);
   float2* X = x_smem ? reinterpret_cast<float2*>(smem + o2) : reinterpret_cast<float2*>(S);
   const int64_t nn = int64_t(nf) * nf;
   for (int64_t i = tid; i < nn; i += nt) {
@@ -272,7 +297,7 @@ __global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64
   for (int i = tid; i < nf; i += nt) alive[i] = 1;
   if (tid == 0) s_nsing = 0;
   __syncthreads();
-  gj_invert<float>(X, nf, nf, piv, colk, &s_nsing);
+  gj_invert2<float>(X, nf, nf, piv, colk, Rrow, &s_nsing);
   __syncthreads();
   for (int t = 0; t < k; ++t) {
     float bv = -1.f;
@@ -752,8 +777,9 @@ void Kern<T>::assemble(const Work& w, const AssembleDesc* d, int count, const in
 template <typename T>
 void Kern<T>::delay(const Work& w, const DelayDesc* d, int count, int max_nf, const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  const size_t base = (((size_t(max_nf) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_nf) * sizeof(float2) +
-                       size_t(3) * max_nf * sizeof(int) + 15) & ~size_t(15);
+  const size_t base = ((((size_t(max_nf) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_nf) * sizeof(float2) +
+                        size_t(3) * max_nf * sizeof(int) + 15) & ~size_t(15)) +
+                      size_t(max_nf) * sizeof(float2);
   const size_t xs = size_t(max_nf) * max_nf * sizeof(float2);
   const int x_smem = base + xs <= size_t(200 * 1024) ? 1 : 0;  // up to nf = 158
   const size_t shm = base + (x_smem ? xs : 0);
@@ -765,7 +791,7 @@ template <typename T>
 void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, double* scratch, int64_t scratch_stride,
                       int* n_singular, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  const size_t base = ((size_t(max_n) * sizeof(int) + 15) & ~size_t(15)) + size_t(max_n) * sizeof(double2);
+  const size_t base = ((size_t(max_n) * sizeof(int) + 15) & ~size_t(15)) + size_t(2) * max_n * sizeof(double2);
   // blocks with base + n^2 elements within 72 KB (n <= 64 for 16-byte elements)
   // are inverted in shared memory; larger ones in place in global memory
   int cap = 0;
@@ -781,8 +807,10 @@ template <typename T, bool SMALL>
 static void launch_gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
   using G = GemmCfg<T, SMALL>;
   constexpr int NT = (G::BM / G::TM) * (G::BN / G::TN);
-  k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN><<<dim3(n_tiles, w.n_e), NT, 0, s>>>(
-      d, tiles, (cx<T>*)w.arena, w.se, (const cx<T>*)w.aux, w.sa);
+  constexpr size_t shm = (sizeof(cx<T>) + sizeof(typename O<T>::S)) * 2 * G::BK * (G::BM + 1 + G::BN + 1);
+  auto kern = k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN>;
+  if (shm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
+  kern<<<dim3(n_tiles, w.n_e), NT, shm, s>>>(d, tiles, (cx<T>*)w.arena, w.se, (const cx<T>*)w.aux, w.sa);
 }
 
 template <typename T>

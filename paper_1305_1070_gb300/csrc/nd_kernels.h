@@ -78,6 +78,11 @@ struct Kern {
   static int gemm_tile(bool small);
 };
 
+// FP32-pair GEMM of one schedule step on the tensor cores (nd_gemm_tc.cu):
+// exact BF16 digit products, 32 x 32 tiles.
+int gemm_tc_tile();
+void launch_gemm_tc(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
+
 // Final positions of the unknowns after the delayed pivots (one tree level).
 void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s);
 // Certificate entries 0..3 set to -1 (no residual terms with delayed pivots).

@@ -24,6 +24,8 @@ ND_PREC_FP32X2 = 2
 ND_FACT_PHONON = 1
 ND_FACT_TILE_LARGE = 2
 ND_FACT_TILE_SMALL = 4
+ND_FACT_GEMM_TC = 8
+ND_FACT_GEMM_ALU = 16
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",

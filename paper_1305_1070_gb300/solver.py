@@ -31,7 +31,8 @@ class Solver:
         self.max_ne = int(max_ne or tr.n_e)
         self.precision = precision
         flags = ndgf.ND_FACT_PHONON if tr.gamma_ph > 0.0 else 0
-        flags |= {"auto": 0, "large": ndgf.ND_FACT_TILE_LARGE, "small": ndgf.ND_FACT_TILE_SMALL}[tile]
+        flags |= {"auto": 0, "large": ndgf.ND_FACT_TILE_LARGE, "small": ndgf.ND_FACT_TILE_SMALL,
+                  "tc": ndgf.ND_FACT_GEMM_TC, "alu": ndgf.ND_FACT_GEMM_ALU}[tile]
         self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision, flags)
         self.leads = [ndgf.nd_lead_create(l.H00, l.H01, l.tau) for l in dev.leads]
         kw = dict(device=self.device)
