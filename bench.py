@@ -173,6 +173,7 @@ def main_ours(a) -> None:
     Gl = torch.zeros_like(Gr)
     Gg = torch.zeros_like(Gr)
     dens = torch.zeros(n, dtype=torch.float64, device="cuda")
+    cur = torch.zeros(2, n_e, dtype=torch.float64, device="cuda")  # terminal current spectra i_L, i_R
     cert_max = {}
 
     redo = {}
@@ -190,6 +191,8 @@ def main_ours(a) -> None:
                 calls["n"] += 1
                 r, l, g = solver.step(E_all[c0:c0 + m])
                 Gr[c0:c0 + m], Gl[c0:c0 + m], Gg[c0:c0 + m] = r, l, g
+                for c in range(2):
+                    cur[c, c0:c0 + m] = solver.current(c, m)[0]
                 cert = solver.certificate(m)
                 cmax = torch.maximum(cmax, cert.amax(dim=0))
                 if fallback is not None:
@@ -204,6 +207,8 @@ def main_ours(a) -> None:
                     calls["n"] += 1
                     r, l, g = fallback.step(E_all[sel])
                     Gr[sel], Gl[sel], Gg[sel] = r, l, g
+                    for c in range(2):
+                        cur[c, sel] = fallback.current(c, int(sel.numel()))[0]
             ndgf.nd_density(Gl, weights, n_e, n, scale, 0, dens)
             cert_max[name] = cmax
             redo[name] = nredo
@@ -251,7 +256,7 @@ def main_ours(a) -> None:
             ms = timed(step, 1, 1)
         else:
             ms = timed(step, a.steps, a.warmup if name == "fp32x2" else min(a.warmup, 1))
-        results[name] = (dens.clone(), Gl[:, ::97].clone(), Gr[pick].clone(), Gl[pick].clone())
+        results[name] = (dens.clone(), Gl[:, ::97].clone(), Gr[pick].clone(), Gl[pick].clone(), cur.clone())
         c = cert_max[name].tolist()
         paths[name] = {"energies_per_s": round(n_e * world / (ms * 1e-3), 3), "ms_per_step": round(ms, 3),
                        "delay": delay,
@@ -280,6 +285,7 @@ def main_ours(a) -> None:
         paths[name]["diag_Gl_rel_err_vs_fp64_sampled"] = float(
             ((results[name][1] - g64).abs().amax(dim=1) / g64.abs().amax(dim=1)).max())
         paths[name]["gate_1e-6"] = paths[name]["density_rel_err_vs_fp64"] <= GATE
+        paths[name]["current_rel_err_vs_fp64"] = rel(results[name][4], results["fp64_nd"][4])
     gate = paths["fp32x2"]["gate_1e-6"]
     head = "fp32x2" if gate else "fp64_nd"
     paths["speedup_fp32x2_over_fp64"] = round(solvers["fp64_nd"][2] / solvers["fp32x2"][2], 3)
@@ -302,9 +308,9 @@ def main_ours(a) -> None:
         torch.cuda.synchronize()
         prof[name] = ndgf.nd_profile(solver.fact, False)
         extra = ndgf.nd_profile(f64.fact, False) if name == "fp32x2" else []
-        # schedule launches (profiled) + 10 per solver call (assembly, outputs, certificate,
-        # leads, lesser self-energies) + the density epilogue
-        launches[name] = sum(p["launches"] for p in prof[name] + extra) + 10 * calls["n"] + 1
+        # schedule launches (profiled) + 12 per solver call (assembly, outputs, certificate,
+        # leads, lesser self-energies, two contact currents) + the density epilogue
+        launches[name] = sum(p["launches"] for p in prof[name] + extra) + 12 * calls["n"] + 1
         if extra:
             prof[name + "_fp64_redo"] = extra
 
@@ -335,6 +341,7 @@ def main_ours(a) -> None:
     E_host = torch.as_tensor(tr.energies).pin_memory()
     out_host = [torch.empty(n_e, n, dtype=torch.complex128).pin_memory() for _ in range(3)]
     dens_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    cur_host = torch.empty(2, n_e, dtype=torch.float64).pin_memory()
 
     def step_e2e():
         solver.H.copy_(H_host, non_blocking=True)
@@ -345,10 +352,11 @@ def main_ours(a) -> None:
         for dst, src in zip(out_host, (Gr, Gl, Gg)):
             dst.copy_(src, non_blocking=True)
         dens_host.copy_(dens, non_blocking=True)
+        cur_host.copy_(cur, non_blocking=True)
 
     ms_e2e = timed(step_e2e, a.steps, 1)
     h2d = H_host.numel() * 8 + E_host.numel() * 8
-    d2h = 3 * n_e * n * 16 + n * 8
+    d2h = 3 * n_e * n * 16 + n * 8 + 2 * n_e * 8
     info = solver.info
 
     if rank == 0:
@@ -377,6 +385,7 @@ def main_ours(a) -> None:
                        "delayed_pivots_per_cluster": a.delay,
                        "l2": "inputs larger than L2 (~100-200 GB workspace per step)"},
             "paths": paths,
+            "current_spectrum_integral_eV": {"L": float((cur[0] * weights).sum()), "R": float((cur[1] * weights).sum())},
             "roofline": roofline,
             "roofline_other": roof["fp64_nd" if head == "fp32x2" else "fp32x2"],
             "kernel_profile": prof,

@@ -214,6 +214,18 @@ nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double*
  * host or device.  Stream ordered after the nd_diag_green call. */
 nd_status nd_certificate(nd_fact* fact, double* cert, void* stream);
 
+/* S10 terminal current spectrum of one contact (Meir-Wingreen; paper Sec. 1,
+ * the current is the physical output next to the density):
+ *     i_c(E) = Tr[Sigma^<_c(E) G^>_cc(E) - Sigma^>_c(E) G^<_cc(E)]
+ * over the contact's own m_c x m_c block, for every energy of the last
+ * nd_factor / nd_diag_green pair (which must have been given Sigma^< and
+ * Sigma^>).  The terminal current is (2e/h) times the integral over E.
+ * current[n_e] receives the real part, current_im[n_e] (may be NULL) the
+ * imaginary part, which is zero up to rounding; both host or device.
+ * Errors: ND_ERR_INVALID_ARG (contact out of range, no preceding G^</G^>). */
+nd_status nd_contact_current(nd_fact* fact, int32_t contact, double* current, double* current_im,
+                             void* stream);
+
 /* ---- S10: density epilogue --------------------------------------------------
  * out[j] = (accumulate ? out[j] : 0) + scale * sum_e weights[e] Im X[e][j],
  * X = diag G^< ([n_e][n] complex, caller order).  With trapezoid weights and

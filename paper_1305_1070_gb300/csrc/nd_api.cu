@@ -119,7 +119,8 @@ struct nd_fact {
   // inputs of the last nd_factor / nd_diag_green (staged copies) for nd_certificate
   double eta = 0.0;
   const double *cur_H = nullptr, *cur_sr = nullptr, *cur_ph = nullptr, *cur_E = nullptr;
-  const double *cur_sl = nullptr, *cur_pl = nullptr;
+  const double *cur_sl = nullptr, *cur_sg = nullptr, *cur_pl = nullptr;
+  double* d_current = nullptr;  // [max_ne][2]: Re and Im of the last current spectrum
   bool have_lesser = false;
   double* d_cert = nullptr;
   int32_t *d_cert_ptr = nullptr, *d_cert_terms = nullptr, *d_cl_ldG2 = nullptr;
@@ -401,6 +402,7 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dupload(f, p->cert_ptr, &f->d_cert_ptr));
   TRY(dupload(f, p->cert_terms, &f->d_cert_terms));
   TRY(dalloc(f, (void**)&f->d_cert, size_t(max_ne) * 8 * sizeof(double)));
+  TRY(dalloc(f, (void**)&f->d_current, size_t(max_ne) * 2 * sizeof(double)));
   TRY(dupload(f, p->psi_desc, &f->d_psi));
   f->step_flops_factor = step_flops(p, p->sched_factor);
   f->step_flops_green = step_flops(p, p->sched_green);
@@ -536,6 +538,7 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
   if (st != ND_OK) return st;
   f->have_lesser = (Gl || Gg);
   f->cur_sl = sl;
+  f->cur_sg = sg;
   f->cur_pl = pl;
   for (int k = 0; k < 3; ++k)
     if (host[k]) ND_CUDA(cudaMemcpyAsync(user[k], dev[k], size_t(n_e) * p->n * 16, cudaMemcpyDeviceToHost, s));
@@ -580,6 +583,41 @@ extern "C" nd_status nd_certificate(nd_fact* f, double* cert, void* stream) {
   ND_CUDA(cudaGetLastError());
   ND_CUDA(cudaMemcpyAsync(cert, f->d_cert, bytes, is_device_ptr(cert) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_contact_current(nd_fact* f, int32_t contact, double* current, double* current_im,
+                                        void* stream) {
+  if (!f || !current) return fail(ND_ERR_INVALID_ARG, "nd_contact_current: NULL argument");
+  const nd_plan* p = f->plan;
+  if (contact < 0 || contact >= p->n_contacts) return fail(ND_ERR_INVALID_ARG, "nd_contact_current: bad contact");
+  if (f->n_e <= 0 || !f->have_lesser || !f->cur_sl || !f->cur_sg)
+    return fail(ND_ERR_INVALID_ARG,
+                "nd_contact_current: needs a preceding nd_diag_green with Sigma^< and Sigma^> (G^< or G^> requested)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int q = p->contact_cluster[contact];
+  const ndgf::Cluster& c = p->cl[q];
+  const int m = p->contact_ptr[contact + 1] - p->contact_ptr[contact];
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
+  double* dre = f->d_current;
+  double* dim = f->d_current + f->n_e;
+  const int ld = c.n + c.b;
+  if (f->precision == ND_PREC_FP64)
+    Kern<double>::current(w, c.off_P[0], c.off_P[1], ld, p->contact_row[contact], m, f->cur_sl, f->cur_sg,
+                          p->sigma_elems, p->contact_soff[contact], dre, dim, s);
+  else if (f->precision == ND_PREC_MIXED)
+    Kern<float>::current(w, c.off_P[0], c.off_P[1], ld, p->contact_row[contact], m, f->cur_sl, f->cur_sg,
+                         p->sigma_elems, p->contact_soff[contact], dre, dim, s);
+  else
+    Kern<DF>::current(w, c.off_P[0], c.off_P[1], ld, p->contact_row[contact], m, f->cur_sl, f->cur_sg,
+                      p->sigma_elems, p->contact_soff[contact], dre, dim, s);
+  ND_CUDA(cudaGetLastError());
+  const size_t bytes = size_t(f->n_e) * sizeof(double);
+  ND_CUDA(cudaMemcpyAsync(current, dre, bytes, is_device_ptr(current) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          s));
+  if (current_im)
+    ND_CUDA(cudaMemcpyAsync(current_im, dim, bytes,
+                            is_device_ptr(current_im) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   return ND_OK;
 }
 

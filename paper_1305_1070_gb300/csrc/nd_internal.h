@@ -242,6 +242,10 @@ struct nd_plan {
   // sum_k A_jk X_kj, each {cluster, element index in its [X_II | X_IB] front,
   // coefficient source (CSR index >= 0, or -1 - packed Sigma index), flag 1 when
   // the stored element is X_jk with k an ancestor site (X^< needs -conj)}
+  // per contact: cluster holding its sites, first front row there, offset of
+  // its block in the packed Sigma arrays (elements)
+  std::vector<int32_t> contact_cluster, contact_row;
+  std::vector<int64_t> contact_soff;
   std::vector<ndgf::ZeroDesc> psi_desc;  // Psi regions (growth indicator)
   std::vector<int32_t> cert_ptr;
   std::vector<int32_t> cert_terms;  // 4 ints per term

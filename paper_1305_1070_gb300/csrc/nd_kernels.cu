@@ -903,6 +903,58 @@ void Kern<T>::certificate(const Work& w, const CertArgs& a, cudaStream_t s) {
       a.energies, a.eta, a.lesser, a.cert);
 }
 
+// S10 terminal current spectrum (Meir-Wingreen) of one contact:
+//   i_c(E) = Tr[Sigma^<_c G^>_cc - Sigma^>_c G^<_cc]
+// over the contact block, G^< and G^> from the contact cluster's [P_II | P_IB]
+// fronts (rows row0 .. row0+m of its interior), Sigma from the FP64 inputs.
+// One CTA per energy; out[e] = Re, out_im[e] = Im (zero up to rounding: the
+// trace of a product of two skew-Hermitian matrices is real).
+template <typename T>
+__global__ void k_current(const cx<T>* arena, int64_t se, int64_t offPl, int64_t offPg, int ld, int row0, int m,
+                          const double2* __restrict__ sl, const double2* __restrict__ sg, int64_t sstride, int64_t soff,
+                          double* out, double* out_im) {
+  const int e = blockIdx.x;
+  const cx<T>* Pl = arena + int64_t(e) * se + offPl;
+  const cx<T>* Pg = arena + int64_t(e) * se + offPg;
+  const double2* L = sl + int64_t(e) * sstride + soff;
+  const double2* Gt = sg + int64_t(e) * sstride + soff;
+  double re = 0.0, im = 0.0;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int a = idx / m, b = idx % m;
+    const double2 s1 = L[idx], s2 = Gt[idx];
+    const double2 gg = O<T>::to_d2(Pg[int64_t(row0 + b) * ld + row0 + a]);
+    const double2 gl = O<T>::to_d2(Pl[int64_t(row0 + b) * ld + row0 + a]);
+    re += (s1.x * gg.x - s1.y * gg.y) - (s2.x * gl.x - s2.y * gl.y);
+    im += (s1.x * gg.y + s1.y * gg.x) - (s2.x * gl.y + s2.y * gl.x);
+  }
+  __shared__ double rr[32], ri[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_down_sync(0xffffffffu, re, o);
+    im += __shfl_down_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rr[threadIdx.x >> 5] = re;
+    ri[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) {
+      re += rr[w];
+      im += ri[w];
+    }
+    out[e] = re;
+    if (out_im) out_im[e] = im;
+  }
+}
+
+template <typename T>
+void Kern<T>::current(const Work& w, int64_t offPl, int64_t offPg, int ld, int row0, int m, const double* sl,
+                      const double* sg, int64_t sstride, int64_t soff, double* out, double* out_im, cudaStream_t s) {
+  if (w.n_e <= 0 || m <= 0) return;
+  k_current<T><<<w.n_e, 256, 0, s>>>((const cx<T>*)w.arena, w.se, offPl, offPg, ld, row0, m, (const double2*)sl,
+                                     (const double2*)sg, sstride, soff, out, out_im);
+}
+
 template struct Kern<double>;
 template struct Kern<float>;
 template struct Kern<DF>;

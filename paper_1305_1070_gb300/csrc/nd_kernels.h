@@ -74,6 +74,8 @@ struct Kern {
                        const DelayTabs& dt, cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
                           cudaStream_t s);
+  static void current(const Work& w, int64_t offPl, int64_t offPg, int ld, int row0, int m, const double* sl,
+                      const double* sg, int64_t sstride, int64_t soff, double* out, double* out_im, cudaStream_t s);
   // tile edge (BM = BN) of the large and the small GEMM configuration
   static int gemm_tile(bool small);
 };

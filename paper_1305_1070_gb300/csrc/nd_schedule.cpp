@@ -103,6 +103,15 @@ void build_schedules(nd_plan* p) {
     int m = p->contact_ptr[c + 1] - p->contact_ptr[c];
     soff[c + 1] = soff[c] + m * m;
   }
+  p->contact_cluster.assign(p->n_contacts, -1);
+  p->contact_row.assign(p->n_contacts, 0);
+  p->contact_soff.assign(p->n_contacts, 0);
+  for (int c = 0; c < p->n_contacts; ++c) p->contact_soff[c] = soff[c];
+  for (int i = 0; i < nc; ++i)
+    for (auto& ct : cl[i].contacts) {
+      p->contact_cluster[ct.first] = i;
+      p->contact_row[ct.first] = ct.second;
+    }
   // ---- S1 assembly lists ----------------------------------------------------
   {
     std::vector<int> posB(p->n + p->n_virtual, -1);

@@ -87,6 +87,14 @@ class Solver:
     def singular_pivots(self) -> int:
         return ndgf.nd_fact_status(self.fact)
 
+    def current(self, contact: int, n_e: int):
+        """Terminal current spectrum i_c(E) = Tr[Sigma^<_c G^>_cc - Sigma^>_c G^<_cc] of the last step
+        (real and imaginary parts, the latter zero up to rounding)."""
+        re = torch.zeros(n_e, dtype=torch.float64, device=self.device)
+        im = torch.zeros(n_e, dtype=torch.float64, device=self.device)
+        ndgf.nd_contact_current(self.fact, contact, re, im)
+        return re, im
+
     def lead_status(self):
         """Per lead (n_unconverged, n_singular) of the decimation since the last query."""
         return [ndgf.nd_lead_status(lead) for lead in self.leads]
