@@ -758,7 +758,7 @@ template <> struct GemmCfg<double, true> { static constexpr int BM = 16, BN = 16
 template <> struct GemmCfg<float, false> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct GemmCfg<float, true> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
 template <> struct GemmCfg<DF, false> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
-template <> struct GemmCfg<DF, true> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1; };
+template <> struct GemmCfg<DF, true> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 2, TN = 2; };
 
 template <typename T> int Kern<T>::gemm_tile(bool small) {
   return small ? GemmCfg<T, true>::BM : GemmCfg<T, false>::BM;
@@ -799,8 +799,11 @@ void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, dou
   const int smem_max_n = cap < max_n ? cap : max_n;
   const size_t shm = base + size_t(smem_max_n) * smem_max_n * sizeof(cx<T>);
   if (shm > 48 * 1024) cudaFuncSetAttribute(k_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
-  k_inverse<T><<<dim3(count, w.n_e), 256, shm, s>>>(d, (cx<T>*)w.arena, w.se, (double2*)scratch, scratch_stride,
-                                                    n_singular, smem_max_n);
+  // the n x n update of every pivot step is spread over the CTA: large blocks
+  // (the few fronts near the root) get more threads
+  const int nt = max_n <= 64 ? 256 : (max_n <= 128 ? 512 : 1024);
+  k_inverse<T><<<dim3(count, w.n_e), nt, shm, s>>>(d, (cx<T>*)w.arena, w.se, (double2*)scratch, scratch_stride,
+                                                   n_singular, smem_max_n);
 }
 
 template <typename T, bool SMALL>
