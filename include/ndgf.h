@@ -288,7 +288,8 @@ void nd_lead_destroy(nd_lead* lead);
 /* Lesser/greater contact self-energies from the retarded ones (device arrays,
  * packed like nd_factor's sigma_r): Gamma_c = i (Sigma_c - Sigma_c^dagger),
  * Sigma^<_c = i f_c Gamma_c, Sigma^>_c = -i (1 - f_c) Gamma_c with the Fermi
- * function f_c = 1/(1 + exp((E - mu_c)/kT)).  m_c, mu: host [n_contacts]. */
+ * function f_c = 1/(1 + exp((E - mu_c)/kT)).  m_c, mu: host [n_contacts]; any
+ * number of contacts (a batch of devices in one graph has two per device). */
 nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, int32_t n_contacts,
                                 const int32_t* m_c, const double* mu, double kT,
                                 const double* energies, double* sigma_lesser,

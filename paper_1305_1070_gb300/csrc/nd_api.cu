@@ -840,18 +840,23 @@ extern "C" nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, i
                                            double* sigma_greater, void* stream) {
   if (!sigma_r || !m_c || !mu || !energies || n_e <= 0 || n_contacts <= 0 || !(kT > 0))
     return fail(ND_ERR_INVALID_ARG, "nd_sigma_lesser_fermi: bad argument");
-  if (n_contacts > MAX_CONTACTS) return fail(ND_ERR_UNSUPPORTED, "nd_sigma_lesser_fermi: too many contacts");
-  ContactTable ct{};
-  ct.n = n_contacts;
-  int64_t tot = 0;
+  std::vector<int64_t> off(n_contacts + 1, 0);
   for (int c = 0; c < n_contacts; ++c) {
     if (m_c[c] <= 0) return fail(ND_ERR_INVALID_ARG, "nd_sigma_lesser_fermi: contact size must be positive");
-    ct.m[c] = m_c[c];
-    ct.off[c] = tot;
-    ct.mu[c] = mu[c];
-    tot += int64_t(m_c[c]) * m_c[c];
+    off[c + 1] = off[c] + int64_t(m_c[c]) * m_c[c];
   }
-  launch_sigma_lesser(sigma_r, n_e, ct, kT, energies, tot, sigma_lesser, sigma_greater, (cudaStream_t)stream);
+  // contacts in groups of MAX_CONTACTS per launch, each with its offset in the packed arrays
+  for (int c0 = 0; c0 < n_contacts; c0 += MAX_CONTACTS) {
+    ContactTable ct{};
+    ct.n = std::min(MAX_CONTACTS, n_contacts - c0);
+    for (int j = 0; j < ct.n; ++j) {
+      ct.m[j] = m_c[c0 + j];
+      ct.off[j] = off[c0 + j];
+      ct.mu[j] = mu[c0 + j];
+    }
+    launch_sigma_lesser(sigma_r, n_e, ct, kT, energies, off[n_contacts], sigma_lesser, sigma_greater,
+                        (cudaStream_t)stream);
+  }
   ND_CUDA(cudaGetLastError());
   return ND_OK;
 }

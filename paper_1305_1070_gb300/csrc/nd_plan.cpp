@@ -145,6 +145,33 @@ struct Dissector {
       leaf_node(D, parent);
       return;
     }
+    // a set that falls apart (several devices in one graph, or a cut that
+    // isolated pieces) is dissected component by component under one parent
+    {
+      const int inD = ++tag;
+      for (int v : D) mark[v] = inD;
+      std::vector<std::vector<int>> comps;
+      for (int v0 : D) {
+        if (mark[v0] != inD) continue;
+        const int seen = ++tag;
+        std::vector<int> comp{v0};
+        mark[v0] = seen;
+        for (size_t h = 0; h < comp.size(); ++h)
+          for (int p = aptr[comp[h]]; p < aptr[comp[h] + 1]; ++p)
+            if (mark[adj[p]] == inD) {
+              mark[adj[p]] = seen;
+              comp.push_back(adj[p]);
+            }
+        comps.push_back(std::move(comp));
+      }
+      if (comps.size() > 1) {
+        for (auto& comp : comps) {
+          std::sort(comp.begin(), comp.end());
+          rec(std::move(comp), parent);
+        }
+        return;
+      }
+    }
     std::vector<double> key;
     keys(D, key);
     std::vector<double> sk = key;

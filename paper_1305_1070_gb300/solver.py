@@ -67,7 +67,9 @@ class Solver:
         for c, lead in enumerate(self.leads):
             ndgf.nd_lead_sigma(lead, E, n_e, tr.eta, self.sig_r, self.sigma_elems, int(self.off[c]))
         if self.leads:
-            ndgf.nd_sigma_lesser_fermi(self.sig_r, n_e, self.m_c, list(tr.mu), tr.kT, E, self.sig_l, self.sig_g)
+            # Fermi level per contact: the pattern of tr.mu repeats over the devices of a union
+            mu = [tr.mu[c % len(tr.mu)] for c in range(len(self.m_c))]
+            ndgf.nd_sigma_lesser_fermi(self.sig_r, n_e, self.m_c, mu, tr.kT, E, self.sig_l, self.sig_g)
         if self.ph:
             mu_ph = tr.mu_ph if tr.mu_ph is not None else 0.5 * (tr.mu[0] + tr.mu[1])
             ndgf.nd_phonon_const(self.n, n_e, tr.gamma_ph, mu_ph, tr.kT, E, self.ph_r, self.ph_l, self.ph_g)

@@ -287,6 +287,45 @@ def energy_grid(emin: float, emax: float, n_e: int) -> np.ndarray:
     return np.linspace(emin, emax, n_e)
 
 
+def union(devices, name: str = "union", gap_nm: float = 1.0e3) -> Device:
+    """Disjoint union of devices as one graph (block-diagonal H): sites of
+    device d follow those of devices 0..d-1; every device keeps its contacts
+    and leads; coordinates are shifted apart along the second axis by gap_nm
+    per device.  ``site_offsets[d]`` marks where device d starts."""
+    offs = np.concatenate([[0], np.cumsum([d.n for d in devices])]).astype(np.int64)
+    rowptr = [np.zeros(1, dtype=np.int64)]
+    colind, values, coords = [], [], []
+    for k, d in enumerate(devices):
+        rowptr.append(d.rowptr[1:].astype(np.int64) + rowptr[-1][-1])
+        colind.append(d.colind.astype(np.int64) + offs[k])
+        values.append(d.values)
+        c = d.coords.copy()
+        c[:, 1] += gap_nm * k
+        coords.append(c)
+    dev = Device(name=name, n=int(offs[-1]), rowptr=np.concatenate(rowptr).astype(np.int32),
+                 colind=np.concatenate(colind).astype(np.int32), values=np.concatenate(values),
+                 coords=np.concatenate(coords),
+                 layers=[l + offs[k] for k, d in enumerate(devices) for l in d.layers],
+                 contacts=[c + offs[k] for k, d in enumerate(devices) for c in d.contacts],
+                 leads=[l for d in devices for l in d.leads], transport_axis=devices[0].transport_axis)
+    dev.site_offsets = offs
+    return dev
+
+
+def uneven_batch(n_devices: int = 64, *, widths=(16, 32, 64, 96), lengths=(128, 1024), disorder: float = 0.02,
+                 seed: int | None = None) -> tuple:
+    """Superlattices of uneven size in one graph: width uniform over ``widths``,
+    length a uniform integer in [lengths[0], lengths[1]] (PCG64 stream of
+    ``seed``), onsite disorder from a seed per device.  Returns (union device,
+    list of the devices)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    W = rng.choice(np.asarray(widths), size=n_devices)
+    L = rng.integers(lengths[0], lengths[1] + 1, size=n_devices)
+    devs = [superlattice(int(l), int(w), disorder=disorder, seed=(seed or 0) * 1000 + k) for k, (l, w) in
+            enumerate(zip(L, W))]
+    return union(devs, name=f"uneven_{n_devices}"), devs
+
+
 SEED_BASE = 1305
 
 
@@ -297,6 +336,8 @@ def workload(name: str):
     superlattice_512x128  : 512 x 128 = 65,536 sites, disorder +-0.02 eV, 256 energies
     cnt_10_0_400          : (10,0) tube, 400 cells = 16,000 atoms, disorder +-0.1 eV,
                             phonon broadening 5 meV, 1,024 energies in [-1, 1] eV
+    uneven_64             : 64 superlattices in one graph, widths in {16, 32, 64, 96},
+                            lengths in [128, 1024], disorder +-0.02 eV, 64 energies in [0, 0.5] eV
     """
     if name == "superlattice_64x16":
         dev = superlattice(64, 16)
@@ -304,6 +345,9 @@ def workload(name: str):
     elif name == "superlattice_512x128":
         dev = superlattice(512, 128, disorder=0.02, seed=SEED_BASE + 1)
         tr = Transport(energies=energy_grid(0.0, 0.5, 256))
+    elif name == "uneven_64":
+        dev, _ = uneven_batch(64, seed=SEED_BASE + 3)
+        tr = Transport(energies=energy_grid(0.0, 0.5, 64))
     elif name == "cnt_10_0_400":
         dev = cnt_zigzag(400, disorder=0.1, seed=SEED_BASE + 2)
         tr = Transport(energies=energy_grid(-1.0, 1.0, 1024), gamma_ph=5e-3, mu_ph=0.05)

@@ -190,3 +190,22 @@ def test_delay_out_of_range_rejected():
     dev = workloads.superlattice(8, 4)
     with pytest.raises(RuntimeError):
         _plan_sets(dev, 8, 9)
+
+
+def test_union_of_devices_gets_one_tree_per_device():
+    """A disconnected graph is dissected component by component: a batch of
+    devices in one graph gives one root per device, and no cluster mixes
+    sites of two devices."""
+    devs = [workloads.superlattice(L, W, disorder=0.02, seed=L) for L, W in ((12, 4), (20, 8), (9, 6), (16, 5))]
+    dev = workloads.union(devs)
+    cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])]).astype(np.int32)
+    ci = np.concatenate(dev.contacts).astype(np.int32)
+    for coords in (dev.coords, None):
+        plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, coords, 16, 0, delay=2)
+        info = ndgf.nd_plan_query(plan)
+        assert info["n_roots"] == len(devs) and info["n_contacts"] == 2 * len(devs)
+        tree = ndgf.nd_plan_tree(plan)
+        owner = tree["cluster_of_site"]
+        device_of = np.searchsorted(dev.site_offsets, np.arange(dev.n), side="right") - 1
+        for c in range(info["n_clusters"]):
+            assert len(set(device_of[owner == c].tolist())) <= 1
