@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--chunk-fp64", type=int, default=64)
     ap.add_argument("--chunk-x2", type=int, default=128, help="energies per call of the FP32-pair path")
     ap.add_argument("--leaf", type=int, default=16, help="leaf size of the nested-dissection tree")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "uneven_64"],
+                    help="the headline workload, or the uneven 64-device batch (its own JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
     ap.add_argument("--growth-max", type=float, default=10.0, help="fold growth above which fp32x2 redoes in FP64")
     ap.add_argument("--delay", type=int, default=2, help="delayed pivots per cluster (0 = the paper's elimination)")
@@ -405,6 +407,97 @@ def main_ours(a) -> None:
         dist.destroy_process_group()
 
 
+def main_uneven(a) -> None:
+    """Row c4: 64 superlattices of uneven size (widths 16-96, lengths 128-1024,
+    1.82 M sites in all) in one graph, 64 energies; one tree per device, every
+    level launch spans all devices.  Prints its own JSON line (not the headline
+    metric): device-energy points per second of the FP32-pair path with
+    delayed pivots, gated on its density against the complex128 path."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1070_gb300 import ndgf, workloads
+    from paper_1305_1070_gb300.solver import Solver
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev, tr = workloads.workload("uneven_64")
+    n_dev = len(dev.site_offsets) - 1
+    n_e = tr.n_e
+    E_all = torch.as_tensor(tr.energies, device="cuda")
+    w = np.zeros(n_e)
+    d = np.diff(tr.energies)
+    w[:-1] += 0.5 * d
+    w[1:] += 0.5 * d
+    weights = torch.as_tensor(w, device="cuda")
+    dens = {}
+    res = {}
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    for name, prec, K, W in (("fp32x2", ndgf.ND_PREC_FP32X2, a.steps, max(1, min(a.warmup, 1))),
+                             ("fp64_nd", ndgf.ND_PREC_FP64, 1, 0)):
+        chunk = 4
+        s = Solver(dev, tr, precision=prec, max_ne=chunk, delay=a.delay, leaf_size=a.leaf)
+        out = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
+
+        def step():
+            for c0 in range(0, n_e, chunk):
+                _, l, _ = s.step(E_all[c0:c0 + chunk])
+                ndgf.nd_density(l, weights[c0:c0 + chunk].contiguous(), chunk, dev.n, 2.0 / (2.0 * np.pi),
+                                1 if c0 else 0, out)
+
+        for _ in range(W):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(K):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / K
+        ndgf.nd_profile(s.fact, True)
+        step()
+        torch.cuda.synchronize()
+        prof = ndgf.nd_profile(s.fact, False)
+        dens[name] = out.clone()
+        res[name] = {"ms_per_step": round(ms, 1), "device_energies_per_s": round(n_dev * n_e / (ms * 1e-3), 2),
+                     "useful_tflops": round((s.info["flops_factor"] + s.info["flops_green_r"] +
+                                             s.info["flops_green_lesser"]) * n_e / (ms * 1e-3) / 1e12, 3),
+                     "gemm": [p for p in prof if p["name"] == "gemm"][0]}
+        del s
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    err = float((dens["fp32x2"] - dens["fp64_nd"]).abs().max() / dens["fp64_nd"].abs().max())
+    g = res["fp32x2"]["gemm"]
+    ach = g["flops"] / (g["ms"] * 1e-3) / 1e12
+    peak = 152 * 128 * 2 * 2070e6 / 1e12 * 8.0 / 72.0
+    # CPU oracle: block RGF of the first devices at one energy
+    t0 = time.perf_counter()
+    from oracle import rgf
+    devs_done = 0
+    _, devs = workloads.uneven_batch(64, seed=workloads.SEED_BASE + 3)
+    for sub in devs[:2]:
+        rgf.RGF(sub, tr).solve(float(tr.energies[n_e // 2]))
+        devs_done += 1
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "device-energy points/sec, 64 uneven superlattices in one graph (mixed, rel density err vs FP64 <= 1e-6)",
+            "value": res["fp32x2"]["device_energies_per_s"], "unit": "device-energies/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": 1, "ms_per_step": res["fp32x2"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32x2 (FP32-pair complex) + c128 root",
+            "data": "synthetic (seeded uneven superlattice batch, PCG64 seed 1308)",
+            "config": {"workload": "uneven_64", "devices": n_dev, "sites": dev.n, "energies": n_e,
+                       "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": 4},
+            "paths": res, "density_rel_err_fp32x2_vs_fp64": err, "gate_1e-6": err <= GATE,
+            "roofline": {"kernel": "complex-fp32x2:gemm", "bound": "alu", "achieved": round(ach, 3),
+                         "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None},
+            "clocks": clocks,
+            "cpu_baseline": {"value": round(devs_done / cpu_s, 4), "unit": "device-energies/s",
+                             "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"block RGF (oracle/rgf.py), {devs_done} devices at one energy, {cpu_s:.1f} s"}}
+    print(json.dumps(line), flush=True)
+
+
 def main_reference(a) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -435,5 +528,7 @@ if __name__ == "__main__":
         cpu_worker(args.cpu_worker, args.cpu_save)
     elif args.impl == "reference":
         main_reference(args)
+    elif args.workload == "uneven_64":
+        main_uneven(args)
     else:
         main_ours(args)

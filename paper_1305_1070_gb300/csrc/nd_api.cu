@@ -348,12 +348,9 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   } while (0)
   TRY(dalloc(f, &f->arena, size_t(f->se) * f->esize * max_ne));
   TRY(dalloc(f, &f->aux, size_t(std::max<int64_t>(1, 2 * p->sigma_elems)) * f->esize * max_ne));
-  if (precision != ND_PREC_FP64) {
-    int64_t rmax = 0;
-    for (const auto& c : p->cl)
-      if (c.b == 0) rmax = std::max<int64_t>(rmax, int64_t(c.n) * c.n);
-    f->root_stride = rmax;
-    TRY(dalloc(f, (void**)&f->root_scratch, size_t(rmax) * 16 * max_ne));
+  if (precision != ND_PREC_FP64) {  // one complex128 region per root block and energy
+    f->root_stride = p->root_scratch_elems;
+    TRY(dalloc(f, (void**)&f->root_scratch, size_t(p->root_scratch_elems) * 16 * max_ne));
   }
   TRY(dalloc(f, (void**)&f->d_status, sizeof(int)));
   cudaMemset(f->d_status, 0, sizeof(int));

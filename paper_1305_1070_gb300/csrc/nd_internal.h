@@ -71,6 +71,7 @@ struct InvDesc {
   int32_t n, ld;
   int32_t cluster;
   int32_t fp64; // 1: invert in complex128 even on the mixed path
+  int64_t scr;  // fp64 blocks: offset of this block's complex128 scratch within an energy's
 };
 
 enum : int32_t { OP_N = 0, OP_T = 1, OP_C = 2, OP_H = 3 };
@@ -211,6 +212,7 @@ struct nd_plan {
   int64_t arena_elems = 0;         // complex elements per energy (base regions)
   int64_t ext_elems[2] = {0, 0};   // extra elements of the G^< blocks, per variant
   int64_t sigma_elems = 0;         // sum_c m_c^2
+  int64_t root_scratch_elems = 0;  // complex128 scratch of the root blocks per energy (single-precision paths)
   double flops_factor = 0, flops_green_r = 0, flops_green_lesser = 0;
 
   // device-independent descriptor tables (uploaded by nd_fact_create)

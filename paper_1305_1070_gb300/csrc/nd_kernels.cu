@@ -90,7 +90,7 @@ __global__ void k_inverse(const InvDesc* __restrict__ descs, cx<T>* arena, int64
   const size_t r_off = colk_off + size_t(d.n) * sizeof(double2);
   const int64_t nn = int64_t(d.n) * d.n;
   if (!std::is_same<T, double>::value && d.fp64 && scratch) {  // root block in complex128
-    double2* W = scratch + int64_t(e) * scratch_stride;
+    double2* W = scratch + int64_t(e) * scratch_stride + d.scr;
     for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = O<T>::to_d2(M[(i / d.n) * d.ld + i % d.n]);
     __syncthreads();
     gj_invert2<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off),

@@ -84,6 +84,7 @@ void build_schedules(nd_plan* p) {
   auto& cl = p->cl;
   const int nc = int(cl.size());
   std::vector<int32_t> site_begin(nc), map_begin(nc);
+  p->root_scratch_elems = 0;
   p->unk_q.clear();
   p->unk_r.clear();
   for (int i = 0; i < nc; ++i) {
@@ -181,7 +182,14 @@ void build_schedules(nd_plan* p) {
     B.begin(&p->sched_factor, ST_INVERSE);
     for (int i : lev[l]) {
       const Cluster& c = cl[i];
-      p->inv_desc.push_back(InvDesc{c.off_F, c.n, c.n + c.b, i, c.b == 0 ? 1 : 0});
+      // roots are inverted in complex128 on the single-precision paths, each in
+      // its own scratch region (several roots share a launch in a batch of devices)
+      int64_t scr = 0;
+      if (c.b == 0) {
+        scr = p->root_scratch_elems;
+        p->root_scratch_elems += int64_t(c.n) * c.n;
+      }
+      p->inv_desc.push_back(InvDesc{c.off_F, c.n, c.n + c.b, i, c.b == 0 ? 1 : 0, scr});
       B.dim(c.n);
     }
     B.end();

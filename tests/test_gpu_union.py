@@ -50,3 +50,24 @@ def test_union_matches_each_device(precision, tol):
                                                              full["Gl"][np.ix_(idx, idx)], full["Gg"][np.ix_(idx, idx)]))
                 assert abs(cur[2 * d + c][e] - i_ref) <= tol * max(1e-3, abs(i_ref))
     print(f"union precision {precision}: worst {worst:.3e}")
+
+
+@pytest.mark.parametrize("precision,tol", [(ndgf.ND_PREC_FP32X2, 1e-9), (ndgf.ND_PREC_MIXED, 1e-3)])
+def test_union_roots_in_one_launch(precision, tol):
+    """Six devices of one shape: their roots sit on one tree level and are
+    inverted in one launch, each in its own complex128 scratch region."""
+    from paper_1305_1070_gb300.solver import Solver
+    devs = [workloads.superlattice(14, 6, disorder=0.05, seed=100 + k) for k in range(6)]
+    dev = workloads.union(devs)
+    tr = workloads.Transport(energies=np.array([0.11, 0.37]), mu=(0.25, 0.0), kT=0.03)
+    s = Solver(dev, tr, precision=precision, leaf_size=16, delay=2)
+    Gr, Gl, Gg = s.step(tr.energies)
+    torch.cuda.synchronize()
+    assert s.singular_pivots() == 0
+    got = {"Gr": Gr.cpu().numpy(), "Gl": Gl.cpu().numpy(), "Gg": Gg.cpu().numpy()}
+    for d, sub in enumerate(devs):
+        lo, hi = dev.site_offsets[d], dev.site_offsets[d + 1]
+        ref = dense.green_diag(sub, tr)
+        for k in ("Gr", "Gl", "Gg"):
+            for e in range(tr.n_e):
+                assert observables.rel_err(got[k][e, lo:hi], ref[k][e]) <= tol, (d, k, e)
