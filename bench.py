@@ -55,8 +55,9 @@ def parse():
     ap.add_argument("--chunk-fp64", type=int, default=64)
     ap.add_argument("--chunk-x2", type=int, default=128, help="energies per call of the FP32-pair path")
     ap.add_argument("--leaf", type=int, default=16, help="leaf size of the nested-dissection tree")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "uneven_64"],
-                    help="the headline workload, or the uneven 64-device batch (its own JSON line)")
+    ap.add_argument("--chunk-aux", type=int, default=0, help="energies per call for the other workloads (0: default)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "uneven_64", "cnt_10_0_400"],
+                    help="the headline workload, or another one (its own JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
     ap.add_argument("--growth-max", type=float, default=10.0, help="fold growth above which fp32x2 redoes in FP64")
     ap.add_argument("--delay", type=int, default=2, help="delayed pivots per cluster (0 = the paper's elimination)")
@@ -69,6 +70,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-save", default="", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-world", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -81,11 +83,15 @@ def oracle_pick(n_e: int, n_energies: int):
     return np.linspace(0, n_e - 1, n_energies).round().astype(int)
 
 
-def cpu_worker(n_energies: int, save: str) -> None:
+def cpu_worker(n_energies: int, save: str, world: int = 1) -> None:
     import numpy as np
     from oracle import rgf
+    from paper_1305_1070_gb300 import dist as ndist
     from paper_1305_1070_gb300 import workloads
     dev, tr = workloads.workload(WORKLOAD)
+    if world > 1:  # rank 0's block of the finer grid of a multi-GPU run
+        grid = ndist.global_grid(float(tr.energies[0]), float(tr.energies[-1]), tr.n_e, world)
+        tr.energies = grid[ndist.shard(len(grid), 0, world)]
     pick = oracle_pick(tr.n_e, n_energies)
     solver = rgf.RGF(dev, tr)
     res = []
@@ -98,12 +104,14 @@ def cpu_worker(n_energies: int, save: str) -> None:
     print(json.dumps({"energies": int(n_energies), "seconds": dt}))
 
 
-def run_cpu_oracle(n_energies: int, save: str = "") -> dict:
+def run_cpu_oracle(n_energies: int, save: str = "", world: int = 1) -> dict:
     cores = os.cpu_count() or 1
     env = dict(os.environ, OPENBLAS_NUM_THREADS=str(cores), OMP_NUM_THREADS=str(cores), MKL_NUM_THREADS=str(cores))
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", str(n_energies)]
     if save:
         cmd += ["--cpu-save", save]
+    if world > 1:
+        cmd += ["--cpu-world", str(world)]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True, check=True)
     out = json.loads(r.stdout.strip().splitlines()[-1])
     out["cores"] = cores
@@ -158,15 +166,20 @@ def main_ours(a) -> None:
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
+    from paper_1305_1070_gb300 import dist as ndist
     dev, tr = workloads.workload(WORKLOAD)
+    # weak scaling: every rank keeps the batch size, the grid over [0, 0.5] eV
+    # gets finer with the ranks; each integrates its block with the global
+    # trapezoid weights and one all-reduce sums the density
+    grid = ndist.global_grid(float(tr.energies[0]), float(tr.energies[-1]), tr.n_e, world)
+    mine = ndist.shard(len(grid), rank, world)
+    tr.energies = grid[mine]
+    w = ndist.trapezoid_weights(grid)[mine]
     if a.energies:
         tr.energies = tr.energies[:a.energies]
+        w = w[:a.energies]
     n_e = tr.n_e
     E_all = torch.as_tensor(tr.energies, device="cuda")
-    w = np.zeros(n_e)
-    d = np.diff(tr.energies)
-    w[:-1] += 0.5 * d
-    w[1:] += 0.5 * d
     weights = torch.as_tensor(w, device="cuda")
     scale = 2.0 / (2.0 * np.pi)
 
@@ -212,6 +225,8 @@ def main_ours(a) -> None:
                     for c in range(2):
                         cur[c, sel] = fallback.current(c, int(sel.numel()))[0]
             ndgf.nd_density(Gl, weights, n_e, n, scale, 0, dens)
+            if world > 1:
+                ndist.reduce_sum(dens)
             cert_max[name] = cmax
             redo[name] = nredo
         return step
@@ -363,7 +378,7 @@ def main_ours(a) -> None:
 
     if rank == 0:
         save = os.path.join(tempfile.gettempdir(), f"ndgf_oracle_{os.getpid()}.npz")
-        cpu = run_cpu_oracle(a.cpu_sample, save) if not a.no_cpu else {"energies": 0, "seconds": 1.0, "cores": 0}
+        cpu = run_cpu_oracle(a.cpu_sample, save, world) if not a.no_cpu else {"energies": 0, "seconds": 1.0, "cores": 0}
         cpu_val = cpu["energies"] / cpu["seconds"]
         if not a.no_cpu:  # every path against the oracle at the sampled energies, all sites
             ref = np.load(save)
@@ -382,7 +397,9 @@ def main_ours(a) -> None:
             "dtype": ("fp32x2 (FP32-pair complex) + c128 root" + (" and redo" if paths["fp32x2"]["fp64_redo_energies"] else ""))
             if gate else "c128",
             "data": "synthetic (seeded superlattice, PCG64 seed 1306)",
-            "config": {"workload": WORKLOAD, "sites": n, "energies_per_gpu": n_e, "clusters": info["n_clusters"],
+            "config": {"workload": WORKLOAD, "sites": n, "energies_per_gpu": n_e,
+                       "energy_grid": f"{len(grid)} energies in [0, 0.5] eV, a block of {n_e} per GPU",
+                       "clusters": info["n_clusters"],
                        "levels": info["n_levels"], "leaf_size": a.leaf, "eta": tr.eta, "path": head,
                        "delayed_pivots_per_cluster": a.delay,
                        "l2": "inputs larger than L2 (~100-200 GB workspace per step)"},
@@ -407,12 +424,24 @@ def main_ours(a) -> None:
         dist.destroy_process_group()
 
 
-def main_uneven(a) -> None:
-    """Row c4: 64 superlattices of uneven size (widths 16-96, lengths 128-1024,
-    1.82 M sites in all) in one graph, 64 energies; one tree per device, every
-    level launch spans all devices.  Prints its own JSON line (not the headline
-    metric): device-energy points per second of the FP32-pair path with
-    delayed pivots, gated on its density against the complex128 path."""
+AUX = {
+    "uneven_64": dict(metric="device-energy points/sec, 64 uneven superlattices in one graph (mixed, rel density err "
+                             "vs FP64 <= 1e-6)", unit="device-energies/s", chunk=4,
+                      data="synthetic (seeded uneven superlattice batch, PCG64 seed 1308)"),
+    "cnt_10_0_400": dict(metric="energy points/sec for diag G^r,G^< of the (10,0) nanotube, 16,000 atoms, phonon "
+                                "broadening (mixed, rel density err vs FP64 <= 1e-6)", unit="energies/s", chunk=512,
+                         data="synthetic (seeded (10,0) tube, PCG64 seed 1307)"),
+}
+
+
+def main_aux(a) -> None:
+    """The other workloads (their own JSON line, not the headline metric):
+    uneven_64 = 64 superlattices of uneven size (widths 16-96, lengths
+    128-1024, 1.82 M sites in all) in one graph, 64 energies, one tree per
+    device and every level launch spanning all devices; cnt_10_0_400 = the
+    (10,0) tube, 1,024 energies, decimated leads, constant phonon broadening.
+    FP32-pair path with delayed pivots, gated on its density against the
+    complex128 path."""
     import numpy as np
     import torch
 
@@ -421,9 +450,10 @@ def main_uneven(a) -> None:
     from paper_1305_1070_gb300 import ndgf, workloads
     from paper_1305_1070_gb300.solver import Solver
 
+    cfg = AUX[a.workload]
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    dev, tr = workloads.workload("uneven_64")
-    n_dev = len(dev.site_offsets) - 1
+    dev, tr = workloads.workload(a.workload)
+    n_dev = len(dev.site_offsets) - 1 if hasattr(dev, "site_offsets") else 1
     n_e = tr.n_e
     E_all = torch.as_tensor(tr.energies, device="cuda")
     w = np.zeros(n_e)
@@ -434,17 +464,17 @@ def main_uneven(a) -> None:
     dens = {}
     res = {}
     clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    chunk = min(a.chunk_aux or cfg["chunk"], n_e)
     for name, prec, K, W in (("fp32x2", ndgf.ND_PREC_FP32X2, a.steps, max(1, min(a.warmup, 1))),
                              ("fp64_nd", ndgf.ND_PREC_FP64, 1, 0)):
-        chunk = 4
         s = Solver(dev, tr, precision=prec, max_ne=chunk, delay=a.delay, leaf_size=a.leaf)
         out = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
 
         def step():
             for c0 in range(0, n_e, chunk):
-                _, l, _ = s.step(E_all[c0:c0 + chunk])
-                ndgf.nd_density(l, weights[c0:c0 + chunk].contiguous(), chunk, dev.n, 2.0 / (2.0 * np.pi),
-                                1 if c0 else 0, out)
+                m = min(chunk, n_e - c0)
+                _, l, _ = s.step(E_all[c0:c0 + m])
+                ndgf.nd_density(l, weights[c0:c0 + m].contiguous(), m, dev.n, 2.0 / (2.0 * np.pi), 1 if c0 else 0, out)
 
         for _ in range(W):
             step()
@@ -461,7 +491,7 @@ def main_uneven(a) -> None:
         torch.cuda.synchronize()
         prof = ndgf.nd_profile(s.fact, False)
         dens[name] = out.clone()
-        res[name] = {"ms_per_step": round(ms, 1), "device_energies_per_s": round(n_dev * n_e / (ms * 1e-3), 2),
+        res[name] = {"ms_per_step": round(ms, 1), "points_per_s": round(n_dev * n_e / (ms * 1e-3), 2),
                      "useful_tflops": round((s.info["flops_factor"] + s.info["flops_green_r"] +
                                              s.info["flops_green_lesser"]) * n_e / (ms * 1e-3) / 1e12, 3),
                      "gemm": [p for p in prof if p["name"] == "gemm"][0]}
@@ -472,29 +502,26 @@ def main_uneven(a) -> None:
     g = res["fp32x2"]["gemm"]
     ach = g["flops"] / (g["ms"] * 1e-3) / 1e12
     peak = 152 * 128 * 2 * 2070e6 / 1e12 * 8.0 / 72.0
-    # CPU oracle: block RGF of the first devices at one energy
-    t0 = time.perf_counter()
+    # CPU oracle: block RGF at one energy (of the first two devices of a batch)
     from oracle import rgf
-    devs_done = 0
-    _, devs = workloads.uneven_batch(64, seed=workloads.SEED_BASE + 3)
-    for sub in devs[:2]:
+    subs = workloads.uneven_batch(64, seed=workloads.SEED_BASE + 3)[1][:2] if n_dev > 1 else [dev]
+    t0 = time.perf_counter()
+    for sub in subs:
         rgf.RGF(sub, tr).solve(float(tr.energies[n_e // 2]))
-        devs_done += 1
     cpu_s = time.perf_counter() - t0
-    line = {"metric": "device-energy points/sec, 64 uneven superlattices in one graph (mixed, rel density err vs FP64 <= 1e-6)",
-            "value": res["fp32x2"]["device_energies_per_s"], "unit": "device-energies/s", "n_gpus": 1,
+    line = {"metric": cfg["metric"], "value": res["fp32x2"]["points_per_s"], "unit": cfg["unit"], "n_gpus": 1,
             "steps": a.steps, "warmup": 1, "ms_per_step": res["fp32x2"]["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32x2 (FP32-pair complex) + c128 root",
-            "data": "synthetic (seeded uneven superlattice batch, PCG64 seed 1308)",
-            "config": {"workload": "uneven_64", "devices": n_dev, "sites": dev.n, "energies": n_e,
-                       "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": 4},
+            "data": cfg["data"],
+            "config": {"workload": a.workload, "devices": n_dev, "sites": dev.n, "energies": n_e,
+                       "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": chunk},
             "paths": res, "density_rel_err_fp32x2_vs_fp64": err, "gate_1e-6": err <= GATE,
             "roofline": {"kernel": "complex-fp32x2:gemm", "bound": "alu", "achieved": round(ach, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None},
             "clocks": clocks,
-            "cpu_baseline": {"value": round(devs_done / cpu_s, 4), "unit": "device-energies/s",
-                             "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"block RGF (oracle/rgf.py), {devs_done} devices at one energy, {cpu_s:.1f} s"}}
+            "cpu_baseline": {"value": round(len(subs) / cpu_s, 4), "unit": cfg["unit"], "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"block RGF (oracle/rgf.py), {len(subs)} device(s) at one energy, {cpu_s:.1f} s"}}
     print(json.dumps(line), flush=True)
 
 
@@ -525,10 +552,10 @@ def main_reference(a) -> None:
 if __name__ == "__main__":
     args = parse()
     if args.cpu_worker:
-        cpu_worker(args.cpu_worker, args.cpu_save)
+        cpu_worker(args.cpu_worker, args.cpu_save, args.cpu_world)
     elif args.impl == "reference":
         main_reference(args)
-    elif args.workload == "uneven_64":
-        main_uneven(args)
+    elif args.workload != WORKLOAD:
+        main_aux(args)
     else:
         main_ours(args)
