@@ -78,6 +78,9 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
  * launch, ND_FACT_GEMM_ALU never uses them. */
 #define ND_FACT_GEMM_TC 8
 #define ND_FACT_GEMM_ALU 16
+/* Reserve the workspace of nd_density_gradient (M right-hand sides per
+ * cluster, M = number of contact sites). */
+#define ND_FACT_ADJOINT 32
 
 /* Sparsity pattern of H plus the contact site sets (host arrays).
  * rowptr[n+1], colind[nnz]: CSR pattern, 0-based, must be structurally
@@ -213,6 +216,23 @@ nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double*
  * Entries 2 and 3 are 0 when G^< was not computed.  cert: [n_e][8] doubles,
  * host or device.  Stream ordered after the nd_diag_green call. */
 nd_status nd_certificate(nd_fact* fact, double* cert, void* stream);
+
+/* Adjoint of the density (spec extension; the paper computes the
+ * density only): for every energy of the last nd_factor / nd_diag_green pair
+ * and every site k,
+ *     t_k(E) = sum_{a,b in contacts} Sigma^<_ab conj(U_kb) conj(Z_ka),
+ *     U = G^r[:, contact sites],  Z = G^r diag(c) conj(U),
+ * so that for L = sum_j c_j n_j with n_j = (1/pi) sum_E w_E Im G^<_jj(E) and
+ * H_kk = H0_kk + V_k (dA/dV_k = -e_k e_k^T):
+ *     dL/dV_k = (2/pi) sum_E w_E Im t_k(E)       (nd_density with scale 2/pi).
+ * U and Z come from two solves with the stored factorization (upward sweep
+ * RB += Psi^T XI, downward XS = A_ii^{-1} XI + Psi XB), in the workspace's
+ * precision.  c: [n] real weights (host or device, caller order);
+ * t_out: device [n_e][n] complex.  Needs a workspace created with
+ * ND_FACT_ADJOINT, a preceding nd_diag_green given Sigma^<, no phonon
+ * Sigma^< (its support is every site) and at most 8 contacts.
+ * Errors: ND_ERR_INVALID_ARG, ND_ERR_UNSUPPORTED. */
+nd_status nd_density_gradient(nd_fact* fact, const double* c, double* t_out, void* stream);
 
 /* S10 terminal current spectrum of one contact (Meir-Wingreen; paper Sec. 1,
  * the current is the physical output next to the density):

@@ -121,6 +121,18 @@ struct nd_fact {
   const double *cur_H = nullptr, *cur_sr = nullptr, *cur_ph = nullptr, *cur_E = nullptr;
   const double *cur_sl = nullptr, *cur_sg = nullptr, *cur_pl = nullptr;
   double* d_current = nullptr;  // [max_ne][2]: Re and Im of the last current spectrum
+  // adjoint solves (ND_FACT_ADJOINT)
+  bool adj = false;
+  int64_t adj_base = 0;
+  std::vector<Step> sched_adj_fwd, sched_adj_bwd;
+  std::vector<TileRange> tr_adj_fwd, tr_adj_bwd;
+  std::vector<double> step_flops_adj_fwd, step_flops_adj_bwd;
+  RowsDesc* d_rows_adj = nullptr;
+  AdjDesc* d_adj_desc = nullptr;
+  int n_adj_desc = 0;
+  int64_t* d_ones = nullptr;
+  int n_ones = 0;
+  double* d_cvec = nullptr;
   bool have_lesser = false;
   double* d_cert = nullptr;
   int32_t *d_cert_ptr = nullptr, *d_cert_terms = nullptr, *d_cl_ldG2 = nullptr;
@@ -282,6 +294,10 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
       case ST_LOC:
         launch_loc(f->d_loc + st.begin, st.count, w.n_e, dt, s);
         break;
+      case ST_ROWS_ADD:
+      case ST_ROWS_GATHER:
+        Kern<T>::rows(w, f->d_rows_adj + st.begin, st.count, f->d_maps, p->adj_cols, st.kind == ST_ROWS_GATHER, dt, s);
+        break;
     }
     if (f->prof.on) {
       cudaEventRecord(rec.b, s);
@@ -294,14 +310,16 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
 
 // Algorithmic flops per energy of every step (8 per complex multiply-add for
 // GEMMs, n^3 complex multiply-adds per inverse); 0 for data movement steps.
-std::vector<double> step_flops(const nd_plan* p, const std::vector<Step>& sched) {
+std::vector<double> step_flops(const nd_plan* p, const std::vector<Step>& sched,
+                               const std::vector<GemmDesc>* gemms = nullptr) {
+  const std::vector<GemmDesc>& gd = gemms ? *gemms : p->gemm_desc;
   std::vector<double> out(sched.size(), 0.0);
   for (size_t si = 0; si < sched.size(); ++si) {
     const Step& st = sched[si];
     double f = 0.0;
     if (st.kind == ST_GEMM)
       for (int k = st.begin; k < st.begin + st.count; ++k) {
-        const GemmDesc& g = p->gemm_desc[k];
+        const GemmDesc& g = gd[k];
         f += 8.0 * double(g.m) * g.n * g.k;
       }
     if (st.kind == ST_INVERSE)
@@ -317,6 +335,110 @@ std::vector<double> step_flops(const nd_plan* p, const std::vector<Step>& sched)
     out[si] = f;
   }
   return out;
+}
+
+// Schedules of the adjoint solves (nd_density_gradient), appended to the
+// GEMM table: per level, upward RB += Psi^T XI then the rows of RB into the
+// parent (one launch per child slot); downward the boundary rows from the
+// parent, XS = A_ii^{-1} XI, XS += Psi XB.  Offsets are per-energy elements,
+// `base` the start of the adjoint blocks in the workspace.
+void build_adjoint(const nd_plan* p, int64_t base, std::vector<GemmDesc>& gemms, std::vector<RowsDesc>& rows,
+                   std::vector<Step>& fwd, std::vector<Step>& bwd, std::vector<AdjDesc>& adesc,
+                   std::vector<int64_t>& ones) {
+  const auto& cl = p->cl;
+  const int nc = int(cl.size());
+  const int M = p->adj_cols;
+  std::vector<int32_t> site_begin(nc), map_begin(nc);
+  int32_t sb = 0, mb = 0;
+  for (int i = 0; i < nc; ++i) {
+    site_begin[i] = sb;
+    map_begin[i] = mb;
+    sb += cl[i].nf();
+    mb += int32_t(cl[i].map.size());
+  }
+  std::vector<std::vector<int>> lev(p->n_levels + 1);
+  int max_slot = 0;
+  for (int i = 0; i < nc; ++i) {
+    lev[cl[i].level].push_back(i);
+    max_slot = std::max(max_slot, cl[i].slot);
+  }
+  auto gemm = [&](int64_t C, int ldc, int64_t D, int ldd, int64_t A, int lda, int opA, int64_t B, int ldb, int m,
+                  int n, int k, double beta) {
+    GemmDesc g{};
+    g.offA = A; g.offB = B; g.offC = C; g.offD = D;
+    g.m = m; g.n = n; g.k = k;
+    g.lda = lda; g.ldb = ldb; g.ldc = ldc; g.ldd = ldd;
+    g.opA = opA; g.opB = OP_N;
+    g.alpha = 1.0; g.beta = beta;
+    gemms.push_back(g);
+  };
+  auto step = [&](std::vector<Step>& S, int kind, int begin, int end, int dim) {
+    if (end > begin) S.push_back(Step{kind, begin, end - begin, dim});
+  };
+  for (int l = 1; l <= p->n_levels; ++l) {
+    int b0 = int(gemms.size()), dim = 0;
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0 || c.n == 0) continue;
+      gemm(base + c.adj_RB, M, base + c.adj_RB, M, c.off_Psi, c.b, OP_T, base + c.adj_XI, M, c.b, M, c.n, 1.0);
+      dim = std::max(dim, std::max(c.b, M));
+    }
+    step(fwd, ST_GEMM, b0, int(gemms.size()), dim);
+    for (int sl = 0; sl <= max_slot; ++sl) {
+      int r0 = int(rows.size());
+      dim = 0;
+      for (int i : lev[l]) {
+        const Cluster& c = cl[i];
+        if (c.b == 0 || c.slot != sl) continue;
+        const Cluster& P = cl[c.parent];
+        rows.push_back(RowsDesc{base + c.adj_RB, base + P.adj_XI, base + P.adj_RB, c.b, P.n, P.k,
+                                site_begin[c.parent], map_begin[i]});
+        dim = std::max(dim, c.b);
+      }
+      step(fwd, ST_ROWS_ADD, r0, int(rows.size()), dim);
+    }
+  }
+  for (int l = p->n_levels; l >= 1; --l) {
+    int r0 = int(rows.size()), dim = 0;
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0) continue;
+      const Cluster& P = cl[c.parent];
+      rows.push_back(RowsDesc{base + c.adj_XB, base + P.adj_XS, base + P.adj_XB, c.b, P.n, P.k, site_begin[c.parent],
+                              map_begin[i]});
+      dim = std::max(dim, c.b);
+    }
+    step(bwd, ST_ROWS_GATHER, r0, int(rows.size()), dim);
+    int b0 = int(gemms.size());
+    dim = 0;
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.n == 0) continue;
+      gemm(base + c.adj_XS, M, base + c.adj_XS, M, c.off_F, c.n + c.b, OP_N, base + c.adj_XI, M, c.n, M, c.n, 0.0);
+      dim = std::max(dim, std::max(c.n, M));
+    }
+    step(bwd, ST_GEMM, b0, int(gemms.size()), dim);
+    b0 = int(gemms.size());
+    dim = 0;
+    for (int i : lev[l]) {
+      const Cluster& c = cl[i];
+      if (c.b == 0 || c.n == 0) continue;
+      gemm(base + c.adj_XS, M, base + c.adj_XS, M, c.off_Psi, c.b, OP_N, base + c.adj_XB, M, c.n, M, c.b, 1.0);
+      dim = std::max(dim, std::max(c.n, M));
+    }
+    step(bwd, ST_GEMM, b0, int(gemms.size()), dim);
+  }
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = cl[i];
+    adesc.push_back(AdjDesc{base + c.adj_XI, base + c.adj_RB, base + c.adj_XS, base + c.adj_U, c.n, c.b,
+                            site_begin[i], 0});
+  }
+  for (int ct = 0; ct < p->n_contacts; ++ct) {
+    const Cluster& c = cl[p->contact_cluster[ct]];
+    const int m = p->contact_ptr[ct + 1] - p->contact_ptr[ct];
+    for (int a = 0; a < m; ++a)
+      ones.push_back(base + c.adj_XI + int64_t(p->contact_row[ct] + a) * M + p->contact_ptr[ct] + a);
+  }
 }
 
 }  // namespace
@@ -337,6 +459,11 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   f->esize = precision == ND_PREC_MIXED ? 8 : 16;
   f->flags = flags;
   f->se = p->arena_elems + ((flags & ND_FACT_PHONON) ? std::max(p->ext_elems[0], p->ext_elems[1]) : p->ext_elems[0]);
+  if (flags & ND_FACT_ADJOINT) {  // the adjoint blocks follow the rest of each energy's workspace
+    f->adj = true;
+    f->adj_base = f->se;
+    f->se += p->adj_elems;
+  }
   nd_status st;
 #define TRY(x)          \
   do {                  \
@@ -360,7 +487,22 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dupload(f, p->ent_src, &f->d_ent_src));
   TRY(dupload(f, p->asm_desc, &f->d_asm));
   TRY(dupload(f, p->inv_desc, &f->d_inv));
-  TRY(dupload(f, p->gemm_desc, &f->d_gemm));
+  std::vector<GemmDesc> gemm_all = p->gemm_desc;
+  if (f->adj) {
+    std::vector<RowsDesc> rows;
+    std::vector<AdjDesc> adesc;
+    std::vector<int64_t> ones;
+    build_adjoint(p, f->adj_base, gemm_all, rows, f->sched_adj_fwd, f->sched_adj_bwd, adesc, ones);
+    TRY(dupload(f, rows, &f->d_rows_adj));
+    TRY(dupload(f, adesc, &f->d_adj_desc));
+    TRY(dupload(f, ones, &f->d_ones));
+    f->n_adj_desc = int(adesc.size());
+    f->n_ones = int(ones.size());
+    TRY(dalloc(f, (void**)&f->d_cvec, size_t(std::max(1, p->n)) * sizeof(double)));
+    f->step_flops_adj_fwd = step_flops(p, f->sched_adj_fwd, &gemm_all);
+    f->step_flops_adj_bwd = step_flops(p, f->sched_adj_bwd, &gemm_all);
+  }
+  TRY(dupload(f, gemm_all, &f->d_gemm));
   TRY(dupload(f, p->scat_desc, &f->d_scat));
   TRY(dupload(f, p->gath_desc, &f->d_gath));
   TRY(dupload(f, p->diag_g, &f->d_diag_g));
@@ -419,6 +561,10 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
     build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_green);
     build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_lesser[0]);
     build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_lesser[1]);
+    if (f->adj) {
+      build_tiles(f->sched_adj_fwd, gemm_all, tl, ts, flags, sc, ttc, tiles, f->tr_adj_fwd);
+      build_tiles(f->sched_adj_bwd, gemm_all, tl, ts, flags, sc, ttc, tiles, f->tr_adj_bwd);
+    }
     TRY(dupload(f, tiles, &f->d_tiles));
   }
   const size_t ne = size_t(max_ne), n = size_t(p->n), se = size_t(p->sigma_elems);
@@ -616,6 +762,55 @@ extern "C" nd_status nd_contact_current(nd_fact* f, int32_t contact, double* cur
     ND_CUDA(cudaMemcpyAsync(current_im, dim, bytes,
                             is_device_ptr(current_im) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   return ND_OK;
+}
+
+template <typename T>
+static nd_status density_gradient_t(nd_fact* f, const double* c, double* t_out, cudaStream_t s) {
+  const nd_plan* p = f->plan;
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
+  const int M = p->adj_cols;
+  nd_status st;
+  // U = G^r E_C: unit right-hand sides at the contact sites
+  Kern<T>::zero_range(w, f->adj_base, p->adj_elems, s);
+  Kern<T>::adj_ones(w, f->d_ones, f->n_ones, s);
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1)  // Z = G^r diag(c) conj(U)
+      Kern<T>::adj_mid(w, f->d_adj_desc, f->n_adj_desc, M, c, f->d_sites, f->dt, s);
+    if ((st = run_schedule<T>(f, f->sched_adj_fwd, f->tr_adj_fwd, w, nullptr, nullptr, s, 0,
+                              &f->step_flops_adj_fwd)) != ND_OK)
+      return st;
+    if ((st = run_schedule<T>(f, f->sched_adj_bwd, f->tr_adj_bwd, w, nullptr, nullptr, s, 0,
+                              &f->step_flops_adj_bwd)) != ND_OK)
+      return st;
+  }
+  ContactTable ct{};
+  ct.n = p->n_contacts;
+  for (int k = 0; k < p->n_contacts; ++k) {
+    ct.m[k] = p->contact_ptr[k + 1] - p->contact_ptr[k];
+    ct.off[k] = p->contact_soff[k];
+  }
+  Kern<T>::adj_contract(w, f->d_adj_desc, f->n_adj_desc, M, ct, f->cur_sl, p->sigma_elems, f->d_sites, f->dt, t_out,
+                        p->n, s);
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}
+
+extern "C" nd_status nd_density_gradient(nd_fact* f, const double* c, double* t_out, void* stream) {
+  if (!f || !c || !t_out) return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: NULL argument");
+  const nd_plan* p = f->plan;
+  if (!f->adj) return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: workspace created without ND_FACT_ADJOINT");
+  if (f->n_e <= 0 || !f->have_lesser || !f->cur_sl)
+    return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: needs a preceding nd_diag_green with Sigma^<");
+  if (f->cur_pl) return fail(ND_ERR_UNSUPPORTED, "nd_density_gradient: phonon Sigma^< is not supported");
+  if (p->n_contacts < 1 || p->n_contacts > MAX_CONTACTS)
+    return fail(ND_ERR_UNSUPPORTED, "nd_density_gradient: needs 1 to 8 contacts");
+  if (!is_device_ptr(t_out)) return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: t_out must be a device array");
+  cudaStream_t s = (cudaStream_t)stream;
+  ND_CUDA(cudaMemcpyAsync(f->d_cvec, c, size_t(p->n) * sizeof(double),
+                          is_device_ptr(c) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (f->precision == ND_PREC_FP64) return density_gradient_t<double>(f, f->d_cvec, t_out, s);
+  if (f->precision == ND_PREC_MIXED) return density_gradient_t<float>(f, f->d_cvec, t_out, s);
+  return density_gradient_t<DF>(f, f->d_cvec, t_out, s);
 }
 
 extern "C" nd_status nd_profile(nd_fact* f, int32_t enable, nd_kernel_stats* stats, int32_t max_stats,

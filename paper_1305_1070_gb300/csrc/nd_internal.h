@@ -53,6 +53,12 @@ struct Cluster {
     int64_t off_NB[2] = {-1, -1}; // b x A    : fold accumulator N_{B_i, anc(i)}
     int64_t off_PX[2] = {-1, -1}; // n x (n+A): A_ii^{-1} N_{I_i, Y_i}
   } ext[2];
+  // adjoint solves (nd_density_gradient), offsets relative to the adjoint
+  // part of the workspace, M columns = all contact sites:
+  // XI (n x M) right-hand side / upward accumulator, RB (b x M) boundary
+  // updates, XB (b x M) gathered boundary solution, XS (n x M) solution,
+  // U (n x M) solution of the first solve
+  int64_t adj_XI = 0, adj_RB = 0, adj_XB = 0, adj_XS = 0, adj_U = 0;
 };
 
 // ---- device descriptors (plain structs, copied to the GPU) -----------------
@@ -150,6 +156,24 @@ struct DelayDesc {
   int32_t sb, sb_p, dslot;
 };
 
+// Row moves of the adjoint solves between a child's b x M block and its
+// parent's interior (m_p x M) and boundary (b_p x M) blocks, through the map
+// of the child's boundary into the parent's front (per-energy row order of
+// the parent when it has delayed rows).
+struct RowsDesc {
+  int64_t off_child;  // child's b x M block
+  int64_t off_pi;     // parent's interior block (m_p x M)
+  int64_t off_pb;     // parent's boundary block (b_p x M)
+  int32_t b, m_p, k_p, sb_p;
+  int32_t map_begin;
+};
+
+// Per-cluster blocks of the adjoint solves (absolute per-energy offsets).
+struct AdjDesc {
+  int64_t off_XI, off_RB, off_XS, off_U;
+  int32_t m, b, site_begin, pad;
+};
+
 // Final position of every front row after the delayed pivots (k_loc).
 struct LocDesc {
   int32_t sb, nf, n;  // first unknown, front rows, rows eliminated here
@@ -184,6 +208,8 @@ enum StepKind : int32_t {
   ST_COLGATHER = 9,
   ST_DELAY = 10,
   ST_LOC = 11,
+  ST_ROWS_ADD = 12,     // adjoint solves: rows of a child's update into its parent
+  ST_ROWS_GATHER = 13,  // adjoint solves: a child's boundary rows from its parent
 };
 
 struct Step {
@@ -213,6 +239,8 @@ struct nd_plan {
   int64_t ext_elems[2] = {0, 0};   // extra elements of the G^< blocks, per variant
   int64_t sigma_elems = 0;         // sum_c m_c^2
   int64_t root_scratch_elems = 0;  // complex128 scratch of the root blocks per energy (single-precision paths)
+  int64_t adj_elems = 0;           // per-energy elements of the adjoint blocks
+  int32_t adj_cols = 0;            // M: number of contact sites
   double flops_factor = 0, flops_green_r = 0, flops_green_lesser = 0;
 
   // device-independent descriptor tables (uploaded by nd_fact_create)

@@ -958,6 +958,168 @@ void Kern<T>::current(const Work& w, int64_t offPl, int64_t offPg, int ld, int r
                                      (const double2*)sg, sstride, soff, out, out_im);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint solves (nd_density_gradient): A X = R for M right-hand sides with
+// the stored factorization, in the cluster layout of the fold.
+//   upward:   RB_i += Psi_i^T XI_i, rows of RB_i added to the parent's XI / RB;
+//   downward: XB_i gathered from the parent's XS / XB, XS_i = A_ii^{-1} XI_i + Psi_i XB_i.
+template <typename T>
+__global__ void k_rows_add(const RowsDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                           const int32_t* __restrict__ maps, int M, DelayTabs dt) {
+  const RowsDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const int32_t* ip = dt.iperm ? dt.iperm + int64_t(blockIdx.y) * dt.n_unk + d.sb_p : nullptr;
+  const int32_t* map = maps + d.map_begin;
+  const cx<T>* src = base + d.off_child;
+  const int nfp = d.m_p + d.k_p;
+  const int64_t tot = int64_t(d.b) * M;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / M), j = int(idx % M);
+    int pr = map[r];
+    if (ip && pr < nfp) pr = ip[pr];
+    cx<T>& dst = pr < d.m_p ? base[d.off_pi + int64_t(pr) * M + j] : base[d.off_pb + int64_t(pr - d.m_p) * M + j];
+    dst = O<T>::add(dst, src[idx]);
+  }
+}
+
+template <typename T>
+__global__ void k_rows_gather(const RowsDesc* __restrict__ descs, cx<T>* arena, int64_t se,
+                              const int32_t* __restrict__ maps, int M, DelayTabs dt) {
+  const RowsDesc d = descs[blockIdx.x];
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  const int32_t* ip = dt.iperm ? dt.iperm + int64_t(blockIdx.y) * dt.n_unk + d.sb_p : nullptr;
+  const int32_t* map = maps + d.map_begin;
+  cx<T>* dst = base + d.off_child;
+  const int nfp = d.m_p + d.k_p;
+  const int64_t tot = int64_t(d.b) * M;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / M), j = int(idx % M);
+    int pr = map[r];
+    if (ip && pr < nfp) pr = ip[pr];
+    dst[idx] = pr < d.m_p ? base[d.off_pi + int64_t(pr) * M + j] : base[d.off_pb + int64_t(pr - d.m_p) * M + j];
+  }
+}
+
+// Unit right-hand sides at the contact sites: element offsets (per energy) of
+// the ones.
+template <typename T>
+__global__ void k_set_one(const int64_t* __restrict__ offs, int count, cx<T>* arena, int64_t se) {
+  cx<T>* base = arena + int64_t(blockIdx.y) * se;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    base[offs[i]] = O<T>::from_d2(make_double2(1.0, 0.0));
+}
+
+// Between the two solves of one cluster: U = XS, XI = c_site conj(XS), RB = 0.
+template <typename T>
+__global__ void k_adj_mid(const AdjDesc* __restrict__ descs, cx<T>* arena, int64_t se, int M,
+                          const double* __restrict__ c, const int32_t* __restrict__ sites, DelayTabs dt) {
+  const AdjDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  cx<T>* base = arena + int64_t(e) * se;
+  const int64_t tot = int64_t(d.m) * M;
+  for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int r = int(idx / M);
+    const int site = dt.rsite ? dt.rsite[int64_t(e) * dt.n_unk + d.site_begin + r] : sites[d.site_begin + r];
+    const cx<T> x = base[d.off_XS + idx];
+    base[d.off_U + idx] = x;
+    base[d.off_XI + idx] = O<T>::scale(O<T>::conj(x), c[site]);
+  }
+  const int64_t tb = int64_t(d.b) * M;
+  for (int64_t idx = threadIdx.x; idx < tb; idx += blockDim.x) base[d.off_RB + idx] = O<T>::zero();
+}
+
+// t_k = sum_{a,b} Sigma^<_ab conj(U_kb) conj(Z_ka) over the contact blocks,
+// for every eliminated row k of one cluster (Z = XS of the second solve);
+// one warp per row, in complex128.
+template <typename T>
+__global__ void k_adj_contract(const AdjDesc* __restrict__ descs, const cx<T>* arena, int64_t se, int M,
+                               ContactTable ct, const double2* __restrict__ sl, int64_t sstride,
+                               const int32_t* __restrict__ sites, DelayTabs dt, double2* out, int n) {
+  const AdjDesc d = descs[blockIdx.x];
+  const int e = blockIdx.y;
+  const cx<T>* base = arena + int64_t(e) * se;
+  const double2* S = sl + int64_t(e) * sstride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < d.m; r += nw) {
+    const cx<T>* U = base + d.off_U + int64_t(r) * M;
+    const cx<T>* Z = base + d.off_XS + int64_t(r) * M;
+    double re = 0.0, im = 0.0;
+    int col0 = 0;
+    for (int c = 0; c < ct.n; ++c) {
+      const int m = ct.m[c];
+      const double2* Sc = S + ct.off[c];
+      for (int a = lane; a < m; a += 32) {
+        const double2 za = O<T>::to_d2(Z[col0 + a]);
+        double sr = 0.0, si = 0.0;  // sum_b S_ab conj(U_b)
+        for (int bb = 0; bb < m; ++bb) {
+          const double2 s = Sc[int64_t(a) * m + bb];
+          const double2 u = O<T>::to_d2(U[col0 + bb]);
+          sr += s.x * u.x + s.y * u.y;
+          si += s.y * u.x - s.x * u.y;
+        }
+        re += sr * za.x + si * za.y;  // (sr + i si) conj(za)
+        im += si * za.x - sr * za.y;
+      }
+      col0 += m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      re += __shfl_down_sync(0xffffffffu, re, o);
+      im += __shfl_down_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      const int site = dt.rsite ? dt.rsite[int64_t(e) * dt.n_unk + d.site_begin + r] : sites[d.site_begin + r];
+      out[int64_t(e) * n + site] = make_double2(re, im);
+    }
+  }
+}
+
+template <typename T>
+void Kern<T>::rows(const Work& w, const RowsDesc* d, int count, const int32_t* maps, int M, bool gather,
+                   const DelayTabs& dt, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  if (gather)
+    k_rows_gather<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps, M, dt);
+  else
+    k_rows_add<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, maps, M, dt);
+}
+
+template <typename T>
+__global__ void k_zero_range(cx<T>* arena, int64_t se, int64_t off, int64_t count) {
+  cx<T>* p = arena + int64_t(blockIdx.y) * se + off;
+  const cx<T> z = O<T>::zero();
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = z;
+}
+
+template <typename T>
+void Kern<T>::zero_range(const Work& w, int64_t off, int64_t count, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  int blocks = int(std::min<int64_t>((count + 255) / 256, 1024));
+  k_zero_range<T><<<dim3(blocks, w.n_e), 256, 0, s>>>((cx<T>*)w.arena, w.se, off, count);
+}
+
+template <typename T>
+void Kern<T>::adj_ones(const Work& w, const int64_t* offs, int count, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_set_one<T><<<dim3((count + 255) / 256, w.n_e), 256, 0, s>>>(offs, count, (cx<T>*)w.arena, w.se);
+}
+
+template <typename T>
+void Kern<T>::adj_mid(const Work& w, const AdjDesc* d, int count, int M, const double* c, const int32_t* sites,
+                      const DelayTabs& dt, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_adj_mid<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, M, c, sites, dt);
+}
+
+template <typename T>
+void Kern<T>::adj_contract(const Work& w, const AdjDesc* d, int count, int M, const ContactTable& ct,
+                           const double* sl, int64_t sstride, const int32_t* sites, const DelayTabs& dt,
+                           double* out, int n, cudaStream_t s) {
+  if (count <= 0 || w.n_e <= 0) return;
+  k_adj_contract<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (const cx<T>*)w.arena, w.se, M, ct, (const double2*)sl,
+                                                       sstride, sites, dt, (double2*)out, n);
+}
+
 template struct Kern<double>;
 template struct Kern<float>;
 template struct Kern<DF>;

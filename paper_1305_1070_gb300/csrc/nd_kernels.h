@@ -47,6 +47,16 @@ struct CertArgs {
   int n_psi;
 };
 
+// Contacts passed by value to a kernel (nd_sigma_lesser_fermi in groups of
+// this size, the adjoint contraction).
+static constexpr int MAX_CONTACTS = 8;
+struct ContactTable {
+  int32_t n;
+  int32_t m[MAX_CONTACTS];
+  int64_t off[MAX_CONTACTS];
+  double mu[MAX_CONTACTS];
+};
+
 template <typename T>
 struct Kern {
   static void assemble(const Work& w, const AssembleDesc* d, int count, const int32_t* ent_dst,
@@ -74,6 +84,15 @@ struct Kern {
                        const DelayTabs& dt, cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
                           cudaStream_t s);
+  static void rows(const Work& w, const RowsDesc* d, int count, const int32_t* maps, int M, bool gather,
+                   const DelayTabs& dt, cudaStream_t s);
+  static void adj_ones(const Work& w, const int64_t* offs, int count, cudaStream_t s);
+  static void zero_range(const Work& w, int64_t off, int64_t count, cudaStream_t s);
+  static void adj_mid(const Work& w, const AdjDesc* d, int count, int M, const double* c, const int32_t* sites,
+                      const DelayTabs& dt, cudaStream_t s);
+  static void adj_contract(const Work& w, const AdjDesc* d, int count, int M, const ContactTable& ct,
+                           const double* sl, int64_t sstride, const int32_t* sites, const DelayTabs& dt, double* out,
+                           int n, cudaStream_t s);
   static void current(const Work& w, int64_t offPl, int64_t offPg, int ld, int row0, int m, const double* sl,
                       const double* sg, int64_t sstride, int64_t soff, double* out, double* out_im, cudaStream_t s);
   // tile edge (BM = BN) of the large and the small GEMM configuration
@@ -97,14 +116,6 @@ void launch_lead_decimation(const double* H00, const double* H01, const double* 
                             double* out, int64_t stride, int64_t offset, double* work, int* status, cudaStream_t s);
 void launch_lead_modes(const double* U, const double* eps, int m, double hop, const double* energies, int n_e,
                        double eta, double* out, int64_t stride, int64_t offset, cudaStream_t s);
-// Contacts of nd_sigma_lesser_fermi, passed by value.
-static constexpr int MAX_CONTACTS = 8;
-struct ContactTable {
-  int32_t n;
-  int32_t m[MAX_CONTACTS];
-  int64_t off[MAX_CONTACTS];
-  double mu[MAX_CONTACTS];
-};
 void launch_sigma_lesser(const double* sigma_r, int n_e, const ContactTable& ct, double kT, const double* energies,
                          int64_t stride, double* lesser, double* greater, cudaStream_t s);
 void launch_density(const double* X, const double* w, int n_e, int n, double scale, int accumulate, double* out,

@@ -604,6 +604,21 @@ extern "C" nd_status nd_analyze(const nd_graph* g, const nd_opts* opts, nd_plan*
     plan->ext_elems[v] = eo - off;
   }
   plan->arena_elems = off;
+  // adjoint blocks (used only by workspaces created with ND_FACT_ADJOINT)
+  {
+    const int64_t M = plan->n_contacts > 0 ? plan->contact_ptr[plan->n_contacts] : 0;
+    plan->adj_cols = int32_t(M);
+    int64_t ao = 0;
+    for (auto& c : cl) {
+      const int64_t m = c.n, b = c.b;
+      c.adj_XI = ao; ao = align16(ao + m * M);
+      c.adj_RB = ao; ao = align16(ao + b * M);
+      c.adj_XB = ao; ao = align16(ao + b * M);
+      c.adj_XS = ao; ao = align16(ao + m * M);
+      c.adj_U = ao; ao = align16(ao + m * M);
+    }
+    plan->adj_elems = ao;
+  }
   plan->flops_factor = ff;
   plan->flops_green_r = fg;
   plan->flops_green_lesser = fl;

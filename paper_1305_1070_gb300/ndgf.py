@@ -26,11 +26,12 @@ ND_FACT_TILE_LARGE = 2
 ND_FACT_TILE_SMALL = 4
 ND_FACT_GEMM_TC = 8
 ND_FACT_GEMM_ALU = 16
+ND_FACT_ADJOINT = 32
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
-           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_sigma_lesser_fermi", "nd_phonon_const",
+           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_sigma_lesser_fermi", "nd_phonon_const",
            "nd_last_error", "nd_version"]
 
 
@@ -97,6 +98,7 @@ def lib():
             "nd_lead_sigma": ([_P, _P, _I32, _D, _P, _I64, _I64, _P], _I32),
             "nd_lead_status": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], _I32),
             "nd_contact_current": ([_P, _I32, _P, _P, _P], _I32),
+            "nd_density_gradient": ([_P, _P, _P, _P], _I32),
             "nd_lead_destroy": ([_P], None),
             "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
             "nd_phonon_const": ([_I32, _I32, _D, _D, _D, _P, _P, _P, _P, _P], _I32),
@@ -295,6 +297,13 @@ def nd_lead_sigma(lead: Lead, energies, n_e: int, eta: float, sigma_out, stride:
     keep = []
     _check(lib().nd_lead_sigma(lead.ptr, _ptr(energies, keep), n_e, eta, _ptr(sigma_out, keep), stride, offset,
                                _stream(stream)), "nd_lead_sigma")
+
+
+def nd_density_gradient(fact: Fact, c, t_out, stream=None):
+    """t_out[e][k] = sum_ab Sigma^<_ab conj(U_kb) conj(Z_ka) of the last step (see ndgf.h)."""
+    keep = []
+    _check(lib().nd_density_gradient(fact.ptr, _ptr(c, keep), _ptr(t_out, keep), _stream(stream)),
+           "nd_density_gradient")
 
 
 def nd_contact_current(fact: Fact, contact: int, current, current_im=None, stream=None):

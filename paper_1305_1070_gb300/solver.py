@@ -16,7 +16,7 @@ from . import ndgf
 class Solver:
     def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
                  leaf_size: int = 64, split_permille: int = 0, delay: int = 0, tile: str = "auto",
-                 device: str = "cuda"):
+                 adjoint: bool = False, device: str = "cuda"):
         self.dev, self.tr = dev, tr
         self.device = torch.device(device)
         self.n = dev.n
@@ -33,10 +33,21 @@ class Solver:
         flags = ndgf.ND_FACT_PHONON if tr.gamma_ph > 0.0 else 0
         flags |= {"auto": 0, "large": ndgf.ND_FACT_TILE_LARGE, "small": ndgf.ND_FACT_TILE_SMALL,
                   "tc": ndgf.ND_FACT_GEMM_TC, "alu": ndgf.ND_FACT_GEMM_ALU}[tile]
+        if adjoint:
+            flags |= ndgf.ND_FACT_ADJOINT
         self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision, flags)
         self.leads = [ndgf.nd_lead_create(l.H00, l.H01, l.tau) for l in dev.leads]
         kw = dict(device=self.device)
         self.H = torch.as_tensor(dev.values, dtype=torch.float64, **kw).contiguous()
+        self.H0 = self.H.clone()
+        # CSR position of every diagonal entry (onsite potentials enter there)
+        diag = np.full(dev.n, -1, dtype=np.int64)
+        for r in range(dev.n):
+            row = dev.colind[dev.rowptr[r]:dev.rowptr[r + 1]]
+            hit = np.nonzero(row == r)[0]
+            if hit.size:
+                diag[r] = dev.rowptr[r] + hit[0]
+        self.diag_pos = torch.as_tensor(diag, **kw)
         self.E = torch.zeros(self.max_ne, dtype=torch.float64, **kw)
         se = max(1, self.sigma_elems)
         self.sig_r = torch.zeros(self.max_ne, se, dtype=torch.complex128, **kw)
@@ -96,6 +107,20 @@ class Solver:
         im = torch.zeros(n_e, dtype=torch.float64, device=self.device)
         ndgf.nd_contact_current(self.fact, contact, re, im)
         return re, im
+
+    def set_onsite(self, V):
+        """H = H0 + diag(V) for the following steps (V: [n] float64, caller order)."""
+        if bool((self.diag_pos < 0).any()):
+            raise ValueError("the pattern of H lacks diagonal entries")
+        self.H.copy_(self.H0)
+        self.H.index_add_(0, self.diag_pos, torch.as_tensor(V, dtype=torch.float64, device=self.device))
+
+    def density_gradient_terms(self, c, n_e: int):
+        """t[e][k] of the last step for the weights c (see nd_density_gradient):
+        d(sum_j c_j n_j)/dV_k = (2/pi) sum_e w_e Im t[e][k]."""
+        t = torch.zeros(n_e, self.n, dtype=torch.complex128, device=self.device)
+        ndgf.nd_density_gradient(self.fact, torch.as_tensor(c, dtype=torch.float64, device=self.device).contiguous(), t)
+        return t
 
     def lead_status(self):
         """Per lead (n_unconverged, n_singular) of the decimation since the last query."""
