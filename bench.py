@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--chunk-x2", type=int, default=128, help="energies per call of the FP32-pair path")
     ap.add_argument("--leaf", type=int, default=16, help="leaf size of the nested-dissection tree")
     ap.add_argument("--chunk-aux", type=int, default=0, help="energies per call for the other workloads (0: default)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "uneven_64", "cnt_10_0_400"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "uneven_64", "cnt_10_0_400", "gradient_256x64"],
                     help="the headline workload, or another one (its own JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
     ap.add_argument("--growth-max", type=float, default=10.0, help="fold growth above which fp32x2 redoes in FP64")
@@ -525,6 +525,98 @@ def main_aux(a) -> None:
     print(json.dumps(line), flush=True)
 
 
+def main_gradient(a) -> None:
+    """Row c5: the density of the 256 x 64 superlattice (128 energies) and its
+    gradient with respect to all 16,384 onsite potentials, for the loss
+    L = sum_j c_j n_j with seeded weights c_j ~ U(0, 1).  Times the density
+    alone and the density plus gradient (adjoint: two solves per energy with
+    the stored factorization), FP32 pairs and complex128 with delayed pivots;
+    checks the complex128 gradient against central differences of the
+    complex128 density at 3 sites.  Prints its own JSON line."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1070_gb300 import autograd, ndgf, workloads
+    from paper_1305_1070_gb300.solver import Solver
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev, tr = workloads.workload("superlattice_256x64")
+    n_e = tr.n_e
+    E = torch.as_tensor(tr.energies, device="cuda")
+    w = np.zeros(n_e)
+    d = np.diff(tr.energies)
+    w[:-1] += 0.5 * d
+    w[1:] += 0.5 * d
+    W = torch.as_tensor(w, device="cuda")
+    c = torch.as_tensor(np.random.Generator(np.random.PCG64(workloads.SEED_BASE + 5)).uniform(0.0, 1.0, dev.n),
+                        device="cuda")
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    res, grads = {}, {}
+
+    def timed(fn, K, Wm):
+        for _ in range(Wm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K
+
+    for name, prec in (("fp32x2", ndgf.ND_PREC_FP32X2), ("fp64_nd", ndgf.ND_PREC_FP64)):
+        s = Solver(dev, tr, precision=prec, max_ne=32, delay=a.delay, leaf_size=a.leaf, adjoint=True)
+        V = torch.zeros(dev.n, dtype=torch.float64, device="cuda", requires_grad=True)
+
+        def fwd():
+            with torch.no_grad():
+                autograd.density(V, s, E, W)
+
+        def fwd_bwd():
+            V.grad = None
+            (c * autograd.density(V, s, E, W)).sum().backward()
+
+        ms_f = timed(fwd, a.steps, 1)
+        ms_fb = timed(fwd_bwd, a.steps, 1)
+        grads[name] = V.grad.detach().clone()
+        res[name] = {"density_ms": round(ms_f, 1), "density_and_gradient_ms": round(ms_fb, 1),
+                     "energies_per_s_density_and_gradient": round(n_e / (ms_fb * 1e-3), 2),
+                     "gradient_over_density_time": round(ms_fb / ms_f, 3)}
+        if name == "fp64_nd":
+            h = 1e-5
+            fd = []
+            for k in (dev.n // 7, dev.n // 2, dev.n - 3):
+                vals = []
+                for sg in (1.0, -1.0):
+                    dV = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
+                    dV[k] = sg * h
+                    with torch.no_grad():
+                        vals.append(float((c * autograd.density(dV, s, E, W)).sum()))
+                g_fd = (vals[0] - vals[1]) / (2 * h)
+                fd.append({"site": k, "adjoint": float(grads[name][k]), "central_difference": g_fd})
+            res[name]["finite_difference_check"] = fd
+        del s
+        torch.cuda.empty_cache()
+    clocks = clk.stop()
+    err = float((grads["fp32x2"] - grads["fp64_nd"]).abs().max() / grads["fp64_nd"].abs().max())
+    line = {"metric": "energy points/sec for the density of a 256 x 64 superlattice and its gradient w.r.t. all "
+                      "16,384 onsite potentials (mixed; gradient rel err vs FP64)",
+            "value": res["fp32x2"]["energies_per_s_density_and_gradient"], "unit": "energies/s", "n_gpus": 1,
+            "steps": a.steps, "warmup": 1, "ms_per_step": res["fp32x2"]["density_and_gradient_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32x2 (FP32-pair complex) + c128 root",
+            "data": "synthetic (seeded 256 x 64 superlattice, PCG64 seed 1309; weights seed 1310)",
+            "config": {"workload": "superlattice_256x64", "sites": dev.n, "energies": n_e, "leaf_size": a.leaf,
+                       "delayed_pivots_per_cluster": a.delay, "energies_per_call": 32},
+            "paths": res, "gradient_rel_err_fp32x2_vs_fp64": err, "clocks": clocks, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main_reference(a) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -555,6 +647,8 @@ if __name__ == "__main__":
         cpu_worker(args.cpu_worker, args.cpu_save, args.cpu_world)
     elif args.impl == "reference":
         main_reference(args)
+    elif args.workload == "gradient_256x64":
+        main_gradient(args)
     elif args.workload != WORKLOAD:
         main_aux(args)
     else:

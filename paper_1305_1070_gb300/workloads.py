@@ -336,6 +336,7 @@ def workload(name: str):
     superlattice_512x128  : 512 x 128 = 65,536 sites, disorder +-0.02 eV, 256 energies
     cnt_10_0_400          : (10,0) tube, 400 cells = 16,000 atoms, disorder +-0.1 eV,
                             phonon broadening 5 meV, 1,024 energies in [-1, 1] eV
+    superlattice_256x64   : 256 x 64 = 16,384 sites, disorder +-0.02 eV, 128 energies (density gradient)
     uneven_64             : 64 superlattices in one graph, widths in {16, 32, 64, 96},
                             lengths in [128, 1024], disorder +-0.02 eV, 64 energies in [0, 0.5] eV
     """
@@ -345,6 +346,9 @@ def workload(name: str):
     elif name == "superlattice_512x128":
         dev = superlattice(512, 128, disorder=0.02, seed=SEED_BASE + 1)
         tr = Transport(energies=energy_grid(0.0, 0.5, 256))
+    elif name == "superlattice_256x64":
+        dev = superlattice(256, 64, disorder=0.02, seed=SEED_BASE + 4)
+        tr = Transport(energies=energy_grid(0.0, 0.5, 128))
     elif name == "uneven_64":
         dev, _ = uneven_batch(64, seed=SEED_BASE + 3)
         tr = Transport(energies=energy_grid(0.0, 0.5, 64))
