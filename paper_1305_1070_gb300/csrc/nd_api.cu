@@ -55,6 +55,7 @@ struct Profiler {
     int kind;
     cudaEvent_t a, b;
     double flops, bytes;
+    int count = 0, max_dim = 0, n_e = 0;
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -253,6 +254,9 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
       rec.b = f->prof.get();
       rec.flops = step_flops ? (*step_flops)[si] * w.n_e : 0.0;
       rec.bytes = 0.0;
+      rec.count = st.count;
+      rec.max_dim = st.max_dim;
+      rec.n_e = w.n_e;
       cudaEventRecord(rec.a, s);
     }
     switch (st.kind) {
@@ -811,6 +815,22 @@ extern "C" nd_status nd_density_gradient(nd_fact* f, const double* c, double* t_
   if (f->precision == ND_PREC_FP64) return density_gradient_t<double>(f, f->d_cvec, t_out, s);
   if (f->precision == ND_PREC_MIXED) return density_gradient_t<float>(f, f->d_cvec, t_out, s);
   return density_gradient_t<DF>(f, f->d_cvec, t_out, s);
+}
+
+extern "C" nd_status nd_profile_launches(nd_fact* f, nd_launch_stats* out, int32_t max_out, int32_t* n_out) {
+  if (!f || !n_out) return fail(ND_ERR_INVALID_ARG, "nd_profile_launches: NULL argument");
+  ND_CUDA(cudaDeviceSynchronize());
+  int cnt = 0;
+  for (auto& r : f->prof.recs) {
+    if (out && cnt < max_out) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      out[cnt] = nd_launch_stats{r.kind, r.count, r.max_dim, r.n_e, double(ms), r.flops};
+    }
+    ++cnt;
+  }
+  *n_out = cnt;
+  return ND_OK;
 }
 
 extern "C" nd_status nd_profile(nd_fact* f, int32_t enable, nd_kernel_stats* stats, int32_t max_stats,

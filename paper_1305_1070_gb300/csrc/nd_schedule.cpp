@@ -80,6 +80,47 @@ struct Builder {
 
 }  // namespace
 
+namespace {
+
+// Size class of a block edge: launches of one class share a CTA shape.
+int size_class(int d) { return d <= 24 ? 0 : d <= 48 ? 1 : d <= 96 ? 2 : d <= 192 ? 3 : 4; }
+
+// Every inverse, delay and GEMM step of a schedule becomes one launch per size
+// class of its blocks (descriptors reordered inside the step's range), so
+// that a few large blocks (the contact leaves, say) do not set the CTA shape,
+// shared memory and tile of thousands of small ones.
+template <typename D, typename Dim>
+void split_kind(std::vector<Step>& sched, int kind, std::vector<D>& table, Dim dim) {
+  std::vector<Step> out;
+  for (const Step& st : sched) {
+    if (st.kind != kind || st.count <= 1) {
+      out.push_back(st);
+      continue;
+    }
+    std::vector<D> part(table.begin() + st.begin, table.begin() + st.begin + st.count);
+    std::stable_sort(part.begin(), part.end(),
+                     [&](const D& a, const D& b) { return size_class(dim(a)) < size_class(dim(b)); });
+    std::copy(part.begin(), part.end(), table.begin() + st.begin);
+    int i = 0;
+    while (i < st.count) {
+      const int cls = size_class(dim(part[i]));
+      int j = i, md = 0;
+      while (j < st.count && size_class(dim(part[j])) == cls) md = std::max(md, dim(part[j++]));
+      out.push_back(Step{st.kind, st.begin + i, j - i, md});
+      i = j;
+    }
+  }
+  sched = std::move(out);
+}
+
+void split_by_size(nd_plan* p, std::vector<Step>& sched) {
+  split_kind(sched, ST_INVERSE, p->inv_desc, [](const InvDesc& d) { return d.n; });
+  split_kind(sched, ST_DELAY, p->delay_desc, [](const DelayDesc& d) { return d.nf; });
+  split_kind(sched, ST_GEMM, p->gemm_desc, [](const GemmDesc& g) { return std::max(g.m, std::max(g.n, g.k)); });
+}
+
+}  // namespace
+
 void build_schedules(nd_plan* p) {
   auto& cl = p->cl;
   const int nc = int(cl.size());
@@ -499,6 +540,10 @@ void build_schedules(nd_plan* p) {
       B.end();
     }
   }
+  split_by_size(p, p->sched_factor);
+  split_by_size(p, p->sched_green);
+  split_by_size(p, p->sched_lesser[0]);
+  split_by_size(p, p->sched_lesser[1]);
 }
 
 }  // namespace ndgf

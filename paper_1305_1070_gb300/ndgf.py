@@ -31,7 +31,7 @@ ND_FACT_ADJOINT = 32
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
-           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_sigma_lesser_fermi", "nd_phonon_const",
+           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const",
            "nd_last_error", "nd_version"]
 
 
@@ -99,6 +99,7 @@ def lib():
             "nd_lead_status": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], _I32),
             "nd_contact_current": ([_P, _I32, _P, _P, _P], _I32),
             "nd_density_gradient": ([_P, _P, _P, _P], _I32),
+            "nd_profile_launches": ([_P, _P, _I32, ctypes.POINTER(_I32)], _I32),
             "nd_lead_destroy": ([_P], None),
             "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
             "nd_phonon_const": ([_I32, _I32, _D, _D, _D, _P, _P, _P, _P, _P], _I32),
@@ -297,6 +298,21 @@ def nd_lead_sigma(lead: Lead, energies, n_e: int, eta: float, sigma_out, stride:
     keep = []
     _check(lib().nd_lead_sigma(lead.ptr, _ptr(energies, keep), n_e, eta, _ptr(sigma_out, keep), stride, offset,
                                _stream(stream)), "nd_lead_sigma")
+
+
+class nd_launch_stats(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("count", ctypes.c_int32), ("max_dim", ctypes.c_int32),
+                ("n_e", ctypes.c_int32), ("ms", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+def nd_profile_launches(fact: Fact):
+    """Per-launch records of the profiler (see nd_profile), in launch order."""
+    n = _I32()
+    _check(lib().nd_profile_launches(fact.ptr, None, 0, ctypes.byref(n)), "nd_profile_launches")
+    arr = (nd_launch_stats * max(1, n.value))()
+    _check(lib().nd_profile_launches(fact.ptr, arr, n.value, ctypes.byref(n)), "nd_profile_launches")
+    return [dict(kind=r.kind, count=r.count, max_dim=r.max_dim, n_e=r.n_e, ms=r.ms, flops=r.flops)
+            for r in arr[:n.value]]
 
 
 def nd_density_gradient(fact: Fact, c, t_out, stream=None):
