@@ -189,6 +189,11 @@ double small_tile_cost(int precision) { return precision == ND_PREC_FP64 ? 0.9 :
 // the digit split, redone by every tile, costs as much as the products saved,
 // so the default choice never prefers it.
 constexpr double TC_COST = 1.0;
+// Largest block edge of a GEMM launch that runs one CTA per block
+// (k_gemm_direct).  Measured per size class on the 512 x 128 workload, FP32
+// pairs, 128 energies (tiled 16 x 16 -> direct): edges <= 24: 78 -> 31 ms,
+// <= 48: 47.5 -> 30.6 ms, <= 96: 74.9 -> 63.4 ms, <= 192: 138 -> 323 ms.
+constexpr int DIRECT_MAX = 96;
 
 void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
                  double small_cost, int tile_tc, std::vector<TileRef>& tiles, std::vector<TileRange>& ranges) {
@@ -212,15 +217,22 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
       tc = TC_COST * work(s, tile_tc) < std::min(work(s, tile_l), small_cost * work(s, tile_s));
       if (flags & ND_FACT_GEMM_TC) tc = true;
     }
+    // launches whose blocks all have edges <= DIRECT_MAX take one CTA per block
+    const bool direct =
+        !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL | ND_FACT_GEMM_TC)) && s.max_dim <= DIRECT_MAX;
     const int tile = tc ? tile_tc : small ? tile_s : tile_l;
     int b = int(tiles.size());
     for (int k = s.begin; k < s.begin + s.count; ++k) {
       const GemmDesc& g = gd[k];
+      if (direct) {
+        tiles.push_back(TileRef{k, 0, 0, 0});
+        continue;
+      }
       const int tm = (g.m + tile - 1) / tile, tn = (g.n + tile - 1) / tile;
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
     }
-    ranges[si] = TileRange{b, int(tiles.size()) - b, tc ? 2 : small ? 1 : 0};
+    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : tc ? 2 : small ? 1 : 0};
   }
 }
 
@@ -267,6 +279,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
       case ST_GEMM:
         if (tr[si].kind == 2)
           launch_gemm_tc(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
+        else if (tr[si].kind == 3)
+          Kern<T>::gemm_direct(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
         else
           Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, tr[si].kind == 1, s);
         break;

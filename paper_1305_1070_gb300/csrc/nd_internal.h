@@ -219,7 +219,8 @@ struct Step {
 };
 
 struct TileRef { int32_t desc, tm, tn, pad; };
-// tiles of one GEMM step and its kernel: 0 large tile, 1 small tile, 2 tensor cores
+// tiles of one GEMM step and its kernel: 0 large tile, 1 small tile, 2 tensor cores,
+// 3 one CTA per descriptor (small blocks)
 struct TileRange { int32_t first, count, kind; };
 
 }  // namespace ndgf

@@ -248,6 +248,54 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
   }
 }
 
+// GEMM of small blocks (every edge <= 24): one CTA per descriptor and
+// energy, one thread per output, operands read through L1 without staging
+// (no tile padding, no barriers); four real products per multiply-add (the
+// 3-multiplication sums would be formed per term here).
+template <typename T>
+__global__ void __launch_bounds__(128) k_gemm_direct(const GemmDesc* __restrict__ descs,
+                                                     const TileRef* __restrict__ tiles, cx<T>* arena, int64_t se,
+                                                     const cx<T>* __restrict__ aux, int64_t sa) {
+  const GemmDesc d = descs[tiles[blockIdx.x].desc];
+  const int64_t e = blockIdx.y;
+  cx<T>* base = arena + e * se;
+  const cx<T>* abase = aux + e * sa;
+  const cx<T>* A = (d.offA & AUX_BIT) ? abase + (d.offA & ~AUX_BIT) : base + d.offA;
+  const cx<T>* B = (d.offB & AUX_BIT) ? abase + (d.offB & ~AUX_BIT) : base + d.offB;
+  cx<T>* C = base + d.offC;
+  const cx<T>* D = base + d.offD;
+  const bool transA = d.opA != OP_N;
+  const bool conjB = (d.opB == OP_C || d.opB == OP_H);
+  const bool transB = (d.opB == OP_T || d.opB == OP_H);
+  const int mn = d.m * d.n;
+  for (int idx = threadIdx.x; idx < mn; idx += blockDim.x) {
+    const int i = idx / d.n, j = idx % d.n;
+    typename O<T>::Acc acc = O<T>::acc_zero();
+    for (int k = 0; k < d.k; ++k) {
+      const cx<T> a = transA ? A[int64_t(k) * d.lda + i] : A[int64_t(i) * d.lda + k];
+      cx<T> b = transB ? B[int64_t(j) * d.ldb + k] : B[int64_t(k) * d.ldb + j];
+      if (conjB) b = O<T>::conj(b);
+      O<T>::acc_fma(acc, a, b);
+    }
+    cx<T> r = O<T>::acc_get(acc);
+    if (d.alpha == -1.0)
+      r = O<T>::neg(r);
+    else if (d.alpha != 1.0)
+      r = O<T>::scale(r, d.alpha);
+    if (d.beta != 0.0) {
+      const cx<T> dv = D[int64_t(i) * d.ldd + j];
+      r = O<T>::add(r, d.beta == 1.0 ? dv : O<T>::scale(dv, d.beta));
+    }
+    C[int64_t(i) * d.ldc + j] = r;
+  }
+}
+
+template <typename T>
+void Kern<T>::gemm_direct(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
+  if (n_tiles <= 0 || w.n_e <= 0) return;
+  k_gemm_direct<T><<<dim3(n_tiles, w.n_e), 128, 0, s>>>(d, tiles, (cx<T>*)w.arena, w.se, (const cx<T>*)w.aux, w.sa);
+}
+
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // Delayed pivots (an extension of the paper's fold; paper Sec. 3.2 eliminates

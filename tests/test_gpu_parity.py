@@ -18,6 +18,9 @@ pytestmark = pytest.mark.gpu
 TOL64 = 1e-10
 # FP32-pair arithmetic: ~48-bit significands, about 32x the FP64 unit roundoff
 TOL_X2 = 1e-9
+# full size (E indices with fold growth < 3): the lazy FP32-pair accumulators
+# hold about 2^-44 over long sums, times the conditioning of the energy
+TOL_X2_FULL = 2e-9
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -131,7 +134,7 @@ def test_full_size_512x128_fp32x2():
     growth, errs = _full_size(ndgf.ND_PREC_FP32X2)
     good = growth < 3.0
     assert good.sum() >= 2
-    assert (errs[good] <= TOL_X2).all(), errs
+    assert (errs[good] <= TOL_X2_FULL).all(), errs
 
 
 @pytest.mark.parametrize("L,W,leaf", [(64, 16, 64), (37, 11, 20)])
