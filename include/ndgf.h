@@ -71,11 +71,13 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
 #define ND_FACT_TILE_LARGE 2
 #define ND_FACT_TILE_SMALL 4
 /* FP32-pair precision only: the Schur products may instead run on the tensor
- * cores, as exact products of 8-bit digits of a 46-bit fixed-point form of
- * each row and column (BF16 in, FP32 accumulate; same accuracy class).  By
- * default a launch takes them when the padded work, weighted by their lower
- * cost per flop, is smallest; ND_FACT_GEMM_TC forces them for every GEMM
- * launch, ND_FACT_GEMM_ALU never uses them. */
+ * cores (tcgen05), as exact products of 8-bit digits of a 54-bit fixed-point
+ * form of each row and column (BF16 in, exact FP32 group sums in tensor
+ * memory, FP32-pair accumulation; same accuracy class).  By default the
+ * launches whose largest block edge exceeds 192 take them, unless their digit
+ * planes would exceed 256 MiB per energy; ND_FACT_GEMM_TC forces them for
+ * every GEMM launch, ND_FACT_GEMM_ALU never uses them.  Their waits are
+ * bounded: a wait that gives up makes nd_fact_status return ND_ERR_TIMEOUT. */
 #define ND_FACT_GEMM_TC 8
 #define ND_FACT_GEMM_ALU 16
 /* Reserve the workspace of nd_density_gradient (M right-hand sides per
@@ -281,7 +283,8 @@ nd_status nd_profile_launches(nd_fact* fact, nd_launch_stats* out, int32_t max_o
 
 /* Status of the last factor/diag call (synchronises the handle's stream):
  * n_singular = number of (energy, cluster) pivots that were exactly zero;
- * returns ND_ERR_SINGULAR when n_singular > 0. */
+ * returns ND_ERR_SINGULAR when n_singular > 0, ND_ERR_TIMEOUT when a bounded
+ * wait of a tensor-core product gave up (the results are then invalid). */
 nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
 
 /* ---- S1a: contact self-energies (paper Sec. 2) ----------------------------

@@ -142,6 +142,12 @@ struct nd_fact {
   Profiler prof;
   std::vector<double> step_flops_factor, step_flops_green, step_flops_lesser[2];  // per step, per energy
   TileRef* d_tiles = nullptr;
+  // tensor-core steps (FP32 pairs): layouts, split items, per-energy scratch
+  TcDesc* d_tcd = nullptr;
+  TcSplit* d_tcsplit = nullptr;
+  unsigned char* tc_scratch = nullptr;
+  int64_t tc_stride = 0;  // bytes per energy
+  int* d_tc_timeout = nullptr;
   // tile range of every GEMM step: index = step index in its schedule
   std::vector<TileRange> tr_factor, tr_green, tr_lesser[2];
   // staging buffers for host inputs / outputs
@@ -183,21 +189,31 @@ nd_status dupload(nd_fact* f, const std::vector<V>& h, V** d) {
 // complex128 ran fastest with the small tile on every step, FP32 pairs with
 // this per-step choice).
 double small_tile_cost(int precision) { return precision == ND_PREC_FP64 ? 0.9 : 1.15; }
-// FP32 pairs: padded work of the tensor-core kernel relative to the large ALU
-// tile.  Measured equal on the 512 x 128 workload (GEMM time per step with
-// every launch forced: 1209.6 ms tensor cores, 1206.7 ms 32 x 32 FP32 pipe):
-// the digit split, redone by every tile, costs as much as the products saved,
-// so the default choice never prefers it.
-constexpr double TC_COST = 1.0;
+// FP32 pairs: launches whose largest block edge exceeds TC_MIN_DIM take the
+// tensor cores by default (their 128 x 64 tiles pad smaller blocks too much),
+// unless the digit planes of the launch exceed TC_MAX_SCRATCH bytes per
+// energy (thin blocks with many columns, as in the phonon G^< products).
+// Measured on the 512 x 128 workload, 128 energies, GEMM time per size class
+// (FP32 pipe -> tensor cores): edges in (96, 192]: 138.0 -> 170.5 ms,
+// > 192: 139.9 -> 99.0 ms.
+constexpr int TC_MIN_DIM = 192;
+constexpr int64_t TC_MAX_SCRATCH = int64_t(256) << 20;
 // Largest block edge of a GEMM launch that runs one CTA per block
 // (k_gemm_direct).  Measured per size class on the 512 x 128 workload, FP32
 // pairs, 128 energies (tiled 16 x 16 -> direct): edges <= 24: 78 -> 31 ms,
 // <= 48: 47.5 -> 30.6 ms, <= 96: 74.9 -> 63.4 ms, <= 192: 138 -> 323 ms.
 constexpr int DIRECT_MAX = 96;
 
+struct TcTables {
+  std::vector<TcDesc> desc;
+  std::vector<TcSplit> split;
+  int64_t bytes = 0;  // largest per-energy scratch of a step
+};
+
 void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
-                 double small_cost, int tile_tc, std::vector<TileRef>& tiles, std::vector<TileRange>& ranges) {
-  ranges.assign(sched.size(), TileRange{0, 0, 0});
+                 double small_cost, bool tc_ok, TcTables& tct, std::vector<TileRef>& tiles,
+                 std::vector<TileRange>& ranges) {
+  ranges.assign(sched.size(), TileRange{0, 0, 0, 0, 0});
   auto work = [&](const Step& s, int tile) {
     double w = 0.0;
     for (int k = s.begin; k < s.begin + s.count; ++k) {
@@ -213,15 +229,41 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
     if (flags & ND_FACT_TILE_LARGE) small = false;
     if (flags & ND_FACT_TILE_SMALL) small = true;
     bool tc = false;
-    if (tile_tc > 0 && !(flags & ND_FACT_GEMM_ALU)) {
-      tc = TC_COST * work(s, tile_tc) < std::min(work(s, tile_l), small_cost * work(s, tile_s));
+    if (tc_ok && !(flags & ND_FACT_GEMM_ALU)) {
+      tc = !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && s.max_dim > TC_MIN_DIM;
+      if (tc) {
+        int64_t off = 0;
+        for (int k = s.begin; k < s.begin + s.count; ++k) {
+          TcDesc t{};
+          off = gemm_tc_scratch(gd[k], t, off);
+        }
+        tc = off <= TC_MAX_SCRATCH;
+      }
       if (flags & ND_FACT_GEMM_TC) tc = true;
     }
     // launches whose blocks all have edges <= DIRECT_MAX take one CTA per block
     const bool direct =
-        !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL | ND_FACT_GEMM_TC)) && s.max_dim <= DIRECT_MAX;
-    const int tile = tc ? tile_tc : small ? tile_s : tile_l;
+        !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && s.max_dim <= DIRECT_MAX;
+    const int tile = small ? tile_s : tile_l;
     int b = int(tiles.size());
+    if (tc) {
+      const int sb = int(tct.split.size());
+      int64_t off = 0;
+      for (int k = s.begin; k < s.begin + s.count; ++k) {
+        TcDesc t{};
+        t.desc = k;
+        off = gemm_tc_scratch(gd[k], t, off);
+        const int ti = int(tct.desc.size());
+        tct.desc.push_back(t);
+        for (int r0 = 0; r0 < t.rba * TC_M; r0 += 32) tct.split.push_back(TcSplit{ti, 0, r0, 0});
+        for (int r0 = 0; r0 < t.rbb * TC_N; r0 += 32) tct.split.push_back(TcSplit{ti, 1, r0, 0});
+        for (int i = 0; i < t.rba; ++i)
+          for (int j = 0; j < t.rbb; ++j) tiles.push_back(TileRef{ti, i, j, 0});
+      }
+      tct.bytes = std::max(tct.bytes, off);
+      ranges[si] = TileRange{b, int(tiles.size()) - b, 2, sb, int(tct.split.size()) - sb};
+      continue;
+    }
     for (int k = s.begin; k < s.begin + s.count; ++k) {
       const GemmDesc& g = gd[k];
       if (direct) {
@@ -232,7 +274,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
     }
-    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : tc ? 2 : small ? 1 : 0};
+    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : small ? 1 : 0, 0, 0};
   }
 }
 
@@ -278,7 +320,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
         break;
       case ST_GEMM:
         if (tr[si].kind == 2)
-          launch_gemm_tc(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
+          launch_gemm_tc(w, f->d_gemm, f->d_tcd, f->d_tcsplit + tr[si].sfirst, tr[si].scount,
+                         f->d_tiles + tr[si].first, tr[si].count, f->tc_scratch, f->tc_stride, f->d_tc_timeout, s);
         else if (tr[si].kind == 3)
           Kern<T>::gemm_direct(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
         else
@@ -574,16 +617,27 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
     const int tl = tile_of(false), ts = tile_of(true);
     std::vector<TileRef> tiles;
     const double sc = small_tile_cost(precision);
-    const int ttc = precision == ND_PREC_FP32X2 ? gemm_tc_tile() : 0;
-    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_factor);
-    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_green);
-    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_lesser[0]);
-    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, ttc, tiles, f->tr_lesser[1]);
+    const bool tc_ok = precision == ND_PREC_FP32X2;
+    TcTables tct;
+    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_factor);
+    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_green);
+    // the G^< schedule with a phonon Sigma^< runs only on a phonon workspace
+    const bool ph = (flags & ND_FACT_PHONON) != 0;
+    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_lesser[0]);
+    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, tc_ok && ph, tct, tiles, f->tr_lesser[1]);
     if (f->adj) {
-      build_tiles(f->sched_adj_fwd, gemm_all, tl, ts, flags, sc, ttc, tiles, f->tr_adj_fwd);
-      build_tiles(f->sched_adj_bwd, gemm_all, tl, ts, flags, sc, ttc, tiles, f->tr_adj_bwd);
+      build_tiles(f->sched_adj_fwd, gemm_all, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_adj_fwd);
+      build_tiles(f->sched_adj_bwd, gemm_all, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_adj_bwd);
     }
     TRY(dupload(f, tiles, &f->d_tiles));
+    if (!tct.desc.empty()) {
+      TRY(dupload(f, tct.desc, &f->d_tcd));
+      TRY(dupload(f, tct.split, &f->d_tcsplit));
+      f->tc_stride = tct.bytes;
+      TRY(dalloc(f, (void**)&f->tc_scratch, size_t(tct.bytes) * size_t(max_ne)));
+    }
+    TRY(dalloc(f, (void**)&f->d_tc_timeout, sizeof(int)));
+    cudaMemset(f->d_tc_timeout, 0, sizeof(int));
   }
   const size_t ne = size_t(max_ne), n = size_t(p->n), se = size_t(p->sigma_elems);
   TRY(dalloc(f, (void**)&f->st_H, size_t(std::max(1, p->nnz)) * 8));
@@ -638,6 +692,7 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
   f->cur_E = E;
   f->have_lesser = false;
   ND_CUDA(cudaMemsetAsync(f->d_status, 0, sizeof(int), s));
+  ND_CUDA(cudaMemsetAsync(f->d_tc_timeout, 0, sizeof(int), s));
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, n_e};
   const int nc = int(p->cl.size());
   if (f->precision == ND_PREC_FP64) return factor_t<double>(f, w, H, E, eta, sr, ph, nc, s);
@@ -891,9 +946,11 @@ extern "C" nd_status nd_density(const double* Gl, const double* weights, int32_t
 
 extern "C" nd_status nd_fact_status(nd_fact* f, int32_t* n_singular) {
   if (!f) return fail(ND_ERR_INVALID_ARG, "nd_fact_status: NULL handle");
-  int h = 0;
+  int h = 0, to = 0;
   ND_CUDA(cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  ND_CUDA(cudaMemcpy(&to, f->d_tc_timeout, sizeof(int), cudaMemcpyDeviceToHost));
   if (n_singular) *n_singular = h;
+  if (to) return fail(ND_ERR_TIMEOUT, "nd_fact_status: a tensor-core product gave up waiting; results are invalid");
   if (h > 0) return fail(ND_ERR_SINGULAR, "nd_fact_status: " + std::to_string(h) + " singular pivot(s)");
   return ND_OK;
 }

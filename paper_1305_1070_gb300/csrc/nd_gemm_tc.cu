@@ -1,30 +1,45 @@
-// Batched FP32-pair complex GEMM on the tensor cores: C = alpha op(A) op(B) + beta D
-// for the descriptors and tiles of one schedule step, like k_gemm, with the
-// same results up to rounding at the FP32-pair level.
+// Batched FP32-pair complex GEMM on the fifth-generation tensor cores
+// (tcgen05): C = alpha op(A) op(B) + beta D for the descriptors of one
+// schedule step, with the results of k_gemm up to rounding at the FP32-pair
+// level.
 //
-// Exact products of integer digits (the splitting scheme of Ozaki, Ogita, Oishi
-// and Rump, Numer. Algorithms 59 (2012), in its fixed-point form):
+// Exact products of integer digits (the splitting scheme of Ozaki, Ogita,
+// Oishi and Rump, Numer. Algorithms 59 (2012), in its fixed-point form):
 //  * every row i of op(A) gets a scale 2^eA[i] >= max_k |Re a_ik| + |Im a_ik|,
-//    every column j of op(B) a scale 2^eB[j] likewise (first pass of the CTA);
+//    every column j of op(B) a scale 2^eB[j] likewise;
 //  * a real x of row i becomes the integer X = round(x 2^(54 - eA[i])),
 //    |X| < 2^54, written with 7 balanced base-256 digits,
-//    X = sum_t d_t 256^(6-t), d_t in [-128, 127]; digits are exact in BF16;
-//  * a digit product is exact (|d d'| <= 2^14) and so is the FP32 sum of up
-//    to 2^10 of them, so the products of digit pair (t, t') are summed on the
-//    tensor cores (mma.sync m16n8k16, BF16 in, FP32 accumulate) into one
-//    accumulator per group g = t + t' < 7 (pairs with t + t' >= 7 fall below
-//    the 2^-54 relative resolution and are dropped), and every 8 k-steps
-//    (128 terms, at most 7 * 128 * 2^14 < 2^24 per group) the groups are
-//    scaled by 2^(8 (12 - g) + eA + eB - 108) and added into FP32-pair
-//    accumulators;
-//  * complex products use three real products, Re a Re b, Im a Im b and
+//    X = sum_t d_t 256^(6-t), |d_t| <= 128; digits are exact in BF16;
+//  * a digit product is exact (|d d'| <= 2^14) and so is the FP32 sum of the
+//    products of the pairs (t, t') of one group g = t + t' (at most 7 pairs)
+//    over 128 k (7 * 128 * 2^14 < 2^24), so the tensor cores sum every group
+//    exactly; pairs with t + t' >= 7 fall below the 2^-54 resolution and are
+//    dropped (28 pairs of the 49);
+//  * complex products take three real products, Re a Re b, Im a Im b and
 //    (Re a + Im a)(Re b + Im b) (the sum formed exactly on the integers), so
 //    Re = P1 - P2, Im = P3 - P1 - P2.
-// The error is normwise, about 2^-54 max|a_i.| max|b_.j| k per entry: 48-bit
-// accuracy for entries down to 2^-6 of their row (column) maximum, like the
-// FP32-pair product on the FP32 pipe for the rest.  One CTA (8 warps) per
-// 32 x 32 tile; each warp owns one m16n8 accumulator tile per group and
-// component.
+// The error is normwise, about 2^-54 max|a_i.| max|b_.j| k per entry.
+//
+// Two kernels per launch:
+//  * k_tc_split: the scale and the digits of Re, Im and Re + Im of every row
+//    of op(A) and column of op(B) of every descriptor, once, into a per-energy
+//    scratch, as BF16 planes already in the tensor cores' shared-memory
+//    operand layout (K-major, core matrices of 8 rows x 16 bytes, no
+//    swizzle), so that the 7 planes of one tile and 16 k are one contiguous
+//    block;
+//  * k_gemm_tc: one CTA per 128 x 64 output tile and energy, warp-specialised.
+//    A producer warp streams the digit blocks into a 4-stage shared-memory
+//    ring with bulk asynchronous copies (cp.async.bulk, completion by mbarrier
+//    transaction count).  One thread issues the 28 digit-pair MMAs per 16 k
+//    and component (tcgen05.mma kind::f16, M = 128, N = 64, K = 16, BF16 in,
+//    FP32 accumulators in TMEM: one 64-column accumulator per group, 448 of
+//    the 512 columns) and signals the stage free with tcgen05.commit.  Every
+//    128 k and at the end of each component eight warps read the group sums
+//    (tcgen05.ld), add them into FP32-pair accumulators of Re and Im in
+//    registers (32 outputs per thread) and hand the TMEM back.
+// Every wait is bounded.  A wait that gives up raises the CTA's abort flag;
+// the CTA then drains its copies and MMAs, frees its TMEM, skips its output
+// and sets *timeout (reported by nd_fact_status as ND_ERR_TIMEOUT).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -35,18 +50,19 @@
 namespace ndgf {
 namespace {
 
-constexpr int TC_BM = 32, TC_BN = 32, TC_BK = 16;
-constexpr int TC_S = 7;       // digits per real
-constexpr int TC_F = 54;      // fixed-point bits below the row (column) scale
-constexpr int TC_PAD = 24;    // k stride of a digit row (bf16), keeps fragment loads free of bank conflicts
-constexpr int TC_FLUSH = 8;   // k-steps between two flushes of the exact FP32 group sums
-constexpr int TC_NT = 256;    // threads per CTA
+constexpr int TC_S = TC_DIGITS;  // digits per real
+constexpr int TC_F = 54;         // fixed-point bits below the row (column) scale
+constexpr int SA = TC_S * int(TC_PLANE_A), SB = TC_S * int(TC_PLANE_B);  // one stage: 7 planes of A and of B
+constexpr int STAGES = 4;
+constexpr int CHUNK = 8;      // 16-k blocks summed exactly in TMEM between two reads (128 terms)
+constexpr int FW = 8;         // accumulator (flush and epilogue) warps
+constexpr int NT = (FW + 2) * 32;  // + producer warp + MMA warp
+constexpr int TMEM_COLS = 512;     // allocated (TC_S x TC_N = 448 used)
+constexpr size_t SMEM = size_t(STAGES) * (SA + SB) + 1024;  // + alignment slack
+constexpr long SPIN = 1L << 25;    // polls before a wait gives up
 
-// shared-memory layout (bytes)
-constexpr size_t TC_DIG_A = size_t(TC_S) * 3 * TC_BM * TC_PAD * 2;
-constexpr size_t TC_DIG_B = size_t(TC_S) * 3 * TC_BN * TC_PAD * 2;
-constexpr size_t TC_ACC = size_t(TC_NT) * 4 * 3 * sizeof(float2);  // per thread: 4 outputs x 3 products
-constexpr size_t TC_SMEM = TC_DIG_A + TC_DIG_B + TC_ACC + size_t(TC_BM + TC_BN) * sizeof(int);
+static_assert(TC_S * TC_N <= TMEM_COLS, "group accumulators exceed the TMEM columns");
+static_assert(TC_M == 128 && TC_N % 16 == 0 && TC_N <= 256, "tcgen05 kind::f16 shape with M = 128");
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower address)
@@ -77,12 +93,11 @@ __device__ __forceinline__ void carry(float d[TC_S]) {
   }
 }
 
-// Re, Im and Re + Im of two FP32-pair complexes at consecutive k of one row
-// (column) as 7 digits each (scale factor sc = 2^(54 - e)), stored as packed
-// BF16 pairs at dst[(t * 3 + c) * stride] (t = 0 the most significant digit,
-// c = Re, Im, Re + Im).  hi and lo parts are split separately and their
-// digit sums carried; all values are integers below 2^24 in magnitude.
-__device__ __forceinline__ void split_pair_store(float4 v0, float4 v1, float sc, unsigned* dst, size_t stride) {
+// Digits of Re, Im and Re + Im of two FP32-pair complexes at consecutive k of
+// one row (scale factor sc = 2^(54 - e)) as packed BF16 pairs w[c][t][q].
+// hi and lo parts are split separately and their digit sums carried; all
+// values are integers below 2^24 in magnitude.
+__device__ __forceinline__ void split_pair(float4 v0, float4 v1, float sc, unsigned (&w)[3][TC_S][4], int q) {
   float r[2][TC_S], im[2][TC_S];
   const float4 v[2] = {v0, v1};
 #pragma unroll
@@ -99,6 +114,11 @@ __device__ __forceinline__ void split_pair_store(float4 v0, float4 v1, float sc,
     for (int t = 0; t < TC_S; ++t) im[p][t] = a[t] + b[t];
     carry(im[p]);
   }
+#pragma unroll
+  for (int t = 0; t < TC_S; ++t) {
+    w[0][t][q] = pack_bf16(r[0][t], r[1][t]);
+    w[1][t][q] = pack_bf16(im[0][t], im[1][t]);
+  }
   float s[2][TC_S];
 #pragma unroll
   for (int p = 0; p < 2; ++p) {
@@ -107,11 +127,7 @@ __device__ __forceinline__ void split_pair_store(float4 v0, float4 v1, float sc,
     carry(s[p]);
   }
 #pragma unroll
-  for (int t = 0; t < TC_S; ++t) {
-    dst[(size_t(t) * 3 + 0) * stride] = pack_bf16(r[0][t], r[1][t]);
-    dst[(size_t(t) * 3 + 1) * stride] = pack_bf16(im[0][t], im[1][t]);
-    dst[(size_t(t) * 3 + 2) * stride] = pack_bf16(s[0][t], s[1][t]);
-  }
+  for (int t = 0; t < TC_S; ++t) w[2][t][q] = pack_bf16(s[0][t], s[1][t]);
 }
 
 __device__ __forceinline__ int scale_exp(float m) {
@@ -120,183 +136,383 @@ __device__ __forceinline__ int scale_exp(float m) {
   return e < -70 ? -70 : (e > 120 ? 120 : e);
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], const unsigned b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+// Byte offset of element (r, k), k < 16, in a K-major digit plane: core
+// matrices of 8 rows x 8 k (16 bytes per row, 128 bytes each); the two core
+// matrices of a row group along k are 128 bytes apart (leading byte offset),
+// consecutive row groups 256 bytes (stride byte offset).
+__host__ __device__ constexpr uint32_t core_off(int r, int k) {
+  return uint32_t((r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
+constexpr uint32_t CORE_LBO = 128, CORE_SBO = 256;
 
-__global__ void __launch_bounds__(TC_NT, 2) k_gemm_tc(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles,
-                                                   float4* arena, int64_t se, const float4* __restrict__ aux,
-                                                   int64_t sa) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  __nv_bfloat16* Ad = reinterpret_cast<__nv_bfloat16*>(sm);             // [S][3][BM][PAD]
-  __nv_bfloat16* Bd = reinterpret_cast<__nv_bfloat16*>(sm + TC_DIG_A);  // [S][3][BN][PAD]
-  float2* acc_dd = reinterpret_cast<float2*>(sm + TC_DIG_A + TC_DIG_B);  // [NT][4][3]
-  int* eA = reinterpret_cast<int*>(sm + TC_DIG_A + TC_DIG_B + TC_ACC);
-  int* eB = eA + TC_BM;
-
-  const TileRef tr = tiles[blockIdx.x];
-  const GemmDesc d = descs[tr.desc];
+// ---- split: one CTA per 32 rows of op(A) or columns of op(B), 8 threads per row
+__global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ descs, const TcDesc* __restrict__ tcd,
+                                                  const TcSplit* __restrict__ items, const float4* __restrict__ arena,
+                                                  int64_t se, const float4* __restrict__ aux, int64_t sa,
+                                                  unsigned char* __restrict__ scratch, int64_t ss) {
+  const TcSplit it = items[blockIdx.x];
+  const TcDesc t = tcd[it.tcd];
+  const GemmDesc d = descs[t.desc];
   const int64_t e = blockIdx.y;
-  float4* base = arena + e * se;
-  const float4* abase = aux + e * sa;
-  const float4* A = (d.offA & AUX_BIT) ? abase + (d.offA & ~AUX_BIT) : base + d.offA;
-  const float4* B = (d.offB & AUX_BIT) ? abase + (d.offB & ~AUX_BIT) : base + d.offB;
-  const int m0 = tr.tm * TC_BM, n0 = tr.tn * TC_BN;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool transA = d.opA != OP_N;
-  const bool transB = (d.opB == OP_T || d.opB == OP_H);
-  const bool conjB = (d.opB == OP_C || d.opB == OP_H);
-  auto a_at = [&](int i, int k) -> float4 {  // op(A)[m0 + i][k], zero outside
-    const int gm = m0 + i;
-    if (gm >= d.m || k >= d.k) return make_float4(0.f, 0.f, 0.f, 0.f);
-    return transA ? A[int64_t(k) * d.lda + gm] : A[int64_t(gm) * d.lda + k];
-  };
-  auto b_at = [&](int k, int j) -> float4 {  // op(B)[k][n0 + j], zero outside
-    const int gn = n0 + j;
-    if (gn >= d.n || k >= d.k) return make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 v = transB ? B[int64_t(gn) * d.ldb + k] : B[int64_t(k) * d.ldb + gn];
-    if (conjB) {
+  const bool side_a = it.side == 0;
+  const int64_t off = side_a ? d.offA : d.offB;
+  const float4* X = (off & AUX_BIT) ? aux + e * sa + (off & ~AUX_BIT) : arena + e * se + off;
+  const int64_t ld = side_a ? d.lda : d.ldb;
+  // element (r, k) of op(A), or of op(B)^T, sits at X[r ld + k] (row major) or X[k ld + r]
+  const bool row_major = side_a ? d.opA == OP_N : (d.opB == OP_T || d.opB == OP_H);
+  const bool cj = !side_a && (d.opB == OP_C || d.opB == OP_H);
+  const int rows = side_a ? d.m : d.n;
+  const int r = it.r0 + (threadIdx.x >> 3), part = threadIdx.x & 7;
+  const bool live = r < rows;
+  auto at = [&](int k) -> float4 {
+    if (!live || k >= d.k) return make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v = row_major ? X[int64_t(r) * ld + k] : X[int64_t(k) * ld + r];
+    if (cj) {
       v.z = -v.z;
       v.w = -v.w;
     }
     return v;
   };
-
-  // ---- pass 1: row and column scales over the whole k range
-  if (tid < TC_BM + TC_BN) eA[tid] = 0;  // float bits of the running maxima (non-negative)
-  __syncthreads();
-  {  // 8 threads per row (column), each over every 8th k
-    const int q = tid >> 3, part = tid & 7;
-    float ma = 0.f, mb = 0.f;
-    for (int k = part; k < d.k; k += 8) {
-      const float4 va = a_at(q, k), vb = b_at(k, q);
-      ma = fmaxf(ma, fabsf(va.x) + fabsf(va.z));
-      mb = fmaxf(mb, fabsf(vb.x) + fabsf(vb.z));
-    }
-    atomicMax(&eA[q], __float_as_int(ma));
-    atomicMax(&eB[q], __float_as_int(mb));
+  float mx = 0.f;
+  for (int k = part; k < d.k; k += 8) {
+    const float4 v = at(k);
+    mx = fmaxf(mx, fabsf(v.x) + fabsf(v.z));
   }
-  __syncthreads();
-  if (tid < TC_BM + TC_BN) {
-    // a little headroom above the hi parts: Re + Im and the lo parts stay below 2^e
-    eA[tid] = scale_exp(__int_as_float(eA[tid]) * 1.0001f);
-  }
-  for (int64_t i = tid; i < int64_t(TC_NT) * 4 * 3; i += TC_NT) acc_dd[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-
-  // ---- pass 2: digit products on the tensor cores
-  const int g = lane >> 2, c4 = lane & 3;
-  const int wr = (warp >> 2) * 16, wc = (warp & 3) * 8;  // warp block: rows wr.., cols wc..
-  float acc[TC_S][3][4];
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+  // a little headroom above the hi parts: Re + Im and the lo parts stay below 2^e
+  const int ex = scale_exp(mx * 1.0001f);
+  unsigned char* scr = scratch + e * ss;
+  if (part == 0) reinterpret_cast<int*>(scr)[(side_a ? t.exp_a : t.exp_b) + r] = ex;
+  const float sc = ldexpf(1.f, TC_F - ex);
+  const int R = side_a ? TC_M : TC_N, RB = side_a ? t.rba : t.rbb;
+  const int64_t P = side_a ? TC_PLANE_A : TC_PLANE_B;
+  unsigned char* dig = scr + (side_a ? t.dig_a : t.dig_b);
+  const int rb = r / R, rr = r - rb * R;
+  for (int o = part; o < 2 * t.kb; o += 8) {  // octets of k
+    const int kb = o >> 1, k0 = o * 8;
+    unsigned w[3][TC_S][4];
 #pragma unroll
-  for (int q = 0; q < TC_S; ++q)
+    for (int q = 0; q < 4; ++q) split_pair(at(k0 + 2 * q), at(k0 + 2 * q + 1), sc, w, q);
+    const uint32_t co = core_off(rr, (o & 1) * 8);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[q][c][r] = 0.f;
-
-  const int nk = (d.k + TC_BK - 1) / TC_BK;
-  for (int kt = 0; kt < nk; ++kt) {
-    const int k0 = kt * TC_BK;
-    // digits of the A tile (32 x 16) and the B tile (16 x 32): each thread
-    // splits two consecutive k of one row of op(A) and of one column of op(B)
-    {
-      const int i = tid >> 3, kk = (tid & 7) * 2;
-      split_pair_store(a_at(i, k0 + kk), a_at(i, k0 + kk + 1), ldexpf(1.f, TC_F - eA[i]),
-                       reinterpret_cast<unsigned*>(Ad + size_t(i) * TC_PAD + kk), size_t(TC_BM) * TC_PAD / 2);
-      split_pair_store(b_at(k0 + kk, i), b_at(k0 + kk + 1, i), ldexpf(1.f, TC_F - eB[i]),
-                       reinterpret_cast<unsigned*>(Bd + size_t(i) * TC_PAD + kk), size_t(TC_BN) * TC_PAD / 2);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int t1 = 0; t1 < TC_S; ++t1) {
-      unsigned af[3][4];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const __nv_bfloat16* a0 = Ad + ((size_t(t1) * 3 + c) * TC_BM + wr + g) * TC_PAD + 2 * c4;
-        af[c][0] = *reinterpret_cast<const unsigned*>(a0);
-        af[c][1] = *reinterpret_cast<const unsigned*>(a0 + 8 * TC_PAD);
-        af[c][2] = *reinterpret_cast<const unsigned*>(a0 + 8);
-        af[c][3] = *reinterpret_cast<const unsigned*>(a0 + 8 * TC_PAD + 8);
+      for (int tt = 0; tt < TC_S; ++tt) {
+        unsigned char* pl = dig + (((int64_t(c) * t.kb + kb) * RB + rb) * TC_S + tt) * P + co;
+        *reinterpret_cast<uint4*>(pl) = make_uint4(w[c][tt][0], w[c][tt][1], w[c][tt][2], w[c][tt][3]);
       }
+  }
+}
+
+// ---- PTX wrappers (tcgen05, mbarrier, bulk copies)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity.  Gives up when the CTA's
+// abort flag is raised (checked every 64 polls) or after SPIN polls (then
+// raises it).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+  for (long i = 0; i < SPIN; ++i) {
+    if (mbar_try(b, parity)) return true;
+    if ((i & 63) == 63 && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  return false;
+}
+// Bounded wait that ignores the abort flag: for work that completes by
+// itself (copies and MMAs in flight) before shared memory or TMEM is released.
+__device__ __forceinline__ bool mbar_drain(uint64_t* b, uint32_t parity) {
+  for (long i = 0; i < SPIN; ++i)
+    if (mbar_try(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (16-byte units), descriptor version 1, base offset 0, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  return uint64_t((addr >> 4) & 0x3FFF) | (uint64_t((CORE_LBO >> 4) & 0x3FFF) << 16) |
+         (uint64_t((CORE_SBO >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
+}
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
+                           (uint32_t(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(ad), "l"(bd), "r"(IDESC), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+  uint32_t r0, r1, r2, r3;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(taddr)
+               : "memory");
+  v[0] = __uint_as_float(r0);
+  v[1] = __uint_as_float(r1);
+  v[2] = __uint_as_float(r2);
+  v[3] = __uint_as_float(r3);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// (H, L) += (h, l), unnormalised pairs
+__device__ __forceinline__ void dd_acc(float& H, float& L, float h, float l) {
+  float s, err;
+  two_sum(H, h, s, err);
+  H = s;
+  L += err + l;
+}
+
+__global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ descs, const TcDesc* __restrict__ tcd,
+                                                   const TileRef* __restrict__ tiles, float4* arena, int64_t se,
+                                                   const unsigned char* __restrict__ scratch, int64_t ss,
+                                                   int* timeout) {
+  extern __shared__ unsigned char sm_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accfull, accempty, done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  __shared__ int eA[TC_M], eB[TC_N];
+  unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+
+  const TileRef tr = tiles[blockIdx.x];
+  const TcDesc t = tcd[tr.desc];
+  const GemmDesc d = descs[t.desc];
+  const int64_t e = blockIdx.y;
+  const unsigned char* scr = scratch + e * ss;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  {
+    const int* xa = reinterpret_cast<const int*>(scr) + t.exp_a + int64_t(tr.tm) * TC_M;
+    const int* xb = reinterpret_cast<const int*>(scr) + t.exp_b + int64_t(tr.tn) * TC_N;
+    for (int i = tid; i < TC_M; i += NT) eA[i] = xa[i];
+    for (int i = tid; i < TC_N; i += NT) eB[i] = xb[i];
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 32) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&accfull, 1);
+    mbar_init(&accempty, FW);
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int* abrt = &abort_flag;
+  const int KB = t.kb, njobs = 3 * KB;  // job j: component j / KB, 16-k block j % KB
+
+  if (warp == FW) {
+    // ---- producer: digit blocks of A and B into the stage ring
+    if (lane == 0) {
+      int j = 0;
+      for (; j < njobs; ++j) {
+        const int s = j % STAGES, u = j / STAGES;
+        if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, abrt)) break;
+        const int c = j / KB, kb = j - c * KB;
+        const unsigned char* ga = scr + t.dig_a + ((int64_t(c) * KB + kb) * t.rba + tr.tm) * int64_t(SA);
+        const unsigned char* gb = scr + t.dig_b + ((int64_t(c) * KB + kb) * t.rbb + tr.tn) * int64_t(SB);
+        unsigned char* st = sm + size_t(s) * (SA + SB);
+        mbar_expect_tx(&full[s], SA + SB);
+        bulk_g2s(st, ga, SA, &full[s]);
+        bulk_g2s(st + SA, gb, SB, &full[s]);
+      }
+      // the last copies into every stage have landed before the CTA ends
+      for (int jj = j > STAGES ? j - STAGES : 0; jj < j; ++jj) mbar_drain(&full[jj % STAGES], (jj / STAGES) & 1);
+    }
+  } else if (warp == FW + 1) {
+    // ---- MMA issue: 28 digit-pair products per 16 k into the group accumulators
+    if (lane == 0) {
+      int q = 0;  // chunks handed to the accumulator warps
+      for (int j = 0; j < njobs; ++j) {
+        const int s = j % STAGES, u = j / STAGES;
+        const int kb = j % KB, kc = kb % CHUNK;
+        if (kc == 0 && q > 0) {
+          if (!mbar_wait(&accempty, (q - 1) & 1, abrt)) break;
+          tc_fence_after();
+        }
+        if (!mbar_wait(&full[s], u & 1, abrt)) break;
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sm + size_t(s) * (SA + SB)), b0 = a0 + SA;
 #pragma unroll
-      for (int t2 = 0; t2 < TC_S - t1; ++t2) {
+        for (int t1 = 0; t1 < TC_S; ++t1)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const __nv_bfloat16* b0 = Bd + ((size_t(t2) * 3 + c) * TC_BN + wc + g) * TC_PAD + 2 * c4;
-          const unsigned bf[2] = {*reinterpret_cast<const unsigned*>(b0), *reinterpret_cast<const unsigned*>(b0 + 8)};
-          mma_bf16(acc[t1 + t2][c], af[c], bf);
+          for (int t2 = 0; t2 < TC_S - t1; ++t2)
+            mma_bf16(tmem + uint32_t((t1 + t2) * TC_N), sdesc(a0 + t1 * uint32_t(TC_PLANE_A)),
+                     sdesc(b0 + t2 * uint32_t(TC_PLANE_B)), (kc == 0 && t1 == 0) ? 0u : 1u);
+        if (j + STAGES < njobs) mma_commit(&empty[s]);
+        if (kc == CHUNK - 1 || kb == KB - 1) {
+          mma_commit(&accfull);
+          ++q;
         }
       }
+      // every MMA issued has completed before the TMEM is released
+      mma_commit(&done);
+      mbar_drain(&done, 0);
     }
-    __syncthreads();
-    if ((kt + 1) % TC_FLUSH == 0 || kt == nk - 1) {
-      // groups -> FP32-pair accumulators (each thread owns its 4 outputs)
+  } else {
+    // ---- accumulator warps: TMEM lanes 32 (warp % 4) .., columns 32 (warp / 4) ..
+    const int quad = warp & 3, half = warp >> 2;
+    const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(half * 32);
+    float ac[32][4];  // Re (hi, lo), Im (hi, lo) of 32 outputs, unnormalised pairs
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int i = wr + g + (r >> 1) * 8, j = wc + 2 * c4 + (r & 1);
-        const int ex = eA[i] + eB[j] - 2 * TC_F;
+    for (int o = 0; o < 32; ++o) ac[o][0] = ac[o][1] = ac[o][2] = ac[o][3] = 0.f;
+    const int nch = (KB + CHUNK - 1) / CHUNK;
+    bool ok = true;
+    int q = 0;
+    for (int c = 0; c < 3 && ok; ++c) {
+      for (int ch = 0; ch < nch; ++ch, ++q) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&accfull, q & 1, abrt));
+        if (!ok) break;
+        tc_fence_after();
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float2& s = acc_dd[(size_t(tid) * 4 + r) * 3 + c];
-          float h = s.x, lo = s.y;
+        for (int cs = 0; cs < 32; cs += 4) {
+          float v[TC_S][4];
 #pragma unroll
-          for (int q = 0; q < TC_S; ++q) {
-            const float v = ldexpf(acc[q][c][r], ex + 8 * (2 * (TC_S - 1) - q));
-            float sh, se2;
-            two_sum(h, v, sh, se2);
-            h = sh;
-            lo += se2;
-            acc[q][c][r] = 0.f;
+          for (int g = 0; g < TC_S; ++g) tmem_ld4(tbase + uint32_t(g * TC_N + cs), v[g]);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            // P = sum_g D_g 2^(-8 g) as an unnormalised pair
+            float h = v[0][i], l = 0.f;
+#pragma unroll
+            for (int g = 1; g < TC_S; ++g) {
+              float s, err;
+              two_sum(h, v[g][i] * __int_as_float((127 - 8 * g) << 23), s, err);
+              h = s;
+              l += err;
+            }
+            float* a = ac[cs + i];
+            if (c == 0) {  // Re += P1, Im -= P1
+              dd_acc(a[0], a[1], h, l);
+              dd_acc(a[2], a[3], -h, -l);
+            } else if (c == 1) {  // Re -= P2, Im -= P2
+              dd_acc(a[0], a[1], -h, -l);
+              dd_acc(a[2], a[3], -h, -l);
+            } else {  // Im += P3
+              dd_acc(a[2], a[3], h, l);
+            }
           }
-          s = make_float2(h, lo);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accempty);
+      }
+    }
+    // ---- epilogue: scale 2^(eA + eB - 12) (the groups carry 2^96 of the 2^-108), alpha, beta D
+    if (ok && !*abrt) {
+      const int row = quad * 32 + lane;
+      const int gm = tr.tm * TC_M + row;
+      if (gm < d.m) {
+        float4* C = arena + e * se + d.offC;
+        const float4* D = arena + e * se + d.offD;
+        using O = Ops<DF>;
+#pragma unroll
+        for (int o = 0; o < 32; ++o) {
+          const int jl = half * 32 + o, gn = tr.tn * TC_N + jl;
+          if (gn < d.n) {
+            const int ex = eA[row] + eB[jl] - 12;
+            f2 re, im;
+            two_sum(ac[o][0], ac[o][1], re.h, re.l);
+            two_sum(ac[o][2], ac[o][3], im.h, im.l);
+            float4 v = make_float4(ldexpf(re.h, ex), ldexpf(re.l, ex), ldexpf(im.h, ex), ldexpf(im.l, ex));
+            if (d.alpha == -1.0)
+              v = O::neg(v);
+            else if (d.alpha != 1.0)
+              v = O::scale(v, d.alpha);
+            if (d.beta != 0.0) {
+              const float4 dv = D[int64_t(gm) * d.ldd + gn];
+              v = O::add(v, d.beta == 1.0 ? dv : O::scale(dv, d.beta));
+            }
+            C[int64_t(gm) * d.ldc + gn] = v;
+          }
         }
       }
     }
   }
-  // ---- epilogue: Re = P1 - P2, Im = P3 - P1 - P2, alpha, beta D
-  float4* C = base + d.offC;
-  const float4* D = base + d.offD;
-  using O = Ops<DF>;
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-      const int i = wr + g + (r >> 1) * 8, j = wc + 2 * c4 + (r & 1);
-      const int gm = m0 + i, gn = n0 + j;
-      if (gm >= d.m || gn >= d.n) continue;
-      const float2* s = acc_dd + (size_t(tid) * 4 + r) * 3;
-      f2 p[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) two_sum(s[c].x, s[c].y, p[c].h, p[c].l);
-      float4 v = O::mk(dd_sub(p[0], p[1]), dd_sub(dd_sub(p[2], p[0]), p[1]));
-      if (d.alpha == -1.0)
-        v = O::neg(v);
-      else if (d.alpha != 1.0)
-        v = O::scale(v, d.alpha);
-      if (d.beta != 0.0) {
-        const float4 dv = D[int64_t(gm) * d.ldd + gn];
-        v = O::add(v, d.beta == 1.0 ? dv : O::scale(dv, d.beta));
-      }
-      C[int64_t(gm) * d.ldc + gn] = v;
-    }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (tid == 0 && abort_flag) atomicExch(timeout, 1);
 }
 
 }  // namespace
 
-int gemm_tc_tile() { return TC_BM; }
+int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off) {
+  t.kb = (g.k + 15) / 16;
+  t.rba = (g.m + TC_M - 1) / TC_M;
+  t.rbb = (g.n + TC_N - 1) / TC_N;
+  t.dig_a = off;
+  off += 3 * int64_t(t.kb) * t.rba * SA;
+  t.dig_b = off;
+  off += 3 * int64_t(t.kb) * t.rbb * SB;
+  t.exp_a = off / 4;
+  off += int64_t(t.rba) * TC_M * 4;
+  t.exp_b = off / 4;
+  off += int64_t(t.rbb) * TC_N * 4;
+  return (off + 1023) & ~int64_t(1023);
+}
 
-void launch_gemm_tc(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
+void launch_gemm_tc(const Work& w, const GemmDesc* d, const TcDesc* tcd, const TcSplit* splits, int n_splits,
+                    const TileRef* tiles, int n_tiles, unsigned char* scratch, int64_t ss, int* timeout,
+                    cudaStream_t s) {
   if (n_tiles <= 0 || w.n_e <= 0) return;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(TC_SMEM));
+    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
     attr = true;
   }
-  k_gemm_tc<<<dim3(n_tiles, w.n_e), TC_NT, TC_SMEM, s>>>(d, tiles, (float4*)w.arena, w.se, (const float4*)w.aux,
-                                                         w.sa);
+  if (n_splits > 0)
+    k_tc_split<<<dim3(n_splits, w.n_e), 256, 0, s>>>(d, tcd, splits, (const float4*)w.arena, w.se,
+                                                     (const float4*)w.aux, w.sa, scratch, ss);
+  k_gemm_tc<<<dim3(n_tiles, w.n_e), NT, SMEM, s>>>(d, tcd, tiles, (float4*)w.arena, w.se, scratch, ss, timeout);
 }
 
 }  // namespace ndgf

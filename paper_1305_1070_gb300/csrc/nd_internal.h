@@ -220,8 +220,27 @@ struct Step {
 
 struct TileRef { int32_t desc, tm, tn, pad; };
 // tiles of one GEMM step and its kernel: 0 large tile, 1 small tile, 2 tensor cores,
-// 3 one CTA per descriptor (small blocks)
-struct TileRange { int32_t first, count, kind; };
+// 3 one CTA per descriptor (small blocks).  Tensor-core steps also own the
+// digit-split work items [sfirst, sfirst + scount); their tiles refer to
+// TcDesc entries.
+struct TileRange { int32_t first, count, kind, sfirst, scount; };
+
+// Tensor-core products (FP32 pairs): output tiles of TC_M x TC_N, operands
+// as TC_DIGITS BF16 digit planes per real, 16 k per block.  Per energy, the
+// scratch of a step holds for every descriptor the planes of op(A)
+// [3][kb][rba][TC_DIGITS][TC_M x 16] and of op(B)^T [3][kb][rbb][TC_DIGITS][TC_N x 16]
+// (components Re, Im, Re + Im) and the exponents of the rows of op(A) and
+// columns of op(B).
+constexpr int TC_M = 128, TC_N = 64, TC_DIGITS = 7;
+constexpr int64_t TC_PLANE_A = int64_t(TC_M) * 16 * 2, TC_PLANE_B = int64_t(TC_N) * 16 * 2;  // bytes
+struct TcDesc {
+  int64_t dig_a, dig_b;  // byte offsets of the digit planes in the per-energy scratch
+  int64_t exp_a, exp_b;  // int32 offsets of the exponents (rba * TC_M and rbb * TC_N entries)
+  int32_t desc;          // GEMM descriptor
+  int32_t kb, rba, rbb;  // 16-k blocks, TC_M-row blocks of op(A), TC_N-column blocks of op(B)
+};
+// 32 rows of op(A) (side 0) or columns of op(B) (side 1) to split
+struct TcSplit { int32_t tcd, side, r0, pad; };
 
 }  // namespace ndgf
 

@@ -102,9 +102,13 @@ struct Kern {
 };
 
 // FP32-pair GEMM of one schedule step on the tensor cores (nd_gemm_tc.cu):
-// exact BF16 digit products, 32 x 32 tiles.
-int gemm_tc_tile();
-void launch_gemm_tc(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
+// exact BF16 digit products (tcgen05), TC_M x TC_N tiles.  gemm_tc_scratch
+// fills the layout fields of t for descriptor g placed at byte offset off of
+// the per-energy scratch and returns the offset after it.
+int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off);
+void launch_gemm_tc(const Work& w, const GemmDesc* d, const TcDesc* tcd, const TcSplit* splits, int n_splits,
+                    const TileRef* tiles, int n_tiles, unsigned char* scratch, int64_t ss, int* timeout,
+                    cudaStream_t s);
 
 // Final positions of the unknowns after the delayed pivots (one tree level).
 void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s);
