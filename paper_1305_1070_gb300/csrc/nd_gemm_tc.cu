@@ -9,12 +9,13 @@
 //    every column j of op(B) a scale 2^eB[j] likewise;
 //  * a real x of row i becomes the integer X = round(x 2^(54 - eA[i])),
 //    |X| < 2^54, written with 7 balanced base-256 digits,
-//    X = sum_t d_t 256^(6-t), |d_t| <= 128; digits are exact in BF16;
-//  * a digit product is exact (|d d'| <= 2^14) and so is the FP32 sum of the
-//    products of the pairs (t, t') of one group g = t + t' (at most 7 pairs)
-//    over 128 k (7 * 128 * 2^14 < 2^24), so the tensor cores sum every group
-//    exactly; pairs with t + t' >= 7 fall below the 2^-54 resolution and are
-//    dropped (28 pairs of the 49);
+//    X = sum_t d_t 256^(6-t), d_t in [-128, 127] and |d_0| <= 64; digits are
+//    exact in 8 bits and in BF16;
+//  * a digit product is exact (at most 2^14, 2^13 with d_0) and so is the
+//    FP32 sum of the products of the pairs (t, t') of one group g = t + t'
+//    (at most g 2^14 per k for g >= 1) over 160 k (6 * 160 * 2^14 < 2^24), so
+//    the tensor cores sum every group exactly; pairs with t + t' >= 7 fall
+//    below the 2^-54 resolution and are dropped (28 pairs of the 49);
 //  * complex products take three real products, Re a Re b, Im a Im b and
 //    (Re a + Im a)(Re b + Im b) (the sum formed exactly on the integers), so
 //    Re = P1 - P2, Im = P3 - P1 - P2.
@@ -23,20 +24,22 @@
 // Two kernels per launch:
 //  * k_tc_split: the scale and the digits of Re, Im and Re + Im of every row
 //    of op(A) and column of op(B) of every descriptor, once, into a per-energy
-//    scratch, as BF16 planes already in the tensor cores' shared-memory
-//    operand layout (K-major, core matrices of 8 rows x 16 bytes, no
+//    scratch, as 8-bit planes in the byte image of the tensor cores'
+//    shared-memory operand layout (K-major, core matrices of 8 rows x 8 k, no
 //    swizzle), so that the 7 planes of one tile and 16 k are one contiguous
-//    block;
+//    block and widening every byte to BF16 in place gives the operands;
 //  * k_gemm_tc: one CTA per 128 x 64 output tile and energy, warp-specialised.
-//    A producer warp streams the digit blocks into a 4-stage shared-memory
-//    ring with bulk asynchronous copies (cp.async.bulk, completion by mbarrier
-//    transaction count).  One thread issues the 28 digit-pair MMAs per 16 k
-//    and component (tcgen05.mma kind::f16, M = 128, N = 64, K = 16, BF16 in,
-//    FP32 accumulators in TMEM: one 64-column accumulator per group, 448 of
-//    the 512 columns) and signals the stage free with tcgen05.commit.  Every
-//    128 k and at the end of each component eight warps read the group sums
-//    (tcgen05.ld), add them into FP32-pair accumulators of Re and Im in
-//    registers (32 outputs per thread) and hand the TMEM back.
+//    A producer warp streams the 8-bit digit blocks into a 4-stage
+//    shared-memory ring with bulk asynchronous copies (cp.async.bulk,
+//    completion by mbarrier transaction count); eight accumulator warps widen
+//    them to BF16 into a 2-stage operand ring.  One thread issues the 28
+//    digit-pair MMAs per 16 k and component (tcgen05.mma kind::f16, M = 128,
+//    N = 64, K = 16, BF16 in, FP32 accumulators in TMEM: one 64-column
+//    accumulator per group, 448 of the 512 columns) and signals the stage free
+//    with tcgen05.commit.  Every 160 k and at the end of each component the
+//    accumulator warps read the group sums (tcgen05.ld), add them into
+//    FP32-pair accumulators of Re and Im in registers (32 outputs per thread)
+//    and hand the TMEM back.
 // Every wait is bounded.  A wait that gives up raises the CTA's abort flag;
 // the CTA then drains its copies and MMAs, frees its TMEM, skips its output
 // and sets *timeout (reported by nd_fact_status as ND_ERR_TIMEOUT).
@@ -52,13 +55,15 @@ namespace {
 
 constexpr int TC_S = TC_DIGITS;  // digits per real
 constexpr int TC_F = 54;         // fixed-point bits below the row (column) scale
-constexpr int SA = TC_S * int(TC_PLANE_A), SB = TC_S * int(TC_PLANE_B);  // one stage: 7 planes of A and of B
-constexpr int STAGES = 4;
-constexpr int CHUNK = 8;      // 16-k blocks summed exactly in TMEM between two reads (128 terms)
-constexpr int FW = 8;         // accumulator (flush and epilogue) warps
+// one stage: the 7 digit planes of A and of B for 16 k, as bytes and as BF16
+constexpr int SA8 = TC_S * int(TC_PLANE_A), SB8 = TC_S * int(TC_PLANE_B);
+constexpr int SA = 2 * SA8, SB = 2 * SB8;
+constexpr int S8 = 4, S16 = 2;  // byte stages (bulk copies), BF16 stages (MMA operands)
+constexpr int CHUNK = 10;     // 16-k blocks summed exactly in TMEM between two reads (160 terms)
+constexpr int FW = 8;         // accumulator warps: widening, flush, epilogue
 constexpr int NT = (FW + 2) * 32;  // + producer warp + MMA warp
 constexpr int TMEM_COLS = 512;     // allocated (TC_S x TC_N = 448 used)
-constexpr size_t SMEM = size_t(STAGES) * (SA + SB) + 1024;  // + alignment slack
+constexpr size_t SMEM = size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB) + 1024;  // + alignment slack
 constexpr long SPIN = 1L << 25;    // polls before a wait gives up
 
 static_assert(TC_S * TC_N <= TMEM_COLS, "group accumulators exceed the TMEM columns");
@@ -68,36 +73,58 @@ __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower address)
   return *reinterpret_cast<const unsigned*>(&p);
 }
+// Four signed bytes of w (byte 0 first) as two packed BF16 pairs (exact:
+// |value| <= 128); arithmetic shifts sign-extend each byte.
+__device__ __forceinline__ uint2 widen4(unsigned w) {
+  const int v = int(w);
+  const float f0 = float((v << 24) >> 24), f1 = float((v << 16) >> 24);
+  const float f2 = float((v << 8) >> 24), f3 = float(v >> 24);
+  return make_uint2(pack_bf16(f0, f1), pack_bf16(f2, f3));
+}
 
 // Balanced base-256 digits of an integer-valued float V (|V| < 2^54 after
-// rounding): d[6] least significant.  Each step is exact: q = rint(V / 256)
-// and V - 256 q are integers below 2^24 or multiples of the ulp of V.
+// rounding): d[6] least significant, d[t] in [-128, 127] for t >= 1.  Each
+// step is exact: q = rint(V / 256) and V - 256 q are integers below 2^24 or
+// multiples of the ulp of V; a remainder of 128 moves to the next digit.
 __device__ __forceinline__ void digits_f(float V, float d[TC_S]) {
   V = rintf(V);
 #pragma unroll
   for (int t = TC_S - 1; t > 0; --t) {
     const float q = rintf(V * 0.00390625f);
-    d[t] = fmaf(q, -256.f, V);
-    V = q;
+    const float r = fmaf(q, -256.f, V);
+    const float up = r >= 128.f ? 1.f : 0.f;
+    d[t] = fmaf(up, -256.f, r);
+    V = q + up;
   }
   d[0] = V;
 }
 
-// Brings digits in [-2^9, 2^9] back to [-128, 128] by carries toward the top.
+// Brings digits in [-2^9, 2^9] back to [-128, 127] by carries toward the top.
 __device__ __forceinline__ void carry(float d[TC_S]) {
 #pragma unroll
   for (int t = TC_S - 1; t > 0; --t) {
-    const float c = rintf(d[t] * 0.00390625f);
-    d[t] = fmaf(c, -256.f, d[t]);
-    d[t - 1] += c;
+    float c = rintf(d[t] * 0.00390625f);
+    float r = fmaf(c, -256.f, d[t]);
+    const float up = r >= 128.f ? 1.f : 0.f;
+    d[t] = fmaf(up, -256.f, r);
+    d[t - 1] += c + up;
   }
 }
 
-// Digits of Re, Im and Re + Im of two FP32-pair complexes at consecutive k of
-// one row (scale factor sc = 2^(54 - e)) as packed BF16 pairs w[c][t][q].
-// hi and lo parts are split separately and their digit sums carried; all
-// values are integers below 2^24 in magnitude.
-__device__ __forceinline__ void split_pair(float4 v0, float4 v1, float sc, unsigned (&w)[3][TC_S][4], int q) {
+// Low byte of an integer-valued float d, |d| < 2^22: adding 1.5 * 2^23 puts d
+// in two's complement into the low bits of the significand.
+__device__ __forceinline__ unsigned byte_of(float d) { return __float_as_uint(d + 12582912.f); }
+
+// Digits of Re, Im and Re + Im of two FP32-pair complexes at consecutive k
+// (bytes q and q + 1, q even, of an 8-byte row segment) of one row (scale
+// factor sc = 2^(54 - e)), into w[c][t][q / 4].  hi and lo parts are split
+// separately and their digit sums carried; all values are integers below
+// 2^24 in magnitude.
+__device__ __forceinline__ void put2(unsigned& word, float d0, float d1, int q) {
+  const unsigned pair = __byte_perm(byte_of(d0), byte_of(d1), 0x0040);  // low half: bytes d0, d1
+  word = (q & 2) ? __byte_perm(word, pair, 0x5410) : (pair & 0xffffu);
+}
+__device__ __forceinline__ void split_pair(float4 v0, float4 v1, float sc, unsigned (&w)[3][TC_S][2], int q) {
   float r[2][TC_S], im[2][TC_S];
   const float4 v[2] = {v0, v1};
 #pragma unroll
@@ -116,8 +143,8 @@ __device__ __forceinline__ void split_pair(float4 v0, float4 v1, float sc, unsig
   }
 #pragma unroll
   for (int t = 0; t < TC_S; ++t) {
-    w[0][t][q] = pack_bf16(r[0][t], r[1][t]);
-    w[1][t][q] = pack_bf16(im[0][t], im[1][t]);
+    put2(w[0][t][q >> 2], r[0][t], r[1][t], q);
+    put2(w[1][t][q >> 2], im[0][t], im[1][t], q);
   }
   float s[2][TC_S];
 #pragma unroll
@@ -127,7 +154,7 @@ __device__ __forceinline__ void split_pair(float4 v0, float4 v1, float sc, unsig
     carry(s[p]);
   }
 #pragma unroll
-  for (int t = 0; t < TC_S; ++t) w[2][t][q] = pack_bf16(s[0][t], s[1][t]);
+  for (int t = 0; t < TC_S; ++t) put2(w[2][t][q >> 2], s[0][t], s[1][t], q);
 }
 
 __device__ __forceinline__ int scale_exp(float m) {
@@ -136,20 +163,24 @@ __device__ __forceinline__ int scale_exp(float m) {
   return e < -70 ? -70 : (e > 120 ? 120 : e);
 }
 
-// Byte offset of element (r, k), k < 16, in a K-major digit plane: core
-// matrices of 8 rows x 8 k (16 bytes per row, 128 bytes each); the two core
-// matrices of a row group along k are 128 bytes apart (leading byte offset),
-// consecutive row groups 256 bytes (stride byte offset).
-__host__ __device__ constexpr uint32_t core_off(int r, int k) {
-  return uint32_t((r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+// Byte offset of element (r, k), k < 16, in an 8-bit digit plane: the byte
+// image of the BF16 operand layout, where core matrices of 8 rows x 8 k take
+// 16 bytes per row and 128 bytes each, the two core matrices of a row group
+// along k are 128 bytes apart (leading byte offset) and consecutive row
+// groups 256 bytes (stride byte offset); the BF16 element sits at twice the
+// byte offset.
+__host__ __device__ constexpr uint32_t core_off8(int r, int k) {
+  return uint32_t((r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7));
 }
 constexpr uint32_t CORE_LBO = 128, CORE_SBO = 256;
 
-// ---- split: one CTA per 32 rows of op(A) or columns of op(B), 8 threads per row
+// ---- split: one CTA per 32 rows of op(A) or columns of op(B); lane = row,
+// warp w takes the k octets w, w + 8, ...
 __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ descs, const TcDesc* __restrict__ tcd,
                                                   const TcSplit* __restrict__ items, const float4* __restrict__ arena,
                                                   int64_t se, const float4* __restrict__ aux, int64_t sa,
                                                   unsigned char* __restrict__ scratch, int64_t ss) {
+  __shared__ float red[8][32];
   const TcSplit it = items[blockIdx.x];
   const TcDesc t = tcd[it.tcd];
   const GemmDesc d = descs[t.desc];
@@ -162,7 +193,8 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
   const bool row_major = side_a ? d.opA == OP_N : (d.opB == OP_T || d.opB == OP_H);
   const bool cj = !side_a && (d.opB == OP_C || d.opB == OP_H);
   const int rows = side_a ? d.m : d.n;
-  const int r = it.r0 + (threadIdx.x >> 3), part = threadIdx.x & 7;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int r = it.r0 + lane;
   const bool live = r < rows;
   auto at = [&](int k) -> float4 {
     if (!live || k >= d.k) return make_float4(0.f, 0.f, 0.f, 0.f);
@@ -173,35 +205,39 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
     }
     return v;
   };
+  const int n_oct = 2 * t.kb;
   float mx = 0.f;
-  for (int k = part; k < d.k; k += 8) {
-    const float4 v = at(k);
-    mx = fmaxf(mx, fabsf(v.x) + fabsf(v.z));
-  }
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-  mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+  for (int o = w; o < n_oct; o += 8)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = at(8 * o + q);
+      mx = fmaxf(mx, fabsf(v.x) + fabsf(v.z));
+    }
+  red[w][lane] = mx;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 8; ++i) mx = fmaxf(mx, red[i][lane]);
   // a little headroom above the hi parts: Re + Im and the lo parts stay below 2^e
   const int ex = scale_exp(mx * 1.0001f);
   unsigned char* scr = scratch + e * ss;
-  if (part == 0) reinterpret_cast<int*>(scr)[(side_a ? t.exp_a : t.exp_b) + r] = ex;
+  if (w == 0) reinterpret_cast<int*>(scr)[(side_a ? t.exp_a : t.exp_b) + r] = ex;
   const float sc = ldexpf(1.f, TC_F - ex);
   const int R = side_a ? TC_M : TC_N, RB = side_a ? t.rba : t.rbb;
   const int64_t P = side_a ? TC_PLANE_A : TC_PLANE_B;
   unsigned char* dig = scr + (side_a ? t.dig_a : t.dig_b);
   const int rb = r / R, rr = r - rb * R;
-  for (int o = part; o < 2 * t.kb; o += 8) {  // octets of k
+  for (int o = w; o < n_oct; o += 8) {
     const int kb = o >> 1, k0 = o * 8;
-    unsigned w[3][TC_S][4];
+    unsigned wd[3][TC_S][2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) split_pair(at(k0 + 2 * q), at(k0 + 2 * q + 1), sc, w, q);
-    const uint32_t co = core_off(rr, (o & 1) * 8);
+    for (int q = 0; q < 8; q += 2) split_pair(at(k0 + q), at(k0 + q + 1), sc, wd, q);
+    const uint32_t co = core_off8(rr, (o & 1) * 8);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int tt = 0; tt < TC_S; ++tt) {
         unsigned char* pl = dig + (((int64_t(c) * t.kb + kb) * RB + rb) * TC_S + tt) * P + co;
-        *reinterpret_cast<uint4*>(pl) = make_uint4(w[c][tt][0], w[c][tt][1], w[c][tt][2], w[c][tt][3]);
+        *reinterpret_cast<uint2*>(pl) = make_uint2(wd[c][tt][0], wd[c][tt][1]);
       }
   }
 }
@@ -304,11 +340,13 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
                                                    const unsigned char* __restrict__ scratch, int64_t ss,
                                                    int* timeout) {
   extern __shared__ unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accfull, accempty, done;
+  __shared__ __align__(8) uint64_t full8[S8], empty8[S8], full16[S16], empty16[S16], accfull, accempty, done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int eA[TC_M], eB[TC_N];
   unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
+  unsigned char* ring8 = sm;                                   // S8 x (SA8 + SB8) bytes
+  unsigned char* ring16 = sm + size_t(S8) * (SA8 + SB8);       // S16 x (SA + SB) bytes
 
   const TileRef tr = tiles[blockIdx.x];
   const TcDesc t = tcd[tr.desc];
@@ -329,9 +367,13 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+    for (int s = 0; s < S8; ++s) {
+      mbar_init(&full8[s], 1);
+      mbar_init(&empty8[s], FW);
+    }
+    for (int s = 0; s < S16; ++s) {
+      mbar_init(&full16[s], FW);
+      mbar_init(&empty16[s], 1);
     }
     mbar_init(&accfull, 1);
     mbar_init(&accempty, FW);
@@ -347,44 +389,44 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
   const int KB = t.kb, njobs = 3 * KB;  // job j: component j / KB, 16-k block j % KB
 
   if (warp == FW) {
-    // ---- producer: digit blocks of A and B into the stage ring
+    // ---- producer: 8-bit digit blocks of A and B into the byte ring
     if (lane == 0) {
       int j = 0;
       for (; j < njobs; ++j) {
-        const int s = j % STAGES, u = j / STAGES;
-        if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, abrt)) break;
+        const int s = j % S8, u = j / S8;
+        if (u > 0 && !mbar_wait(&empty8[s], (u - 1) & 1, abrt)) break;
         const int c = j / KB, kb = j - c * KB;
-        const unsigned char* ga = scr + t.dig_a + ((int64_t(c) * KB + kb) * t.rba + tr.tm) * int64_t(SA);
-        const unsigned char* gb = scr + t.dig_b + ((int64_t(c) * KB + kb) * t.rbb + tr.tn) * int64_t(SB);
-        unsigned char* st = sm + size_t(s) * (SA + SB);
-        mbar_expect_tx(&full[s], SA + SB);
-        bulk_g2s(st, ga, SA, &full[s]);
-        bulk_g2s(st + SA, gb, SB, &full[s]);
+        const unsigned char* ga = scr + t.dig_a + ((int64_t(c) * KB + kb) * t.rba + tr.tm) * int64_t(SA8);
+        const unsigned char* gb = scr + t.dig_b + ((int64_t(c) * KB + kb) * t.rbb + tr.tn) * int64_t(SB8);
+        unsigned char* st = ring8 + size_t(s) * (SA8 + SB8);
+        mbar_expect_tx(&full8[s], SA8 + SB8);
+        bulk_g2s(st, ga, SA8, &full8[s]);
+        bulk_g2s(st + SA8, gb, SB8, &full8[s]);
       }
       // the last copies into every stage have landed before the CTA ends
-      for (int jj = j > STAGES ? j - STAGES : 0; jj < j; ++jj) mbar_drain(&full[jj % STAGES], (jj / STAGES) & 1);
+      for (int jj = j > S8 ? j - S8 : 0; jj < j; ++jj) mbar_drain(&full8[jj % S8], (jj / S8) & 1);
     }
   } else if (warp == FW + 1) {
     // ---- MMA issue: 28 digit-pair products per 16 k into the group accumulators
     if (lane == 0) {
       int q = 0;  // chunks handed to the accumulator warps
       for (int j = 0; j < njobs; ++j) {
-        const int s = j % STAGES, u = j / STAGES;
+        const int s = j % S16, u = j / S16;
         const int kb = j % KB, kc = kb % CHUNK;
         if (kc == 0 && q > 0) {
           if (!mbar_wait(&accempty, (q - 1) & 1, abrt)) break;
           tc_fence_after();
         }
-        if (!mbar_wait(&full[s], u & 1, abrt)) break;
+        if (!mbar_wait(&full16[s], u & 1, abrt)) break;
         tc_fence_after();
-        const uint32_t a0 = smem_u32(sm + size_t(s) * (SA + SB)), b0 = a0 + SA;
+        const uint32_t a0 = smem_u32(ring16 + size_t(s) * (SA + SB)), b0 = a0 + SA;
 #pragma unroll
         for (int t1 = 0; t1 < TC_S; ++t1)
 #pragma unroll
           for (int t2 = 0; t2 < TC_S - t1; ++t2)
-            mma_bf16(tmem + uint32_t((t1 + t2) * TC_N), sdesc(a0 + t1 * uint32_t(TC_PLANE_A)),
-                     sdesc(b0 + t2 * uint32_t(TC_PLANE_B)), (kc == 0 && t1 == 0) ? 0u : 1u);
-        if (j + STAGES < njobs) mma_commit(&empty[s]);
+            mma_bf16(tmem + uint32_t((t1 + t2) * TC_N), sdesc(a0 + t1 * uint32_t(2 * TC_PLANE_A)),
+                     sdesc(b0 + t2 * uint32_t(2 * TC_PLANE_B)), (kc == 0 && t1 == 0) ? 0u : 1u);
+        if (j + S16 < njobs) mma_commit(&empty16[s]);
         if (kc == CHUNK - 1 || kb == KB - 1) {
           mma_commit(&accfull);
           ++q;
@@ -395,17 +437,46 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
       mbar_drain(&done, 0);
     }
   } else {
-    // ---- accumulator warps: TMEM lanes 32 (warp % 4) .., columns 32 (warp / 4) ..
+    // ---- accumulator warps: widen the byte stages into the BF16 ring (up to
+    // S16 jobs ahead of the MMAs); flush the TMEM lanes 32 (warp % 4) ..,
+    // columns 32 (warp / 4) .. after every chunk
     const int quad = warp & 3, half = warp >> 2;
     const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(half * 32);
+    auto widen = [&](int j) -> bool {
+      const int s8 = j % S8, s16 = j % S16, u16 = j / S16;
+      if (!mbar_wait(&full8[s8], (j / S8) & 1, abrt)) return false;
+      if (u16 > 0 && !mbar_wait(&empty16[s16], (u16 - 1) & 1, abrt)) return false;
+      const uint4* src = reinterpret_cast<const uint4*>(ring8 + size_t(s8) * (SA8 + SB8));
+      uint4* dst = reinterpret_cast<uint4*>(ring16 + size_t(s16) * (SA + SB));
+      for (int i = tid; i < (SA8 + SB8) / 16; i += FW * 32) {
+        const uint4 v = src[i];
+        const uint2 a = widen4(v.x), b = widen4(v.y), c = widen4(v.z), w = widen4(v.w);
+        dst[2 * i] = make_uint4(a.x, a.y, b.x, b.y);
+        dst[2 * i + 1] = make_uint4(c.x, c.y, w.x, w.y);
+      }
+      // the generic-proxy writes are seen by the tensor cores (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&full16[s16]);
+        mbar_arrive(&empty8[s8]);
+      }
+      return true;
+    };
     float ac[32][4];  // Re (hi, lo), Im (hi, lo) of 32 outputs, unnormalised pairs
 #pragma unroll
     for (int o = 0; o < 32; ++o) ac[o][0] = ac[o][1] = ac[o][2] = ac[o][3] = 0.f;
     const int nch = (KB + CHUNK - 1) / CHUNK;
     bool ok = true;
-    int q = 0;
+    int q = 0, jw = 0;  // chunks flushed, jobs widened
     for (int c = 0; c < 3 && ok; ++c) {
       for (int ch = 0; ch < nch; ++ch, ++q) {
+        // jobs up to the end of this chunk and S16 beyond, so that the MMAs
+        // of the next chunk can start as soon as the flush is done
+        const int last = c * KB + min(KB, (ch + 1) * CHUNK) - 1;
+        const int upto = min(njobs - 1, last + S16);
+        for (; ok && jw <= upto; ++jw) ok = __all_sync(0xffffffffu, widen(jw));
+        if (!ok) break;
         ok = __all_sync(0xffffffffu, mbar_wait(&accfull, q & 1, abrt));
         if (!ok) break;
         tc_fence_after();
@@ -490,9 +561,9 @@ int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off) {
   t.rba = (g.m + TC_M - 1) / TC_M;
   t.rbb = (g.n + TC_N - 1) / TC_N;
   t.dig_a = off;
-  off += 3 * int64_t(t.kb) * t.rba * SA;
+  off += 3 * int64_t(t.kb) * t.rba * SA8;
   t.dig_b = off;
-  off += 3 * int64_t(t.kb) * t.rbb * SB;
+  off += 3 * int64_t(t.kb) * t.rbb * SB8;
   t.exp_a = off / 4;
   off += int64_t(t.rba) * TC_M * 4;
   t.exp_b = off / 4;

@@ -226,13 +226,13 @@ struct TileRef { int32_t desc, tm, tn, pad; };
 struct TileRange { int32_t first, count, kind, sfirst, scount; };
 
 // Tensor-core products (FP32 pairs): output tiles of TC_M x TC_N, operands
-// as TC_DIGITS BF16 digit planes per real, 16 k per block.  Per energy, the
+// as TC_DIGITS 8-bit digit planes per real, 16 k per block.  Per energy, the
 // scratch of a step holds for every descriptor the planes of op(A)
 // [3][kb][rba][TC_DIGITS][TC_M x 16] and of op(B)^T [3][kb][rbb][TC_DIGITS][TC_N x 16]
 // (components Re, Im, Re + Im) and the exponents of the rows of op(A) and
 // columns of op(B).
 constexpr int TC_M = 128, TC_N = 64, TC_DIGITS = 7;
-constexpr int64_t TC_PLANE_A = int64_t(TC_M) * 16 * 2, TC_PLANE_B = int64_t(TC_N) * 16 * 2;  // bytes
+constexpr int64_t TC_PLANE_A = int64_t(TC_M) * 16, TC_PLANE_B = int64_t(TC_N) * 16;  // bytes
 struct TcDesc {
   int64_t dig_a, dig_b;  // byte offsets of the digit planes in the per-energy scratch
   int64_t exp_a, exp_b;  // int32 offsets of the exponents (rba * TC_M and rbb * TC_N entries)
