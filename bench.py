@@ -45,6 +45,35 @@ UNIT = "energies/s"
 GATE = 1e-6
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
+# ncu capture of the launch list, averaged over the kernel's launches of one
+# step; see profiles/), valid only for the kernel sources it was measured on:
+# a source digest that no longer matches turns the figure into null.
+KERNEL_SOURCES = ["nd_kernels.cu", "nd_arith.cuh", "nd_gemm_tc.cu", "nd_gj.cuh"]
+TRAFFIC = {  # kernel name -> (bytes per launch, source digest)
+    # FP32-pipe GEMM launches (k_gemm 16 x 16 and 32 x 32 tiles, k_gemm_direct): 1008.3 GB over 404 launches
+    "complex-fp32x2:gemm": (2495807717, "17837be18d24965f"),
+    # tensor-core GEMM steps (k_tc_split + k_gemm_tc): 379.6 GB over 104 steps
+    "complex-fp32x2:gemm_tc": (3650217061, "17837be18d24965f"),
+}
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1305_1070_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel: str):
+    entry = TRAFFIC.get(kernel)
+    if not entry or entry[1] != kernel_digest():
+        return None
+    return entry[0]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -335,13 +364,33 @@ def main_ours(a) -> None:
         tot = sum(p["ms"] for p in pr) or 1.0
         top = max(pr, key=lambda p: p["ms"])
         ach = top["flops"] / (top["ms"] * 1e-3) / 1e12 if top["ms"] > 0 else 0.0
-        out = {"kernel": f"{label}:{top['name']}", "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
-               "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+        kname = f"{label}:{top['name']}"
+        out = {"kernel": kname, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
+               "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic_per_launch(kname),
                "share": round(top["ms"] / tot, 4), "launches": top["launches"],
                "ms_per_launch": round(top["ms"] / max(1, top["launches"]), 4)}
         if note:
             out["note"] = note
         return out
+
+    def tensor_roof(pr):
+        """The tensor-core GEMM launches (FP32 pairs): executed BF16 tensor flops
+        (28 digit-pair products of 2 flops per real multiply-add, 3 real products
+        per complex one: 168 per complex multiply-add, 21 x the useful 8) against
+        the measured BF16 peak; the useful complex rate beside it."""
+        tc = [p for p in pr if p["name"] == "gemm_tc"]
+        if not tc or tc[0]["ms"] <= 0:
+            return None
+        tot = sum(p["ms"] for p in pr) or 1.0
+        useful = tc[0]["flops"] / (tc[0]["ms"] * 1e-3) / 1e12
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        return {"kernel": "complex-fp32x2:gemm_tc", "bound": "tensor", "achieved": round(21.0 * useful, 3),
+                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(21.0 * useful / peak, 4),
+                "useful_tflops": round(useful, 3), "traffic": traffic_per_launch("complex-fp32x2:gemm_tc"),
+                "share": round(tc[0]["ms"] / tot, 4), "launches": tc[0]["launches"],
+                "ms_per_launch": round(tc[0]["ms"] / max(1, tc[0]["launches"]), 4),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
+                "note": "achieved = executed BF16 tensor flops of the digit products (21 x useful), unpadded"}
 
     roof = {"fp64_nd": dominant(prof["fp64_nd"], fp64_peak, "complex128"),
             # one complex multiply-add in FP32 pairs with 3-multiplication products: 36 FP32 instructions
@@ -407,6 +456,7 @@ def main_ours(a) -> None:
             "current_spectrum_integral_eV": {"L": float((cur[0] * weights).sum()), "R": float((cur[1] * weights).sum())},
             "roofline": roofline,
             "roofline_other": roof["fp64_nd" if head == "fp32x2" else "fp32x2"],
+            "roofline_tensor": tensor_roof(prof["fp32x2"]),
             "kernel_profile": prof,
             "flops_per_energy": {"factor": info["flops_factor"], "green_r": info["flops_green_r"],
                                  "green_lesser": info["flops_green_lesser"]},

@@ -272,7 +272,8 @@ typedef struct nd_kernel_stats {
 nd_status nd_profile(nd_fact* fact, int32_t enable, nd_kernel_stats* stats, int32_t max_stats, int32_t* n_stats);
 /* The launches recorded since profiling was enabled, one entry each, in launch
  * order (without clearing them; nd_profile clears): step kind (the order of
- * nd_profile's names: 0 inverse, 1 gemm, 2 scatter, ...), descriptors in the
+ * nd_profile's names: 0 inverse, 1 gemm, 2 scatter, ..., 11 loc, 12 gemm_tc =
+ * the GEMM launches on the tensor cores), descriptors in the
  * launch, largest block edge, energies, CUDA-event time (ms) and algorithmic
  * flops.  n_out receives the number recorded (out may be NULL to query it). */
 typedef struct nd_launch_stats {

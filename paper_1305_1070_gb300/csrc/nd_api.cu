@@ -49,6 +49,8 @@ bool is_device_ptr(const void* p) {
 
 namespace {
 // Per-kind launch timing with CUDA events on the launching stream.
+constexpr int PROF_GEMM_TC = 12;  // profiler kind of the tensor-core GEMM launches
+
 struct Profiler {
   bool on = false;
   struct Rec {
@@ -303,7 +305,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
     const Step& st = sched[si];
     Profiler::Rec rec{};
     if (f->prof.on) {
-      rec.kind = st.kind;
+      // tensor-core GEMM launches are recorded apart (kind 12, "gemm_tc")
+      rec.kind = (st.kind == ST_GEMM && tr[si].kind == 2) ? PROF_GEMM_TC : st.kind;
       rec.a = f->prof.get();
       rec.b = f->prof.get();
       rec.flops = step_flops ? (*step_flops)[si] * w.n_e : 0.0;
@@ -909,7 +912,8 @@ extern "C" nd_status nd_profile(nd_fact* f, int32_t enable, nd_kernel_stats* sta
   if (stats && max_stats > 0) {
     ND_CUDA(cudaDeviceSynchronize());
     static const char* names[] = {"inverse",    "gemm",         "scatter",   "gather_sym", "gather_skew", "zero",
-                                  "nph",        "gather_anc",   "scatter_rows", "colgather", "delay",     "loc"};
+                                  "nph",        "gather_anc",   "scatter_rows", "colgather", "delay",     "loc",
+                                  "gemm_tc"};
     const int nk = int(sizeof(names) / sizeof(names[0]));
     std::vector<nd_kernel_stats> acc(nk);
     for (int k = 0; k < nk; ++k) {
