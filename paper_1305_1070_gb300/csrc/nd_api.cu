@@ -215,7 +215,7 @@ struct TcTables {
 void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
                  double small_cost, bool tc_ok, TcTables& tct, std::vector<TileRef>& tiles,
                  std::vector<TileRange>& ranges) {
-  ranges.assign(sched.size(), TileRange{0, 0, 0, 0, 0});
+  ranges.assign(sched.size(), TileRange{0, 0, 0, 0, 0, 0});
   auto work = [&](const Step& s, int tile) {
     double w = 0.0;
     for (int k = s.begin; k < s.begin + s.count; ++k) {
@@ -244,8 +244,9 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
       if (flags & ND_FACT_GEMM_TC) tc = true;
     }
     // launches whose blocks all have edges <= DIRECT_MAX take one CTA per block
-    const bool direct =
-        !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && s.max_dim <= DIRECT_MAX;
+    int dim = 0;
+    for (int k = s.begin; k < s.begin + s.count; ++k) dim = std::max(dim, std::max(gd[k].m, std::max(gd[k].n, gd[k].k)));
+    const bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && dim <= DIRECT_MAX;
     const int tile = small ? tile_s : tile_l;
     int b = int(tiles.size());
     if (tc) {
@@ -263,7 +264,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
           for (int j = 0; j < t.rbb; ++j) tiles.push_back(TileRef{ti, i, j, 0});
       }
       tct.bytes = std::max(tct.bytes, off);
-      ranges[si] = TileRange{b, int(tiles.size()) - b, 2, sb, int(tct.split.size()) - sb};
+      ranges[si] = TileRange{b, int(tiles.size()) - b, 2, sb, int(tct.split.size()) - sb, s.max_dim};
       continue;
     }
     for (int k = s.begin; k < s.begin + s.count; ++k) {
@@ -276,7 +277,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
     }
-    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : small ? 1 : 0, 0, 0};
+    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : small ? 1 : 0, 0, 0, dim};
   }
 }
 
@@ -445,7 +446,7 @@ void build_adjoint(const nd_plan* p, int64_t base, std::vector<GemmDesc>& gemms,
       const Cluster& c = cl[i];
       if (c.b == 0 || c.n == 0) continue;
       gemm(base + c.adj_RB, M, base + c.adj_RB, M, c.off_Psi, c.b, OP_T, base + c.adj_XI, M, c.b, M, c.n, 1.0);
-      dim = std::max(dim, std::max(c.b, M));
+      dim = std::max(dim, std::max(c.n, std::max(c.b, M)));
     }
     step(fwd, ST_GEMM, b0, int(gemms.size()), dim);
     for (int sl = 0; sl <= max_slot; ++sl) {
@@ -488,7 +489,7 @@ void build_adjoint(const nd_plan* p, int64_t base, std::vector<GemmDesc>& gemms,
       const Cluster& c = cl[i];
       if (c.b == 0 || c.n == 0) continue;
       gemm(base + c.adj_XS, M, base + c.adj_XS, M, c.off_Psi, c.b, OP_N, base + c.adj_XB, M, c.n, M, c.b, 1.0);
-      dim = std::max(dim, std::max(c.n, M));
+      dim = std::max(dim, std::max(c.b, std::max(c.n, M)));
     }
     step(bwd, ST_GEMM, b0, int(gemms.size()), dim);
   }

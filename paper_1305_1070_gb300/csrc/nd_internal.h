@@ -223,7 +223,7 @@ struct TileRef { int32_t desc, tm, tn, pad; };
 // 3 one CTA per descriptor (small blocks).  Tensor-core steps also own the
 // digit-split work items [sfirst, sfirst + scount); their tiles refer to
 // TcDesc entries.
-struct TileRange { int32_t first, count, kind, sfirst, scount; };
+struct TileRange { int32_t first, count, kind, sfirst, scount, dim; };  // dim: largest m, n or k of the launch
 
 // Tensor-core products (FP32 pairs): output tiles of TC_M x TC_N, operands
 // as TC_DIGITS 8-bit digit planes per real, 16 k per block.  Per energy, the
