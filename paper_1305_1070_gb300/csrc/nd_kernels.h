@@ -67,7 +67,7 @@ struct Kern {
   static void inverse(const Work& w, const InvDesc* d, int count, int max_n, double* fp64_scratch,
                       int64_t scratch_stride, int* n_singular, cudaStream_t s);
   static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, bool small, cudaStream_t s);
-  // one CTA per descriptor (blocks with every edge <= 24)
+  // one CTA per descriptor (launches whose blocks have every edge <= 96)
   static void gemm_direct(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
   static void scatter(const Work& w, const ScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
   static void gather(const Work& w, const GatherDesc* d, int count, const int32_t* maps, bool skew,
