@@ -225,8 +225,10 @@ def main_ours(a) -> None:
 
     def make_step(solver, chunk, name, fallback=None):
         """One pass over all energies; with a fallback solver, energies whose
-        certificate growth exceeds --growth-max are recomputed by it."""
-        def step():
+        certificate growth exceeds --growth-max are recomputed by it.
+        step(after_chunk) calls after_chunk(c0, m) once a call's diagonals are
+        in Gr, Gl, Gg (the end-to-end step starts their host copies there)."""
+        def step(after_chunk=None):
             cmax = torch.zeros(8, dtype=torch.float64, device="cuda")
             flagged = []
             calls["n"] = 0
@@ -241,6 +243,8 @@ def main_ours(a) -> None:
                 cmax = torch.maximum(cmax, cert.amax(dim=0))
                 if fallback is not None:
                     flagged.append(torch.nonzero(cert[:, 4] > a.growth_max).flatten() + c0)
+                if after_chunk is not None:
+                    after_chunk(c0, m)
             nredo = 0
             if fallback is not None:
                 idx = torch.cat(flagged)
@@ -409,16 +413,32 @@ def main_ours(a) -> None:
     dens_host = torch.empty(n, dtype=torch.float64).pin_memory()
     cur_host = torch.empty(2, n_e, dtype=torch.float64).pin_memory()
 
+    copy_stream = torch.cuda.Stream()
+
+    def copy_out(c0, m):
+        # this call's diagonals go to the host on a copy stream while the next call computes
+        ev = torch.cuda.Event()
+        ev.record()
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev)
+            for dst, src in zip(out_host, (Gr, Gl, Gg)):
+                dst[c0:c0 + m].copy_(src[c0:c0 + m], non_blocking=True)
+
     def step_e2e():
         solver.H.copy_(H_host, non_blocking=True)
         if head == "fp32x2":
             solvers["fp64_nd"][0].H.copy_(H_host, non_blocking=True)
         E_all.copy_(E_host, non_blocking=True)
-        step()
-        for dst, src in zip(out_host, (Gr, Gl, Gg)):
-            dst.copy_(src, non_blocking=True)
+        step(copy_out)
+        # energies recomputed by the fallback path overwrite their rows: copy those again
+        if redo.get(head, 0):
+            torch.cuda.current_stream().wait_stream(copy_stream)
+            for dst, src in zip(out_host, (Gr, Gl, Gg)):
+                dst.copy_(src, non_blocking=True)
         dens_host.copy_(dens, non_blocking=True)
         cur_host.copy_(cur, non_blocking=True)
+        # the step ends when the host has every result
+        torch.cuda.current_stream().wait_stream(copy_stream)
 
     ms_e2e = timed(step_e2e, a.steps, 1)
     h2d = H_host.numel() * 8 + E_host.numel() * 8
