@@ -95,6 +95,23 @@ def test_gradient_terms_match_oracle(precision, tol, delay):
         assert err <= tol
 
 
+def test_gradient_terms_tensor_cores():
+    """The adjoint solves with every Schur product on the tensor cores (FP32 pairs,
+    exact BF16 digit products): the same terms at the FP32-pair tolerance."""
+    from paper_1305_1070_gb300.solver import Solver
+    dev, tr = _dev(), _tr()
+    c = np.random.default_rng(2).uniform(0.0, 1.0, dev.n)
+    s = Solver(dev, tr, precision=ndgf.ND_PREC_FP32X2, leaf_size=16, delay=2, adjoint=True, tile="tc")
+    s.step(tr.energies)
+    t = s.density_gradient_terms(c, tr.n_e).cpu().numpy()
+    assert s.singular_pivots() == 0
+    ref = _t_oracle(dev, tr, c)
+    for e in range(tr.n_e):
+        err = np.abs(t[e] - ref[e]).max() / np.abs(ref[e]).max()
+        print(f"tensor cores energy {e}: rel err {err:.3e}")
+        assert err <= 1e-9
+
+
 def test_autograd_matches_finite_differences():
     from paper_1305_1070_gb300 import autograd
     from paper_1305_1070_gb300.solver import Solver
