@@ -17,6 +17,9 @@ Devices (paper Sec. 2, Fig. 1-2 and Sec. 4.2):
   nearest-neighbour hopping (tight binding, Sec. 4.2.2 uses the same model on a
   planar ribbon).  Rings of n atoms are the transport layers; the leads are
   perfect semi-infinite tubes.
+* ``agnr`` -- planar armchair graphene nanoribbon, one p_z orbital per atom,
+  nearest-neighbour hopping -3.1 eV, on-site 0 (Sec. 4.2.2); atom columns are
+  the transport layers, four per cell, and the leads are perfect ribbons.
 * ``chain`` -- 1D tight-binding chain (W = 1), used for closed-form checks.
 
 Site order ("caller order"): transport layer by layer, so that layer ``k``
@@ -262,6 +265,68 @@ def _cnt_perfect_blocks(nring: int, t: float, acc: float) -> tuple:
     Hb = np.where((d < 1.1 * acc) & (d > 1e-9), t, 0.0)
     del dev
     return Hb[:m, :m].copy(), Hb[:m, m:].copy()
+
+
+# Armchair ribbon cell (transport along x, one C-C bond parallel to x): four
+# atom columns at x / acc = 0, 1, 1.5, 2.5, the last two shifted by half a
+# period sqrt(3) acc along y; the cell repeats every 3 acc.
+_AGNR_X = (0.0, 1.0, 1.5, 2.5)
+_AGNR_YOFF = (0.0, 0.0, 0.5, 0.5)
+
+
+def _agnr_coords(n_cells: int, ny: int, acc: float) -> np.ndarray:
+    xyz = np.zeros((4 * ny * n_cells, 2))
+    k = np.arange(ny)
+    for c in range(n_cells):
+        for r in range(4):
+            sl = slice((4 * c + r) * ny, (4 * c + r + 1) * ny)
+            xyz[sl, 0] = (3.0 * c + _AGNR_X[r]) * acc
+            xyz[sl, 1] = (k + _AGNR_YOFF[r]) * math.sqrt(3.0) * acc
+    return xyz
+
+
+def agnr(n_cells: int, ny: int, *, t: float = -3.1, acc: float = 0.142, disorder: float = 0.0,
+         seed: int | None = None) -> Device:
+    """Armchair graphene nanoribbon, n_cells cells of four atom columns with ny
+    atoms each (4 ny n_cells atoms, 2 ny dimer lines across).
+
+    Connectivity: pairs closer than 1.1 acc (bonds only join adjacent columns).
+    On-site 0 + U(-disorder, +disorder), hopping t.  Caller order is column by
+    column along x.  The leads are perfect semi-infinite ribbons whose
+    principal layer is one cell.
+    """
+    m = ny
+    n = 4 * m * n_cells
+    coords = _agnr_coords(n_cells, ny, acc)
+    onsite = np.zeros(n)
+    if disorder > 0.0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        onsite = onsite + rng.uniform(-disorder, disorder, size=n)
+    rs, cs, vs = [np.arange(n)], [np.arange(n)], [onsite]
+    cut = 1.1 * acc
+    for col in range(4 * n_cells - 1):
+        A = np.arange(col * m, (col + 1) * m)
+        B = np.arange((col + 1) * m, (col + 2) * m)
+        d = np.linalg.norm(coords[A][:, None, :] - coords[B][None, :, :], axis=2)
+        ia, ib = np.nonzero(d < cut)
+        rs += [A[ia], B[ib]]; cs += [B[ib], A[ia]]; vs += [np.full(ia.size, t)] * 2
+    rowptr, colind, values = _csr_from_coo(n, np.concatenate(rs), np.concatenate(cs), np.concatenate(vs))
+    layers = [np.arange(k * m, (k + 1) * m) for k in range(4 * n_cells)]
+    # lead blocks read off a perfect two-cell ribbon
+    two = _agnr_coords(2, ny, acc)
+    d = np.linalg.norm(two[:, None, :] - two[None, :, :], axis=2)
+    Hb = np.where((d < cut) & (d > 1e-9), t, 0.0)
+    H00, H01 = Hb[:4 * m, :4 * m].copy(), Hb[:4 * m, 4 * m:].copy()
+    DA = H01[3 * m:4 * m, 0:m]  # column 3 of a cell -> column 0 of the next cell
+    tauR = np.zeros((m, 4 * m))
+    tauR[:, 0:m] = DA  # the device's last column couples to column 0 of the right lead's first cell
+    tauL = np.zeros((m, 4 * m))
+    tauL[:, 3 * m:4 * m] = DA.T  # the device's first column couples to column 3 of the left lead's first cell
+    leadL = Lead(H00=H00.copy(), H01=H01.T.copy(), tau=tauL)
+    leadR = Lead(H00=H00.copy(), H01=H01.copy(), tau=tauR)
+    return Device(name=f"agnr_{2 * ny}_{n_cells}cells", n=n, rowptr=rowptr, colind=colind, values=values,
+                  coords=coords, layers=layers, contacts=[layers[0].copy(), layers[-1].copy()],
+                  leads=[leadL, leadR], transport_axis=0)
 
 
 @dataclasses.dataclass

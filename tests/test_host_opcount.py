@@ -86,6 +86,28 @@ def test_growth_exponents(counts):
     assert all(2.85 <= s <= 3.25 for s in hsc[1:]), hsc
 
 
+def test_armchair_ribbon_exponent():
+    """The paper's graphene comparison: square armchair ribbons (N atoms per
+    direction: N / 4 cells of four N-atom columns), no contacts.  The exponent
+    rises towards 3 (the ribbon is about twice as wide as long, so the
+    separators reach their asymptotic share later than on the grid)."""
+    from paper_1305_1070_gb300 import workloads
+    vals = []
+    ns = (16, 32, 64, 128, 256)
+    for N in ns:
+        dev = workloads.agnr(N // 4, N)
+        plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, coords=dev.coords, leaf_size=16)
+        tree = ndgf.nd_plan_tree(plan)
+        n = tree["n_i"].astype(float)
+        b = tree["b_i"].astype(float)
+        vals.append(float(np.sum(n ** 3 + n * n * b + b * n * b + n * b * b + n * b * n)))
+    s = np.diff(np.log(vals)) / np.diff(np.log(np.array(ns, float)))
+    print("armchair ribbon exponents", np.round(s, 3), "RGF / nested dissection at N = 256:",
+          round(3.0 * 256 ** 4 / vals[-1], 2))
+    assert all(x2 > x1 for x1, x2 in zip(s, s[1:])), s  # rising towards 3
+    assert 2.85 <= s[-1] <= 3.25, s
+
+
 def test_nested_dissection_needs_fewer_operations(counts):
     ratio = [counts[N]["rgf"] / counts[N]["hsc"] for N in NS]
     print("RGF / nested dissection:", np.round(ratio, 2))
