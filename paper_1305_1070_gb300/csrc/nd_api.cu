@@ -205,6 +205,14 @@ constexpr int64_t TC_MAX_SCRATCH = int64_t(256) << 20;
 // pairs, 128 energies (tiled 16 x 16 -> direct): edges <= 24: 78 -> 31 ms,
 // <= 48: 47.5 -> 30.6 ms, <= 96: 74.9 -> 63.4 ms, <= 192: 138 -> 323 ms.
 constexpr int DIRECT_MAX = 96;
+// Above DIRECT_SMALL the direct kernel needs many blocks per launch (it runs
+// one CTA per block and energy, each doing much sequential work): measured on
+// the 256 x 64 superlattice, 128 energies, edges in (48, 96] with 16 blocks
+// per launch: direct 32.4 ms, tiled 24.7 ms per call; on the 512 x 128 one,
+// 163 blocks per launch: direct 63.4 ms, tiled 74.9 ms.  With this rule:
+// 23.3 and 59.0 ms.
+constexpr int DIRECT_SMALL = 48;
+constexpr int64_t DIRECT_MIN_CTAS = 8192;
 
 struct TcTables {
   std::vector<TcDesc> desc;
@@ -213,7 +221,7 @@ struct TcTables {
 };
 
 void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
-                 double small_cost, bool tc_ok, TcTables& tct, std::vector<TileRef>& tiles,
+                 double small_cost, bool tc_ok, int max_ne, TcTables& tct, std::vector<TileRef>& tiles,
                  std::vector<TileRange>& ranges) {
   ranges.assign(sched.size(), TileRange{0, 0, 0, 0, 0, 0});
   auto work = [&](const Step& s, int tile) {
@@ -246,7 +254,8 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
     // launches whose blocks all have edges <= DIRECT_MAX take one CTA per block
     int dim = 0;
     for (int k = s.begin; k < s.begin + s.count; ++k) dim = std::max(dim, std::max(gd[k].m, std::max(gd[k].n, gd[k].k)));
-    const bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && dim <= DIRECT_MAX;
+    const bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && dim <= DIRECT_MAX &&
+                        (dim <= DIRECT_SMALL || int64_t(s.count) * max_ne >= DIRECT_MIN_CTAS);
     const int tile = small ? tile_s : tile_l;
     int b = int(tiles.size());
     if (tc) {
@@ -623,15 +632,15 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
     const double sc = small_tile_cost(precision);
     const bool tc_ok = precision == ND_PREC_FP32X2;
     TcTables tct;
-    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_factor);
-    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_green);
+    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_factor);
+    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_green);
     // the G^< schedule with a phonon Sigma^< runs only on a phonon workspace
     const bool ph = (flags & ND_FACT_PHONON) != 0;
-    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_lesser[0]);
-    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, tc_ok && ph, tct, tiles, f->tr_lesser[1]);
+    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_lesser[0]);
+    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, tc_ok && ph, max_ne, tct, tiles, f->tr_lesser[1]);
     if (f->adj) {
-      build_tiles(f->sched_adj_fwd, gemm_all, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_adj_fwd);
-      build_tiles(f->sched_adj_bwd, gemm_all, tl, ts, flags, sc, tc_ok, tct, tiles, f->tr_adj_bwd);
+      build_tiles(f->sched_adj_fwd, gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_fwd);
+      build_tiles(f->sched_adj_bwd, gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_bwd);
     }
     TRY(dupload(f, tiles, &f->d_tiles));
     if (!tct.desc.empty()) {
