@@ -329,6 +329,20 @@ nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, int32_t n_co
                                 const double* energies, double* sigma_lesser,
                                 double* sigma_greater, void* stream);
 
+/* Self-consistent Born update of an elastic local phonon (dephasing)
+ * self-energy (a model the paper leaves open, Sec. 2; S. Datta, Superlattices
+ * Microstruct. 28, 253 (2000)): with the diagonals of the last nd_diag_green
+ * call (caller order), Sigma^r_ph,jj <- Sigma + mix (D G^r_jj - Sigma), and
+ * likewise Sigma^< from G^< and Sigma^> from G^> (D in eV^2, 0 < mix <= 1).
+ * All arrays are device [n_e][n] complex; the phonon arrays are updated in
+ * place and are the inputs of the next nd_factor / nd_diag_green.
+ * stats (device, 2 doubles) receives max |D G - Sigma| and max |D G| over the
+ * three self-energies (their ratio is the relative change of the iteration).
+ * Errors: ND_ERR_INVALID_ARG (sizes, NULL, host pointers, D or mix). */
+nd_status nd_phonon_scba(int32_t n, int32_t n_e, double D, double mix, const double* Gr,
+                         const double* Gl, const double* Gg, double* ph_r, double* ph_lesser,
+                         double* ph_greater, double* stats, void* stream);
+
 /* Constant-broadening phonon self-energy on every site (device outputs
  * [n_e][n] complex, any may be NULL): Sigma^r = -i gamma/2,
  * Sigma^< = i f(E; mu) gamma, Sigma^> = -i (1 - f) gamma. */

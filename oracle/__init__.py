@@ -24,6 +24,8 @@ precision).  Contents:
 * ``nd_reference`` -- the paper's multilevel fold/extract algorithm (Sec. 3.2)
                     written out block by block on a cluster tree; a test aid
                     that checks the block algebra, not the parity oracle.
+* ``scba``       -- self-consistent Born iteration of an elastic local phonon
+                    self-energy (Sigma_ph,jj = D G_jj), densely per energy.
 * ``observables`` -- density, terminal current, transmission, error metric.
 * ``transfer``   -- 2x2 transfer-matrix transmission of a 1D chain, an
                     independent textbook method used to pin the oracle.

@@ -1158,6 +1158,23 @@ extern "C" nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, i
   return ND_OK;
 }
 
+extern "C" nd_status nd_phonon_scba(int32_t n, int32_t n_e, double D, double mix, const double* Gr, const double* Gl,
+                                    const double* Gg, double* ph_r, double* ph_lesser, double* ph_greater,
+                                    double* stats, void* stream) {
+  if (n <= 0 || n_e <= 0 || !Gr || !Gl || !Gg || !ph_r || !ph_lesser || !ph_greater || !stats)
+    return fail(ND_ERR_INVALID_ARG, "nd_phonon_scba: bad argument");
+  if (!(D >= 0.0) || !(mix > 0.0 && mix <= 1.0))
+    return fail(ND_ERR_INVALID_ARG, "nd_phonon_scba: need D >= 0 and 0 < mix <= 1");
+  const void* ptrs[7] = {Gr, Gl, Gg, ph_r, ph_lesser, ph_greater, stats};
+  for (const void* q : ptrs)
+    if (!is_device_ptr(q)) return fail(ND_ERR_INVALID_ARG, "nd_phonon_scba: arrays must be device pointers");
+  cudaStream_t s = (cudaStream_t)stream;
+  ND_CUDA(cudaMemsetAsync(stats, 0, 2 * sizeof(double), s));
+  launch_phonon_scba(n, n_e, D, mix, Gr, Gl, Gg, ph_r, ph_lesser, ph_greater, stats, s);
+  ND_CUDA(cudaGetLastError());
+  return ND_OK;
+}
+
 extern "C" nd_status nd_phonon_const(int32_t n, int32_t n_e, double gamma, double mu, double kT,
                                      const double* energies, double* ph_r, double* ph_lesser, double* ph_greater,
                                      void* stream) {

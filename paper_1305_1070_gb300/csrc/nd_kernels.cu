@@ -1415,4 +1415,46 @@ void launch_phonon(int n, int n_e, double gamma, double mu, double kT, const dou
   k_phonon<<<blocks, 256, 0, s>>>(n, n_e, gamma, mu, kT, energies, (double2*)r, (double2*)l, (double2*)g);
 }
 
+// Self-consistent Born update of an elastic local phonon self-energy:
+// Sigma_jj <- Sigma_jj + mix (D G_jj - Sigma_jj) for r, <, >.  stats[0] and
+// stats[1] receive the largest |D G_jj - Sigma_jj| and the largest |D G_jj|
+// through atomic maxima on their bit patterns (non-negative doubles order like
+// their bits as unsigned integers).
+__global__ void k_phonon_scba(int64_t tot, double D, double mix, const double2* __restrict__ Gr,
+                              const double2* __restrict__ Gl, const double2* __restrict__ Gg, double2* r, double2* l,
+                              double2* g, unsigned long long* stats) {
+  double dmax = 0.0, smax = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < tot; i += int64_t(gridDim.x) * blockDim.x) {
+    const double2* src[3] = {Gr, Gl, Gg};
+    double2* dst[3] = {r, l, g};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const double2 v = src[q][i];
+      const double2 nw = make_double2(D * v.x, D * v.y);
+      const double2 od = dst[q][i];
+      const double dx = nw.x - od.x, dy = nw.y - od.y;
+      dmax = fmax(dmax, hypot(dx, dy));
+      smax = fmax(smax, hypot(nw.x, nw.y));
+      dst[q][i] = make_double2(od.x + mix * dx, od.y + mix * dy);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(stats, (unsigned long long)__double_as_longlong(dmax));
+    atomicMax(stats + 1, (unsigned long long)__double_as_longlong(smax));
+  }
+}
+
+void launch_phonon_scba(int n, int n_e, double D, double mix, const double* Gr, const double* Gl, const double* Gg,
+                        double* r, double* l, double* g, double* stats, cudaStream_t s) {
+  const int64_t tot = int64_t(n) * n_e;
+  int blocks = int((tot + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_phonon_scba<<<blocks, 256, 0, s>>>(tot, D, mix, (const double2*)Gr, (const double2*)Gl, (const double2*)Gg,
+                                       (double2*)r, (double2*)l, (double2*)g, (unsigned long long*)stats);
+}
+
 }  // namespace ndgf

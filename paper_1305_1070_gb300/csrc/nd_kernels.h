@@ -128,5 +128,7 @@ void launch_density(const double* X, const double* w, int n_e, int n, double sca
                     cudaStream_t s);
 void launch_phonon(int n, int n_e, double gamma, double mu, double kT, const double* energies, double* r,
                    double* l, double* g, cudaStream_t s);
+void launch_phonon_scba(int n, int n_e, double D, double mix, const double* Gr, const double* Gl, const double* Gg,
+                        double* r, double* l, double* g, double* stats, cudaStream_t s);
 
 }  // namespace ndgf

@@ -31,7 +31,7 @@ ND_FACT_ADJOINT = 32
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
-           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const",
+           "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const", "nd_phonon_scba",
            "nd_last_error", "nd_version"]
 
 
@@ -103,6 +103,7 @@ def lib():
             "nd_lead_destroy": ([_P], None),
             "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
             "nd_phonon_const": ([_I32, _I32, _D, _D, _D, _P, _P, _P, _P, _P], _I32),
+            "nd_phonon_scba": ([_I32, _I32, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
             "nd_last_error": ([], ctypes.c_char_p),
             "nd_version": ([], ctypes.c_char_p),
         }
@@ -351,6 +352,14 @@ def nd_phonon_const(n, n_e, gamma, mu, kT, energies, ph_r, ph_lesser, ph_greater
     keep = []
     _check(lib().nd_phonon_const(n, n_e, gamma, mu, kT, _ptr(energies, keep), _ptr(ph_r, keep),
                                  _ptr(ph_lesser, keep), _ptr(ph_greater, keep), _stream(stream)), "nd_phonon_const")
+
+
+def nd_phonon_scba(n, n_e, D, mix, Gr, Gl, Gg, ph_r, ph_lesser, ph_greater, stats, stream=None):
+    """Self-consistent Born update of the elastic local phonon self-energy (see ndgf.h)."""
+    keep = []
+    _check(lib().nd_phonon_scba(n, n_e, D, mix, _ptr(Gr, keep), _ptr(Gl, keep), _ptr(Gg, keep), _ptr(ph_r, keep),
+                                _ptr(ph_lesser, keep), _ptr(ph_greater, keep), _ptr(stats, keep), _stream(stream)),
+           "nd_phonon_scba")
 
 
 def nd_version() -> str:

@@ -84,11 +84,42 @@ class Solver:
         if self.ph:
             mu_ph = tr.mu_ph if tr.mu_ph is not None else 0.5 * (tr.mu[0] + tr.mu[1])
             ndgf.nd_phonon_const(self.n, n_e, tr.gamma_ph, mu_ph, tr.kT, E, self.ph_r, self.ph_l, self.ph_g)
-        ndgf.nd_factor(self.fact, self.H, self.sig_r if self.leads else None, self.ph_r, E, n_e, tr.eta)
+        return self._solve(n_e, lesser)
+
+    def _solve(self, n_e: int, lesser: bool = True):
+        """Fold and diagonals for the energies, contact and phonon self-energies in place."""
+        E = self.E[:n_e]
+        ndgf.nd_factor(self.fact, self.H, self.sig_r if self.leads else None, self.ph_r, E, n_e, self.tr.eta)
         ndgf.nd_diag_green(self.fact, self.sig_l if lesser else None, self.sig_g if lesser else None,
                            self.ph_l if lesser else None, self.ph_g if lesser else None,
                            self.Gr, self.Gl if lesser else None, self.Gg if lesser else None)
         return self.Gr[:n_e], self.Gl[:n_e], self.Gg[:n_e]
+
+    def scba(self, energies, D: float, *, mix: float = 1.0, updates: int | None = None, tol: float = 1e-13,
+             max_updates: int = 2000):
+        """Self-consistent Born iteration of an elastic local phonon self-energy,
+        Sigma_ph,jj = D G_jj for r, <, > (D in eV^2; nd_phonon_scba), starting from
+        the constant broadening of the transport parameters (gamma_ph > 0: it also
+        reserves the phonon workspace).  Each update is followed by a solve; the
+        loop stops after `updates` updates, or when the relative change of the
+        self-energies falls to `tol`.  Returns (Gr, Gl, Gg, updates, last change)."""
+        if not self.ph:
+            raise ValueError("scba needs gamma_ph > 0 (phonon workspace and first iterate)")
+        n_e = len(energies)
+        self.step(energies)
+        stats = torch.zeros(2, dtype=torch.float64, device=self.device)
+        n_upd, change = 0, float("inf")
+        limit = updates if updates is not None else max_updates
+        while n_upd < limit:
+            ndgf.nd_phonon_scba(self.n, n_e, D, mix, self.Gr, self.Gl, self.Gg, self.ph_r, self.ph_l, self.ph_g,
+                                stats)
+            self._solve(n_e)
+            n_upd += 1
+            st = stats.cpu().numpy()
+            change = float(st[0] / st[1]) if st[1] > 0 else float(st[0])
+            if updates is None and change <= tol:
+                break
+        return self.Gr[:n_e], self.Gl[:n_e], self.Gg[:n_e], n_upd, change
 
     def certificate(self, n_e: int):
         """Per-energy certificate of the last step: [n_e, 8] = (max|A G - I|_jj,
