@@ -62,4 +62,5 @@ def scba(dev, tr, E: float, D: float, *, updates: int | None = None, tol: float 
         cur.append(np.trace(sl @ Gg[cc] - sg @ Gl[cc]))
     i_ph = np.sum(terms.ph_lesser * np.diag(Gg) - terms.ph_greater * np.diag(Gl))
     return {"Gr": np.diag(G), "Gl": np.diag(Gl), "Gg": np.diag(Gg), "updates": n_upd, "change": change,
-            "currents": np.array(cur), "i_ph": i_ph}
+            "currents": np.array(cur), "i_ph": i_ph,
+            "ph_r": terms.ph_r, "ph_lesser": terms.ph_lesser, "ph_greater": terms.ph_greater}

@@ -6,7 +6,10 @@ Sigma_ph,jj = D G_jj for r, <, >) against what the physics fixes:
   the eta leak, while the constant broadening (not self-consistent) does not;
 * D = 0: one update removes the phonon self-energy and the result is the
   ballistic dense definition;
-* the iteration contracts (the relative change falls geometrically)."""
+* the iteration contracts (the relative change falls geometrically);
+* the converged self-energy is causal and consistent: its broadening
+  -2 Im Sigma^r_ph equals i (Sigma^>_ph - Sigma^<_ph) (= D times the local
+  spectral function), up to the eta term."""
 import numpy as np
 import pytest
 
@@ -30,6 +33,10 @@ def test_fixed_point_conserves_current(E):
     iL, iR = r["currents"]
     assert abs(r["i_ph"]) <= 1e-12 * abs(iL)
     assert abs(iL + iR) <= 1e-8 * abs(iL), (iL, iR)
+    gamma_r = -2.0 * r["ph_r"].imag
+    gamma_lg = (1j * (r["ph_greater"] - r["ph_lesser"])).real
+    assert np.all(gamma_r >= 0.0)
+    assert np.abs(gamma_r - gamma_lg).max() <= 1e-4 * gamma_r.max()
     # the constant broadening (the first iterate) exchanges current with the bath
     r0 = scba.scba(dev, tr, E, D=0.02, updates=0)
     assert abs(r0["currents"].sum()) > 1e-2 * abs(r0["currents"][0])
