@@ -209,3 +209,24 @@ def test_union_of_devices_gets_one_tree_per_device():
         device_of = np.searchsorted(dev.site_offsets, np.arange(dev.n), side="right") - 1
         for c in range(info["n_clusters"]):
             assert len(set(device_of[owner == c].tolist())) <= 1
+
+
+def test_phonon_scba_rejects_bad_arguments():
+    """nd_phonon_scba validates its arguments before any device work (no GPU
+    needed): sizes, NULL arrays, the strength D >= 0, the mixing 0 < mix <= 1,
+    and host arrays (it works on device arrays only)."""
+    a = np.zeros(8, dtype=np.complex128)
+    st = np.zeros(2)
+    with pytest.raises(ndgf.NDError) as e:
+        ndgf.nd_phonon_scba(0, 1, 0.01, 1.0, a, a, a, a, a, a, st)
+    assert e.value.status == 1
+    with pytest.raises(ndgf.NDError) as e:
+        ndgf.nd_phonon_scba(4, 2, 0.01, 1.0, None, a, a, a, a, a, st)
+    assert e.value.status == 1
+    for D, mix in ((-0.01, 1.0), (0.01, 0.0), (0.01, 1.5)):
+        with pytest.raises(ndgf.NDError) as e:
+            ndgf.nd_phonon_scba(4, 2, D, mix, a, a, a, a, a, a, st)
+        assert e.value.status == 1
+    with pytest.raises(ndgf.NDError) as e:  # host arrays
+        ndgf.nd_phonon_scba(4, 2, 0.01, 1.0, a, a, a, a, a, a, st)
+    assert e.value.status == 1
