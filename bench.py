@@ -99,6 +99,8 @@ def parse():
                     help="the headline workload, or another one (its own JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
     ap.add_argument("--growth-max", type=float, default=10.0, help="fold growth above which fp32x2 redoes in FP64")
+    ap.add_argument("--resid-max", type=float, default=1e-8,
+                    help="FP64 certificate residual above which fp32x2 redoes in FP64")
     ap.add_argument("--delay", type=int, default=2, help="delayed pivots per cluster (0 = the paper's elimination)")
     ap.add_argument("--no-plain", action="store_true", help="skip the reference timing without delayed pivots")
     ap.add_argument("--tile", default="auto", choices=["auto", "large", "small", "tc", "alu"],
@@ -197,7 +199,7 @@ def main_ours(a) -> None:
     import __graft_entry__
     __graft_entry__.build()
     from paper_1305_1070_gb300 import ndgf, workloads
-    from paper_1305_1070_gb300.solver import Solver
+    from paper_1305_1070_gb300.solver import Solver, certificate_flags
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,6 +231,7 @@ def main_ours(a) -> None:
     dens = torch.zeros(n, dtype=torch.float64, device="cuda")
     cur = torch.zeros(2, n_e, dtype=torch.float64, device="cuda")  # terminal current spectra i_L, i_R
     cert_max = {}
+    cert_all = {}  # per path: [n_e, 8] certificate of the last step
 
     redo = {}
     calls = {"n": 0}  # solver.step calls of the last step (each launches 10 kernels outside the schedules)
@@ -238,6 +241,8 @@ def main_ours(a) -> None:
         certificate growth exceeds --growth-max are recomputed by it.
         step(after_chunk) calls after_chunk(c0, m) once a call's diagonals are
         in Gr, Gl, Gg (the end-to-end step starts their host copies there)."""
+        certs = torch.zeros(n_e, 8, dtype=torch.float64, device="cuda")
+
         def step(after_chunk=None):
             cmax = torch.zeros(8, dtype=torch.float64, device="cuda")
             flagged = []
@@ -250,9 +255,10 @@ def main_ours(a) -> None:
                 for c in range(2):
                     cur[c, c0:c0 + m] = solver.current(c, m)[0]
                 cert = solver.certificate(m)
+                certs[c0:c0 + m] = cert
                 cmax = torch.maximum(cmax, cert.amax(dim=0))
                 if fallback is not None:
-                    flagged.append(torch.nonzero(cert[:, 4] > a.growth_max).flatten() + c0)
+                    flagged.append(torch.nonzero(certificate_flags(cert, a.resid_max, a.growth_max)).flatten() + c0)
                 if after_chunk is not None:
                     after_chunk(c0, m)
             nredo = 0
@@ -271,6 +277,7 @@ def main_ours(a) -> None:
             if world > 1:
                 ndist.reduce_sum(dens)
             cert_max[name] = cmax
+            cert_all[name] = certs
             redo[name] = nredo
         return step
 
@@ -318,10 +325,18 @@ def main_ours(a) -> None:
             ms = timed(step, a.steps, a.warmup if name == "fp32x2" else min(a.warmup, 1))
         results[name] = (dens.clone(), Gl[:, ::97].clone(), Gr[pick].clone(), Gl[pick].clone(), cur.clone())
         c = cert_max[name].tolist()
+        ca = cert_all[name].cpu().numpy()
+        rel_l = ca[:, 2] / np.maximum(ca[:, 3], 1e-300)
         paths[name] = {"energies_per_s": round(n_e * world / (ms * 1e-3), 3), "ms_per_step": round(ms, 3),
                        "delay": delay,
                        "certificate_max": {"resid_r": c[0], "resid_lesser": c[2], "max_Gr": c[1], "max_Gl": c[3],
-                                           "growth_max_psi": c[4]},
+                                           "growth_max_psi": c[4], "entries_not_found": c[5]},
+                       "certificate_per_energy": {
+                           "resid_r": [float(f"{v:.3g}") for v in ca[:, 0]],
+                           "resid_lesser_rel": [float(f"{v:.3g}") for v in rel_l],
+                           "growth": [float(f"{v:.3g}") for v in ca[:, 4]],
+                           "flagged": int(((ca[:, 0] > a.resid_max) | (rel_l > a.resid_max) |
+                                           (ca[:, 4] > a.growth_max) | (ca[:, 5] > 0)).sum())},
                        "fp64_redo_energies": redo.get(name, 0)}
         if name in ("fp64_nd", "fp32x2"):
             solvers[name] = (solver, step, ms)
@@ -415,44 +430,74 @@ def main_ours(a) -> None:
     roofline = roof[head]
     launches_per_step = launches[head]
 
-    # end to end through the public API with host buffers (pinned)
+    # end to end through the C ABI with host buffers (pinned): nd_factor stages
+    # H and the energies from the host, nd_diag_green writes the diagonals into
+    # host memory, nd_fact_density / nd_contact_current / nd_certificate return
+    # host arrays; the copies are inside the timed region
     solver, step, _ = solvers[head]
+    f64 = solvers["fp64_nd"][0]
+    chunk = solver.max_ne
     H_host = torch.as_tensor(dev.values).pin_memory()
     E_host = torch.as_tensor(tr.energies).pin_memory()
+    w_host = torch.as_tensor(w).pin_memory()
     out_host = [torch.empty(n_e, n, dtype=torch.complex128).pin_memory() for _ in range(3)]
-    dens_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    dens_host = torch.zeros(n, dtype=torch.float64).pin_memory()
     cur_host = torch.empty(2, n_e, dtype=torch.float64).pin_memory()
-
-    copy_stream = torch.cuda.Stream()
-
-    def copy_out(c0, m):
-        # this call's diagonals go to the host on a copy stream while the next call computes
-        ev = torch.cuda.Event()
-        ev.record()
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(ev)
-            for dst, src in zip(out_host, (Gr, Gl, Gg)):
-                dst[c0:c0 + m].copy_(src[c0:c0 + m], non_blocking=True)
+    cert_host = torch.empty(chunk, 8, dtype=torch.float64).pin_memory()
+    red_host = [torch.empty(f64.max_ne, n, dtype=torch.complex128).pin_memory() for _ in range(3)]
+    red_cur = torch.empty(2, f64.max_ne, dtype=torch.float64).pin_memory()
+    io = {"h2d": 0, "d2h": 0, "redo": 0}
 
     def step_e2e():
-        solver.H.copy_(H_host, non_blocking=True)
-        if head == "fp32x2":
-            solvers["fp64_nd"][0].H.copy_(H_host, non_blocking=True)
-        E_all.copy_(E_host, non_blocking=True)
-        step(copy_out)
-        # energies recomputed by the fallback path overwrite their rows: copy those again
-        if redo.get(head, 0):
-            torch.cuda.current_stream().wait_stream(copy_stream)
-            for dst, src in zip(out_host, (Gr, Gl, Gg)):
-                dst.copy_(src, non_blocking=True)
-        dens_host.copy_(dens, non_blocking=True)
-        cur_host.copy_(cur, non_blocking=True)
-        # the step ends when the host has every result
-        torch.cuda.current_stream().wait_stream(copy_stream)
+        io.update(h2d=0, d2h=0, redo=0)
+
+        def one_call(s, E_h, outs, w_h, first, cur_dst):
+            k = len(E_h)
+            s.step_host(E_h, *outs, H_host=H_host)
+            for c in range(2):
+                ndgf.nd_contact_current(s.fact, c, cur_dst[c], None)
+            ndgf.nd_fact_density(s.fact, w_h, scale, 0 if first else 1, dens_host)
+            # H, the energies (nd_factor and the leads), weights, density when accumulating
+            io["h2d"] += H_host.numel() * 8 + 2 * k * 8 + k * 8 + (0 if first else n * 8)
+            io["d2h"] += 3 * k * n * 16 + 2 * k * 8 + n * 8
+
+        for c0 in range(0, n_e, chunk):
+            m = min(chunk, n_e - c0)
+            wk = w_host[c0:c0 + m].clone()
+            one_call(solver, E_host[c0:c0 + m], [o[c0:c0 + m] for o in out_host], wk, c0 == 0,
+                     [cur_host[c, c0:c0 + m] for c in range(2)])
+            if head != "fp32x2":
+                continue
+            ndgf.nd_certificate(solver.fact, cert_host[:m])
+            io["d2h"] += m * 64
+            torch.cuda.current_stream().synchronize()
+            bad = np.nonzero(certificate_flags(cert_host[:m], a.resid_max, a.growth_max).numpy())[0]
+            for r0 in range(0, len(bad), f64.max_ne):  # complex128 recomputation of flagged energies
+                sel = c0 + bad[r0:r0 + f64.max_ne]
+                k = len(sel)
+                # take the flagged energies' FP32-pair contribution out of the density, add the complex128 one
+                neg = torch.zeros(m, dtype=torch.float64).pin_memory()
+                neg[sel - c0] = -w_host[sel]
+                ndgf.nd_fact_density(solver.fact, neg, scale, 1, dens_host)
+                io["h2d"] += m * 8 + n * 8
+                io["d2h"] += n * 8
+                one_call(f64, E_host[sel].pin_memory(), [o[:k] for o in red_host], w_host[sel].pin_memory(), False,
+                         [red_cur[c, :k] for c in range(2)])
+                torch.cuda.current_stream().synchronize()
+                for o, rr in zip(out_host, red_host):
+                    o[sel] = rr[:k]
+                cur_host[:, sel] = red_cur[:, :k]
+                io["redo"] += k
+        if world > 1:  # the density integral over all ranks' energies
+            dd = dens_host.to("cuda")
+            ndist.reduce_sum(dd)
+            dens_host.copy_(dd)
+            io["h2d"] += n * 8
+            io["d2h"] += n * 8
+        torch.cuda.current_stream().synchronize()
 
     ms_e2e = timed(step_e2e, a.steps, 1)
-    h2d = H_host.numel() * 8 + E_host.numel() * 8
-    d2h = 3 * n_e * n * 16 + n * 8 + 2 * n_e * 8
+    h2d, d2h = io["h2d"], io["d2h"]
     info = solver.info
 
     if rank == 0:
@@ -481,7 +526,9 @@ def main_ours(a) -> None:
                        "clusters": info["n_clusters"],
                        "levels": info["n_levels"], "leaf_size": a.leaf, "eta": tr.eta, "path": head,
                        "delayed_pivots_per_cluster": a.delay,
-                       "l2": "inputs larger than L2 (~100-200 GB workspace per step)"},
+                       "l2": "inputs larger than L2 (~100-200 GB workspace per step)",
+                       "fp64_nd_same_gpu_energies_per_s": paths["fp64_nd"]["energies_per_s"],
+                       "mixed_over_fp64_nd": paths["speedup_fp32x2_over_fp64"]},
             "paths": paths,
             "current_spectrum_integral_eV": {"L": float((cur[0] * weights).sum()), "R": float((cur[1] * weights).sum())},
             "roofline": roofline,
@@ -493,7 +540,8 @@ def main_ours(a) -> None:
             "gpu_launches": launches_per_step * a.steps,
             "clocks": clocks,
             "e2e": {"value": round(n_e * world / (ms_e2e * 1e-3), 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h, "path": "C ABI host buffers: nd_factor, nd_diag_green, "
+                    "nd_contact_current, nd_certificate, nd_fact_density", "fp64_redo_energies": io["redo"]},
             "cpu_baseline": {"value": round(cpu_val, 4), "unit": UNIT, "cores": cpu["cores"], "kind": "oracle",
                              "sample": f"block RGF (oracle/rgf.py), {cpu['energies']} of the 256 energies, "
                                        f"{cpu['seconds']:.1f} s"},

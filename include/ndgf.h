@@ -43,7 +43,7 @@ extern "C" {
 typedef enum {
   ND_OK = 0,
   ND_ERR_INVALID_ARG = 1,        /* bad size, NULL, out-of-range index          */
-  ND_ERR_NOT_SYMMETRIC = 2,      /* graph pattern or contact block not symmetric */
+  ND_ERR_NOT_SYMMETRIC = 2,      /* pattern, H values or Sigma^r block not symmetric */
   ND_ERR_SINGULAR = 3,           /* exactly singular pivot in a cluster block   */
   ND_ERR_NOT_SKEW_HERMITIAN = 4, /* Sigma^< / Sigma^> block not skew-Hermitian  */
   ND_ERR_OOM = 5,                /* device or host allocation failed            */
@@ -122,7 +122,7 @@ typedef struct nd_graph {
  * pivoting across clusters is not.  The result is the same matrix function;
  * only the elimination order differs per energy.  delay > 0 adds an unknown
  * id range n .. n + n_virtual - 1 to the cluster site lists
- * (nd_plan_cluster_sites) and turns off the residual part of nd_certificate. */
+ * (nd_plan_cluster_sites). */
 typedef struct nd_opts {
   int32_t leaf_size;
   int32_t split_permille;
@@ -183,9 +183,18 @@ void nd_fact_destroy(nd_fact* fact);
  *                          blocks must be complex symmetric.
  * sigma_ph_r             : [n_e][n] complex diagonal Sigma^r_ph, or NULL.
  * energies               : [n_e] real.
- * eta                    : positive broadening added to the device diagonal.
+ * eta                    : positive broadening added to the device diagonal
+ *                          (eta <= 0 or not finite: ND_ERR_INVALID_ARG; with
+ *                          eta = 0 an interior block E - H_ii can be exactly
+ *                          singular).
  * Folds every cluster level by level (Psi_i = -A_ii^{-1} A_{i,B}, Schur update
- * of the parent front) and inverts the root.  Errors: ND_ERR_INVALID_ARG,
+ * of the parent front) and inverts the root.  The elimination relies on
+ * A = A^T (paper Sec. 3.1, LDL^T), so H must have symmetric values and every
+ * Sigma^r_c block must be complex symmetric, within the relative tolerance of
+ * nd_check_factor_inputs: host arrays are checked before any device work
+ * (ND_ERR_NOT_SYMMETRIC from this call), device arrays by a kernel on the
+ * stream (ND_ERR_NOT_SYMMETRIC from the next nd_fact_status; the results are
+ * then invalid).  Errors: ND_ERR_INVALID_ARG, ND_ERR_NOT_SYMMETRIC,
  * ND_ERR_CUDA; ND_ERR_SINGULAR is reported by nd_fact_status after the stream
  * is synchronised (no device trap). */
 nd_status nd_factor(nd_fact* fact, const double* H_values, const double* sigma_r,
@@ -199,7 +208,12 @@ nd_status nd_factor(nd_fact* fact, const double* H_values, const double* sigma_r
  * Gr, Gl, Gg                  : [n_e][n] complex outputs (diag G^r, G^<, G^>)
  *                               in caller order; NULL skips that output (Gl
  *                               and Gg need the matching Sigma terms).
- * Uses the factorization of the last nd_factor call on this handle. */
+ * Uses the factorization of the last nd_factor call on this handle.  The
+ * Sigma^< / Sigma^> inputs must be skew-Hermitian (paper Sec. 3.1, Eq. (5)-(6):
+ * the extraction sets P_BI = -(P_IB)^dagger), within the tolerance of
+ * nd_check_lesser_inputs: host arrays are checked before any device work
+ * (ND_ERR_NOT_SKEW_HERMITIAN from this call), device arrays on the stream
+ * (ND_ERR_NOT_SKEW_HERMITIAN from the next nd_fact_status). */
 nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double* sigma_greater,
                         const double* ph_lesser, const double* ph_greater, double* Gr, double* Gl,
                         double* Gg, void* stream);
@@ -210,14 +224,37 @@ nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double*
  *   cert[e][0] = max_j |(A G^r)_jj - 1|,           cert[e][1] = max_j |G^r_jj|,
  *   cert[e][2] = max_j |(A G^<)_jj - (Sigma^< G^a)_jj|, cert[e][3] = max_j |G^<_jj|
  * (paper Eq. (1): A G^r = I and A G^< = Sigma^< (G^r)^dagger; every nonzero
- * A_jk has its G_kj among the entries the selected inversion stores, Sec. 3.2).
+ * A_jk has its G_kj among the entries the selected inversion stores, Sec. 3.2,
+ * also with delayed pivots, where the entry's place is found per energy).
  *   cert[e][4] = max over clusters of max |Psi_i| (Psi_i = -A_ii^{-1} A_iB), the
  *                growth of the fold: the extraction multiplies rounding errors
  *                of G_BB by Psi_i, so large values flag energies whose diagonal
- *                carries amplified rounding;   cert[e][5..7] = 0 (reserved).
+ *                carries amplified rounding;
+ *   cert[e][5] = 1 if a stored entry could not be located (an internal
+ *                inconsistency of the plan; never expected), else 0;
+ *   cert[e][6..7] = 0 (reserved).
  * Entries 2 and 3 are 0 when G^< was not computed.  cert: [n_e][8] doubles,
- * host or device.  Stream ordered after the nd_diag_green call. */
+ * host or device.  Stream ordered after the nd_diag_green call.  The residual
+ * of the diagonal is the refinement test of the mixed paths: a residual-
+ * correction step G + G (I - A G) would need whole rows of G, which the
+ * selected inversion does not form, so an energy whose residual is too large
+ * is recomputed on the complex128 path instead (the Python driver's
+ * certified step does this). */
 nd_status nd_certificate(nd_fact* fact, double* cert, void* stream);
+
+/* Selected entries of the last nd_factor + nd_diag_green (paper Sec. 3.2: the
+ * selected inversion stores G^(0) on the fill pattern, i.e. G_xy for every
+ * pair x, y that A couples, and every pair inside one cluster's front): for
+ * count pairs (x[p], y[p]) of caller sites, for every energy e,
+ *   Gr[e][p] = G^r_xy, Gl[e][p] = G^<_xy, Gg[e][p] = G^>_xy
+ * ([n_e][count] complex, device; any may be NULL; Gl / Gg need a preceding
+ * nd_diag_green that computed G^< or G^>).  Bond currents
+ * J_xy(E) ~ Re(H_xy G^<_yx) and the S9 residual are built from these.  A pair
+ * whose entry is not stored (not coupled, or out of range) gets NaN and is
+ * counted in *n_missing (device int32, cleared by the call).  x, y: device
+ * int32 [count].  Errors: ND_ERR_INVALID_ARG. */
+nd_status nd_selected_entries(nd_fact* fact, const int32_t* x, const int32_t* y, int32_t count, double* Gr,
+                              double* Gl, double* Gg, int32_t* n_missing, void* stream);
 
 /* Adjoint of the density (spec extension; the paper computes the
  * density only): for every energy of the last nd_factor / nd_diag_green pair
@@ -257,6 +294,17 @@ nd_status nd_contact_current(nd_fact* fact, int32_t contact, double* current, do
 nd_status nd_density(const double* Gl, const double* weights, int32_t n_e, int32_t n, double scale,
                      int32_t accumulate, double* out, void* stream);
 
+/* The same density epilogue on the handle's last diag G^< (wherever
+ * nd_diag_green put it: the caller's device array, or the handle's staging
+ * copy when the caller asked for host output), for the n_e energies of the
+ * last nd_factor: out[j] = (accumulate ? out[j] : 0) + scale * sum_e
+ * weights[e] Im G^<_jj(E_e).  weights [n_e] and out [n] may be host or device
+ * arrays (host arrays are copied on the stream; a host out must stay valid
+ * until the stream is synchronised).  Errors: ND_ERR_INVALID_ARG (no G^< in
+ * the last nd_diag_green). */
+nd_status nd_fact_density(nd_fact* fact, const double* weights, double scale, int32_t accumulate, double* out,
+                          void* stream);
+
 /* ---- launch profiling ------------------------------------------------------
  * While enabled, every launch of the fold / extraction schedules on the
  * handle's stream is bracketed by CUDA events.  nd_profile(f, enable, stats,
@@ -284,8 +332,10 @@ nd_status nd_profile_launches(nd_fact* fact, nd_launch_stats* out, int32_t max_o
 
 /* Status of the last factor/diag call (synchronises the handle's stream):
  * n_singular = number of (energy, cluster) pivots that were exactly zero;
- * returns ND_ERR_SINGULAR when n_singular > 0, ND_ERR_TIMEOUT when a bounded
- * wait of a tensor-core product gave up (the results are then invalid). */
+ * returns, in this order of precedence, ND_ERR_TIMEOUT when a bounded wait of
+ * a tensor-core product gave up, ND_ERR_NOT_SYMMETRIC / ND_ERR_NOT_SKEW_HERMITIAN
+ * when the device inputs of the last nd_factor / nd_diag_green failed their
+ * check, ND_ERR_SINGULAR when n_singular > 0 (the results are then invalid). */
 nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
 
 /* ---- S1a: contact self-energies (paper Sec. 2) ----------------------------
@@ -333,8 +383,10 @@ nd_status nd_sigma_lesser_fermi(const double* sigma_r, int32_t n_e, int32_t n_co
  * self-energy (a model the paper leaves open, Sec. 2; S. Datta, Superlattices
  * Microstruct. 28, 253 (2000)): with the diagonals of the last nd_diag_green
  * call (caller order), Sigma^r_ph,jj <- Sigma + mix (D G^r_jj - Sigma), and
- * likewise Sigma^< from G^< and Sigma^> from G^> (D in eV^2, 0 < mix <= 1).
- * All arrays are device [n_e][n] complex; the phonon arrays are updated in
+ * likewise Sigma^< from i Im G^< and Sigma^> from i Im G^> (D in eV^2,
+ * 0 < mix <= 1; the diagonal of a skew-Hermitian G^< is imaginary, so only the
+ * rounding residue of Re G^<_jj is dropped, which keeps Sigma^< skew-Hermitian
+ * for the input check of nd_diag_green).  All arrays are device [n_e][n] complex; the phonon arrays are updated in
  * place and are the inputs of the next nd_factor / nd_diag_green.
  * stats (device, 2 doubles) receives max |D G - Sigma| and max |D G| over the
  * three self-energies (their ratio is the relative change of the iteration).
@@ -358,8 +410,9 @@ nd_status nd_phonon_const(int32_t n, int32_t n_e, double gamma, double mu, doubl
  * copied to complex128, inverted by Gauss-Jordan with partial pivoting, and
  * rounded back.  The complex128 copies live in a fixed file-scope device array
  * of 2^18 complex128 elements (4 MiB) that every GPU loading the library holds
- * until the process exits; batch * n * n must not exceed 2^18 and n must not
- * exceed 1024, else ND_ERR_INVALID_ARG.  No cudaMalloc/cudaFree is called.
+ * until the process exits; batch * n * n must not exceed 2^18 (so n <= 512),
+ * else ND_ERR_INVALID_ARG, and A and n_singular must be device arrays (else
+ * ND_ERR_INVALID_ARG).  No cudaMalloc/cudaFree is called.
  * n_singular (device int32) receives the number of exactly singular pivots
  * (it is cleared by the call).  The first call on a device looks up the
  * array's device address (once per device, with that device current); make
@@ -367,6 +420,23 @@ nd_status nd_phonon_const(int32_t n, int32_t n_e, double gamma, double mu, doubl
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and must be serialised by the caller. */
 nd_status nd_invert_c64_noalloc(float* A, int32_t n, int32_t batch, int32_t* n_singular, void* stream);
+
+/* ---- input checks (host arrays; callable without a GPU) ----------------------
+ * The checks nd_factor and nd_diag_green apply to their host inputs, on their
+ * own.  nd_check_factor_inputs: H_values[nnz] symmetric on the pattern,
+ * |H_jk - H_kj| <= 1e-8 max(|H_jk|, |H_kj|), and every contact block of
+ * sigma_r ([n_e][sum_c m_c^2] complex, may be NULL when the plan has no
+ * contacts) complex symmetric, |S_ab - S_ba| <= 1e-8 max|S| per block and
+ * energy (paper Sec. 3.1: the fold is an LDL^T elimination of A = A^T):
+ * ND_ERR_NOT_SYMMETRIC.  nd_check_lesser_inputs: every contact block of
+ * sigma_lesser / sigma_greater skew-Hermitian, |S_ab + conj(S_ba)| <= 1e-8
+ * max|S|, and the phonon diagonals ph_lesser / ph_greater ([n_e][n] complex)
+ * purely imaginary, |Re s_j| <= 1e-8 |s_j| (paper Sec. 3.1, Eq. (5)-(6)); any
+ * pointer may be NULL: ND_ERR_NOT_SKEW_HERMITIAN.  Non-finite values fail the
+ * check.  Errors: ND_ERR_INVALID_ARG (NULL plan or H, n_e < 0). */
+nd_status nd_check_factor_inputs(const nd_plan* plan, const double* H_values, const double* sigma_r, int32_t n_e);
+nd_status nd_check_lesser_inputs(const nd_plan* plan, const double* sigma_lesser, const double* sigma_greater,
+                                 const double* ph_lesser, const double* ph_greater, int32_t n_e);
 
 const char* nd_last_error(void);
 const char* nd_version(void);

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "nd_arith.cuh"
+#include "nd_check.h"
 #include "nd_internal.h"
 #include "nd_kernels.h"
 
@@ -96,6 +97,10 @@ struct nd_fact {
   double* root_scratch = nullptr;
   int64_t root_stride = 0;
   int* d_status = nullptr;
+  int* d_inerr = nullptr;  // [0] inputs of nd_factor not symmetric, [1] inputs of nd_diag_green not skew-Hermitian
+  int32_t* d_csrT = nullptr;  // CSR transpose index (symmetry check of device H)
+  int32_t* d_cm = nullptr;    // contact sizes
+  int64_t* d_csoff = nullptr; // contact block offsets in the packed Sigma arrays
   bool has_ph = false;
   // device tables
   int32_t *d_sites = nullptr, *d_maps = nullptr, *d_ent_dst = nullptr, *d_ent_src = nullptr;
@@ -137,9 +142,13 @@ struct nd_fact {
   int n_ones = 0;
   double* d_cvec = nullptr;
   bool have_lesser = false;
+  bool have_green = false;  // an nd_diag_green followed the last nd_factor
+  const double* last_gl = nullptr;  // device diag G^< of the last nd_diag_green (the caller's array or staging)
+  double *d_w = nullptr, *d_dens = nullptr;  // nd_fact_density: weights [max_ne], density [n]
   double* d_cert = nullptr;
-  int32_t *d_cert_ptr = nullptr, *d_cert_terms = nullptr, *d_cl_ldG2 = nullptr;
-  int64_t* d_cl_offP0 = nullptr;
+  int32_t *d_cert_ptr = nullptr, *d_cert_nb = nullptr, *d_cert_coef = nullptr, *d_cert_slot = nullptr;
+  int32_t *d_cert_bslot = nullptr, *d_cert_bidx = nullptr;
+  CertCluster* d_cert_cl = nullptr;
   ZeroDesc* d_psi = nullptr;
   Profiler prof;
   std::vector<double> step_flops_factor, step_flops_green, step_flops_lesser[2];  // per step, per energy
@@ -555,6 +564,15 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   }
   TRY(dalloc(f, (void**)&f->d_status, sizeof(int)));
   cudaMemset(f->d_status, 0, sizeof(int));
+  TRY(dalloc(f, (void**)&f->d_inerr, 2 * sizeof(int)));
+  cudaMemset(f->d_inerr, 0, 2 * sizeof(int));
+  TRY(dupload(f, p->csr_T, &f->d_csrT));
+  {
+    std::vector<int32_t> cm(p->n_contacts);
+    for (int c = 0; c < p->n_contacts; ++c) cm[c] = p->contact_ptr[c + 1] - p->contact_ptr[c];
+    TRY(dupload(f, cm, &f->d_cm));
+    TRY(dupload(f, p->contact_soff, &f->d_csoff));
+  }
   TRY(dupload(f, p->sites, &f->d_sites));
   TRY(dupload(f, p->maps, &f->d_maps));
   TRY(dupload(f, p->ent_dst, &f->d_ent_dst));
@@ -611,11 +629,17 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dupload(f, p->cl_offG, &f->d_cl_offG));
   TRY(dupload(f, p->cl_offGX[0], &f->d_cl_offGX[0]));
   TRY(dupload(f, p->cl_offGX[1], &f->d_cl_offGX[1]));
-  TRY(dupload(f, p->cl_offP[0], &f->d_cl_offP0));
   TRY(dupload(f, p->cert_ptr, &f->d_cert_ptr));
-  TRY(dupload(f, p->cert_terms, &f->d_cert_terms));
+  TRY(dupload(f, p->cert_nb, &f->d_cert_nb));
+  TRY(dupload(f, p->cert_coef, &f->d_cert_coef));
+  TRY(dupload(f, p->cert_slot, &f->d_cert_slot));
+  TRY(dupload(f, p->cert_bslot, &f->d_cert_bslot));
+  TRY(dupload(f, p->cert_bidx, &f->d_cert_bidx));
+  TRY(dupload(f, p->cert_cl, &f->d_cert_cl));
   TRY(dalloc(f, (void**)&f->d_cert, size_t(max_ne) * 8 * sizeof(double)));
   TRY(dalloc(f, (void**)&f->d_current, size_t(max_ne) * 2 * sizeof(double)));
+  TRY(dalloc(f, (void**)&f->d_w, size_t(max_ne) * sizeof(double)));
+  TRY(dalloc(f, (void**)&f->d_dens, size_t(std::max(1, p->n)) * sizeof(double)));
   TRY(dupload(f, p->psi_desc, &f->d_psi));
   f->step_flops_factor = step_flops(p, p->sched_factor);
   f->step_flops_green = step_flops(p, p->sched_green);
@@ -687,12 +711,17 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
                                const double* energies, int32_t n_e, double eta, void* stream) {
   if (!f || !H_values || !energies) return fail(ND_ERR_INVALID_ARG, "nd_factor: NULL argument");
   if (n_e <= 0 || n_e > f->max_ne) return fail(ND_ERR_INVALID_ARG, "nd_factor: n_e outside 1..max_ne");
-  if (!(eta >= 0.0)) return fail(ND_ERR_INVALID_ARG, "nd_factor: eta must be >= 0");
+  if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ND_ERR_INVALID_ARG, "nd_factor: eta must be positive and finite");
   const nd_plan* p = f->plan;
   if (p->n_contacts > 0 && !sigma_r) return fail(ND_ERR_INVALID_ARG, "nd_factor: sigma_r is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const double *H, *sr, *ph, *E;
   nd_status st;
+  // complex symmetry of A (paper Sec. 3.1): host inputs are checked here, device inputs on the stream below
+  const bool H_dev = is_device_ptr(H_values), sr_dev = p->n_contacts > 0 && is_device_ptr(sigma_r);
+  if ((st = host_check_factor(p, H_dev ? nullptr : H_values, (p->n_contacts > 0 && !sr_dev) ? sigma_r : nullptr,
+                              n_e)) != ND_OK)
+    return fail(st, std::string("nd_factor: ") + nd_last_error());
   if ((st = stage_in(H_values, f->st_H, size_t(p->nnz) * 8, s, &H)) != ND_OK) return st;
   if ((st = stage_in(sigma_r, f->st_sr, size_t(n_e) * p->sigma_elems * 16, s, &sr)) != ND_OK) return st;
   if ((st = stage_in(sigma_ph_r, f->st_ph, size_t(n_e) * p->n * 16, s, &ph)) != ND_OK) return st;
@@ -704,8 +733,13 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
   f->cur_ph = ph;
   f->cur_E = E;
   f->have_lesser = false;
+  f->have_green = false;
+  f->last_gl = nullptr;
   ND_CUDA(cudaMemsetAsync(f->d_status, 0, sizeof(int), s));
   ND_CUDA(cudaMemsetAsync(f->d_tc_timeout, 0, sizeof(int), s));
+  ND_CUDA(cudaMemsetAsync(f->d_inerr, 0, 2 * sizeof(int), s));
+  if (H_dev) launch_check_H(H, f->d_csrT, p->nnz, f->d_inerr, s);
+  if (sr_dev) launch_check_blocks(sr, p->sigma_elems, f->d_csoff, f->d_cm, p->n_contacts, n_e, false, f->d_inerr, s);
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, n_e};
   const int nc = int(p->cl.size());
   if (f->precision == ND_PREC_FP64) return factor_t<double>(f, w, H, E, eta, sr, ph, nc, s);
@@ -750,10 +784,25 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
   const int n_e = f->n_e;
   const double *sl, *sg, *pl, *pg;
   nd_status st;
+  // skew-Hermitian Sigma^< / Sigma^> (paper Sec. 3.1): host inputs here, device inputs on the stream below
+  const bool has_c = p->n_contacts > 0;
+  const bool dev_in[4] = {has_c && is_device_ptr(sigma_lesser), has_c && is_device_ptr(sigma_greater),
+                          is_device_ptr(ph_lesser), is_device_ptr(ph_greater)};
+  {
+    const double* blocks[2] = {has_c && !dev_in[0] ? sigma_lesser : nullptr, has_c && !dev_in[1] ? sigma_greater : nullptr};
+    const double* diags[2] = {dev_in[2] ? nullptr : ph_lesser, dev_in[3] ? nullptr : ph_greater};
+    if ((st = host_check_lesser(p, blocks, diags, n_e)) != ND_OK)
+      return fail(st, std::string("nd_diag_green: ") + nd_last_error());
+  }
+  ND_CUDA(cudaMemsetAsync(f->d_inerr + 1, 0, sizeof(int), s));
   if ((st = stage_in(sigma_lesser, f->st_sl, size_t(n_e) * p->sigma_elems * 16, s, &sl)) != ND_OK) return st;
   if ((st = stage_in(sigma_greater, f->st_sg, size_t(n_e) * p->sigma_elems * 16, s, &sg)) != ND_OK) return st;
   if ((st = stage_in(ph_lesser, f->st_pl, size_t(n_e) * p->n * 16, s, &pl)) != ND_OK) return st;
   if ((st = stage_in(ph_greater, f->st_pg, size_t(n_e) * p->n * 16, s, &pg)) != ND_OK) return st;
+  if (dev_in[0]) launch_check_blocks(sl, p->sigma_elems, f->d_csoff, f->d_cm, p->n_contacts, n_e, true, f->d_inerr + 1, s);
+  if (dev_in[1]) launch_check_blocks(sg, p->sigma_elems, f->d_csoff, f->d_cm, p->n_contacts, n_e, true, f->d_inerr + 1, s);
+  if (dev_in[2]) launch_check_diag_skew(pl, int64_t(n_e) * p->n, f->d_inerr + 1, s);
+  if (dev_in[3]) launch_check_diag_skew(pg, int64_t(n_e) * p->n, f->d_inerr + 1, s);
   double* user[3] = {Gr, Gl, Gg};
   double* dev[3];
   bool host[3];
@@ -765,7 +814,9 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
        : f->precision == ND_PREC_MIXED ? diag_green_t<float>(f, sl, sg, pl, pg, dev, s)
                                        : diag_green_t<DF>(f, sl, sg, pl, pg, dev, s);
   if (st != ND_OK) return st;
+  f->have_green = true;
   f->have_lesser = (Gl || Gg);
+  f->last_gl = Gl ? dev[1] : nullptr;
   f->cur_sl = sl;
   f->cur_sg = sg;
   f->cur_pl = pl;
@@ -774,23 +825,19 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
   return ND_OK;
 }
 
-extern "C" nd_status nd_certificate(nd_fact* f, double* cert, void* stream) {
-  if (!f || !cert) return fail(ND_ERR_INVALID_ARG, "nd_certificate: NULL argument");
-  if (f->n_e <= 0) return fail(ND_ERR_INVALID_ARG, "nd_certificate: call nd_factor and nd_diag_green first");
+static CertArgs cert_args(nd_fact* f) {
   const nd_plan* p = f->plan;
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t bytes = size_t(f->n_e) * 8 * sizeof(double);
-  ND_CUDA(cudaMemsetAsync(f->d_cert, 0, bytes, s));
-  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
   CertArgs a{};
   a.n = p->n;
-  a.cptr = p->n_virtual > 0 ? nullptr : f->d_cert_ptr;
-  a.terms = f->d_cert_terms;
-  a.owner = f->d_owner;
-  a.pos = f->d_pos;
-  a.ldG = f->d_cl_ldG;
-  a.offG = f->d_cl_offG;
-  a.offP = f->d_cl_offP0;
+  a.cptr = f->d_cert_ptr;
+  a.nb = f->d_cert_nb;
+  a.coef = f->d_cert_coef;
+  a.slot = f->d_cert_slot;
+  a.bslot = f->d_cert_bslot;
+  a.bidx = f->d_cert_bidx;
+  a.unk_q = f->d_unk_q;
+  a.unk_r = f->d_unk_r;
+  a.cl = f->d_cert_cl;
   a.H = f->cur_H;
   a.sr = f->cur_sr;
   a.sl = f->cur_sl;
@@ -803,15 +850,57 @@ extern "C" nd_status nd_certificate(nd_fact* f, double* cert, void* stream) {
   a.cert = f->d_cert;
   a.psi = f->d_psi;
   a.n_psi = int(p->psi_desc.size());
+  return a;
+}
+
+extern "C" nd_status nd_certificate(nd_fact* f, double* cert, void* stream) {
+  if (!f || !cert) return fail(ND_ERR_INVALID_ARG, "nd_certificate: NULL argument");
+  if (f->n_e <= 0 || !f->have_green)
+    return fail(ND_ERR_INVALID_ARG, "nd_certificate: call nd_factor and nd_diag_green first");
+  const nd_plan* p = f->plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = size_t(f->n_e) * 8 * sizeof(double);
+  ND_CUDA(cudaMemsetAsync(f->d_cert, 0, bytes, s));
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
+  const CertArgs a = cert_args(f);
   if (f->precision == ND_PREC_FP64)
-    Kern<double>::certificate(w, a, s);
+    Kern<double>::certificate(w, a, f->dt, s);
   else if (f->precision == ND_PREC_MIXED)
-    Kern<float>::certificate(w, a, s);
+    Kern<float>::certificate(w, a, f->dt, s);
   else
-    Kern<DF>::certificate(w, a, s);
+    Kern<DF>::certificate(w, a, f->dt, s);
   ND_CUDA(cudaGetLastError());
   ND_CUDA(cudaMemcpyAsync(cert, f->d_cert, bytes, is_device_ptr(cert) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                           s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_selected_entries(nd_fact* f, const int32_t* x, const int32_t* y, int32_t count, double* Gr,
+                                         double* Gl, double* Gg, int32_t* n_missing, void* stream) {
+  if (!f || !x || !y || !n_missing || count < 0) return fail(ND_ERR_INVALID_ARG, "nd_selected_entries: bad argument");
+  if (f->n_e <= 0 || !f->have_green)
+    return fail(ND_ERR_INVALID_ARG, "nd_selected_entries: call nd_factor and nd_diag_green first");
+  if ((Gl || Gg) && !f->have_lesser)
+    return fail(ND_ERR_INVALID_ARG, "nd_selected_entries: G^< / G^> need a preceding nd_diag_green that computed them");
+  const void* dev[] = {x, y, n_missing};
+  for (const void* q : dev)
+    if (!is_device_ptr(q)) return fail(ND_ERR_INVALID_ARG, "nd_selected_entries: x, y, n_missing must be device arrays");
+  const void* outs[] = {Gr, Gl, Gg};
+  for (const void* q : outs)
+    if (q && !is_device_ptr(q)) return fail(ND_ERR_INVALID_ARG, "nd_selected_entries: outputs must be device arrays");
+  const nd_plan* p = f->plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  ND_CUDA(cudaMemsetAsync(n_missing, 0, sizeof(int32_t), s));
+  Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
+  const CertArgs a = cert_args(f);
+  const int les = f->have_lesser ? 1 : 0;
+  if (f->precision == ND_PREC_FP64)
+    Kern<double>::selected(w, a, f->dt, x, y, count, les, Gr, Gl, Gg, n_missing, s);
+  else if (f->precision == ND_PREC_MIXED)
+    Kern<float>::selected(w, a, f->dt, x, y, count, les, Gr, Gl, Gg, n_missing, s);
+  else
+    Kern<DF>::selected(w, a, f->dt, x, y, count, les, Gr, Gl, Gg, n_missing, s);
+  ND_CUDA(cudaGetLastError());
   return ND_OK;
 }
 
@@ -958,13 +1047,44 @@ extern "C" nd_status nd_density(const double* Gl, const double* weights, int32_t
   return ND_OK;
 }
 
+extern "C" nd_status nd_fact_density(nd_fact* f, const double* weights, double scale, int32_t accumulate, double* out,
+                                     void* stream) {
+  if (!f || !weights || !out) return fail(ND_ERR_INVALID_ARG, "nd_fact_density: NULL argument");
+  if (f->n_e <= 0 || !f->last_gl)
+    return fail(ND_ERR_INVALID_ARG, "nd_fact_density: needs a preceding nd_diag_green that computed G^<");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = f->plan->n, n_e = f->n_e;
+  const double* w = weights;
+  if (!is_device_ptr(weights)) {
+    ND_CUDA(cudaMemcpyAsync(f->d_w, weights, size_t(n_e) * sizeof(double), cudaMemcpyHostToDevice, s));
+    w = f->d_w;
+  }
+  const bool out_dev = is_device_ptr(out);
+  double* o = out_dev ? out : f->d_dens;
+  if (!out_dev && accumulate)
+    ND_CUDA(cudaMemcpyAsync(o, out, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_density(f->last_gl, w, n_e, n, scale, accumulate, o, s);
+  ND_CUDA(cudaGetLastError());
+  if (!out_dev) ND_CUDA(cudaMemcpyAsync(out, o, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return ND_OK;
+}
+
 extern "C" nd_status nd_fact_status(nd_fact* f, int32_t* n_singular) {
   if (!f) return fail(ND_ERR_INVALID_ARG, "nd_fact_status: NULL handle");
-  int h = 0, to = 0;
+  int h = 0, to = 0, ie[2] = {0, 0};
   ND_CUDA(cudaMemcpy(&h, f->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   ND_CUDA(cudaMemcpy(&to, f->d_tc_timeout, sizeof(int), cudaMemcpyDeviceToHost));
+  ND_CUDA(cudaMemcpy(ie, f->d_inerr, sizeof(ie), cudaMemcpyDeviceToHost));
   if (n_singular) *n_singular = h;
   if (to) return fail(ND_ERR_TIMEOUT, "nd_fact_status: a tensor-core product gave up waiting; results are invalid");
+  if (ie[0])
+    return fail(ND_ERR_NOT_SYMMETRIC,
+                "nd_fact_status: the device H values or Sigma^r blocks of the last nd_factor are not (complex) "
+                "symmetric or not finite; results are invalid");
+  if (ie[1])
+    return fail(ND_ERR_NOT_SKEW_HERMITIAN,
+                "nd_fact_status: the device Sigma^< / Sigma^> of the last nd_diag_green are not skew-Hermitian or "
+                "not finite; G^< / G^> are invalid");
   if (h > 0) return fail(ND_ERR_SINGULAR, "nd_fact_status: " + std::to_string(h) + " singular pivot(s)");
   return ND_OK;
 }

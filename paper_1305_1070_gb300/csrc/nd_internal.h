@@ -194,6 +194,15 @@ struct ZeroDesc {
   int64_t count;
 };
 
+// Per-cluster geometry used by the S9 certificate to find a stored entry.
+struct CertCluster {
+  int64_t offG, offP, offPg; // [G_II | G_IB] and [P_II | P_IB] fronts of G^< and G^>
+  int32_t sb, n, ld;         // first unknown slot, rows eliminated here, row length n + b
+  int32_t parent, dslot;     // parent (-1: root) and this cluster's virtual rows in the parent's front
+  int32_t first_desc;        // postorder index of the first cluster of the subtree
+  int32_t bs, b;             // sorted boundary slots: cert_bslot[bs .. bs + b)
+};
+
 // A launch of the precomputed schedule.
 enum StepKind : int32_t {
   ST_INVERSE = 0,
@@ -247,6 +256,7 @@ struct TcSplit { int32_t tcd, side, r0, pad; };
 struct nd_plan {
   int32_t n = 0, nnz = 0;
   std::vector<int32_t> rowptr, colind;
+  std::vector<int32_t> csr_T;      // CSR index of the transposed entry (colind[q], row of q)
   int32_t n_contacts = 0;
   std::vector<int32_t> contact_ptr, contact_idx;
   std::vector<ndgf::Cluster> cl;  // postorder
@@ -288,17 +298,18 @@ struct nd_plan {
   // per-cluster tables for the G lookup of AncGatherDesc (variant v = 0, 1)
   std::vector<int32_t> cl_n, cl_A, cl_ldG;
   std::vector<int64_t> cl_offG, cl_offGX[2], cl_offP[2];
-  // residual certificate: for site j, terms [cert_ptr[j], cert_ptr[j+1]) of
-  // sum_k A_jk X_kj, each {cluster, element index in its [X_II | X_IB] front,
-  // coefficient source (CSR index >= 0, or -1 - packed Sigma index), flag 1 when
-  // the stored element is X_jk with k an ancestor site (X^< needs -conj)}
   // per contact: cluster holding its sites, first front row there, offset of
   // its block in the packed Sigma arrays (elements)
   std::vector<int32_t> contact_cluster, contact_row;
   std::vector<int64_t> contact_soff;
   std::vector<ndgf::ZeroDesc> psi_desc;  // Psi regions (growth indicator)
-  std::vector<int32_t> cert_ptr;
-  std::vector<int32_t> cert_terms;  // 4 ints per term
+  // residual certificate: for site j, terms [cert_ptr[j], cert_ptr[j+1]) of
+  // sum_k A_jk X_kj, each with the neighbour site cert_nb and the coefficient
+  // source cert_coef (CSR index >= 0, or -1 - packed Sigma index); where X_kj
+  // is stored is found at run time from cert_slot (static slot of every site),
+  // cert_cl and the sorted boundary slots cert_bslot / cert_bidx
+  std::vector<int32_t> cert_ptr, cert_nb, cert_coef, cert_slot, cert_bslot, cert_bidx;
+  std::vector<ndgf::CertCluster> cert_cl;
   // launch schedules: the fold (S1-S3), the G^r extraction (S4) and the
   // G^< / G^> steps (S5-S8) without (0) or with (1) a phonon self-energy
   std::vector<ndgf::Step> sched_factor, sched_green, sched_lesser[2];

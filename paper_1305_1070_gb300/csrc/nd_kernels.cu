@@ -454,20 +454,11 @@ __global__ void k_loc(const LocDesc* __restrict__ descs, DelayTabs dt) {
   }
 }
 
-__global__ void k_cert_off(double* cert, int n_e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n_e * 4) cert[(i / 4) * 8 + (i % 4)] = -1.0;
-}
-
 void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s) {
   if (count <= 0 || n_e <= 0) return;
   k_loc<<<dim3(count, n_e), 128, 0, s>>>(d, dt);
 }
 
-void launch_cert_off(double* cert, int n_e, cudaStream_t s) {
-  if (n_e <= 0) return;
-  k_cert_off<<<(n_e * 4 + 127) / 128, 128, 0, s>>>(cert, n_e);
-}
 
 // Extend-add of a child's update into its parent's front.  Entries whose row
 // is a boundary site of the parent and whose column is interior to it are
@@ -690,65 +681,136 @@ __global__ void k_convert_aux(const double2* __restrict__ lesser, const double2*
 //   r<_j = sum_k A_jk G<_kj - (Sigma^< G^a)_jj
 // with A = (E + i eta - Sigma_ph) I - H - Sigma_contact.  Every nonzero A_jk
 // pairs with a stored entry of G^(0) (paper Sec. 3.2: the stored entries
-// cover the fill pattern).  Per energy: max |r|, max |G_jj|, max |r<|, max |G<_jj|.
+// cover the fill pattern): when j and k are eliminated by the same cluster,
+// in its [X_II] block; otherwise in the [X_IB] block of the lower of the two
+// clusters, at the boundary column of the other unknown.  With delayed pivots
+// the eliminating cluster and row of every unknown are per energy (locq /
+// locr), and the boundary column is that of the first slot on the unknown's
+// path of delays that lies in a proper ancestor of the lower cluster.
+// Per energy: max |r|, max |G_jj|, max |r<|, max |G<_jj|; entry 5 becomes 1
+// when a stored entry was not found (a planner inconsistency, never expected).
 __device__ __forceinline__ void atomic_max_pos(double* a, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
+struct CertLoc {
+  int q, r;
+};
+
+__device__ __forceinline__ CertLoc cert_loc(const CertArgs& a, const DelayTabs& dt, int64_t eb, int s) {
+  if (dt.locq) return CertLoc{dt.locq[eb + s], dt.locr[eb + s]};
+  return CertLoc{a.unk_q[s], a.unk_r[s]};
+}
+
+// Boundary column, in cluster q, of the unknown that starts in slot s (q is
+// below the cluster that eliminates it); -1 when not found.
+__device__ int cert_bcol(const CertArgs& a, const DelayTabs& dt, int64_t eb, int s, int q) {
+  for (int it = 0; it < 256; ++it) {
+    const int c = a.unk_q[s];
+    if (c > q && a.cl[c].first_desc <= q) {  // s lies in a proper ancestor of q: binary search of q's boundary
+      int lo = a.cl[q].bs, hi = lo + a.cl[q].b;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a.bslot[mid] < s)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      return (lo < a.cl[q].bs + a.cl[q].b && a.bslot[lo] == s) ? a.bidx[lo] : -1;
+    }
+    const int rho = dt.iperm ? dt.iperm[eb + s] : a.unk_r[s];
+    const int n = a.cl[c].n, par = a.cl[c].parent;
+    if (rho < n || par < 0) return -1;  // eliminated at or below q: not an ancestor's unknown
+    s = a.cl[par].sb + a.cl[c].dslot + (rho - n);
+  }
+  return -1;
+}
+
+// Where the entry X_xy of the unknowns in slots ux, uy (coupled, or the same)
+// is stored: the cluster q whose front holds it, the element offset within
+// that cluster's [X_II | X_IB] front, and whether the stored element is X_yx
+// (*transposed).  Returns false when it is not stored.
+__device__ bool cert_entry(const CertArgs& a, const DelayTabs& dt, int64_t eb, int ux, int uy, int* q, int64_t* idx,
+                           bool* transposed) {
+  const CertLoc lx = cert_loc(a, dt, eb, ux), ly = cert_loc(a, dt, eb, uy);
+  if (lx.q == ly.q) {
+    *q = lx.q;
+    *idx = int64_t(lx.r) * a.cl[lx.q].ld + ly.r;
+    *transposed = false;
+    return true;
+  }
+  const bool x_low = lx.q < ly.q;  // the lower cluster (postorder) stores the pair in its I x B block
+  const CertLoc lo = x_low ? lx : ly;
+  const int b = cert_bcol(a, dt, eb, x_low ? uy : ux, lo.q);
+  if (b < 0) return false;
+  *q = lo.q;
+  *idx = int64_t(lo.r) * a.cl[lo.q].ld + a.cl[lo.q].n + b;
+  *transposed = !x_low;
+  return true;
+}
+
 template <typename T>
-__global__ void k_certificate(int n, const int32_t* __restrict__ cptr, const int4* __restrict__ terms,
-                              const int32_t* __restrict__ owner, const int32_t* __restrict__ pos,
-                              const int64_t* __restrict__ offG, const int64_t* __restrict__ offP,
-                              const int32_t* __restrict__ ldG, const cx<T>* arena, int64_t se,
-                              const double* __restrict__ H, const double2* __restrict__ sr,
-                              const double2* __restrict__ sl, int64_t sstride, const double2* __restrict__ ph_r,
-                              const double2* __restrict__ ph_l, const double* __restrict__ energies, double eta,
-                              int lesser, double* cert) {
+__global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int64_t se) {
   const int e = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const double2* ph_r = reinterpret_cast<const double2*>(a.ph_r);
+  const double2* ph_l = reinterpret_cast<const double2*>(a.ph_l);
+  const double2* sr = reinterpret_cast<const double2*>(a.sr);
+  const double2* sl = reinterpret_cast<const double2*>(a.sl);
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  if (j < n) {
+  bool lost = false;
+  if (j < a.n) {
     const cx<T>* base = arena + int64_t(e) * se;
-    const int c = owner[j], r = pos[j];
-    const int64_t dj = int64_t(r) * ldG[c] + r;
-    const double2 gjj = O<T>::to_d2(base[offG[c] + dj]);
+    const int64_t eb = int64_t(e) * dt.n_unk;
+    const int uj = a.slot[j];
+    const CertLoc lj = cert_loc(a, dt, eb, uj);
+    const CertCluster cj = a.cl[lj.q];
+    const int64_t dj = int64_t(lj.r) * cj.ld + lj.r;
+    const double2 gjj = O<T>::to_d2(base[cj.offG + dj]);
     double2 pjj = make_double2(0.0, 0.0);
-    if (lesser) pjj = O<T>::to_d2(base[offP[c] + dj]);
-    double2 d = make_double2(energies[e], eta);
+    if (a.lesser) pjj = O<T>::to_d2(base[cj.offP + dj]);
+    double2 d = make_double2(a.energies[e], a.eta);
     if (ph_r) {
-      const double2 q = ph_r[int64_t(e) * n + j];
+      const double2 q = ph_r[int64_t(e) * a.n + j];
       d.x -= q.x;
       d.y -= q.y;
     }
     double2 rr = make_double2(d.x * gjj.x - d.y * gjj.y - 1.0, d.x * gjj.y + d.y * gjj.x);
     double2 rl = make_double2(d.x * pjj.x - d.y * pjj.y, d.x * pjj.y + d.y * pjj.x);
     double2 rhs = make_double2(0.0, 0.0);
-    if (lesser && ph_l) {  // ph^<_j conj(G_jj)
-      const double2 q = ph_l[int64_t(e) * n + j];
+    if (a.lesser && ph_l) {  // ph^<_j conj(G_jj)
+      const double2 q = ph_l[int64_t(e) * a.n + j];
       rhs.x += q.x * gjj.x + q.y * gjj.y;
       rhs.y += q.y * gjj.x - q.x * gjj.y;
     }
-    for (int t = cptr[j]; t < cptr[j + 1]; ++t) {
-      const int4 tm = terms[t];
-      const double2 g = O<T>::to_d2(base[offG[tm.x] + tm.y]);
-      double2 a;  // -A_jk
-      if (tm.z >= 0) {
-        a = make_double2(H[tm.z], 0.0);
+    for (int t = a.cptr[j]; t < a.cptr[j + 1]; ++t) {
+      const int k = a.nb[t], src = a.coef[t];
+      int q;
+      int64_t idx;
+      bool tr;  // stored element X_jk (tr = false) or X_kj (tr = true)
+      if (!cert_entry(a, dt, eb, uj, a.slot[k], &q, &idx, &tr)) {
+        lost = true;
+        continue;
+      }
+      const double2 g = O<T>::to_d2(base[a.cl[q].offG + idx]);  // G_kj = G_jk (complex symmetric)
+      double2 an;                                                // -A_jk
+      if (src >= 0) {
+        an = make_double2(a.H[src], 0.0);
       } else {
-        a = sr[int64_t(e) * sstride + (-1 - tm.z)];
-        if (lesser && sl) {  // Sigma^<_jk conj(G_jk)
-          const double2 q = sl[int64_t(e) * sstride + (-1 - tm.z)];
-          rhs.x += q.x * g.x + q.y * g.y;
-          rhs.y += q.y * g.x - q.x * g.y;
+        an = sr[int64_t(e) * a.sstride + (-1 - src)];
+        if (a.lesser && sl) {  // Sigma^<_jk conj(G_jk)
+          const double2 q2 = sl[int64_t(e) * a.sstride + (-1 - src)];
+          rhs.x += q2.x * g.x + q2.y * g.y;
+          rhs.y += q2.y * g.x - q2.x * g.y;
         }
       }
-      rr.x -= a.x * g.x - a.y * g.y;
-      rr.y -= a.x * g.y + a.y * g.x;
-      if (lesser) {
-        double2 pv = O<T>::to_d2(base[offP[tm.x] + tm.y]);
-        if (tm.w) pv = make_double2(-pv.x, pv.y);  // G<_kj = -conj(G<_jk)
-        rl.x -= a.x * pv.x - a.y * pv.y;
-        rl.y -= a.x * pv.y + a.y * pv.x;
+      rr.x -= an.x * g.x - an.y * g.y;
+      rr.y -= an.x * g.y + an.y * g.x;
+      if (a.lesser) {
+        double2 pv = O<T>::to_d2(base[a.cl[q].offP + idx]);
+        if (!tr) pv = make_double2(-pv.x, pv.y);  // G<_kj = -conj(G<_jk)
+        rl.x -= an.x * pv.x - an.y * pv.y;
+        rl.y -= an.x * pv.y + an.y * pv.x;
       }
     }
     rl.x -= rhs.x;
@@ -759,6 +821,10 @@ __global__ void k_certificate(int n, const int32_t* __restrict__ cptr, const int
     v[3] = hypot(pjj.x, pjj.y);
   }
   __shared__ double red[4][32];
+  __shared__ int s_lost;
+  if (threadIdx.x == 0) s_lost = 0;
+  __syncthreads();
+  if (lost) s_lost = 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int k = 0; k < 4; ++k) {
     double x = v[k];
@@ -769,8 +835,9 @@ __global__ void k_certificate(int n, const int32_t* __restrict__ cptr, const int
   if (threadIdx.x < 4) {
     double x = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) x = fmax(x, red[threadIdx.x][w]);
-    atomic_max_pos(cert + int64_t(e) * 8 + threadIdx.x, x);
+    atomic_max_pos(a.cert + int64_t(e) * 8 + threadIdx.x, x);
   }
+  if (threadIdx.x == 0 && s_lost) atomic_max_pos(a.cert + int64_t(e) * 8 + 5, 1.0);
 }
 
 // Growth indicator: out[e * 8 + 4] = max over the listed regions of max |x|.
@@ -940,19 +1007,55 @@ void Kern<T>::convert_aux(const Work& w, const double* lesser, const double* gre
                                           sigma_elems, w.n_e);
 }
 
+// Selected entries G^r_xy, G^<_xy, G^>_xy of the pairs (x[p], y[p]) for every
+// energy (out [n_e][count] complex; NaN and a count when not stored).
 template <typename T>
-void Kern<T>::certificate(const Work& w, const CertArgs& a, cudaStream_t s) {
-  if (w.n_e <= 0 || a.n <= 0) return;
-  if (a.n_psi > 0)
-    k_absmax<T><<<dim3(a.n_psi, w.n_e), 256, 0, s>>>(a.psi, (const cx<T>*)w.arena, w.se, a.cert);
-  if (!a.cptr) {  // no residual terms (delayed pivots): entries 0..3 = -1
-    launch_cert_off(a.cert, w.n_e, s);
+__global__ void k_selected(CertArgs a, DelayTabs dt, const cx<T>* arena, int64_t se, const int32_t* __restrict__ px,
+                           const int32_t* __restrict__ py, int count, int lesser, double2* Gr, double2* Gl,
+                           double2* Gg, int* n_missing) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int e = blockIdx.y;
+  if (p >= count) return;
+  const cx<T>* base = arena + int64_t(e) * se;
+  const int64_t eb = int64_t(e) * dt.n_unk, o = int64_t(e) * count + p;
+  const int x = px[p], y = py[p];
+  int q;
+  int64_t idx;
+  bool tr;
+  if (x < 0 || y < 0 || x >= a.n || y >= a.n || !cert_entry(a, dt, eb, a.slot[x], a.slot[y], &q, &idx, &tr)) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    if (Gr) Gr[o] = make_double2(nan, nan);
+    if (Gl) Gl[o] = make_double2(nan, nan);
+    if (Gg) Gg[o] = make_double2(nan, nan);
+    atomicAdd(n_missing, 1);
     return;
   }
-  k_certificate<T><<<dim3((a.n + 255) / 256, w.n_e), 256, 0, s>>>(
-      a.n, a.cptr, (const int4*)a.terms, a.owner, a.pos, a.offG, a.offP, a.ldG, (const cx<T>*)w.arena, w.se, a.H,
-      (const double2*)a.sr, (const double2*)a.sl, a.sstride, (const double2*)a.ph_r, (const double2*)a.ph_l,
-      a.energies, a.eta, a.lesser, a.cert);
+  if (Gr) Gr[o] = O<T>::to_d2(base[a.cl[q].offG + idx]);
+  if (lesser) {  // X_xy = -conj(X_yx) for the skew-Hermitian G^<, G^>
+    double2 l = O<T>::to_d2(base[a.cl[q].offP + idx]), g = O<T>::to_d2(base[a.cl[q].offPg + idx]);
+    if (tr) {
+      l = make_double2(-l.x, l.y);
+      g = make_double2(-g.x, g.y);
+    }
+    if (Gl) Gl[o] = l;
+    if (Gg) Gg[o] = g;
+  }
+}
+
+template <typename T>
+void Kern<T>::selected(const Work& w, const CertArgs& a, const DelayTabs& dt, const int32_t* x, const int32_t* y,
+                       int count, int lesser, double* Gr, double* Gl, double* Gg, int* n_missing, cudaStream_t s) {
+  if (w.n_e <= 0 || count <= 0) return;
+  k_selected<T><<<dim3((count + 255) / 256, w.n_e), 256, 0, s>>>(
+      a, dt, (const cx<T>*)w.arena, w.se, x, y, count, lesser, (double2*)Gr, (double2*)Gl, (double2*)Gg, n_missing);
+}
+
+template <typename T>
+void Kern<T>::certificate(const Work& w, const CertArgs& a, const DelayTabs& dt, cudaStream_t s) {
+  if (w.n_e <= 0) return;
+  if (a.n_psi > 0)
+    k_absmax<T><<<dim3(a.n_psi, w.n_e), 256, 0, s>>>(a.psi, (const cx<T>*)w.arena, w.se, a.cert);
+  k_certificate<T><<<dim3((a.n + 255) / 256, w.n_e), 256, 0, s>>>(a, dt, (const cx<T>*)w.arena, w.se);
 }
 
 // S10 terminal current spectrum (Meir-Wingreen) of one contact:
@@ -1430,7 +1533,9 @@ __global__ void k_phonon_scba(int64_t tot, double D, double mix, const double2* 
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const double2 v = src[q][i];
-      const double2 nw = make_double2(D * v.x, D * v.y);
+      // G^< and G^> are skew-Hermitian (paper Sec. 3.1), so their diagonals are
+      // purely imaginary: the rounding residue of Re is not carried into Sigma
+      const double2 nw = make_double2(q == 0 ? D * v.x : 0.0, D * v.y);
       const double2 od = dst[q][i];
       const double dx = nw.x - od.x, dy = nw.y - od.y;
       dmax = fmax(dmax, hypot(dx, dy));

@@ -36,8 +36,10 @@ struct AncTables {
 
 struct CertArgs {
   int n;
-  const int32_t *cptr, *terms, *owner, *pos, *ldG;
-  const int64_t *offG, *offP;
+  const int32_t *cptr, *nb, *coef;   // terms of site j: [cptr[j], cptr[j+1]), neighbour site, coefficient source
+  const int32_t *slot, *bslot, *bidx; // static slot of every site; sorted boundary slots per cluster
+  const int32_t *unk_q, *unk_r;      // static cluster and front row of every slot
+  const CertCluster* cl;
   const double *H, *sr, *sl, *ph_r, *ph_l, *energies;
   int64_t sstride;
   double eta;
@@ -81,7 +83,9 @@ struct Kern {
                            const DelayTabs& dt, cudaStream_t s);
   static void colgather(const Work& w, const ColGatherDesc* d, int count, const int32_t* cmaps, const AncTables& t,
                         const DelayTabs& dt, cudaStream_t s);
-  static void certificate(const Work& w, const CertArgs& a, cudaStream_t s);
+  static void certificate(const Work& w, const CertArgs& a, const DelayTabs& dt, cudaStream_t s);
+  static void selected(const Work& w, const CertArgs& a, const DelayTabs& dt, const int32_t* x, const int32_t* y,
+                       int count, int lesser, double* Gr, double* Gl, double* Gg, int* n_missing, cudaStream_t s);
   static void diag_out(const Work& w, const DiagDesc* d, int count, const int32_t* sites, double* out, int n,
                        const DelayTabs& dt, cudaStream_t s);
   static void convert_aux(const Work& w, const double* lesser, const double* greater, int64_t sigma_elems,
@@ -112,8 +116,6 @@ void launch_gemm_tc(const Work& w, const GemmDesc* d, const TcDesc* tcd, const T
 
 // Final positions of the unknowns after the delayed pivots (one tree level).
 void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s);
-// Certificate entries 0..3 set to -1 (no residual terms with delayed pivots).
-void launch_cert_off(double* cert, int n_e, cudaStream_t s);
 
 // Per-energy complex128 workspace of launch_lead_decimation, in elements.
 size_t lead_decimation_work_elems(int m, int m_c);

@@ -22,9 +22,10 @@ namespace ndgf {
 namespace {
 
 // Working space: 2^18 complex128 elements (4 MiB), resident on every device
-// that loads the library until the process exits.
+// that loads the library until the process exits.  batch * n * n <= 2^18, so
+// the largest matrix is 512 x 512 (batch 1).
 constexpr int64_t NOALLOC_ELEMS = int64_t(1) << 18;
-constexpr int NOALLOC_MAX_N = 1024;
+constexpr int NOALLOC_MAX_N = 512;
 __device__ __align__(256) double2 g_noalloc_work[NOALLOC_ELEMS];
 
 // Device address of g_noalloc_work, looked up once per device (host code only
@@ -33,6 +34,15 @@ constexpr int MAX_DEVICES = 64;
 double2* g_work_ptr[MAX_DEVICES];
 cudaError_t g_work_err[MAX_DEVICES];
 std::once_flag g_work_once[MAX_DEVICES];
+
+bool on_device(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 
 __global__ void k_invert_c64_noalloc(float2* A, int n, double2* work, int* n_singular) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -55,11 +65,13 @@ using namespace ndgf;
 extern "C" nd_status nd_invert_c64_noalloc(float* A, int32_t n, int32_t batch, int32_t* n_singular, void* stream) {
   if (!A || !n_singular) return fail(ND_ERR_INVALID_ARG, "nd_invert_c64_noalloc: NULL argument");
   if (n < 1 || n > NOALLOC_MAX_N || batch < 1)
-    return fail(ND_ERR_INVALID_ARG, "nd_invert_c64_noalloc: need 1 <= n <= 1024 and batch >= 1");
+    return fail(ND_ERR_INVALID_ARG, "nd_invert_c64_noalloc: need 1 <= n <= 512 and batch >= 1");
   if (int64_t(batch) * n * n > NOALLOC_ELEMS)
     return fail(ND_ERR_INVALID_ARG, "nd_invert_c64_noalloc: batch * n * n = " +
                                         std::to_string(int64_t(batch) * n * n) + " exceeds the fixed working space of " +
                                         std::to_string(NOALLOC_ELEMS) + " complex128 elements");
+  if (!on_device(A) || !on_device(n_singular))
+    return fail(ND_ERR_INVALID_ARG, "nd_invert_c64_noalloc: A and n_singular must be device arrays");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(ND_ERR_CUDA, std::string("nd_invert_c64_noalloc: ") + cudaGetErrorString(e));

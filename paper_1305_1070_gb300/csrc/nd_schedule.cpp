@@ -124,6 +124,22 @@ void split_by_size(nd_plan* p, std::vector<Step>& sched) {
 void build_schedules(nd_plan* p) {
   auto& cl = p->cl;
   const int nc = int(cl.size());
+  // transpose index of every CSR entry (the pattern is structurally symmetric)
+  {
+    std::vector<std::pair<int32_t, int32_t>> byc(p->nnz);  // (column, CSR index), sorted per row
+    for (int r = 0; r < p->n; ++r) {
+      for (int q = p->rowptr[r]; q < p->rowptr[r + 1]; ++q) byc[q] = {p->colind[q], q};
+      std::sort(byc.begin() + p->rowptr[r], byc.begin() + p->rowptr[r + 1]);
+    }
+    p->csr_T.assign(p->nnz, -1);
+    for (int r = 0; r < p->n; ++r)
+      for (int q = p->rowptr[r]; q < p->rowptr[r + 1]; ++q) {
+        const int c = p->colind[q];
+        auto it = std::lower_bound(byc.begin() + p->rowptr[c], byc.begin() + p->rowptr[c + 1],
+                                   std::make_pair(int32_t(r), int32_t(-1)));
+        p->csr_T[q] = it->second;  // present: nd_analyze checked the pattern's symmetry
+      }
+  }
   std::vector<int32_t> site_begin(nc), map_begin(nc);
   p->root_scratch_elems = 0;
   p->unk_q.clear();
@@ -349,27 +365,39 @@ void build_schedules(nd_plan* p) {
   // ---- S9 certificate term lists --------------------------------------------
   for (int i = 0; i < nc; ++i)
     if (cl[i].b) p->psi_desc.push_back(ZeroDesc{cl[i].off_Psi, int64_t(cl[i].n) * cl[i].b});
-  if (p->n_virtual == 0) {  // with delayed pivots the positions are per energy: no residual terms
-    std::unordered_map<int64_t, int32_t> posB;  // (cluster, site) -> index in B
-    for (int i = 0; i < nc; ++i)
-      for (int k = 0; k < cl[i].b; ++k) posB[int64_t(i) * p->n + cl[i].B[k]] = k;
-    // where X_jk (or X_kj) is stored for a coupled pair j, k
-    auto locate = [&](int j, int k, int32_t* cl_out, int32_t* idx_out, int32_t* anc_out) {
-      const int cj = p->owner[j], ck = p->owner[k];
-      if (cj == ck) {  // X_kj in the I x I block
-        *cl_out = cj;
-        *idx_out = p->pos[k] * (cl[cj].n + cl[cj].b) + p->pos[j];
-        *anc_out = 0;
-      } else if (ck > cj) {  // k is an ancestor site of j: X_jk in j's I x B block
-        *cl_out = cj;
-        *idx_out = p->pos[j] * (cl[cj].n + cl[cj].b) + cl[cj].n + posB.at(int64_t(cj) * p->n + k);
-        *anc_out = 1;
-      } else {  // j is an ancestor site of k: X_kj in k's I x B block
-        *cl_out = ck;
-        *idx_out = p->pos[k] * (cl[ck].n + cl[ck].b) + cl[ck].n + posB.at(int64_t(ck) * p->n + j);
-        *anc_out = 0;
-      }
-    };
+  // Where each entry X_kj of a coupled pair is stored is decided at run time
+  // (the rows a cluster eliminates are per energy with delayed pivots): the
+  // static part is the slot of every site, each cluster's front geometry and
+  // its boundary slots sorted for a binary search.
+  p->cert_cl.clear();
+  p->cert_bslot.clear();
+  p->cert_bidx.clear();
+  for (int i = 0; i < nc; ++i) {
+    const Cluster& c = cl[i];
+    CertCluster cc{};
+    cc.offG = c.off_G;
+    cc.offP = c.off_P[0];
+    cc.offPg = c.off_P[1];
+    cc.sb = site_begin[i];
+    cc.n = c.n;
+    cc.ld = c.n + c.b;
+    cc.parent = c.parent;
+    cc.dslot = c.parent >= 0 ? c.dslot : -1;
+    cc.first_desc = c.first_desc;
+    cc.bs = int32_t(p->cert_bslot.size());
+    cc.b = c.b;
+    std::vector<std::pair<int32_t, int32_t>> sl(c.b);
+    for (int k = 0; k < c.b; ++k) sl[k] = {p->site_ids[bsite_begin[i] + k], k};
+    std::sort(sl.begin(), sl.end());
+    for (auto& x : sl) {
+      p->cert_bslot.push_back(x.first);
+      p->cert_bidx.push_back(x.second);
+    }
+    p->cert_cl.push_back(cc);
+  }
+  p->cert_slot.assign(p->n, 0);
+  for (int j = 0; j < p->n; ++j) p->cert_slot[j] = site_begin[p->owner[j]] + p->pos[j];
+  {
     std::vector<int32_t> contact_of(p->n, -1), cpos(p->n, -1);
     for (int c = 0; c < p->n_contacts; ++c)
       for (int q = p->contact_ptr[c]; q < p->contact_ptr[c + 1]; ++q) {
@@ -377,23 +405,22 @@ void build_schedules(nd_plan* p) {
         cpos[p->contact_idx[q]] = q - p->contact_ptr[c];
       }
     p->cert_ptr.assign(1, 0);
+    p->cert_nb.clear();
+    p->cert_coef.clear();
     for (int j = 0; j < p->n; ++j) {
       for (int q = p->rowptr[j]; q < p->rowptr[j + 1]; ++q) {
-        int32_t c, idx, anc;
-        locate(j, p->colind[q], &c, &idx, &anc);
-        p->cert_terms.insert(p->cert_terms.end(), {c, idx, q, anc});
+        p->cert_nb.push_back(p->colind[q]);
+        p->cert_coef.push_back(q);
       }
       const int ct = contact_of[j];
       if (ct >= 0) {
         const int m = p->contact_ptr[ct + 1] - p->contact_ptr[ct];
         for (int q = p->contact_ptr[ct]; q < p->contact_ptr[ct + 1]; ++q) {
-          int32_t c, idx, anc;
-          locate(j, p->contact_idx[q], &c, &idx, &anc);
-          const int32_t sidx = soff[ct] + cpos[j] * m + (q - p->contact_ptr[ct]);
-          p->cert_terms.insert(p->cert_terms.end(), {c, idx, -1 - sidx, anc});
+          p->cert_nb.push_back(p->contact_idx[q]);
+          p->cert_coef.push_back(-1 - int32_t(soff[ct] + cpos[j] * m + (q - p->contact_ptr[ct])));
         }
       }
-      p->cert_ptr.push_back(int32_t(p->cert_terms.size() / 4));
+      p->cert_ptr.push_back(int32_t(p->cert_nb.size()));
     }
   }
   for (int v = 0; v < 2; ++v) {

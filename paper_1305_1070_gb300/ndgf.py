@@ -32,7 +32,8 @@ EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const", "nd_phonon_scba",
-           "nd_last_error", "nd_version"]
+           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_last_error",
+           "nd_version"]
 
 
 class NDError(RuntimeError):
@@ -91,7 +92,9 @@ def lib():
             "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
             "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
             "nd_certificate": ([_P, _P, _P], _I32),
+            "nd_selected_entries": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P], _I32),
             "nd_density": ([_P, _P, _I32, _I32, _D, _I32, _P, _P], _I32),
+            "nd_fact_density": ([_P, _P, _D, _I32, _P, _P], _I32),
             "nd_invert_c64_noalloc": ([_P, _I32, _I32, _P, _P], _I32),
             "nd_profile": ([_P, _I32, _P, _I32, ctypes.POINTER(_I32)], _I32),
             "nd_lead_create": ([_I32, _I32, _P, _P, _P, ctypes.POINTER(_P)], _I32),
@@ -104,6 +107,8 @@ def lib():
             "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
             "nd_phonon_const": ([_I32, _I32, _D, _D, _D, _P, _P, _P, _P, _P], _I32),
             "nd_phonon_scba": ([_I32, _I32, _D, _D, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
+            "nd_check_factor_inputs": ([_P, _P, _P, _I32], _I32),
+            "nd_check_lesser_inputs": ([_P, _P, _P, _P, _P, _I32], _I32),
             "nd_last_error": ([], ctypes.c_char_p),
             "nd_version": ([], ctypes.c_char_p),
         }
@@ -248,15 +253,43 @@ def nd_diag_green(fact: Fact, sigma_lesser, sigma_greater, ph_lesser, ph_greater
                                _stream(stream)), "nd_diag_green")
 
 
+def nd_check_factor_inputs(plan: Plan, H_values, sigma_r, n_e: int):
+    """Host-side symmetry check of nd_factor's inputs (host arrays)."""
+    keep = []
+    _check(lib().nd_check_factor_inputs(plan.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), n_e),
+           "nd_check_factor_inputs")
+
+
+def nd_check_lesser_inputs(plan: Plan, sigma_lesser, sigma_greater, ph_lesser, ph_greater, n_e: int):
+    """Host-side skew-Hermiticity check of nd_diag_green's inputs (host arrays)."""
+    keep = []
+    _check(lib().nd_check_lesser_inputs(plan.ptr, _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep),
+                                        _ptr(ph_lesser, keep), _ptr(ph_greater, keep), n_e), "nd_check_lesser_inputs")
+
+
 def nd_certificate(fact: Fact, cert, stream=None):
     keep = []
     _check(lib().nd_certificate(fact.ptr, _ptr(cert, keep), _stream(stream)), "nd_certificate")
+
+
+def nd_selected_entries(fact: Fact, x, y, count: int, Gr, Gl, Gg, n_missing, stream=None):
+    """Selected entries G^r_xy, G^<_xy, G^>_xy of the last solve (device arrays)."""
+    keep = []
+    _check(lib().nd_selected_entries(fact.ptr, _ptr(x, keep), _ptr(y, keep), count, _ptr(Gr, keep), _ptr(Gl, keep),
+                                     _ptr(Gg, keep), _ptr(n_missing, keep), _stream(stream)), "nd_selected_entries")
 
 
 def nd_density(Gl, weights, n_e, n, scale, accumulate, out, stream=None):
     keep = []
     _check(lib().nd_density(_ptr(Gl, keep), _ptr(weights, keep), n_e, n, scale, int(accumulate), _ptr(out, keep),
                             _stream(stream)), "nd_density")
+
+
+def nd_fact_density(fact: Fact, weights, scale, accumulate, out, stream=None):
+    """Density epilogue on the handle's last diag G^< (host or device weights / out)."""
+    keep = []
+    _check(lib().nd_fact_density(fact.ptr, _ptr(weights, keep), scale, int(accumulate), _ptr(out, keep),
+                                 _stream(stream)), "nd_fact_density")
 
 
 def nd_profile(fact: Fact, enable: bool) -> list:

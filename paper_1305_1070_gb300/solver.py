@@ -13,6 +13,16 @@ import torch
 from . import ndgf
 
 
+def certificate_flags(cert, resid_max: float = 1e-8, growth_max: float = 10.0):
+    """Energies whose S9 certificate ([n_e, 8], nd_certificate) fails: FP64
+    residual max_j |(A G^r)_jj - 1| or max_j |(A G^< - Sigma^< G^a)_jj| relative
+    to max_j |G^<_jj| above resid_max, fold growth max|Psi| above growth_max, a
+    stored entry not found, or a non-finite value."""
+    scale = torch.clamp(cert[:, 3], min=1e-300)
+    bad = (cert[:, 0] > resid_max) | (cert[:, 2] > resid_max * scale) | (cert[:, 4] > growth_max) | (cert[:, 5] > 0)
+    return bad | ~torch.isfinite(cert[:, :5]).all(dim=1)
+
+
 class Solver:
     def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
                  leaf_size: int = 64, split_permille: int = 0, delay: int = 0, tile: str = "auto",
@@ -74,6 +84,12 @@ class Solver:
             E.copy_(energies)
         else:
             E.copy_(torch.as_tensor(np.asarray(energies, dtype=np.float64)))
+        self._self_energies(n_e)
+        return self._solve(n_e, lesser)
+
+    def _self_energies(self, n_e: int):
+        """Contact, lesser/greater and phonon self-energies of self.E[:n_e] (S1a)."""
+        E = self.E[:n_e]
         tr = self.tr
         for c, lead in enumerate(self.leads):
             ndgf.nd_lead_sigma(lead, E, n_e, tr.eta, self.sig_r, self.sigma_elems, int(self.off[c]))
@@ -84,7 +100,22 @@ class Solver:
         if self.ph:
             mu_ph = tr.mu_ph if tr.mu_ph is not None else 0.5 * (tr.mu[0] + tr.mu[1])
             ndgf.nd_phonon_const(self.n, n_e, tr.gamma_ph, mu_ph, tr.kT, E, self.ph_r, self.ph_l, self.ph_g)
-        return self._solve(n_e, lesser)
+
+    def step_host(self, E_host, Gr_host, Gl_host, Gg_host, H_host=None):
+        """step() through the library's host-buffer path: the energies (and H,
+        when given) are host arrays that nd_factor stages to the device, and
+        nd_diag_green writes the three diagonals ([n_e, n] complex128) straight
+        into the host arrays Gr_host, Gl_host, Gg_host (pinned memory keeps the
+        copies asynchronous).  The lead self-energies are computed on the device
+        from a device copy of the energies."""
+        n_e = len(E_host)
+        if n_e > self.max_ne:
+            raise ValueError("more energies than the workspace holds")
+        self.E[:n_e].copy_(torch.as_tensor(E_host), non_blocking=True)
+        self._self_energies(n_e)
+        ndgf.nd_factor(self.fact, self.H if H_host is None else H_host, self.sig_r if self.leads else None, self.ph_r,
+                       E_host, n_e, self.tr.eta)
+        ndgf.nd_diag_green(self.fact, self.sig_l, self.sig_g, self.ph_l, self.ph_g, Gr_host, Gl_host, Gg_host)
 
     def _solve(self, n_e: int, lesser: bool = True):
         """Fold and diagonals for the energies, contact and phonon self-energies in place."""
@@ -127,6 +158,27 @@ class Solver:
         cert = torch.zeros(n_e, 8, dtype=torch.float64, device=self.device)
         ndgf.nd_certificate(self.fact, cert)
         return cert
+
+    def step_certified(self, energies, fallback: "Solver", *, resid_max: float = 1e-8, growth_max: float = 10.0):
+        """step() followed by the S9 certificate: energies whose FP64 residual
+        max_j |(A G^r)_jj - 1| or max_j |(A G^< - Sigma^< G^a)_jj| / max_j |G^<_jj|
+        exceeds resid_max, or whose fold growth max|Psi| exceeds growth_max, are
+        recomputed by `fallback` (a complex128 Solver of the same device) and
+        their rows overwritten.  Returns (Gr, Gl, Gg, cert, redone) with cert the
+        [n_e, 8] certificate of this solver's pass and redone the indices of the
+        recomputed energies (a device tensor)."""
+        n_e = len(energies)
+        E = energies if isinstance(energies, torch.Tensor) else torch.as_tensor(
+            np.asarray(energies, dtype=np.float64), device=self.device)
+        Gr, Gl, Gg = self.step(E)
+        cert = self.certificate(n_e)
+        idx = torch.nonzero(certificate_flags(cert, resid_max, growth_max)).flatten()
+        k = int(idx.numel())
+        for c0 in range(0, k, fallback.max_ne):
+            sel = idx[c0:c0 + fallback.max_ne]
+            r, l, g = fallback.step(E[sel])
+            Gr[sel], Gl[sel], Gg[sel] = r, l, g
+        return Gr, Gl, Gg, cert, idx
 
     def singular_pivots(self) -> int:
         return ndgf.nd_fact_status(self.fact)

@@ -1,0 +1,96 @@
+"""Parity at the benchmark's own configuration: the 512 x 128 superlattice,
+256 energies in two calls of 128, leaf 16, 2 delayed pivots per cluster and the
+default kernel routing (direct, tiled and tensor-core GEMM launches chosen per
+launch), for the FP32-pair path and the complex128 path.
+
+- diag G^r and G^< against the oracle's block RGF (paper Eq. (1)-(2)) at 7
+  energies, among them the indices 97, 205 and 255 where the paper's plain
+  elimination fails worst, element by element over all 65,536 sites;
+- the complex128 path within 1e-10 at every sampled energy;
+- the FP32-pair path within its per-energy bound: 2^10 times the complex128
+  path's error at the same energy (the FP32-pair accumulators carry about
+  2^-44 against the 2^-53 of FP64, a factor 2^9, doubled for the different
+  summation order of its product kernels), plus 2^-34 for the FP32-pair
+  rounding of a well-conditioned energy (2^-44 times the 2^10 growth of the
+  row sums |A| |G| over the 14 tree levels);
+- the FP64 certificate residual of every energy of both paths below 1e-8;
+- the energy-integrated density of the two paths within the metric's 1e-6.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import observables, rgf  # noqa: E402
+from paper_1305_1070_gb300 import build, ndgf, workloads  # noqa: E402
+from paper_1305_1070_gb300.solver import Solver  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+PICK = [0, 51, 97, 153, 204, 205, 255]
+CHUNK, LEAF, DELAY = 128, 16, 2
+TOL64 = 1e-10
+X2_FACTOR, X2_FLOOR = 2.0 ** 10, 2.0 ** -34
+RESID_MAX = 1e-8
+
+
+@pytest.fixture(scope="module")
+def runs():
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    dev, tr = workloads.workload("superlattice_512x128")
+    E = torch.as_tensor(tr.energies, device="cuda")
+    w = torch.as_tensor(observables.trapezoid_weights(tr.energies), device="cuda")
+    out = {}
+    for name, prec in (("fp64", ndgf.ND_PREC_FP64), ("fp32x2", ndgf.ND_PREC_FP32X2)):
+        s = Solver(dev, tr, precision=prec, max_ne=CHUNK, delay=DELAY, leaf_size=LEAF)
+        Gr = torch.zeros(tr.n_e, dev.n, dtype=torch.complex128, device="cuda")
+        Gl = torch.zeros_like(Gr)
+        cert = torch.zeros(tr.n_e, 8, dtype=torch.float64, device="cuda")
+        for c0 in range(0, tr.n_e, CHUNK):
+            r, l, _ = s.step(E[c0:c0 + CHUNK])
+            Gr[c0:c0 + CHUNK], Gl[c0:c0 + CHUNK] = r, l
+            cert[c0:c0 + CHUNK] = s.certificate(CHUNK)
+        dens = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
+        ndgf.nd_density(Gl, w, tr.n_e, dev.n, 2.0 / (2.0 * np.pi), 0, dens)
+        torch.cuda.synchronize()
+        assert s.singular_pivots() == 0
+        out[name] = {"Gr": Gr[PICK].cpu().numpy(), "Gl": Gl[PICK].cpu().numpy(), "cert": cert.cpu().numpy(),
+                     "dens": dens.cpu().numpy()}
+        del s
+        torch.cuda.empty_cache()
+    out["ref"] = rgf.green_diag(dev, tr, energies=tr.energies[PICK])
+    return out
+
+
+def _errs(got, ref):
+    return np.array([max(observables.rel_err(got[k][i], ref[k][i]) for k in ("Gr", "Gl")) for i in range(len(PICK))])
+
+
+def test_bench_config_fp64(runs):
+    e64 = _errs(runs["fp64"], runs["ref"])
+    for i, e in enumerate(PICK):
+        print(f"  complex128 E index {e}: rel err {e64[i]:.3e}")
+    assert (e64 <= TOL64).all(), e64
+
+
+def test_bench_config_fp32x2(runs):
+    e64 = _errs(runs["fp64"], runs["ref"])
+    ex2 = _errs(runs["fp32x2"], runs["ref"])
+    bound = X2_FACTOR * e64 + X2_FLOOR
+    for i, e in enumerate(PICK):
+        print(f"  FP32 pairs E index {e}: rel err {ex2[i]:.3e} (bound {bound[i]:.3e}, complex128 {e64[i]:.3e})")
+    assert (ex2 <= bound).all(), (ex2, bound)
+
+
+def test_bench_config_certificate_and_density(runs):
+    for name in ("fp64", "fp32x2"):
+        c = runs[name]["cert"]
+        print(f"  {name}: max residual {c[:, 0].max():.3e}, lesser {(c[:, 2] / c[:, 3]).max():.3e}, "
+              f"growth {c[:, 4].max():.3g}")
+        assert (c[:, 5] == 0).all()
+        assert (c[:, 0] <= RESID_MAX).all(), c[:, 0].max()
+        assert (c[:, 2] <= RESID_MAX * c[:, 3]).all()
+    d = observables.rel_err(runs["fp32x2"]["dens"], runs["fp64"]["dens"])
+    print(f"  density FP32 pairs vs complex128: {d:.3e}")
+    assert d <= 1e-6

@@ -1,0 +1,100 @@
+"""Input checks of the boundary, on the host (no GPU): nd_factor's H values and
+contact blocks Sigma^r must be (complex) symmetric, because the fold is an
+LDL^T elimination of A = A^T (paper Sec. 3.1); nd_diag_green's Sigma^< and
+Sigma^> must be skew-Hermitian (Sec. 3.1, Eq. (5)-(6)).  The same routines run
+inside nd_factor / nd_diag_green on host arrays, and as kernels on device
+arrays (tests/test_gpu_checks.py).  One test per error code: a valid input
+passes, and each kind of violation is rejected with its code."""
+import numpy as np
+import pytest
+
+from oracle import problem
+from paper_1305_1070_gb300 import build, ndgf, workloads
+
+NOT_SYMMETRIC, NOT_SKEW = 2, 4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _setup(n_e=3):
+    dev = workloads.superlattice(12, 5, disorder=0.03, seed=7)
+    tr = workloads.Transport(energies=np.linspace(0.05, 0.4, n_e))
+    cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])])
+    plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, np.concatenate(dev.contacts), dev.coords, 16)
+    terms = [problem.energy_terms(dev, tr, float(E)) for E in tr.energies]
+    pack = lambda key: np.stack([np.concatenate([s.ravel() for s in getattr(t, key)]) for t in terms])
+    return dev, plan, pack("sigma_r"), pack("sigma_lesser"), pack("sigma_greater")
+
+
+def _status(fn, *args):
+    try:
+        fn(*args)
+        return 0
+    except ndgf.NDError as e:
+        return e.status
+
+
+def test_valid_inputs_pass():
+    dev, plan, sr, sl, sg = _setup()
+    n_e = sr.shape[0]
+    assert _status(ndgf.nd_check_factor_inputs, plan, dev.values, sr, n_e) == 0
+    ph_l = np.full((n_e, dev.n), 0.01j)
+    assert _status(ndgf.nd_check_lesser_inputs, plan, sl, sg, ph_l, -ph_l, n_e) == 0
+    assert _status(ndgf.nd_check_lesser_inputs, plan, None, None, None, None, n_e) == 0
+
+
+def test_not_symmetric():
+    dev, plan, sr, _, _ = _setup()
+    n_e = sr.shape[0]
+    # an off-diagonal H value that differs from its transposed entry
+    H = dev.values.copy()
+    r = 3
+    q = next(q for q in range(dev.rowptr[r], dev.rowptr[r + 1]) if dev.colind[q] != r)
+    H[q] *= 1.0 + 1e-6
+    assert _status(ndgf.nd_check_factor_inputs, plan, H, sr, n_e) == NOT_SYMMETRIC
+    # a non-finite H value
+    H = dev.values.copy()
+    H[q] = np.nan
+    assert _status(ndgf.nd_check_factor_inputs, plan, H, sr, n_e) == NOT_SYMMETRIC
+    # a contact block that is Hermitian-like instead of complex symmetric (one entry pair changed)
+    m = len(dev.contacts[1])
+    m0 = len(dev.contacts[0])
+    bad = sr.copy()
+    bad[2, 0 * m0 + 1] = np.conj(bad[2, 1 * m0 + 0]) + 1e-3  # first contact block, entry (0, 1)
+    assert _status(ndgf.nd_check_factor_inputs, plan, dev.values, bad, n_e) == NOT_SYMMETRIC
+    # a change at the rounding level passes (relative tolerance 1e-8 of the block's largest entry)
+    ok = sr.copy()
+    ok[1, m0 * m0 + 1] *= 1.0 + 1e-13
+    assert m == m0 and _status(ndgf.nd_check_factor_inputs, plan, dev.values, ok, n_e) == 0
+
+
+def test_not_skew_hermitian():
+    dev, plan, sr, sl, sg = _setup()
+    n_e = sr.shape[0]
+    gamma = 1j * (sr - 0.0)  # not skew-Hermitian in general: i Sigma^r is neither
+    assert _status(ndgf.nd_check_lesser_inputs, plan, gamma, sg, None, None, n_e) == NOT_SKEW
+    # Gamma itself (Hermitian) passed as Sigma^> instead of -i (1 - f) Gamma
+    m0 = len(dev.contacts[0])
+    herm = sg / (-1j)
+    assert _status(ndgf.nd_check_lesser_inputs, plan, sl, herm, None, None, n_e) == NOT_SKEW
+    # one entry pair broken
+    bad = sl.copy()
+    bad[0, 1] += 1e-3 * np.abs(sl[0, :m0 * m0]).max()
+    assert _status(ndgf.nd_check_lesser_inputs, plan, bad, sg, None, None, n_e) == NOT_SKEW
+    # a phonon diagonal with a real part
+    ph = np.full((n_e, dev.n), 0.01j)
+    ph[1, 5] += 1e-4
+    assert _status(ndgf.nd_check_lesser_inputs, plan, sl, sg, ph, -ph.conj(), n_e) == NOT_SKEW
+    ph = np.full((n_e, dev.n), 0.01j)
+    ph[2, 0] = np.nan
+    assert _status(ndgf.nd_check_lesser_inputs, plan, None, None, None, ph, n_e) == NOT_SKEW
+
+
+def test_bad_arguments():
+    dev, plan, sr, _, _ = _setup()
+    assert _status(ndgf.nd_check_factor_inputs, plan, None, sr, 3) == 1
+    assert _status(ndgf.nd_check_factor_inputs, plan, dev.values, None, 3) == 1  # contacts need Sigma^r
+    assert _status(ndgf.nd_check_lesser_inputs, plan, None, None, None, None, -1) == 1

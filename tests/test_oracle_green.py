@@ -143,9 +143,30 @@ def test_sampled_equals_dense():
         assert observables.rel_err(s[k], a[k][0][sites]) < 1e-10
 
 
-def test_density_integration_weights():
-    E = np.linspace(0.0, 0.5, 11)
-    w = observables.trapezoid_weights(E)
-    assert w.sum() == pytest.approx(0.5)
-    gl = np.tile(1j * np.ones(3), (11, 1))
-    assert np.allclose(observables.density(gl, E), 2 * 0.5 / (2 * np.pi))
+def test_density_uniform_chain_closed_form():
+    """Pin of observables.density (paper Sec. 1: the density is the energy
+    integral of Im G^<_jj) against a closed form that shares no step with it.
+    On the uniform chain (on-site 0, hopping -t, uniform leads: the infinite
+    chain) G^<_jj(E) = i (f_L + f_R) / (2 t sin k) with E = -2t cos k, so with
+    spin 2, n_j = (1/pi) int dE (f_L + f_R) / (2 t sin k) = (1/pi) int dk (f_L + f_R)
+    over the k range of the grid.  The oracle integrates the dense definition's
+    G^< by the trapezoid rule on an energy grid; the closed form is integrated
+    in k by adaptive quadrature.  A wrong spin factor (x2), a real part taken
+    for the imaginary one (~0), a lead occupation lost (f_L only) or wrong
+    trapezoid weights are each off by far more than the tolerance."""
+    from scipy.integrate import quad
+    t, N = 1.0, 6
+    mu_L, mu_R, kT = 0.3, -0.4, 0.05
+    dev = workloads.chain(N, t=t)
+    k = np.linspace(0.05, np.pi - 0.05, 3001)
+    E = -2.0 * t * np.cos(k)
+    tr = _tr(E, eta=1e-9, mu=(mu_L, mu_R), kT=kT)
+    n = observables.density(dense.green_diag(dev, tr)["Gl"], E)
+    occ = lambda q: selfenergy.fermi(-2 * t * np.cos(q), mu_L, kT) + selfenergy.fermi(-2 * t * np.cos(q), mu_R, kT)
+    expect = quad(occ, k[0], k[-1], limit=200, epsabs=1e-13)[0] / np.pi
+    assert np.abs(n - expect).max() < 2e-5 * expect, (n, expect)
+    # the same device at T -> 0 and mu = 0 on both sides: half filling of the full band
+    k = np.linspace(1e-3, np.pi - 1e-3, 4001)
+    E = -2.0 * t * np.cos(k)
+    n0 = observables.density(dense.green_diag(dev, _tr(E, eta=1e-9, mu=(0.0, 0.0), kT=1e-4))["Gl"], E)
+    assert np.abs(n0 - 1.0).max() < 2e-3

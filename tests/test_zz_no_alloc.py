@@ -45,10 +45,47 @@ def test_noalloc_inverse_matches_existing_path():
             assert resid <= TOL_C64, resid
 
 
-def test_noalloc_rejects_oversize():
+def test_noalloc_near_the_cap_matches_existing_path():
+    """n = 512, batch 1: batch * n * n = 2^18, the whole working space."""
+    build.build()
+    dev = workloads.superlattice(32, 16, disorder=0.05, seed=5)
+    n, eta = dev.n, 1e-3
+    assert n == 512
+    plan = ndgf.nd_analyze(n, dev.rowptr, dev.colind, None, None, dev.coords, leaf_size=1000)
+    assert ndgf.nd_plan_query(plan)["n_clusters"] == 1
+    fact = ndgf.nd_fact_create(plan, 1, ndgf.ND_PREC_MIXED)
+    H = torch.as_tensor(dev.values, device="cuda")
+    Hd = torch.as_tensor(dev.dense(), device="cuda", dtype=torch.complex128)
+    eye = torch.eye(n, device="cuda", dtype=torch.complex128)
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for energy in (0.21, 0.33):  # two calls in a row over the full working space
+        E = torch.tensor([energy], device="cuda", dtype=torch.float64)
+        Gr = torch.zeros(1, n, dtype=torch.complex128, device="cuda")
+        ndgf.nd_factor(fact, H, None, None, E, 1, eta)
+        ndgf.nd_diag_green(fact, None, None, None, None, Gr, None, None)
+        A = ((energy + 1j * eta) * eye - Hd).to(torch.complex64).unsqueeze(0).contiguous()
+        ndgf.nd_invert_c64_noalloc(A, n, 1, cnt)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == 0
+        got = torch.diagonal(A[0]).cpu().numpy().astype(np.complex128)
+        ref = Gr[0].cpu().numpy()
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err <= TOL_C64, err
+
+
+def test_noalloc_rejects_oversize_and_host_arrays():
     build.build()
     A = torch.zeros(1, dtype=torch.complex64, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for n, batch in ((513, 1), (1024, 1), (512, 2), (40, 200)):  # each over 2^18 elements or n > 512
+        with pytest.raises(ndgf.NDError) as e:
+            ndgf.nd_invert_c64_noalloc(A, n, batch, cnt)
+        assert e.value.status == 1
+    A_host = np.zeros((1, 8, 8), dtype=np.complex64)
+    with pytest.raises(ndgf.NDError) as e:  # a host matrix is rejected before any launch
+        ndgf.nd_invert_c64_noalloc(A_host, 8, 1, cnt)
+    assert e.value.status == 1
     with pytest.raises(ndgf.NDError) as e:
-        ndgf.nd_invert_c64_noalloc(A, 1024, 1, cnt)  # 2^20 elements > 2^18
+        ndgf.nd_invert_c64_noalloc(torch.zeros(1, 8, 8, dtype=torch.complex64, device="cuda"), 8, 1,
+                                   np.zeros(1, dtype=np.int32))
     assert e.value.status == 1
