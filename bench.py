@@ -326,17 +326,17 @@ def main_ours(a) -> None:
         results[name] = (dens.clone(), Gl[:, ::97].clone(), Gr[pick].clone(), Gl[pick].clone(), cur.clone())
         c = cert_max[name].tolist()
         ca = cert_all[name].cpu().numpy()
-        rel_l = ca[:, 2] / np.maximum(ca[:, 3], 1e-300)
+        rel_r, rel_l = ca[:, 6], ca[:, 7]
         paths[name] = {"energies_per_s": round(n_e * world / (ms * 1e-3), 3), "ms_per_step": round(ms, 3),
                        "delay": delay,
                        "certificate_max": {"resid_r": c[0], "resid_lesser": c[2], "max_Gr": c[1], "max_Gl": c[3],
-                                           "growth_max_psi": c[4], "entries_not_found": c[5]},
+                                           "growth_max_psi": c[4], "entries_not_found": c[5],
+                                           "resid_r_rel": c[6], "resid_lesser_rel": c[7]},
                        "certificate_per_energy": {
-                           "resid_r": [float(f"{v:.3g}") for v in ca[:, 0]],
+                           "resid_r_rel": [float(f"{v:.3g}") for v in rel_r],
                            "resid_lesser_rel": [float(f"{v:.3g}") for v in rel_l],
                            "growth": [float(f"{v:.3g}") for v in ca[:, 4]],
-                           "flagged": int(((ca[:, 0] > a.resid_max) | (rel_l > a.resid_max) |
-                                           (ca[:, 4] > a.growth_max) | (ca[:, 5] > 0)).sum())},
+                           "flagged": int(certificate_flags(cert_all[name], a.resid_max, a.growth_max).sum())},
                        "fp64_redo_energies": redo.get(name, 0)}
         if name in ("fp64_nd", "fp32x2"):
             solvers[name] = (solver, step, ms)

@@ -83,6 +83,14 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
 /* Reserve the workspace of nd_density_gradient (M right-hand sides per
  * cluster, M = number of contact sites). */
 #define ND_FACT_ADJOINT 32
+/* Record the device work of nd_factor and of nd_diag_green (a few hundred
+ * launches each) once per distinct call shape (energy count, which inputs and
+ * outputs are given, eta) into a CUDA graph, and replay it with one
+ * cudaGraphLaunch on the caller's stream afterwards.  The input staging copies
+ * and the output copies stay outside the graph (outputs always go through the
+ * handle's buffers then), so the caller's pointers may change between calls.
+ * Not used while the launch profiler is on. */
+#define ND_FACT_GRAPH 64
 
 /* Sparsity pattern of H plus the contact site sets (host arrays).
  * rowptr[n+1], colind[nnz]: CSR pattern, 0-based, must be structurally
@@ -232,7 +240,13 @@ nd_status nd_diag_green(nd_fact* fact, const double* sigma_lesser, const double*
  *                carries amplified rounding;
  *   cert[e][5] = 1 if a stored entry could not be located (an internal
  *                inconsistency of the plan; never expected), else 0;
- *   cert[e][6..7] = 0 (reserved).
+ *   cert[e][6] = max_j |(A G^r)_jj - 1| / max_j (sum_k |A_jk| |G_kj|),
+ *   cert[e][7] = max_j |(A G^< - Sigma^< G^a)_jj| / max_j (sum_k |A_jk| |G^<_kj|
+ *                + sum_k |Sigma^<_jk| |G_jk|): the residuals relative to the
+ *                magnitude of their terms (normwise backward errors of the
+ *                diagonal, comparable with the unit roundoff of the path:
+ *                ~1e-16 complex128, ~1e-13 FP32 pairs, ~1e-6 complex64).
+ * A NaN anywhere makes the affected entries +inf.
  * Entries 2 and 3 are 0 when G^< was not computed.  cert: [n_e][8] doubles,
  * host or device.  Stream ordered after the nd_diag_green call.  The residual
  * of the diagonal is the refinement test of the mixed paths: a residual-
@@ -337,6 +351,15 @@ nd_status nd_profile_launches(nd_fact* fact, nd_launch_stats* out, int32_t max_o
  * when the device inputs of the last nd_factor / nd_diag_green failed their
  * check, ND_ERR_SINGULAR when n_singular > 0 (the results are then invalid). */
 nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
+
+/* Number of polls after which a wait of the tensor-core products gives up
+ * (0 = the default of 2^25, seconds of waiting).  A wait that gives up makes
+ * its CTA wait for its own copies and products in flight (always with the
+ * default limit), release its tensor memory and skip its output; the next
+ * nd_fact_status returns ND_ERR_TIMEOUT.  A small value makes the waits run
+ * out on purpose, which tests that path without a device fault; the handle
+ * stays usable (the next nd_factor starts clean).  Errors: ND_ERR_INVALID_ARG. */
+nd_status nd_fact_set_wait_limit(nd_fact* fact, int64_t polls);
 
 /* ---- S1a: contact self-energies (paper Sec. 2) ----------------------------
  * A lead is a semi-infinite chain of principal layers with on-site block H00

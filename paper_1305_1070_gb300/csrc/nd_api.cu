@@ -159,6 +159,7 @@ struct nd_fact {
   unsigned char* tc_scratch = nullptr;
   int64_t tc_stride = 0;  // bytes per energy
   int* d_tc_timeout = nullptr;
+  int64_t tc_wait_polls = 0;  // polls before a tensor-core wait gives up (0 = the kernel's default)
   // tile range of every GEMM step: index = step index in its schedule
   std::vector<TileRange> tr_factor, tr_green, tr_lesser[2];
   // staging buffers for host inputs / outputs
@@ -167,7 +168,23 @@ struct nd_fact {
   double *st_out[3] = {nullptr, nullptr, nullptr};
   std::vector<void*> allocs;
 
+  // ND_FACT_GRAPH: the launch sequence of each (call kind, energy count,
+  // inputs present, ...) recorded once into a CUDA graph on a private
+  // capture stream and replayed with one cudaGraphLaunch on the caller's stream
+  struct GraphEntry {
+    uint64_t key[2];
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+
+  void clear_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
   ~nd_fact() {
+    clear_graphs();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : allocs) cudaFree(p);
   }
 };
@@ -312,6 +329,38 @@ nd_status stage_in(const double* src, double* staging, size_t bytes, cudaStream_
   return ND_OK;
 }
 
+// Runs `body` on the caller's stream s, or, with ND_FACT_GRAPH (and the
+// profiler off), replays the graph recorded for `key`, recording it first by
+// running body on the private capture stream under stream capture.  Every
+// pointer and scalar the launches of body take must be fixed by the key.
+template <typename F>
+nd_status graph_run(nd_fact* f, const uint64_t key[2], cudaStream_t s, F&& body) {
+  if (!(f->flags & ND_FACT_GRAPH) || f->prof.on) return body(s);
+  for (auto& g : f->graphs)
+    if (g.key[0] == key[0] && g.key[1] == key[1]) {
+      ND_CUDA(cudaGraphLaunch(g.exec, s));
+      return ND_OK;
+    }
+  if (f->graphs.size() >= 16) f->clear_graphs();
+  cudaStream_t c = f->cap_stream;
+  ND_CUDA(cudaStreamBeginCapture(c, cudaStreamCaptureModeRelaxed));
+  const nd_status st = body(c);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(c, &g);
+  if (st != ND_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (ee != cudaSuccess) return fail(ND_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ee));
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return fail(ND_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  f->graphs.push_back(nd_fact::GraphEntry{{key[0], key[1]}, exec});
+  ND_CUDA(cudaGraphLaunch(exec, s));
+  return ND_OK;
+}
+
 template <typename T>
 nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::vector<TileRange>& tr,
                        const Work& w, const double* ph_l, const double* ph_g, cudaStream_t s, int variant = 0,
@@ -343,7 +392,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
       case ST_GEMM:
         if (tr[si].kind == 2)
           launch_gemm_tc(w, f->d_gemm, f->d_tcd, f->d_tcsplit + tr[si].sfirst, tr[si].scount,
-                         f->d_tiles + tr[si].first, tr[si].count, f->tc_scratch, f->tc_stride, f->d_tc_timeout, s);
+                         f->d_tiles + tr[si].first, tr[si].count, f->tc_scratch, f->tc_stride, f->d_tc_timeout,
+                         f->tc_wait_polls, s);
         else if (tr[si].kind == 3)
           Kern<T>::gemm_direct(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
         else
@@ -687,6 +737,13 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   TRY(dalloc(f, (void**)&f->st_pg, ne * n * 16));
   for (int k = 0; k < 3; ++k) TRY(dalloc(f, (void**)&f->st_out[k], ne * n * 16));
 #undef TRY
+  if (flags & ND_FACT_GRAPH) {
+    if (cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete f;
+      return fail(ND_ERR_CUDA, "nd_fact_create: cannot create the capture stream");
+    }
+  }
+  prepare_kernels();  // function attributes are set here, never during a capture
   cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     delete f;
@@ -742,9 +799,14 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
   if (sr_dev) launch_check_blocks(sr, p->sigma_elems, f->d_csoff, f->d_cm, p->n_contacts, n_e, false, f->d_inerr, s);
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, n_e};
   const int nc = int(p->cl.size());
-  if (f->precision == ND_PREC_FP64) return factor_t<double>(f, w, H, E, eta, sr, ph, nc, s);
-  if (f->precision == ND_PREC_MIXED) return factor_t<float>(f, w, H, E, eta, sr, ph, nc, s);
-  return factor_t<DF>(f, w, H, E, eta, sr, ph, nc, s);
+  uint64_t eta_bits;
+  std::memcpy(&eta_bits, &eta, 8);
+  const uint64_t key[2] = {(uint64_t(n_e) << 8) | (sr ? 2u : 0u) | (ph ? 4u : 0u), eta_bits};
+  return graph_run(f, key, s, [&](cudaStream_t q) {
+    if (f->precision == ND_PREC_FP64) return factor_t<double>(f, w, H, E, eta, sr, ph, nc, q);
+    if (f->precision == ND_PREC_MIXED) return factor_t<float>(f, w, H, E, eta, sr, ph, nc, q);
+    return factor_t<DF>(f, w, H, E, eta, sr, ph, nc, q);
+  });
 }
 
 template <typename T>
@@ -805,14 +867,21 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
   if (dev_in[3]) launch_check_diag_skew(pg, int64_t(n_e) * p->n, f->d_inerr + 1, s);
   double* user[3] = {Gr, Gl, Gg};
   double* dev[3];
-  bool host[3];
+  bool host[3], copy[3];
+  const bool graph = (f->flags & ND_FACT_GRAPH) && !f->prof.on;
   for (int k = 0; k < 3; ++k) {
     host[k] = user[k] && !is_device_ptr(user[k]);
-    dev[k] = host[k] ? f->st_out[k] : user[k];
+    copy[k] = user[k] && (host[k] || graph);  // with graphs the outputs always go through the staging buffers
+    dev[k] = copy[k] ? f->st_out[k] : user[k];
   }
-  st = f->precision == ND_PREC_FP64    ? diag_green_t<double>(f, sl, sg, pl, pg, dev, s)
-       : f->precision == ND_PREC_MIXED ? diag_green_t<float>(f, sl, sg, pl, pg, dev, s)
-                                       : diag_green_t<DF>(f, sl, sg, pl, pg, dev, s);
+  const uint64_t key[2] = {(uint64_t(n_e) << 16) | 1u | (sl ? 2u : 0u) | (sg ? 4u : 0u) | (pl ? 8u : 0u) |
+                               (pg ? 16u : 0u) | (Gr ? 32u : 0u) | (Gl ? 64u : 0u) | (Gg ? 128u : 0u),
+                           0};
+  st = graph_run(f, key, s, [&](cudaStream_t q) {
+    return f->precision == ND_PREC_FP64    ? diag_green_t<double>(f, sl, sg, pl, pg, dev, q)
+           : f->precision == ND_PREC_MIXED ? diag_green_t<float>(f, sl, sg, pl, pg, dev, q)
+                                           : diag_green_t<DF>(f, sl, sg, pl, pg, dev, q);
+  });
   if (st != ND_OK) return st;
   f->have_green = true;
   f->have_lesser = (Gl || Gg);
@@ -821,7 +890,9 @@ extern "C" nd_status nd_diag_green(nd_fact* f, const double* sigma_lesser, const
   f->cur_sg = sg;
   f->cur_pl = pl;
   for (int k = 0; k < 3; ++k)
-    if (host[k]) ND_CUDA(cudaMemcpyAsync(user[k], dev[k], size_t(n_e) * p->n * 16, cudaMemcpyDeviceToHost, s));
+    if (copy[k])
+      ND_CUDA(cudaMemcpyAsync(user[k], dev[k], size_t(n_e) * p->n * 16,
+                              host[k] ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
   return ND_OK;
 }
 
@@ -1066,6 +1137,13 @@ extern "C" nd_status nd_fact_density(nd_fact* f, const double* weights, double s
   launch_density(f->last_gl, w, n_e, n, scale, accumulate, o, s);
   ND_CUDA(cudaGetLastError());
   if (!out_dev) ND_CUDA(cudaMemcpyAsync(out, o, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_fact_set_wait_limit(nd_fact* f, int64_t polls) {
+  if (!f || polls < 0) return fail(ND_ERR_INVALID_ARG, "nd_fact_set_wait_limit: bad argument");
+  f->tc_wait_polls = polls;
+  f->clear_graphs();  // the recorded launches carry the old limit
   return ND_OK;
 }
 

@@ -64,7 +64,7 @@ constexpr int FW = 8;         // accumulator warps: widening, flush, epilogue
 constexpr int NT = (FW + 2) * 32;  // + producer warp + MMA warp
 constexpr int TMEM_COLS = 512;     // allocated (TC_S x TC_N = 448 used)
 constexpr size_t SMEM = size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB) + 1024;  // + alignment slack
-constexpr long SPIN = 1L << 25;    // polls before a wait gives up
+constexpr long SPIN = 1L << 25;    // polls before a wait gives up (default; a drain always uses it)
 
 static_assert(TC_S * TC_N <= TMEM_COLS, "group accumulators exceed the TMEM columns");
 static_assert(TC_M == 128 && TC_N % 16 == 0 && TC_N <= 256, "tcgen05 kind::f16 shape with M = 128");
@@ -258,10 +258,10 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase of the given parity.  Gives up when the CTA's
-// abort flag is raised (checked every 64 polls) or after SPIN polls (then
+// abort flag is raised (checked every 64 polls) or after `spin` polls (then
 // raises it).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
-  for (long i = 0; i < SPIN; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag, long spin) {
+  for (long i = 0; i < spin; ++i) {
     if (mbar_try(b, parity)) return true;
     if ((i & 63) == 63 && *abort_flag) return false;
   }
@@ -338,7 +338,7 @@ __device__ __forceinline__ void dd_acc(float& H, float& L, float h, float l) {
 __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ descs, const TcDesc* __restrict__ tcd,
                                                    const TileRef* __restrict__ tiles, float4* arena, int64_t se,
                                                    const unsigned char* __restrict__ scratch, int64_t ss,
-                                                   int* timeout) {
+                                                   int* timeout, long spin) {
   extern __shared__ unsigned char sm_raw[];
   __shared__ __align__(8) uint64_t full8[S8], empty8[S8], full16[S16], empty16[S16], accfull, accempty, done;
   __shared__ uint32_t tmem_slot;
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
       int j = 0;
       for (; j < njobs; ++j) {
         const int s = j % S8, u = j / S8;
-        if (u > 0 && !mbar_wait(&empty8[s], (u - 1) & 1, abrt)) break;
+        if (u > 0 && !mbar_wait(&empty8[s], (u - 1) & 1, abrt, spin)) break;
         const int c = j / KB, kb = j - c * KB;
         const unsigned char* ga = scr + t.dig_a + ((int64_t(c) * KB + kb) * t.rba + tr.tm) * int64_t(SA8);
         const unsigned char* gb = scr + t.dig_b + ((int64_t(c) * KB + kb) * t.rbb + tr.tn) * int64_t(SB8);
@@ -414,10 +414,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
         const int s = j % S16, u = j / S16;
         const int kb = j % KB, kc = kb % CHUNK;
         if (kc == 0 && q > 0) {
-          if (!mbar_wait(&accempty, (q - 1) & 1, abrt)) break;
+          if (!mbar_wait(&accempty, (q - 1) & 1, abrt, spin)) break;
           tc_fence_after();
         }
-        if (!mbar_wait(&full16[s], u & 1, abrt)) break;
+        if (!mbar_wait(&full16[s], u & 1, abrt, spin)) break;
         tc_fence_after();
         const uint32_t a0 = smem_u32(ring16 + size_t(s) * (SA + SB)), b0 = a0 + SA;
 #pragma unroll
@@ -444,8 +444,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
     const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(half * 32);
     auto widen = [&](int j) -> bool {
       const int s8 = j % S8, s16 = j % S16, u16 = j / S16;
-      if (!mbar_wait(&full8[s8], (j / S8) & 1, abrt)) return false;
-      if (u16 > 0 && !mbar_wait(&empty16[s16], (u16 - 1) & 1, abrt)) return false;
+      if (!mbar_wait(&full8[s8], (j / S8) & 1, abrt, spin)) return false;
+      if (u16 > 0 && !mbar_wait(&empty16[s16], (u16 - 1) & 1, abrt, spin)) return false;
       const uint4* src = reinterpret_cast<const uint4*>(ring8 + size_t(s8) * (SA8 + SB8));
       uint4* dst = reinterpret_cast<uint4*>(ring16 + size_t(s16) * (SA + SB));
       for (int i = tid; i < (SA8 + SB8) / 16; i += FW * 32) {
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
         const int upto = min(njobs - 1, last + S16);
         for (; ok && jw <= upto; ++jw) ok = __all_sync(0xffffffffu, widen(jw));
         if (!ok) break;
-        ok = __all_sync(0xffffffffu, mbar_wait(&accfull, q & 1, abrt));
+        ok = __all_sync(0xffffffffu, mbar_wait(&accfull, q & 1, abrt, spin));
         if (!ok) break;
         tc_fence_after();
 #pragma unroll
@@ -556,6 +556,8 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
 
 }  // namespace
 
+void prepare_gemm_tc() { cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM)); }
+
 int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off) {
   t.kb = (g.k + 15) / 16;
   t.rba = (g.m + TC_M - 1) / TC_M;
@@ -573,17 +575,14 @@ int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off) {
 
 void launch_gemm_tc(const Work& w, const GemmDesc* d, const TcDesc* tcd, const TcSplit* splits, int n_splits,
                     const TileRef* tiles, int n_tiles, unsigned char* scratch, int64_t ss, int* timeout,
-                    cudaStream_t s) {
+                    int64_t wait_polls, cudaStream_t s) {
   if (n_tiles <= 0 || w.n_e <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM));
-    attr = true;
-  }
   if (n_splits > 0)
     k_tc_split<<<dim3(n_splits, w.n_e), 256, 0, s>>>(d, tcd, splits, (const float4*)w.arena, w.se,
                                                      (const float4*)w.aux, w.sa, scratch, ss);
-  k_gemm_tc<<<dim3(n_tiles, w.n_e), NT, SMEM, s>>>(d, tcd, tiles, (float4*)w.arena, w.se, scratch, ss, timeout);
+  const long spin = wait_polls > 0 ? long(wait_polls) : SPIN;
+  k_gemm_tc<<<dim3(n_tiles, w.n_e), NT, SMEM, s>>>(d, tcd, tiles, (float4*)w.arena, w.se, scratch, ss, timeout,
+                                                   spin);
 }
 
 }  // namespace ndgf

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include <cstdint>
 
 #include <type_traits>
@@ -688,7 +690,13 @@ __global__ void k_convert_aux(const double2* __restrict__ lesser, const double2*
 // locr), and the boundary column is that of the first slot on the unknown's
 // path of delays that lies in a proper ancestor of the lower cluster.
 // Per energy: max |r|, max |G_jj|, max |r<|, max |G<_jj|; entry 5 becomes 1
-// when a stored entry was not found (a planner inconsistency, never expected).
+// when a stored entry was not found (a planner inconsistency, never expected);
+// entries 6 and 7 are the residuals relative to the magnitude of their terms,
+// max_j |r_j| / max_j (sum_k |A_jk| |G_kj|) and max_j |r<_j| / max_j
+// (sum_k |A_jk| |G<_kj| + sum_k |Sigma^<_jk| |G_jk|): normwise backward errors
+// of the diagonal entries, comparable with the unit roundoff of the arithmetic
+// that produced G (normwise, because entries of G^< far below the largest
+// ones can lie under the FP32 exponent range of the single-precision paths).
 __device__ __forceinline__ void atomic_max_pos(double* a, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(a), static_cast<unsigned long long>(__double_as_longlong(v)));
 }
@@ -757,7 +765,7 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
   const double2* ph_l = reinterpret_cast<const double2*>(a.ph_l);
   const double2* sr = reinterpret_cast<const double2*>(a.sr);
   const double2* sl = reinterpret_cast<const double2*>(a.sl);
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   bool lost = false;
   if (j < a.n) {
     const cx<T>* base = arena + int64_t(e) * se;
@@ -778,10 +786,13 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
     double2 rr = make_double2(d.x * gjj.x - d.y * gjj.y - 1.0, d.x * gjj.y + d.y * gjj.x);
     double2 rl = make_double2(d.x * pjj.x - d.y * pjj.y, d.x * pjj.y + d.y * pjj.x);
     double2 rhs = make_double2(0.0, 0.0);
+    const double ad = hypot(d.x, d.y);
+    double sr_sum = ad * hypot(gjj.x, gjj.y), sl_sum = ad * hypot(pjj.x, pjj.y);  // magnitudes of the terms
     if (a.lesser && ph_l) {  // ph^<_j conj(G_jj)
       const double2 q = ph_l[int64_t(e) * a.n + j];
       rhs.x += q.x * gjj.x + q.y * gjj.y;
       rhs.y += q.y * gjj.x - q.x * gjj.y;
+      sl_sum += hypot(q.x, q.y) * hypot(gjj.x, gjj.y);
     }
     for (int t = a.cptr[j]; t < a.cptr[j + 1]; ++t) {
       const int k = a.nb[t], src = a.coef[t];
@@ -802,15 +813,19 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
           const double2 q2 = sl[int64_t(e) * a.sstride + (-1 - src)];
           rhs.x += q2.x * g.x + q2.y * g.y;
           rhs.y += q2.y * g.x - q2.x * g.y;
+          sl_sum += hypot(q2.x, q2.y) * hypot(g.x, g.y);
         }
       }
+      const double aa = hypot(an.x, an.y);
       rr.x -= an.x * g.x - an.y * g.y;
       rr.y -= an.x * g.y + an.y * g.x;
+      sr_sum += aa * hypot(g.x, g.y);
       if (a.lesser) {
         double2 pv = O<T>::to_d2(base[a.cl[q].offP + idx]);
         if (!tr) pv = make_double2(-pv.x, pv.y);  // G<_kj = -conj(G<_jk)
         rl.x -= an.x * pv.x - an.y * pv.y;
         rl.y -= an.x * pv.y + an.y * pv.x;
+        sl_sum += aa * hypot(pv.x, pv.y);
       }
     }
     rl.x -= rhs.x;
@@ -819,23 +834,27 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
     v[1] = hypot(gjj.x, gjj.y);
     v[2] = hypot(rl.x, rl.y);
     v[3] = hypot(pjj.x, pjj.y);
+    v[4] = sr_sum;
+    v[5] = sl_sum;
+    for (int k = 0; k < 6; ++k)  // NaN -> +inf, so that the max reduction keeps it
+      if (!(v[k] >= 0.0)) v[k] = __longlong_as_double(0x7ff0000000000000LL);
   }
-  __shared__ double red[4][32];
+  __shared__ double red[6][32];
   __shared__ int s_lost;
   if (threadIdx.x == 0) s_lost = 0;
   __syncthreads();
   if (lost) s_lost = 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < 6; ++k) {
     double x = v[k];
     for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
     if (lane == 0) red[k][warp] = x;
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
+  if (threadIdx.x < 6) {
     double x = 0.0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) x = fmax(x, red[threadIdx.x][w]);
-    atomic_max_pos(a.cert + int64_t(e) * 8 + threadIdx.x, x);
+    atomic_max_pos(a.cert + int64_t(e) * 8 + (threadIdx.x < 4 ? threadIdx.x : threadIdx.x + 2), x);
   }
   if (threadIdx.x == 0 && s_lost) atomic_max_pos(a.cert + int64_t(e) * 8 + 5, 1.0);
 }
@@ -849,7 +868,8 @@ __global__ void k_absmax(const ZeroDesc* __restrict__ descs, const cx<T>* arena,
   double m = 0.0;
   for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) {
     const double2 v = O<T>::to_d2(p[i]);
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    const double a = fmax(fabs(v.x), fabs(v.y));
+    m = fmax(m, a == a ? a : __longlong_as_double(0x7ff0000000000000LL));  // NaN counts as infinite growth
   }
   __shared__ double red[32];
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -898,7 +918,6 @@ void Kern<T>::delay(const Work& w, const DelayDesc* d, int count, int max_nf, co
   const size_t xs = size_t(max_nf) * max_nf * sizeof(float2);
   const int x_smem = base + xs <= size_t(200 * 1024) ? 1 : 0;  // up to nf = 158
   const size_t shm = base + (x_smem ? xs : 0);
-  if (shm > 48 * 1024) cudaFuncSetAttribute(k_delay<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
   const int nt = max_nf <= 24 ? 64 : max_nf <= 48 ? 128 : max_nf <= 96 ? 256 : 512;
   k_delay<T><<<dim3(count, w.n_e), nt, shm, s>>>(d, (cx<T>*)w.arena, w.se, dt, x_smem);
 }
@@ -914,7 +933,6 @@ void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, dou
   while (base + size_t(cap + 1) * (cap + 1) * sizeof(cx<T>) <= size_t(72 * 1024)) ++cap;
   const int smem_max_n = cap < max_n ? cap : max_n;
   const size_t shm = base + size_t(smem_max_n) * smem_max_n * sizeof(cx<T>);
-  if (shm > 48 * 1024) cudaFuncSetAttribute(k_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
   // the n x n update of every pivot step is spread over the CTA: large blocks
   // (the few fronts near the root) get more threads
   const int nt = max_n <= 24 ? 64 : max_n <= 48 ? 128 : max_n <= 64 ? 256 : (max_n <= 128 ? 512 : 1024);
@@ -928,7 +946,6 @@ static void launch_gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, 
   constexpr int NT = (G::BM / G::TM) * (G::BN / G::TN);
   constexpr size_t shm = (sizeof(cx<T>) + sizeof(typename O<T>::S)) * 2 * G::BK * (G::BM + 1 + G::BN + 1);
   auto kern = k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN>;
-  if (shm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shm));
   kern<<<dim3(n_tiles, w.n_e), NT, shm, s>>>(d, tiles, (cx<T>*)w.arena, w.se, (const cx<T>*)w.aux, w.sa);
 }
 
@@ -1050,12 +1067,23 @@ void Kern<T>::selected(const Work& w, const CertArgs& a, const DelayTabs& dt, co
       a, dt, (const cx<T>*)w.arena, w.se, x, y, count, lesser, (double2*)Gr, (double2*)Gl, (double2*)Gg, n_missing);
 }
 
+// Entries 6, 7 hold the largest term magnitudes after k_certificate: divide.
+__global__ void k_cert_ratio(double* cert, int n_e) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_e) return;
+  double* c = cert + int64_t(e) * 8;
+  const double inf = __longlong_as_double(0x7ff0000000000000LL);
+  c[6] = c[6] > 0.0 ? c[0] / c[6] : (c[0] > 0.0 ? inf : 0.0);
+  c[7] = c[7] > 0.0 ? c[2] / c[7] : (c[2] > 0.0 ? inf : 0.0);
+}
+
 template <typename T>
 void Kern<T>::certificate(const Work& w, const CertArgs& a, const DelayTabs& dt, cudaStream_t s) {
   if (w.n_e <= 0) return;
   if (a.n_psi > 0)
     k_absmax<T><<<dim3(a.n_psi, w.n_e), 256, 0, s>>>(a.psi, (const cx<T>*)w.arena, w.se, a.cert);
   k_certificate<T><<<dim3((a.n + 255) / 256, w.n_e), 256, 0, s>>>(a, dt, (const cx<T>*)w.arena, w.se);
+  k_cert_ratio<<<(w.n_e + 127) / 128, 128, 0, s>>>(a.cert, w.n_e);
 }
 
 // S10 terminal current spectrum (Meir-Wingreen) of one contact:
@@ -1270,6 +1298,48 @@ void Kern<T>::adj_contract(const Work& w, const AdjDesc* d, int count, int M, co
   if (count <= 0 || w.n_e <= 0) return;
   k_adj_contract<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (const cx<T>*)w.arena, w.se, M, ct, (const double2*)sl,
                                                        sstride, sites, dt, (double2*)out, n);
+}
+
+// Dynamic shared memory limits of every kernel that may need more than 48 KB
+// (k_delay up to ~200 KB, k_inverse 72 KB, the large GEMM tiles, k_gemm_tc),
+// set once per device, before any launch can be recorded into a graph.
+// The largest dynamic shared memory a kernel may take: the device's opt-in
+// limit per block less the kernel's static shared memory.
+template <typename K>
+static void allow_max_smem(K kern, int optin) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - int(fa.sharedSizeBytes));
+}
+
+template <typename T>
+static void prepare_t(int optin) {
+  allow_max_smem(k_delay<T>, optin);
+  allow_max_smem(k_inverse<T>, optin);
+  using GL = GemmCfg<T, false>;
+  using GS = GemmCfg<T, true>;
+  allow_max_smem(k_gemm<T, GL::BM, GL::BN, GL::BK, GL::TM, GL::TN>, optin);
+  allow_max_smem(k_gemm<T, GS::BM, GS::BN, GS::BK, GS::TM, GS::TN>, optin);
+}
+
+void prepare_kernels() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  int optin = 48 * 1024;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  prepare_t<double>(optin);
+  prepare_t<float>(optin);
+  prepare_t<DF>(optin);
+  prepare_gemm_tc();
+  cudaGetLastError();
+  done[dev] = true;
 }
 
 template struct Kern<double>;

@@ -112,7 +112,12 @@ struct Kern {
 int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off);
 void launch_gemm_tc(const Work& w, const GemmDesc* d, const TcDesc* tcd, const TcSplit* splits, int n_splits,
                     const TileRef* tiles, int n_tiles, unsigned char* scratch, int64_t ss, int* timeout,
-                    cudaStream_t s);
+                    int64_t wait_polls, cudaStream_t s);
+
+// Sets the function attributes (dynamic shared memory limits) of every kernel
+// once; called before any launch can be recorded into a graph.
+void prepare_kernels();
+void prepare_gemm_tc();
 
 // Final positions of the unknowns after the delayed pivots (one tree level).
 void launch_loc(const LocDesc* d, int count, int n_e, const DelayTabs& dt, cudaStream_t s);

@@ -27,12 +27,13 @@ ND_FACT_TILE_SMALL = 4
 ND_FACT_GEMM_TC = 8
 ND_FACT_GEMM_ALU = 16
 ND_FACT_ADJOINT = 32
+ND_FACT_GRAPH = 64
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const", "nd_phonon_scba",
-           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_last_error",
+           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_last_error",
            "nd_version"]
 
 
@@ -91,6 +92,7 @@ def lib():
             "nd_factor": ([_P, _P, _P, _P, _P, _I32, _D, _P], _I32),
             "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
             "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
+            "nd_fact_set_wait_limit": ([_P, _I64], _I32),
             "nd_certificate": ([_P, _P, _P], _I32),
             "nd_selected_entries": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P], _I32),
             "nd_density": ([_P, _P, _I32, _I32, _D, _I32, _P, _P], _I32),
@@ -315,6 +317,11 @@ def nd_fact_status(fact: Fact) -> int:
     if st not in (0, 3):
         _check(st, "nd_fact_status")
     return n.value
+
+
+def nd_fact_set_wait_limit(fact: Fact, polls: int):
+    """Polls before a tensor-core wait gives up (0 = default)."""
+    _check(lib().nd_fact_set_wait_limit(fact.ptr, int(polls)), "nd_fact_set_wait_limit")
 
 
 def nd_lead_create(H00, H01, tau) -> Lead:

@@ -14,19 +14,19 @@ from . import ndgf
 
 
 def certificate_flags(cert, resid_max: float = 1e-8, growth_max: float = 10.0):
-    """Energies whose S9 certificate ([n_e, 8], nd_certificate) fails: FP64
-    residual max_j |(A G^r)_jj - 1| or max_j |(A G^< - Sigma^< G^a)_jj| relative
-    to max_j |G^<_jj| above resid_max, fold growth max|Psi| above growth_max, a
-    stored entry not found, or a non-finite value."""
-    scale = torch.clamp(cert[:, 3], min=1e-300)
-    bad = (cert[:, 0] > resid_max) | (cert[:, 2] > resid_max * scale) | (cert[:, 4] > growth_max) | (cert[:, 5] > 0)
-    return bad | ~torch.isfinite(cert[:, :5]).all(dim=1)
+    """Energies whose S9 certificate ([n_e, 8], nd_certificate) fails: a
+    relative FP64 residual of the diagonal of A G^r = I or of
+    A G^< = Sigma^< G^a (entries 6, 7: backward errors) above resid_max, a fold
+    growth max|Psi| above growth_max, a stored entry not found, or a non-finite
+    value."""
+    bad = (cert[:, 6] > resid_max) | (cert[:, 7] > resid_max) | (cert[:, 4] > growth_max) | (cert[:, 5] > 0)
+    return bad | ~torch.isfinite(cert).all(dim=1)
 
 
 class Solver:
     def __init__(self, dev, tr, *, precision: int = ndgf.ND_PREC_FP64, max_ne: int | None = None,
                  leaf_size: int = 64, split_permille: int = 0, delay: int = 0, tile: str = "auto",
-                 adjoint: bool = False, device: str = "cuda"):
+                 adjoint: bool = False, graph: bool = False, device: str = "cuda"):
         self.dev, self.tr = dev, tr
         self.device = torch.device(device)
         self.n = dev.n
@@ -45,6 +45,8 @@ class Solver:
                   "tc": ndgf.ND_FACT_GEMM_TC, "alu": ndgf.ND_FACT_GEMM_ALU}[tile]
         if adjoint:
             flags |= ndgf.ND_FACT_ADJOINT
+        if graph:
+            flags |= ndgf.ND_FACT_GRAPH
         self.fact = ndgf.nd_fact_create(self.plan, self.max_ne, precision, flags)
         self.leads = [ndgf.nd_lead_create(l.H00, l.H01, l.tau) for l in dev.leads]
         kw = dict(device=self.device)
@@ -154,15 +156,16 @@ class Solver:
 
     def certificate(self, n_e: int):
         """Per-energy certificate of the last step: [n_e, 8] = (max|A G - I|_jj,
-        max|G_jj|, max|A G^< - Sigma^< G^a|_jj, max|G^<_jj|, max|Psi|, 0, 0, 0)."""
+        max|G_jj|, max|A G^< - Sigma^< G^a|_jj, max|G^<_jj|, max|Psi|, entries
+        not found, and the two residuals relative to their terms)."""
         cert = torch.zeros(n_e, 8, dtype=torch.float64, device=self.device)
         ndgf.nd_certificate(self.fact, cert)
         return cert
 
     def step_certified(self, energies, fallback: "Solver", *, resid_max: float = 1e-8, growth_max: float = 10.0):
-        """step() followed by the S9 certificate: energies whose FP64 residual
-        max_j |(A G^r)_jj - 1| or max_j |(A G^< - Sigma^< G^a)_jj| / max_j |G^<_jj|
-        exceeds resid_max, or whose fold growth max|Psi| exceeds growth_max, are
+        """step() followed by the S9 certificate: energies whose relative FP64
+        residual of diag(A G^r - I) or diag(A G^< - Sigma^< G^a) exceeds
+        resid_max, or whose fold growth max|Psi| exceeds growth_max, are
         recomputed by `fallback` (a complex128 Solver of the same device) and
         their rows overwritten.  Returns (Gr, Gl, Gg, cert, redone) with cert the
         [n_e, 8] certificate of this solver's pass and redone the indices of the

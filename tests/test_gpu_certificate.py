@@ -18,7 +18,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import dense, observables, problem  # noqa: E402
+from oracle import dense, observables  # noqa: E402
 from paper_1305_1070_gb300 import build, ndgf, workloads  # noqa: E402
 from paper_1305_1070_gb300.solver import Solver  # noqa: E402
 
@@ -57,6 +57,24 @@ def _selected(s, x, y, n_e):
     return [o.cpu().numpy() for o in out], int(miss.item())
 
 
+def _dense_inputs(s, dev, tr, e):
+    """Dense A(E_e) and Sigma^<(E_e) from the inputs the solver handed to the
+    library for energy e (its Sigma^r / Sigma^< buffers and phonon diagonals)."""
+    A = -dev.dense().astype(complex)
+    A[np.diag_indices(dev.n)] += float(s.E[e]) + 1j * tr.eta
+    Sl = np.zeros((dev.n, dev.n), dtype=complex)
+    sr, sl = s.sig_r[e].cpu().numpy(), s.sig_l[e].cpu().numpy()
+    for c, idx in enumerate(dev.contacts):
+        m = len(idx)
+        o = int(s.off[c])
+        A[np.ix_(idx, idx)] -= sr[o:o + m * m].reshape(m, m)
+        Sl[np.ix_(idx, idx)] += sl[o:o + m * m].reshape(m, m)
+    if s.ph:
+        A[np.diag_indices(dev.n)] -= s.ph_r[e].cpu().numpy()
+        Sl[np.diag_indices(dev.n)] += s.ph_l[e].cpu().numpy()
+    return A, Sl
+
+
 CASES = [  # (L, W, leaf, delay, gamma_ph, precision, tol)
     (22, 7, 10, 0, 0.0, ndgf.ND_PREC_FP64, 1e-10),
     (22, 7, 10, 2, 0.0, ndgf.ND_PREC_FP64, 1e-10),
@@ -82,23 +100,28 @@ def test_selected_entries_and_residual(L, W, leaf, delay, gph, precision, tol):
         for got, key in ((gr, "Gr"), (gl, "Gl"), (gg, "Gg")):
             ref = full[key][x, y]
             assert np.abs(got[e] - ref).max() <= tol * np.abs(full[key]).max(), key
-        # the residuals from the oracle's A and Sigma^< and the GPU's entries
-        A = full["A"]
-        Sl = problem.dense_sigma(dev, full["terms"], "lesser")
+        # the residuals from A and Sigma^< of this call (H, E + i eta, the phonon
+        # term and the device-computed lead blocks) and the GPU's entries: the
+        # same FP64 sums up to rounding
+        A, Sl = _dense_inputs(s, dev, tr, e)
         G = np.zeros((dev.n, dev.n), dtype=complex)
         Gl = np.zeros_like(G)
         G[x, y] = gr[e]
         Gl[x, y] = gl[e]
-        rr = np.abs(np.einsum("jk,kj->j", A, G) - 1.0).max()
+        r = np.abs(np.einsum("jk,kj->j", A, G) - 1.0)
         # (Sigma^< G^a)_jj = sum_k Sigma^<_jk conj(G_jk)
-        rl = np.abs(np.einsum("jk,kj->j", A, Gl) - np.einsum("jk,jk->j", Sl, G.conj())).max()
-        assert cert[e, 0] == pytest.approx(rr, rel=1e-6, abs=1e-15)
-        assert cert[e, 2] == pytest.approx(rl, rel=1e-6, abs=1e-15)
+        rl = np.abs(np.einsum("jk,kj->j", A, Gl) - np.einsum("jk,jk->j", Sl, G.conj()))
+        s_r = np.einsum("jk,kj->j", np.abs(A), np.abs(G))
+        s_l = np.einsum("jk,kj->j", np.abs(A), np.abs(Gl)) + np.einsum("jk,jk->j", np.abs(Sl), np.abs(G))
+        u = 1e3 * 2.0 ** -52
+        assert abs(cert[e, 0] - r.max()) <= u * s_r.max()
+        assert abs(cert[e, 2] - rl.max()) <= u * s_l.max()
+        assert abs(cert[e, 6] - r.max() / s_r.max()) <= u
+        assert abs(cert[e, 7] - rl.max() / s_l.max()) <= u
         assert cert[e, 1] == pytest.approx(np.abs(np.diag(full["Gr"])).max(), rel=tol * 10)
-        # rounding level of the path: relative to the row sums of |A| |G|
-        scale = np.abs(A).sum(axis=1).max() * np.abs(full["Gr"]).max()
-        assert cert[e, 0] <= 50 * tol * scale
-        assert cert[e, 2] <= 50 * tol * scale * np.abs(full["Gl"]).max() / np.abs(full["Gr"]).max()
+        # backward errors within the path's parity tolerance (a missing or wrong
+        # term would leave an O(|A_jk G_kj|) residual)
+        assert cert[e, 6] <= tol and cert[e, 7] <= tol
 
 
 def test_selected_entries_missing_pairs():
@@ -136,7 +159,7 @@ def test_certified_step_redo():
         assert torch.equal(got, w)
     # a residual threshold below the FP32-pair rounding level flags every energy too
     _, _, _, cert, redone = x2.step_certified(tr.energies, f64, resid_max=0.0, growth_max=1e9)
-    assert redone.numel() == tr.n_e and (cert[:, 0] > 0).all()
+    assert redone.numel() == tr.n_e and (cert[:, 6] > 0).all()
 
 
 @pytest.mark.parametrize("precision,tol", [(ndgf.ND_PREC_FP64, 1e-10), (ndgf.ND_PREC_FP32X2, 1e-9)])
