@@ -105,6 +105,9 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the reference timing without delayed pivots")
     ap.add_argument("--tile", default="auto", choices=["auto", "large", "small", "tc", "alu"],
                     help="GEMM kernel per launch: auto, a forced ALU tile size, tensor cores (FP32 pairs) or never")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default kernel rules (no nd_autotune)")
+    ap.add_argument("--tune-plan", action="store_true",
+                    help="also search leaf size and energies per call (paper_1305_1070_gb300.tune)")
     ap.add_argument("--dump-density", default="", help="write the densities of the paths to this .npz")
     ap.add_argument("--only", default="", help="run one path only (fp64_nd, fp32x2, fp32); for profiling")
     ap.add_argument("--energies", type=int, default=0, help="use the first K energies only; for profiling")
@@ -304,6 +307,14 @@ def main_ours(a) -> None:
         return float((x - y).abs().max() / y.abs().max())
 
     paths, results, solvers = {}, {}, {}
+    tuning = {}
+    if a.tune_plan:  # leaf size and energies per call of the headline path, measured
+        from paper_1305_1070_gb300 import tune
+        t0 = time.perf_counter()
+        best, table, _ = tune.tune_plan(dev, tr, precision=ndgf.ND_PREC_FP32X2, delay=a.delay, keep_best=False)
+        tuning["plan_search"] = {"best": best, "table": table, "seconds": round(time.perf_counter() - t0, 1)}
+        a.leaf, a.chunk_x2 = best["leaf"], best["chunk"]
+        torch.cuda.empty_cache()
     pick = torch.as_tensor(oracle_pick(n_e, a.cpu_sample), device="cuda")
     clk = Clocks(local)
     fallback = None
@@ -316,6 +327,10 @@ def main_ours(a) -> None:
             continue
         chunk = min(chunk, n_e)
         solver = Solver(dev, tr, precision=prec, max_ne=chunk, delay=delay, tile=a.tile, leaf_size=a.leaf)
+        if not a.no_tune and a.tile == "auto" and name != "fp64_nd_plain":
+            t0 = time.perf_counter()
+            tinfo = solver.autotune(E_all[:chunk])
+            tuning[name] = dict(tinfo, seconds=round(time.perf_counter() - t0, 2))
         if name == "fp64_nd":
             fallback = solver
         step = make_step(solver, chunk, name, fallback if name == "fp32x2" else None)
@@ -528,7 +543,10 @@ def main_ours(a) -> None:
                        "delayed_pivots_per_cluster": a.delay,
                        "l2": "inputs larger than L2 (~100-200 GB workspace per step)",
                        "fp64_nd_same_gpu_energies_per_s": paths["fp64_nd"]["energies_per_s"],
-                       "mixed_over_fp64_nd": paths["speedup_fp32x2_over_fp64"]},
+                       "mixed_over_fp64_nd": paths["speedup_fp32x2_over_fp64"],
+                       "kernel_choice": "measured per launch (nd_autotune), before the timed region"
+                       if tuning else "default rules"},
+            "tuning": tuning,
             "paths": paths,
             "current_spectrum_integral_eV": {"L": float((cur[0] * weights).sum()), "R": float((cur[1] * weights).sum())},
             "roofline": roofline,
@@ -591,11 +609,15 @@ def main_aux(a) -> None:
     weights = torch.as_tensor(w, device="cuda")
     dens = {}
     res = {}
+    tuned = {}
     clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     chunk = min(a.chunk_aux or cfg["chunk"], n_e)
     for name, prec, K, W in (("fp32x2", ndgf.ND_PREC_FP32X2, a.steps, max(1, min(a.warmup, 1))),
                              ("fp64_nd", ndgf.ND_PREC_FP64, 1, 0)):
         s = Solver(dev, tr, precision=prec, max_ne=chunk, delay=a.delay, leaf_size=a.leaf)
+        if not a.no_tune:
+            t0 = time.perf_counter()
+            tuned[name] = dict(s.autotune(E_all[:chunk]), seconds=round(time.perf_counter() - t0, 2))
         out = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
 
         def step():
@@ -643,7 +665,7 @@ def main_aux(a) -> None:
             "data": cfg["data"],
             "config": {"workload": a.workload, "devices": n_dev, "sites": dev.n, "energies": n_e,
                        "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": chunk},
-            "paths": res, "density_rel_err_fp32x2_vs_fp64": err, "gate_1e-6": err <= GATE,
+            "paths": res, "tuning": tuned, "density_rel_err_fp32x2_vs_fp64": err, "gate_1e-6": err <= GATE,
             "roofline": {"kernel": "complex-fp32x2:gemm", "bound": "alu", "achieved": round(ach, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None},
             "clocks": clocks,

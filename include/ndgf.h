@@ -352,6 +352,32 @@ nd_status nd_profile_launches(nd_fact* fact, nd_launch_stats* out, int32_t max_o
  * check, ND_ERR_SINGULAR when n_singular > 0 (the results are then invalid). */
 nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
 
+/* ---- kernel autotuner (spec batching: tile shapes per workload) ---------
+ * Measures, on the given inputs (those of nd_factor and nd_diag_green, host
+ * or device), every candidate kernel of every GEMM launch of the fold and the
+ * extraction: the default rules, the large and the small tile, the tensor
+ * cores (FP32 pairs) and one CTA per block (blocks up to 192): one pass per
+ * candidate with all its launches on it, each after an untimed pass, `reps`
+ * timed passes averaged, CUDA events on the stream.  Each launch then takes
+ * its fastest kernel for every later call on the handle (the results are
+ * the same up to rounding order).  The call runs 5 (reps + 1) factor +
+ * diag_green passes and synchronises the stream; the recorded graphs of
+ * ND_FACT_GRAPH are dropped.  The adjoint solves keep the default rules.
+ * info (may be NULL): summed GEMM milliseconds of one pass with the default
+ * rules and with the chosen kernels, GEMM launches tuned, launches whose
+ * kernel changed, passes, and the launches per kernel kind (0 large tile,
+ * 1 small tile, 2 tensor cores, 3 one CTA per block).  Errors: those of
+ * nd_factor / nd_diag_green, ND_ERR_INVALID_ARG (reps < 1). */
+typedef struct nd_tune_info {
+  double ms_default, ms_tuned;
+  int32_t gemm_steps, changed, passes;
+  int32_t by_kind[4];
+} nd_tune_info;
+nd_status nd_autotune(nd_fact* fact, const double* H_values, const double* sigma_r, const double* sigma_ph_r,
+                      const double* sigma_lesser, const double* sigma_greater, const double* ph_lesser,
+                      const double* ph_greater, const double* energies, int32_t n_e, double eta, int32_t reps,
+                      nd_tune_info* info, void* stream);
+
 /* Number of polls after which a wait of the tensor-core products gives up
  * (0 = the default of 2^25, seconds of waiting).  A wait that gives up makes
  * its CTA wait for its own copies and products in flight (always with the

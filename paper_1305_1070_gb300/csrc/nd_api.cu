@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -59,6 +60,8 @@ struct Profiler {
     cudaEvent_t a, b;
     double flops, bytes;
     int count = 0, max_dim = 0, n_e = 0;
+    const void* tr = nullptr;  // tile ranges of the schedule and index of the step (the tuner's key)
+    int si = -1;
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
@@ -162,6 +165,8 @@ struct nd_fact {
   int64_t tc_wait_polls = 0;  // polls before a tensor-core wait gives up (0 = the kernel's default)
   // tile range of every GEMM step: index = step index in its schedule
   std::vector<TileRange> tr_factor, tr_green, tr_lesser[2];
+  std::vector<GemmDesc> gemm_all;  // the plan's GEMM table plus the adjoint's (host copy)
+  bool tuned = false;
   // staging buffers for host inputs / outputs
   double *st_H = nullptr, *st_sr = nullptr, *st_ph = nullptr, *st_E = nullptr;
   double *st_sl = nullptr, *st_sg = nullptr, *st_pl = nullptr, *st_pg = nullptr;
@@ -246,9 +251,24 @@ struct TcTables {
   int64_t bytes = 0;  // largest per-energy scratch of a step
 };
 
+// Kernel of a GEMM step chosen by the tuner (nd_autotune): -1 = the default
+// rules below, else a TileRange kind (0 large tile, 1 small tile, 2 tensor
+// cores, 3 one CTA per block).
+using Choice = std::vector<int8_t>;
+
+// Per-energy digit scratch of a step on the tensor cores (bytes).
+int64_t tc_step_scratch(const Step& s, const std::vector<GemmDesc>& gd) {
+  int64_t off = 0;
+  for (int k = s.begin; k < s.begin + s.count; ++k) {
+    TcDesc t{};
+    off = gemm_tc_scratch(gd[k], t, off);
+  }
+  return off;
+}
+
 void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
                  double small_cost, bool tc_ok, int max_ne, TcTables& tct, std::vector<TileRef>& tiles,
-                 std::vector<TileRange>& ranges) {
+                 std::vector<TileRange>& ranges, const Choice* forced = nullptr) {
   ranges.assign(sched.size(), TileRange{0, 0, 0, 0, 0, 0});
   auto work = [&](const Step& s, int tile) {
     double w = 0.0;
@@ -280,8 +300,14 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
     // launches whose blocks all have edges <= DIRECT_MAX take one CTA per block
     int dim = 0;
     for (int k = s.begin; k < s.begin + s.count; ++k) dim = std::max(dim, std::max(gd[k].m, std::max(gd[k].n, gd[k].k)));
-    const bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && dim <= DIRECT_MAX &&
-                        (dim <= DIRECT_SMALL || int64_t(s.count) * max_ne >= DIRECT_MIN_CTAS);
+    bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && dim <= DIRECT_MAX &&
+                  (dim <= DIRECT_SMALL || int64_t(s.count) * max_ne >= DIRECT_MIN_CTAS);
+    if (forced && (*forced)[si] >= 0) {  // the tuner's measured choice
+      const int c = (*forced)[si];
+      tc = c == 2;
+      direct = c == 3;
+      small = c == 1;
+    }
     const int tile = small ? tile_s : tile_l;
     int b = int(tiles.size());
     if (tc) {
@@ -382,6 +408,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
       rec.count = st.count;
       rec.max_dim = st.max_dim;
       rec.n_e = w.n_e;
+      rec.tr = &tr;
+      rec.si = int(si);
       cudaEventRecord(rec.a, s);
     }
     switch (st.kind) {
@@ -576,6 +604,67 @@ void build_adjoint(const nd_plan* p, int64_t base, std::vector<GemmDesc>& gemms,
 
 }  // namespace
 
+// Schedules whose GEMM steps carry a tile list, in a fixed order (the tuner's
+// choices are indexed by it): factor, G^r, G^< without / with phonons, and the
+// adjoint solves.
+constexpr int N_SCHED = 6;
+
+void free_tracked(nd_fact* f, void* p) {
+  if (!p) return;
+  auto it = std::find(f->allocs.begin(), f->allocs.end(), p);
+  if (it != f->allocs.end()) f->allocs.erase(it);
+  cudaFree(p);
+}
+
+// Tile lists of every GEMM step (default rules, or the choices of
+// nd_autotune), uploaded with the tensor-core tables; the digit scratch grows
+// when the new choices need more.
+nd_status build_all_tiles(nd_fact* f, const std::array<Choice, N_SCHED>* forced) {
+  const nd_plan* p = f->plan;
+  const int precision = f->precision, flags = f->flags, max_ne = f->max_ne;
+  auto tile_of = [&](bool small) {
+    return precision == ND_PREC_FP64    ? Kern<double>::gemm_tile(small)
+           : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile(small)
+                                        : Kern<DF>::gemm_tile(small);
+  };
+  const int tl = tile_of(false), ts = tile_of(true);
+  std::vector<TileRef> tiles;
+  const double sc = small_tile_cost(precision);
+  const bool tc_ok = precision == ND_PREC_FP32X2;
+  const bool ph = (flags & ND_FACT_PHONON) != 0;  // the phonon G^< schedule runs only on a phonon workspace
+  TcTables tct;
+  auto fc = [&](int q) { return forced ? &(*forced)[q] : nullptr; };
+  build_tiles(p->sched_factor, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_factor, fc(0));
+  build_tiles(p->sched_green, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_green, fc(1));
+  build_tiles(p->sched_lesser[0], f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_lesser[0], fc(2));
+  build_tiles(p->sched_lesser[1], f->gemm_all, tl, ts, flags, sc, tc_ok && ph, max_ne, tct, tiles, f->tr_lesser[1],
+              fc(3));
+  if (f->adj) {
+    build_tiles(f->sched_adj_fwd, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_fwd, fc(4));
+    build_tiles(f->sched_adj_bwd, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_bwd, fc(5));
+  }
+  free_tracked(f, f->d_tiles);
+  free_tracked(f, f->d_tcd);
+  free_tracked(f, f->d_tcsplit);
+  f->d_tiles = nullptr;
+  f->d_tcd = nullptr;
+  f->d_tcsplit = nullptr;
+  nd_status st;
+  if ((st = dupload(f, tiles, &f->d_tiles)) != ND_OK) return st;
+  if (!tct.desc.empty()) {
+    if ((st = dupload(f, tct.desc, &f->d_tcd)) != ND_OK) return st;
+    if ((st = dupload(f, tct.split, &f->d_tcsplit)) != ND_OK) return st;
+    if (tct.bytes > f->tc_stride || !f->tc_scratch) {
+      free_tracked(f, f->tc_scratch);
+      f->tc_scratch = nullptr;
+      f->tc_stride = tct.bytes;
+      if ((st = dalloc(f, (void**)&f->tc_scratch, size_t(tct.bytes) * size_t(max_ne))) != ND_OK) return st;
+    }
+  }
+  f->clear_graphs();
+  return ND_OK;
+}
+
 extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t precision, int32_t flags,
                                     nd_fact** out) {
   if (!p || !out || max_ne <= 0) return fail(ND_ERR_INVALID_ARG, "nd_fact_create: bad argument");
@@ -645,6 +734,7 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
     f->step_flops_adj_bwd = step_flops(p, f->sched_adj_bwd, &gemm_all);
   }
   TRY(dupload(f, gemm_all, &f->d_gemm));
+  f->gemm_all = gemm_all;
   TRY(dupload(f, p->scat_desc, &f->d_scat));
   TRY(dupload(f, p->gath_desc, &f->d_gath));
   TRY(dupload(f, p->diag_g, &f->d_diag_g));
@@ -695,37 +785,9 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   f->step_flops_green = step_flops(p, p->sched_green);
   f->step_flops_lesser[0] = step_flops(p, p->sched_lesser[0]);
   f->step_flops_lesser[1] = step_flops(p, p->sched_lesser[1]);
-  {
-    auto tile_of = [&](bool small) {
-      return precision == ND_PREC_FP64    ? Kern<double>::gemm_tile(small)
-             : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile(small)
-                                          : Kern<DF>::gemm_tile(small);
-    };
-    const int tl = tile_of(false), ts = tile_of(true);
-    std::vector<TileRef> tiles;
-    const double sc = small_tile_cost(precision);
-    const bool tc_ok = precision == ND_PREC_FP32X2;
-    TcTables tct;
-    build_tiles(p->sched_factor, p->gemm_desc, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_factor);
-    build_tiles(p->sched_green, p->gemm_desc, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_green);
-    // the G^< schedule with a phonon Sigma^< runs only on a phonon workspace
-    const bool ph = (flags & ND_FACT_PHONON) != 0;
-    build_tiles(p->sched_lesser[0], p->gemm_desc, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_lesser[0]);
-    build_tiles(p->sched_lesser[1], p->gemm_desc, tl, ts, flags, sc, tc_ok && ph, max_ne, tct, tiles, f->tr_lesser[1]);
-    if (f->adj) {
-      build_tiles(f->sched_adj_fwd, gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_fwd);
-      build_tiles(f->sched_adj_bwd, gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_bwd);
-    }
-    TRY(dupload(f, tiles, &f->d_tiles));
-    if (!tct.desc.empty()) {
-      TRY(dupload(f, tct.desc, &f->d_tcd));
-      TRY(dupload(f, tct.split, &f->d_tcsplit));
-      f->tc_stride = tct.bytes;
-      TRY(dalloc(f, (void**)&f->tc_scratch, size_t(tct.bytes) * size_t(max_ne)));
-    }
-    TRY(dalloc(f, (void**)&f->d_tc_timeout, sizeof(int)));
-    cudaMemset(f->d_tc_timeout, 0, sizeof(int));
-  }
+  TRY(build_all_tiles(f, nullptr));
+  TRY(dalloc(f, (void**)&f->d_tc_timeout, sizeof(int)));
+  cudaMemset(f->d_tc_timeout, 0, sizeof(int));
   const size_t ne = size_t(max_ne), n = size_t(p->n), se = size_t(p->sigma_elems);
   TRY(dalloc(f, (void**)&f->st_H, size_t(std::max(1, p->nnz)) * 8));
   TRY(dalloc(f, (void**)&f->st_sr, std::max<size_t>(1, ne * se) * 16));
@@ -1137,6 +1199,118 @@ extern "C" nd_status nd_fact_density(nd_fact* f, const double* weights, double s
   launch_density(f->last_gl, w, n_e, n, scale, accumulate, o, s);
   ND_CUDA(cudaGetLastError());
   if (!out_dev) ND_CUDA(cudaMemcpyAsync(out, o, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, s));
+  return ND_OK;
+}
+
+extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const double* sigma_r, const double* sigma_ph_r,
+                                 const double* sigma_lesser, const double* sigma_greater, const double* ph_lesser,
+                                 const double* ph_greater, const double* energies, int32_t n_e, double eta,
+                                 int32_t reps, nd_tune_info* info, void* stream) {
+  if (!f || reps < 1) return fail(ND_ERR_INVALID_ARG, "nd_autotune: bad argument");
+  const nd_plan* p = f->plan;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool ph = (f->flags & ND_FACT_PHONON) != 0;
+  const bool lesser = sigma_lesser || sigma_greater || ph_lesser || ph_greater;
+  const std::vector<Step>* sched[4] = {&p->sched_factor, &p->sched_green, &p->sched_lesser[0], &p->sched_lesser[1]};
+  const std::vector<TileRange>* trs[4] = {&f->tr_factor, &f->tr_green, &f->tr_lesser[0], &f->tr_lesser[1]};
+  // candidate kernels per GEMM step: the default rules (-1), the large and the
+  // small tile, the tensor cores (FP32 pairs, digit scratch within the limit)
+  // and one CTA per block (blocks up to 192)
+  auto allowed = [&](int q, int si, int c) {
+    const Step& st = (*sched[q])[si];
+    if (st.kind != ST_GEMM) return false;
+    if (c == 2)
+      return f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_step_scratch(st, f->gemm_all) <= TC_MAX_SCRATCH;
+    if (c == 3) return st.max_dim <= 192;
+    return true;
+  };
+  std::array<std::vector<std::array<double, 5>>, 4> ms;  // [schedule][step][candidate + 1]
+  for (int q = 0; q < 4; ++q) ms[q].assign(sched[q]->size(), {-1.0, -1.0, -1.0, -1.0, -1.0});
+  const bool prof_was = f->prof.on;
+  nd_status st = ND_OK;
+  int passes = 0;
+  for (int c = -1; c < 4 && st == ND_OK; ++c) {
+    std::array<Choice, N_SCHED> forced;
+    for (int q = 0; q < N_SCHED; ++q) {
+      const size_t ns = q < 4 ? sched[q]->size() : (q == 4 ? f->sched_adj_fwd.size() : f->sched_adj_bwd.size());
+      forced[q].assign(ns, -1);
+      if (q < 4 && c >= 0)
+        for (size_t si = 0; si < ns; ++si)
+          if (allowed(q, int(si), c)) forced[q][si] = int8_t(c);
+    }
+    if ((st = build_all_tiles(f, &forced)) != ND_OK) break;
+    for (int r = 0; r <= reps && st == ND_OK; ++r) {  // one untimed pass, then reps timed ones
+      f->prof.clear();
+      f->prof.on = r > 0;
+      st = nd_factor(f, H_values, sigma_r, sigma_ph_r, energies, n_e, eta, stream);
+      if (st == ND_OK)
+        st = nd_diag_green(f, sigma_lesser, sigma_greater, ph_lesser, ph_greater, f->st_out[0],
+                           lesser ? f->st_out[1] : nullptr, lesser ? f->st_out[2] : nullptr, stream);
+      if (st != ND_OK) break;
+      if (cudaStreamSynchronize(s) != cudaSuccess) {
+        st = fail(ND_ERR_CUDA, "nd_autotune: a tuning pass failed");
+        break;
+      }
+      if (r == 0) continue;
+      for (auto& rec : f->prof.recs)
+        for (int q = 0; q < 4; ++q)
+          if (rec.tr == trs[q] && rec.si >= 0) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, rec.a, rec.b);
+            const bool ok = c < 0 || forced[q][rec.si] == c;
+            if (ok && (*sched[q])[rec.si].kind == ST_GEMM) {
+              double& m = ms[q][rec.si][c + 1];
+              m = m < 0.0 ? t / reps : m + t / reps;
+            }
+          }
+    }
+    ++passes;
+  }
+  f->prof.clear();
+  f->prof.on = prof_was;
+  if (st != ND_OK) {
+    build_all_tiles(f, nullptr);
+    return st;
+  }
+  // per step the fastest measured kernel
+  std::array<Choice, N_SCHED> best;
+  double t_def = 0.0, t_best = 0.0;
+  int steps = 0, changed = 0, by_kind[4] = {0, 0, 0, 0};
+  for (int q = 0; q < N_SCHED; ++q) {
+    const size_t ns = q < 4 ? sched[q]->size() : (q == 4 ? f->sched_adj_fwd.size() : f->sched_adj_bwd.size());
+    best[q].assign(ns, -1);
+    if (q >= 4) continue;
+    for (size_t si = 0; si < ns; ++si) {
+      if ((*sched[q])[si].kind != ST_GEMM) continue;
+      const auto& m = ms[q][si];
+      if (m[0] < 0.0) continue;  // not run (the phonon schedule without phonon inputs)
+      int bc = -1;
+      double bt = m[0];
+      for (int c = 0; c < 4; ++c)
+        if (m[c + 1] >= 0.0 && m[c + 1] < bt) {
+          bt = m[c + 1];
+          bc = c;
+        }
+      best[q][si] = int8_t(bc);
+      ++steps;
+      t_def += m[0];
+      t_best += bt;
+      if (bc >= 0) ++changed;
+    }
+  }
+  if ((st = build_all_tiles(f, &best)) != ND_OK) return st;
+  for (int q = 0; q < 4; ++q)
+    for (size_t si = 0; si < sched[q]->size(); ++si)
+      if ((*sched[q])[si].kind == ST_GEMM && ms[q][si][0] >= 0.0) ++by_kind[(*trs[q])[si].kind];
+  f->tuned = true;
+  if (info) {
+    info->ms_default = t_def;
+    info->ms_tuned = t_best;
+    info->gemm_steps = steps;
+    info->changed = changed;
+    info->passes = passes;
+    for (int k = 0; k < 4; ++k) info->by_kind[k] = by_kind[k];
+  }
   return ND_OK;
 }
 

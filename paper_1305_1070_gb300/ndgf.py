@@ -33,7 +33,7 @@ EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const", "nd_phonon_scba",
-           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_last_error",
+           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_autotune", "nd_last_error",
            "nd_version"]
 
 
@@ -57,6 +57,11 @@ class nd_opts(ctypes.Structure):
 class nd_kernel_stats(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32), ("ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class nd_tune_info(ctypes.Structure):
+    _fields_ = [("ms_default", ctypes.c_double), ("ms_tuned", ctypes.c_double), ("gemm_steps", ctypes.c_int32),
+                ("changed", ctypes.c_int32), ("passes", ctypes.c_int32), ("by_kind", ctypes.c_int32 * 4)]
 
 
 class nd_plan_info(ctypes.Structure):
@@ -93,6 +98,7 @@ def lib():
             "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
             "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
             "nd_fact_set_wait_limit": ([_P, _I64], _I32),
+            "nd_autotune": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _I32, _D, _I32, _P, _P], _I32),
             "nd_certificate": ([_P, _P, _P], _I32),
             "nd_selected_entries": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P], _I32),
             "nd_density": ([_P, _P, _I32, _I32, _D, _I32, _P, _P], _I32),
@@ -322,6 +328,19 @@ def nd_fact_status(fact: Fact) -> int:
 def nd_fact_set_wait_limit(fact: Fact, polls: int):
     """Polls before a tensor-core wait gives up (0 = default)."""
     _check(lib().nd_fact_set_wait_limit(fact.ptr, int(polls)), "nd_fact_set_wait_limit")
+
+
+def nd_autotune(fact: Fact, H_values, sigma_r, sigma_ph_r, sigma_lesser, sigma_greater, ph_lesser, ph_greater,
+                energies, n_e: int, eta: float, reps: int = 1, stream=None) -> dict:
+    """Measured kernel choice per GEMM launch (see ndgf.h); returns nd_tune_info as a dict."""
+    keep = []
+    info = nd_tune_info()
+    _check(lib().nd_autotune(fact.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), _ptr(sigma_ph_r, keep),
+                             _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep), _ptr(ph_lesser, keep),
+                             _ptr(ph_greater, keep), _ptr(energies, keep), n_e, eta, reps, ctypes.byref(info),
+                             _stream(stream)), "nd_autotune")
+    return {"ms_default": info.ms_default, "ms_tuned": info.ms_tuned, "gemm_steps": info.gemm_steps,
+            "changed": info.changed, "passes": info.passes, "by_kind": list(info.by_kind)}
 
 
 def nd_lead_create(H00, H01, tau) -> Lead:

@@ -128,6 +128,17 @@ class Solver:
                            self.Gr, self.Gl if lesser else None, self.Gg if lesser else None)
         return self.Gr[:n_e], self.Gl[:n_e], self.Gg[:n_e]
 
+    def autotune(self, energies, reps: int = 1) -> dict:
+        """nd_autotune on these energies (at most max_ne): each GEMM launch of
+        the fold and the extraction takes the kernel measured fastest on this
+        workload for all later steps.  Returns the tuning summary."""
+        n_e = len(energies)
+        E = self.E[:n_e]
+        E.copy_(energies if isinstance(energies, torch.Tensor) else torch.as_tensor(np.asarray(energies, dtype=np.float64)))
+        self._self_energies(n_e)
+        return ndgf.nd_autotune(self.fact, self.H, self.sig_r if self.leads else None, self.ph_r, self.sig_l,
+                                self.sig_g, self.ph_l, self.ph_g, E, n_e, self.tr.eta, reps)
+
     def scba(self, energies, D: float, *, mix: float = 1.0, updates: int | None = None, tol: float = 1e-13,
              max_updates: int = 2000):
         """Self-consistent Born iteration of an elastic local phonon self-energy,

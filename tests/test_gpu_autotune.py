@@ -1,0 +1,70 @@
+"""The kernel autotuner (nd_autotune): every GEMM launch of the fold and the
+extraction is timed with each candidate kernel (default rules, large and
+small tile, tensor cores for FP32 pairs, one CTA per block) and keeps the
+fastest.  After tuning, the results still match the oracle (paper
+Eq. (1)-(2)) at the path's tolerance, on one device and on an uneven batch of
+devices in one graph; the summary reports the launches tuned and the passes
+run."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dense, observables  # noqa: E402
+from paper_1305_1070_gb300 import build, ndgf, tune, workloads  # noqa: E402
+from paper_1305_1070_gb300.solver import Solver  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+
+
+def _check(s, dev, tr, devs=None, tol=1e-9):
+    Gr, Gl, Gg = s.step(tr.energies)
+    torch.cuda.synchronize()
+    assert ndgf.nd_fact_status(s.fact) == 0
+    got = {"Gr": Gr.cpu().numpy(), "Gl": Gl.cpu().numpy(), "Gg": Gg.cpu().numpy()}
+    parts = [(dev, 0, dev.n)] if devs is None else [(d, dev.site_offsets[i], dev.site_offsets[i + 1])
+                                                      for i, d in enumerate(devs)]
+    for sub, lo, hi in parts:
+        ref = dense.green_diag(sub, tr)
+        for k in ("Gr", "Gl", "Gg"):
+            for e in range(tr.n_e):
+                assert observables.rel_err(got[k][e, lo:hi], ref[k][e]) <= tol, (k, e)
+
+
+@pytest.mark.parametrize("precision,tol", [(ndgf.ND_PREC_FP64, 1e-10), (ndgf.ND_PREC_FP32X2, 1e-9)])
+def test_autotune_single_device(precision, tol):
+    dev = workloads.superlattice(40, 12, disorder=0.03, seed=21)
+    tr = workloads.Transport(energies=np.linspace(0.03, 0.47, 5), gamma_ph=2e-3, mu_ph=0.05)
+    s = Solver(dev, tr, precision=precision, leaf_size=10, delay=2)
+    info = s.autotune(tr.energies)
+    print(f"  tuner precision {precision}: {info}")
+    assert info["passes"] == 5 and info["gemm_steps"] > 0
+    assert sum(info["by_kind"]) == info["gemm_steps"]
+    assert info["ms_tuned"] <= info["ms_default"] * 1.0001
+    _check(s, dev, tr, tol=tol)
+
+
+def test_autotune_uneven_batch():
+    devs = [workloads.superlattice(L, W, disorder=0.02, seed=L) for L, W in ((12, 4), (20, 8), (9, 6), (16, 5))]
+    dev = workloads.union(devs)
+    tr = workloads.Transport(energies=np.array([0.04, 0.21, 0.43]), mu=(0.25, 0.0), kT=0.03)
+    s = Solver(dev, tr, precision=ndgf.ND_PREC_FP32X2, leaf_size=16, delay=2)
+    info = s.autotune(tr.energies)
+    assert info["gemm_steps"] > 0
+    _check(s, dev, tr, devs=devs)
+
+
+def test_plan_search_small():
+    dev = workloads.superlattice(32, 8, disorder=0.02, seed=4)
+    tr = workloads.Transport(energies=np.linspace(0.05, 0.45, 8))
+    best, table, s = tune.tune_plan(dev, tr, precision=ndgf.ND_PREC_FP32X2, delay=2, leafs=(8, 16), chunks=(4, 8))
+    assert len(table) == 4 and best["leaf"] in (8, 16) and best["chunk"] in (4, 8)
+    assert s.max_ne == best["chunk"]
+    _check(s, dev, workloads.Transport(energies=tr.energies[:best["chunk"]]))

@@ -1,7 +1,8 @@
 """Parity at the benchmark's own configuration: the 512 x 128 superlattice,
 256 energies in two calls of 128, leaf 16, 2 delayed pivots per cluster and the
-default kernel routing (direct, tiled and tensor-core GEMM launches chosen per
-launch), for the FP32-pair path and the complex128 path.
+kernel of every GEMM launch measured by the autotuner on this workload, as the
+benchmark does (direct, tiled or tensor-core launches), for the FP32-pair path
+and the complex128 path.
 
 - diag G^r and G^< against the oracle's block RGF (paper Eq. (1)-(2)) at 7
   energies, among them the indices 97, 205 and 255 where the paper's plain
@@ -48,6 +49,7 @@ def runs():
     out = {}
     for name, prec in (("fp64", ndgf.ND_PREC_FP64), ("fp32x2", ndgf.ND_PREC_FP32X2)):
         s = Solver(dev, tr, precision=prec, max_ne=CHUNK, delay=DELAY, leaf_size=LEAF)
+        print(f"  {name} kernel tuner: {s.autotune(E[:CHUNK])}")  # as the benchmark does before timing
         Gr = torch.zeros(tr.n_e, dev.n, dtype=torch.complex128, device="cuda")
         Gl = torch.zeros_like(Gr)
         cert = torch.zeros(tr.n_e, 8, dtype=torch.float64, device="cuda")
