@@ -27,6 +27,13 @@ precision).  Contents:
 * ``scba``       -- self-consistent Born iteration of an elastic local phonon
                     self-energy (Sigma_ph,jj = D G_jj), densely per energy.
 * ``observables`` -- density, terminal current, transmission, error metric.
+* ``response``   -- the density with an on-site potential U and its Jacobian
+                    dn/dU from the dense definition, and the per-energy terms
+                    of the adjoint (c^T dn/dU) and forward ((dn/dU) v) products.
+* ``poisson``    -- the five-point Poisson operator of the self-consistent
+                    loop (Dirichlet at the transport ends, Neumann at the edges).
+* ``sp``         -- Newton iteration of the Schroedinger-Poisson problem with
+                    the dense Jacobian.
 * ``transfer``   -- 2x2 transfer-matrix transmission of a 1D chain, an
                     independent textbook method used to pin the oracle.
 

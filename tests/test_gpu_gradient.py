@@ -1,8 +1,8 @@
 """Adjoint of the density (nd_density_gradient and autograd.density) against
 the oracle.
 
-For L = sum_j c_j n_j and H_kk = H0_kk + V_k, the dense oracle gives
-dL/dV_k from the full G^r and Sigma^<:
+For L = sum_j c_j n_j and H_kk = H0_kk + V_k, the dense oracle
+(oracle.response.adjoint_terms) gives dL/dV_k from the full G^r and Sigma^<:
     t_k = sum_{a,b in contacts} Sigma^<_ab conj(U_kb) conj(Z_ka),
     U = G^r[:, contacts],  Z = G^r diag(c) conj(U),
     dL/dV_k = (2/pi) sum_e w_e Im t_k(E_e),
@@ -18,7 +18,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
-from oracle import dense  # noqa: E402
+from oracle import dense, response  # noqa: E402
 from paper_1305_1070_gb300 import build, ndgf, workloads  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -32,22 +32,7 @@ def _lib():
 
 
 def _t_oracle(dev, tr, c):
-    out = []
-    cont = np.concatenate(dev.contacts)
-    for E in tr.energies:
-        f = dense.green_full(dev, tr, float(E))
-        G, t = f["Gr"], f["terms"]
-        U = G[:, cont]
-        Z = G @ (c[:, None] * U.conj())
-        M = len(cont)
-        S = np.zeros((M, M), complex)
-        o = 0
-        for ci, idx in enumerate(dev.contacts):
-            m = len(idx)
-            S[o:o + m, o:o + m] = t.sigma_lesser[ci]
-            o += m
-        out.append(np.einsum("ab,kb,ka->k", S, U.conj(), Z.conj()))
-    return np.array(out)
+    return response.adjoint_terms(dev, tr, c)
 
 
 def _dev():
