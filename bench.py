@@ -95,7 +95,8 @@ def parse():
     ap.add_argument("--chunk-x2", type=int, default=128, help="energies per call of the FP32-pair path")
     ap.add_argument("--leaf", type=int, default=16, help="leaf size of the nested-dissection tree")
     ap.add_argument("--chunk-aux", type=int, default=0, help="energies per call for the other workloads (0: default)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "uneven_64", "cnt_10_0_400", "gradient_256x64"],
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "uneven_64", "cnt_10_0_400", "gradient_256x64", "newton_256x64"],
                     help="the headline workload, or another one (its own JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
     ap.add_argument("--growth-max", type=float, default=10.0, help="fold growth above which fp32x2 redoes in FP64")
@@ -767,6 +768,59 @@ def main_gradient(a) -> None:
     print(json.dumps(line), flush=True)
 
 
+def main_newton(a) -> None:
+    """Row c5, second half: 10 Newton steps of the self-consistent
+    Schroedinger-Poisson problem on the 256 x 64 superlattice (128 energies in
+    [-0.6, 0.5] eV, eta = 9 meV: workload superlattice_256x64_sp), F(U) = K U - lam (n(U) - nD) with the five-point Poisson
+    operator (Dirichlet at the ends, Neumann at the edges), lam = e^2 / (eps0
+    eps_r a) = 2.805 eV per electron (eps_r = 12.9, a = 0.5 nm) and nD the
+    flat-band density averaged over each superlattice period; each step is GMRES on J = K - lam dn/dU with
+    the forward density products of nd_density_jvp, preconditioned by the
+    direct solve of the screened Poisson operator, with step halving when the
+    full step does not lower |F|.  FP32 pairs with delayed pivots.  Prints its own
+    JSON line (seconds per Newton step, |F| per step, GMRES iterations)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1070_gb300 import ndgf, sp, workloads
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev, tr = workloads.workload("superlattice_256x64_sp")
+    lam = 1.439964 * 4.0 * np.pi / (12.9 * 0.5)
+    steps = 10
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    run = sp.SchrodingerPoisson(dev, tr, 256, 64, lam, 0.0, precision=ndgf.ND_PREC_FP32X2, delay=a.delay,
+                                leaf_size=a.leaf, chunk=32, gmres_tol=1e-10, gmres_max=60)
+    # background charge: the flat-band density averaged over each 4 nm period of
+    # the superlattice (8 columns) and across the width, so each period is
+    # neutral and the screening moves charge from the wells into the barriers
+    n0 = run.density(run.U, run.dens).cpu().numpy().reshape(256, 64)
+    nD = np.repeat(n0.reshape(32, 8 * 64).mean(axis=1), 8 * 64)
+    run.nD.copy_(torch.as_tensor(nD, device="cuda"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    its, res, kry, lens = run.newton(steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    clocks = clk.stop()
+    line = {"metric": "seconds per Newton Schroedinger-Poisson step, 256 x 64 superlattice, 128 energies (mixed)",
+            "value": round(dt / steps, 3), "unit": "s/step", "n_gpus": 1, "steps": steps, "warmup": 0,
+            "ms_per_step": round(1e3 * dt / steps, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp32x2 (FP32-pair complex) + c128 root", "data": "synthetic (seeded "
+            "256 x 64 superlattice, PCG64 seed 1309)",
+            "config": {"workload": "newton_256x64", "sites": dev.n, "energies": tr.n_e, "lam_eV": round(lam, 4),
+                       "energy_window_eV": [float(tr.energies[0]), float(tr.energies[-1])], "eta_eV": tr.eta,
+                       "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": 32,
+                       "gmres_tol": 1e-10},
+            "residual_norm_per_step": [float(f"{r:.4g}") for r in res], "gmres_iterations": kry,
+            "step_lengths": lens,
+            "potential_range_eV": [float(its[-1].min()), float(its[-1].max())], "clocks": clocks,
+            "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 def main_reference(a) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -799,6 +853,8 @@ if __name__ == "__main__":
         main_reference(args)
     elif args.workload == "gradient_256x64":
         main_gradient(args)
+    elif args.workload == "newton_256x64":
+        main_newton(args)
     elif args.workload != WORKLOAD:
         main_aux(args)
     else:

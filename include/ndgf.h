@@ -287,6 +287,51 @@ nd_status nd_selected_entries(nd_fact* fact, const int32_t* x, const int32_t* y,
  * Errors: ND_ERR_INVALID_ARG, ND_ERR_UNSUPPORTED. */
 nd_status nd_density_gradient(nd_fact* fact, const double* c, double* t_out, void* stream);
 
+/* Forward (directional) derivative of the density, for Newton steps of the
+ * self-consistent loop (spec extension): for a potential change v of
+ * the on-site energies (H_kk = H0_kk + V_k), every energy of the last
+ * nd_factor / nd_diag_green and every site j,
+ *     T_j(E) = sum_{a,b in contacts} W_ja Sigma^<_ab conj(U_jb),
+ *     U = G^r[:, contact sites],  W = G^r diag(v) U,
+ * so that with n_j = (1/pi) sum_E w_E Im G^<_jj(E):
+ *     (dn/dV v)_j = (2/pi) sum_E w_E Im T_j(E)      (nd_density with scale 2/pi)
+ * (dG^r = G^r diag(v) G^r and dG^< = dG^r Sigma^< G^a + G^r Sigma^< dG^a, paper
+ * Eq. (1)-(2)).  U is solved once per factorization and kept, so later calls
+ * on the same factorization (and nd_density_gradient) take one solve each.
+ * v: [n] real (host or device, caller order); t_out: device [n_e][n] complex.
+ * Same requirements and errors as nd_density_gradient. */
+nd_status nd_density_jvp(nd_fact* fact, const double* v, double* t_out, void* stream);
+
+/* ---- Poisson operator of the self-consistent loop (spec extension) ----
+ * On an nx (transport) x ny (transverse) grid, site (x, y) = x * ny + y:
+ *     (K u)_j = sum_{k neighbour of j} (u_j - u_k),
+ * u = 0 on ghost columns x = -1 and x = nx (Dirichlet at the ends, the leads'
+ * potential) and no neighbours across the edges y = 0, ny - 1 (Neumann).  K is
+ * symmetric positive definite.  nd_poisson_apply: out = K u; nd_poisson_solve:
+ * (K + shift I) u = rhs, shift >= 0 (the screened operator of a Newton
+ * preconditioner), directly (cosine transform along y, one tridiagonal solve
+ * per mode along x, transform back), FP64.  Arrays are device [batch][nx * ny]
+ * doubles; work memory grows on demand inside the handle.  The paper motivates
+ * the density by Poisson's equation (Sec. 1) but gives no electrostatics.
+ * Errors: ND_ERR_INVALID_ARG (sizes, host arrays), ND_ERR_OOM, ND_ERR_CUDA. */
+typedef struct nd_poisson nd_poisson;
+nd_status nd_poisson_create(int32_t nx, int32_t ny, nd_poisson** out);
+nd_status nd_poisson_apply(nd_poisson* poisson, const double* u, double* out, int32_t batch, void* stream);
+nd_status nd_poisson_solve(nd_poisson* poisson, double shift, const double* rhs, double* u, int32_t batch,
+                           void* stream);
+void nd_poisson_destroy(nd_poisson* poisson);
+
+/* Vector operations of the Newton-Krylov iteration (device arrays of n
+ * doubles): *out = sum_i x_i y_i (a fixed reduction order, so repeated calls
+ * agree bit for bit; out is a device double), y = a x + b y (b = 0
+ * overwrites y), and the elementwise product.  Errors: ND_ERR_INVALID_ARG
+ * (host arrays, n < 0). */
+nd_status nd_vec_dot(const double* x, const double* y, int64_t n, double* out, void* stream);
+nd_status nd_vec_axpby(double a, const double* x, double b, double* y, int64_t n, void* stream);
+/* y_i = d_i x_i, and y_i = max(0, a x_i) (device arrays of n doubles; y may alias x). */
+nd_status nd_vec_mul(const double* d, const double* x, double* y, int64_t n, void* stream);
+nd_status nd_vec_scale_pos(double a, const double* x, double* y, int64_t n, void* stream);
+
 /* S10 terminal current spectrum of one contact (Meir-Wingreen; paper Sec. 1,
  * the current is the physical output next to the density):
  *     i_c(E) = Tr[Sigma^<_c(E) G^>_cc(E) - Sigma^>_c(E) G^<_cc(E)]

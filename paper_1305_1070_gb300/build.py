@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libndgf.so")
-SOURCES = ["nd_plan.cpp", "nd_schedule.cpp", "nd_api.cu", "nd_kernels.cu", "nd_gemm_tc.cu", "nd_noalloc.cu", "nd_check.cu"]
+SOURCES = ["nd_plan.cpp", "nd_schedule.cpp", "nd_api.cu", "nd_kernels.cu", "nd_gemm_tc.cu", "nd_noalloc.cu", "nd_check.cu", "nd_sp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

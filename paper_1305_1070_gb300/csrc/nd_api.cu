@@ -146,6 +146,7 @@ struct nd_fact {
   double* d_cvec = nullptr;
   bool have_lesser = false;
   bool have_green = false;  // an nd_diag_green followed the last nd_factor
+  bool adj_u_valid = false;  // the adjoint region holds U = G^r E_C of the current factorization
   const double* last_gl = nullptr;  // device diag G^< of the last nd_diag_green (the caller's array or staging)
   double *d_w = nullptr, *d_dens = nullptr;  // nd_fact_density: weights [max_ne], density [n]
   double* d_cert = nullptr;
@@ -853,6 +854,7 @@ extern "C" nd_status nd_factor(nd_fact* f, const double* H_values, const double*
   f->cur_E = E;
   f->have_lesser = false;
   f->have_green = false;
+  f->adj_u_valid = false;
   f->last_gl = nullptr;
   ND_CUDA(cudaMemsetAsync(f->d_status, 0, sizeof(int), s));
   ND_CUDA(cudaMemsetAsync(f->d_tc_timeout, 0, sizeof(int), s));
@@ -1072,25 +1074,32 @@ extern "C" nd_status nd_contact_current(nd_fact* f, int32_t contact, double* cur
   return ND_OK;
 }
 
+// The two solves with the stored factorization behind nd_density_gradient
+// (adjoint) and nd_density_jvp (forward): U = G^r E_C (unit right-hand sides
+// at the contact sites; kept for the later calls on the same factorization),
+// then G^r diag(c) conj(U) or G^r diag(c) U, and the contraction with Sigma^<.
 template <typename T>
-static nd_status density_gradient_t(nd_fact* f, const double* c, double* t_out, cudaStream_t s) {
+static nd_status adjoint_t(nd_fact* f, const double* c, double* t_out, bool forward, cudaStream_t s) {
   const nd_plan* p = f->plan;
   Work w{f->arena, f->se, f->aux, 2 * p->sigma_elems, f->n_e};
   const int M = p->adj_cols;
   nd_status st;
-  // U = G^r E_C: unit right-hand sides at the contact sites
-  Kern<T>::zero_range(w, f->adj_base, p->adj_elems, s);
-  Kern<T>::adj_ones(w, f->d_ones, f->n_ones, s);
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass == 1)  // Z = G^r diag(c) conj(U)
-      Kern<T>::adj_mid(w, f->d_adj_desc, f->n_adj_desc, M, c, f->d_sites, f->dt, s);
-    if ((st = run_schedule<T>(f, f->sched_adj_fwd, f->tr_adj_fwd, w, nullptr, nullptr, s, 0,
-                              &f->step_flops_adj_fwd)) != ND_OK)
-      return st;
-    if ((st = run_schedule<T>(f, f->sched_adj_bwd, f->tr_adj_bwd, w, nullptr, nullptr, s, 0,
-                              &f->step_flops_adj_bwd)) != ND_OK)
-      return st;
+  auto solve = [&]() -> nd_status {
+    nd_status r;
+    if ((r = run_schedule<T>(f, f->sched_adj_fwd, f->tr_adj_fwd, w, nullptr, nullptr, s, 0,
+                             &f->step_flops_adj_fwd)) != ND_OK)
+      return r;
+    return run_schedule<T>(f, f->sched_adj_bwd, f->tr_adj_bwd, w, nullptr, nullptr, s, 0, &f->step_flops_adj_bwd);
+  };
+  const bool cached = f->adj_u_valid;
+  if (!cached) {
+    Kern<T>::zero_range(w, f->adj_base, p->adj_elems, s);
+    Kern<T>::adj_ones(w, f->d_ones, f->n_ones, s);
+    if ((st = solve()) != ND_OK) return st;
   }
+  Kern<T>::adj_mid(w, f->d_adj_desc, f->n_adj_desc, M, c, f->d_sites, f->dt, (forward ? 1 : 0) | (cached ? 2 : 0), s);
+  if ((st = solve()) != ND_OK) return st;
+  f->adj_u_valid = true;
   ContactTable ct{};
   ct.n = p->n_contacts;
   for (int k = 0; k < p->n_contacts; ++k) {
@@ -1098,27 +1107,35 @@ static nd_status density_gradient_t(nd_fact* f, const double* c, double* t_out, 
     ct.off[k] = p->contact_soff[k];
   }
   Kern<T>::adj_contract(w, f->d_adj_desc, f->n_adj_desc, M, ct, f->cur_sl, p->sigma_elems, f->d_sites, f->dt, t_out,
-                        p->n, s);
+                        p->n, forward ? 1 : 0, s);
   ND_CUDA(cudaGetLastError());
   return ND_OK;
 }
 
-extern "C" nd_status nd_density_gradient(nd_fact* f, const double* c, double* t_out, void* stream) {
-  if (!f || !c || !t_out) return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: NULL argument");
+static nd_status adjoint_call(nd_fact* f, const double* c, double* t_out, bool forward, cudaStream_t s,
+                              const char* name) {
+  const std::string nm(name);
+  if (!f || !c || !t_out) return fail(ND_ERR_INVALID_ARG, nm + ": NULL argument");
   const nd_plan* p = f->plan;
-  if (!f->adj) return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: workspace created without ND_FACT_ADJOINT");
+  if (!f->adj) return fail(ND_ERR_INVALID_ARG, nm + ": workspace created without ND_FACT_ADJOINT");
   if (f->n_e <= 0 || !f->have_lesser || !f->cur_sl)
-    return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: needs a preceding nd_diag_green with Sigma^<");
-  if (f->cur_pl) return fail(ND_ERR_UNSUPPORTED, "nd_density_gradient: phonon Sigma^< is not supported");
-  if (p->n_contacts < 1 || p->n_contacts > MAX_CONTACTS)
-    return fail(ND_ERR_UNSUPPORTED, "nd_density_gradient: needs 1 to 8 contacts");
-  if (!is_device_ptr(t_out)) return fail(ND_ERR_INVALID_ARG, "nd_density_gradient: t_out must be a device array");
-  cudaStream_t s = (cudaStream_t)stream;
+    return fail(ND_ERR_INVALID_ARG, nm + ": needs a preceding nd_diag_green with Sigma^<");
+  if (f->cur_pl) return fail(ND_ERR_UNSUPPORTED, nm + ": phonon Sigma^< is not supported");
+  if (p->n_contacts < 1 || p->n_contacts > MAX_CONTACTS) return fail(ND_ERR_UNSUPPORTED, nm + ": needs 1 to 8 contacts");
+  if (!is_device_ptr(t_out)) return fail(ND_ERR_INVALID_ARG, nm + ": t_out must be a device array");
   ND_CUDA(cudaMemcpyAsync(f->d_cvec, c, size_t(p->n) * sizeof(double),
                           is_device_ptr(c) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  if (f->precision == ND_PREC_FP64) return density_gradient_t<double>(f, f->d_cvec, t_out, s);
-  if (f->precision == ND_PREC_MIXED) return density_gradient_t<float>(f, f->d_cvec, t_out, s);
-  return density_gradient_t<DF>(f, f->d_cvec, t_out, s);
+  if (f->precision == ND_PREC_FP64) return adjoint_t<double>(f, f->d_cvec, t_out, forward, s);
+  if (f->precision == ND_PREC_MIXED) return adjoint_t<float>(f, f->d_cvec, t_out, forward, s);
+  return adjoint_t<DF>(f, f->d_cvec, t_out, forward, s);
+}
+
+extern "C" nd_status nd_density_jvp(nd_fact* f, const double* v, double* t_out, void* stream) {
+  return adjoint_call(f, v, t_out, true, (cudaStream_t)stream, "nd_density_jvp");
+}
+
+extern "C" nd_status nd_density_gradient(nd_fact* f, const double* c, double* t_out, void* stream) {
+  return adjoint_call(f, c, t_out, false, (cudaStream_t)stream, "nd_density_gradient");
 }
 
 extern "C" nd_status nd_profile_launches(nd_fact* f, nd_launch_stats* out, int32_t max_out, int32_t* n_out) {

@@ -1189,10 +1189,14 @@ __global__ void k_set_one(const int64_t* __restrict__ offs, int count, cx<T>* ar
     base[offs[i]] = O<T>::from_d2(make_double2(1.0, 0.0));
 }
 
-// Between the two solves of one cluster: U = XS, XI = c_site conj(XS), RB = 0.
+// Between the two solves of one cluster (and RB = 0).
+// Right-hand side of the second solve from the first one's solution U:
+// diag(c) conj(U) (adjoint, mode bit 0 clear) or diag(c) U (forward, bit 0
+// set); U is XS of the first solve, saved here (bit 1 clear), or the copy an
+// earlier call saved (bit 1 set).
 template <typename T>
 __global__ void k_adj_mid(const AdjDesc* __restrict__ descs, cx<T>* arena, int64_t se, int M,
-                          const double* __restrict__ c, const int32_t* __restrict__ sites, DelayTabs dt) {
+                          const double* __restrict__ c, const int32_t* __restrict__ sites, DelayTabs dt, int mode) {
   const AdjDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   cx<T>* base = arena + int64_t(e) * se;
@@ -1200,21 +1204,27 @@ __global__ void k_adj_mid(const AdjDesc* __restrict__ descs, cx<T>* arena, int64
   for (int64_t idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int r = int(idx / M);
     const int site = dt.rsite ? dt.rsite[int64_t(e) * dt.n_unk + d.site_begin + r] : sites[d.site_begin + r];
-    const cx<T> x = base[d.off_XS + idx];
-    base[d.off_U + idx] = x;
-    base[d.off_XI + idx] = O<T>::scale(O<T>::conj(x), c[site]);
+    cx<T> x;
+    if (mode & 2) {
+      x = base[d.off_U + idx];
+    } else {
+      x = base[d.off_XS + idx];
+      base[d.off_U + idx] = x;
+    }
+    base[d.off_XI + idx] = O<T>::scale((mode & 1) ? x : O<T>::conj(x), c[site]);
   }
   const int64_t tb = int64_t(d.b) * M;
   for (int64_t idx = threadIdx.x; idx < tb; idx += blockDim.x) base[d.off_RB + idx] = O<T>::zero();
 }
 
-// t_k = sum_{a,b} Sigma^<_ab conj(U_kb) conj(Z_ka) over the contact blocks,
-// for every eliminated row k of one cluster (Z = XS of the second solve);
-// one warp per row, in complex128.
+// Adjoint (forward = 0): t_k = sum_{a,b} Sigma^<_ab conj(U_kb) conj(Z_ka);
+// forward (forward = 1): T_k = sum_{a,b} W_ka Sigma^<_ab conj(U_kb); over the
+// contact blocks, for every eliminated row k of one cluster (Z or W = XS of
+// the second solve); one warp per row, in complex128.
 template <typename T>
 __global__ void k_adj_contract(const AdjDesc* __restrict__ descs, const cx<T>* arena, int64_t se, int M,
                                ContactTable ct, const double2* __restrict__ sl, int64_t sstride,
-                               const int32_t* __restrict__ sites, DelayTabs dt, double2* out, int n) {
+                               const int32_t* __restrict__ sites, DelayTabs dt, double2* out, int n, int forward) {
   const AdjDesc d = descs[blockIdx.x];
   const int e = blockIdx.y;
   const cx<T>* base = arena + int64_t(e) * se;
@@ -1237,8 +1247,13 @@ __global__ void k_adj_contract(const AdjDesc* __restrict__ descs, const cx<T>* a
           sr += s.x * u.x + s.y * u.y;
           si += s.y * u.x - s.x * u.y;
         }
-        re += sr * za.x + si * za.y;  // (sr + i si) conj(za)
-        im += si * za.x - sr * za.y;
+        if (forward) {  // (sr + i si) za
+          re += sr * za.x - si * za.y;
+          im += si * za.x + sr * za.y;
+        } else {  // (sr + i si) conj(za)
+          re += sr * za.x + si * za.y;
+          im += si * za.x - sr * za.y;
+        }
       }
       col0 += m;
     }
@@ -1286,18 +1301,18 @@ void Kern<T>::adj_ones(const Work& w, const int64_t* offs, int count, cudaStream
 
 template <typename T>
 void Kern<T>::adj_mid(const Work& w, const AdjDesc* d, int count, int M, const double* c, const int32_t* sites,
-                      const DelayTabs& dt, cudaStream_t s) {
+                      const DelayTabs& dt, int mode, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
-  k_adj_mid<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, M, c, sites, dt);
+  k_adj_mid<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (cx<T>*)w.arena, w.se, M, c, sites, dt, mode);
 }
 
 template <typename T>
 void Kern<T>::adj_contract(const Work& w, const AdjDesc* d, int count, int M, const ContactTable& ct,
                            const double* sl, int64_t sstride, const int32_t* sites, const DelayTabs& dt,
-                           double* out, int n, cudaStream_t s) {
+                           double* out, int n, int forward, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
   k_adj_contract<T><<<dim3(count, w.n_e), 256, 0, s>>>(d, (const cx<T>*)w.arena, w.se, M, ct, (const double2*)sl,
-                                                       sstride, sites, dt, (double2*)out, n);
+                                                       sstride, sites, dt, (double2*)out, n, forward);
 }
 
 // Dynamic shared memory limits of every kernel that may need more than 48 KB

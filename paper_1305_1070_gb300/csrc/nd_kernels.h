@@ -95,10 +95,10 @@ struct Kern {
   static void adj_ones(const Work& w, const int64_t* offs, int count, cudaStream_t s);
   static void zero_range(const Work& w, int64_t off, int64_t count, cudaStream_t s);
   static void adj_mid(const Work& w, const AdjDesc* d, int count, int M, const double* c, const int32_t* sites,
-                      const DelayTabs& dt, cudaStream_t s);
+                      const DelayTabs& dt, int mode, cudaStream_t s);
   static void adj_contract(const Work& w, const AdjDesc* d, int count, int M, const ContactTable& ct,
                            const double* sl, int64_t sstride, const int32_t* sites, const DelayTabs& dt, double* out,
-                           int n, cudaStream_t s);
+                           int n, int forward, cudaStream_t s);
   static void current(const Work& w, int64_t offPl, int64_t offPg, int ld, int row0, int m, const double* sl,
                       const double* sg, int64_t sstride, int64_t soff, double* out, double* out_im, cudaStream_t s);
   // tile edge (BM = BN) of the large and the small GEMM configuration

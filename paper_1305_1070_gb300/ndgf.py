@@ -33,7 +33,9 @@ EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const", "nd_phonon_scba",
-           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_autotune", "nd_last_error",
+           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_autotune", "nd_density_jvp", "nd_poisson_create",
+           "nd_poisson_apply", "nd_poisson_solve", "nd_poisson_destroy", "nd_vec_dot", "nd_vec_axpby", "nd_vec_mul", "nd_vec_scale_pos",
+           "nd_last_error",
            "nd_version"]
 
 
@@ -110,6 +112,15 @@ def lib():
             "nd_lead_status": ([_P, ctypes.POINTER(_I32), ctypes.POINTER(_I32)], _I32),
             "nd_contact_current": ([_P, _I32, _P, _P, _P], _I32),
             "nd_density_gradient": ([_P, _P, _P, _P], _I32),
+            "nd_density_jvp": ([_P, _P, _P, _P], _I32),
+            "nd_poisson_create": ([_I32, _I32, ctypes.POINTER(_P)], _I32),
+            "nd_poisson_apply": ([_P, _P, _P, _I32, _P], _I32),
+            "nd_poisson_solve": ([_P, _D, _P, _P, _I32, _P], _I32),
+            "nd_poisson_destroy": ([_P], None),
+            "nd_vec_dot": ([_P, _P, _I64, _P, _P], _I32),
+            "nd_vec_axpby": ([_D, _P, _D, _P, _I64, _P], _I32),
+            "nd_vec_mul": ([_P, _P, _P, _I64, _P], _I32),
+            "nd_vec_scale_pos": ([_D, _P, _P, _I64, _P], _I32),
             "nd_profile_launches": ([_P, _P, _I32, ctypes.POINTER(_I32)], _I32),
             "nd_lead_destroy": ([_P], None),
             "nd_sigma_lesser_fermi": ([_P, _I32, _I32, _P, _P, _D, _P, _P, _P, _P], _I32),
@@ -189,6 +200,10 @@ class Fact(_Handle):
 
 class Lead(_Handle):
     _destroy = "nd_lead_destroy"
+
+
+class Poisson(_Handle):
+    _destroy = "nd_poisson_destroy"
 
 
 def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=None, leaf_size=0,
@@ -341,6 +356,49 @@ def nd_autotune(fact: Fact, H_values, sigma_r, sigma_ph_r, sigma_lesser, sigma_g
                              _stream(stream)), "nd_autotune")
     return {"ms_default": info.ms_default, "ms_tuned": info.ms_tuned, "gemm_steps": info.gemm_steps,
             "changed": info.changed, "passes": info.passes, "by_kind": list(info.by_kind)}
+
+
+def nd_density_jvp(fact: Fact, v, t_out, stream=None):
+    """Forward terms T[e][j] of the density's derivative along v (see ndgf.h)."""
+    keep = []
+    _check(lib().nd_density_jvp(fact.ptr, _ptr(v, keep), _ptr(t_out, keep), _stream(stream)), "nd_density_jvp")
+
+
+def nd_poisson_create(nx: int, ny: int) -> Poisson:
+    out = _P()
+    _check(lib().nd_poisson_create(nx, ny, ctypes.byref(out)), "nd_poisson_create")
+    return Poisson(out.value)
+
+
+def nd_poisson_apply(p: Poisson, u, out, batch: int = 1, stream=None):
+    keep = []
+    _check(lib().nd_poisson_apply(p.ptr, _ptr(u, keep), _ptr(out, keep), batch, _stream(stream)), "nd_poisson_apply")
+
+
+def nd_poisson_solve(p: Poisson, rhs, u, batch: int = 1, shift: float = 0.0, stream=None):
+    keep = []
+    _check(lib().nd_poisson_solve(p.ptr, shift, _ptr(rhs, keep), _ptr(u, keep), batch, _stream(stream)),
+           "nd_poisson_solve")
+
+
+def nd_vec_dot(x, y, n: int, out, stream=None):
+    keep = []
+    _check(lib().nd_vec_dot(_ptr(x, keep), _ptr(y, keep), n, _ptr(out, keep), _stream(stream)), "nd_vec_dot")
+
+
+def nd_vec_axpby(a: float, x, b: float, y, n: int, stream=None):
+    keep = []
+    _check(lib().nd_vec_axpby(a, _ptr(x, keep), b, _ptr(y, keep), n, _stream(stream)), "nd_vec_axpby")
+
+
+def nd_vec_mul(d, x, y, n: int, stream=None):
+    keep = []
+    _check(lib().nd_vec_mul(_ptr(d, keep), _ptr(x, keep), _ptr(y, keep), n, _stream(stream)), "nd_vec_mul")
+
+
+def nd_vec_scale_pos(a: float, x, y, n: int, stream=None):
+    keep = []
+    _check(lib().nd_vec_scale_pos(a, _ptr(x, keep), _ptr(y, keep), n, _stream(stream)), "nd_vec_scale_pos")
 
 
 def nd_lead_create(H00, H01, tau) -> Lead:

@@ -119,10 +119,21 @@ class Solver:
                        E_host, n_e, self.tr.eta)
         ndgf.nd_diag_green(self.fact, self.sig_l, self.sig_g, self.ph_l, self.ph_g, Gr_host, Gl_host, Gg_host)
 
+    def set_potential(self, U):
+        """On-site potential energy U ([n] real, eV, caller order) for the following
+        steps: it enters nd_factor as a real diagonal self-energy term, so that
+        A = (E + i eta) I - H - diag(U) - Sigma (H stays untouched)."""
+        if self.ph:
+            raise ValueError("set_potential with a phonon self-energy is not supported")
+        if not hasattr(self, "pot"):
+            self.pot = torch.zeros(self.max_ne, self.n, dtype=torch.complex128, device=self.device)
+        self.pot.real.copy_(torch.as_tensor(U, dtype=torch.float64, device=self.device).expand(self.max_ne, self.n))
+
     def _solve(self, n_e: int, lesser: bool = True):
         """Fold and diagonals for the energies, contact and phonon self-energies in place."""
         E = self.E[:n_e]
-        ndgf.nd_factor(self.fact, self.H, self.sig_r if self.leads else None, self.ph_r, E, n_e, self.tr.eta)
+        diag = self.ph_r if self.ph else getattr(self, "pot", None)
+        ndgf.nd_factor(self.fact, self.H, self.sig_r if self.leads else None, diag, E, n_e, self.tr.eta)
         ndgf.nd_diag_green(self.fact, self.sig_l if lesser else None, self.sig_g if lesser else None,
                            self.ph_l if lesser else None, self.ph_g if lesser else None,
                            self.Gr, self.Gl if lesser else None, self.Gg if lesser else None)

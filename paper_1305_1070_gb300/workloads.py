@@ -402,6 +402,7 @@ def workload(name: str):
     cnt_10_0_400          : (10,0) tube, 400 cells = 16,000 atoms, disorder +-0.1 eV,
                             phonon broadening 5 meV, 1,024 energies in [-1, 1] eV
     superlattice_256x64   : 256 x 64 = 16,384 sites, disorder +-0.02 eV, 128 energies (density gradient)
+    superlattice_256x64_sp: the same device, 128 energies in [-0.6, 0.5] eV, eta = 9 meV (Schroedinger-Poisson)
     uneven_64             : 64 superlattices in one graph, widths in {16, 32, 64, 96},
                             lengths in [128, 1024], disorder +-0.02 eV, 64 energies in [0, 0.5] eV
     """
@@ -414,6 +415,14 @@ def workload(name: str):
     elif name == "superlattice_256x64":
         dev = superlattice(256, 64, disorder=0.02, seed=SEED_BASE + 4)
         tr = Transport(energies=energy_grid(0.0, 0.5, 128))
+    elif name == "superlattice_256x64_sp":
+        # the self-consistent loop: the window reaches below the flat-band edge
+        # by more than the barrier height (screening pulls the barriers down by
+        # up to ~0.3 eV) and eta is about the grid spacing, so that the
+        # 128-point energy integral resolves the broadened one-dimensional
+        # subband edges and n(U) is smooth in U
+        dev = superlattice(256, 64, disorder=0.02, seed=SEED_BASE + 4)
+        tr = Transport(energies=energy_grid(-0.6, 0.5, 128), eta=9e-3)
     elif name == "uneven_64":
         dev, _ = uneven_batch(64, seed=SEED_BASE + 3)
         tr = Transport(energies=energy_grid(0.0, 0.5, 64))
