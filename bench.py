@@ -405,18 +405,8 @@ def main_ours(a) -> None:
         if extra:
             prof[name + "_fp64_redo"] = extra
 
-    def dominant(pr, peak, label, flop_factor=1.0, note=""):
-        tot = sum(p["ms"] for p in pr) or 1.0
-        top = max(pr, key=lambda p: p["ms"])
-        ach = top["flops"] / (top["ms"] * 1e-3) / 1e12 if top["ms"] > 0 else 0.0
-        kname = f"{label}:{top['name']}"
-        out = {"kernel": kname, "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3),
-               "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": traffic_per_launch(kname),
-               "share": round(top["ms"] / tot, 4), "launches": top["launches"],
-               "ms_per_launch": round(top["ms"] / max(1, top["launches"]), 4)}
-        if note:
-            out["note"] = note
-        return out
+    ALU_NOTE = ("achieved in useful complex flops (8 per complex multiply-add); peak = FP32 rate x 8 / 72 (36 FP32 "
+                "instructions of 2 flops each per complex multiply-add: FP32 pairs, 3-multiplication products)")
 
     def tensor_roof(pr):
         """The tensor-core GEMM launches (FP32 pairs): executed BF16 tensor flops
@@ -435,14 +425,35 @@ def main_ours(a) -> None:
                 "share": round(tc[0]["ms"] / tot, 4), "launches": tc[0]["launches"],
                 "ms_per_launch": round(tc[0]["ms"] / max(1, tc[0]["launches"]), 4),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
-                "note": "achieved = executed BF16 tensor flops of the digit products (21 x useful), unpadded"}
+                "note": "achieved = executed BF16 tensor flops of the digit products (21 x useful), unpadded; the "
+                        "launch time includes the digit split (k_tc_split)"}
 
-    roof = {"fp64_nd": dominant(prof["fp64_nd"], fp64_peak, "complex128"),
-            # one complex multiply-add in FP32 pairs with 3-multiplication products: 36 FP32 instructions
-            "fp32x2": dominant(prof["fp32x2"], fp32_peak * 8.0 / 72.0, "complex-fp32x2",
-                               note="achieved in useful complex flops (8 per complex multiply-add); peak = FP32 rate "
-                                    "x 8 / 72 (36 FP32 instructions of 2 flops each per complex multiply-add: FP32 "
-                                    "pairs, 3-multiplication products)")}
+    def kernel_roofs(pr, alu_peak, label, note=""):
+        """One roofline entry per kernel kind that does arithmetic: the tensor-core
+        GEMM against the BF16 peak, the ALU kernels against the ALU peak of the
+        precision; sorted by time, the first is the dominant kernel."""
+        tot = sum(p["ms"] for p in pr) or 1.0
+        out = []
+        for p in pr:
+            if p["flops"] <= 0 or p["ms"] <= 0:
+                continue
+            if p["name"] == "gemm_tc":
+                out.append(tensor_roof(pr))
+                continue
+            ach = p["flops"] / (p["ms"] * 1e-3) / 1e12
+            kname = f"{label}:{p['name']}"
+            e = {"kernel": kname, "bound": "alu", "achieved": round(ach, 3), "peak": round(alu_peak, 3),
+                 "unit": "TFLOP/s", "frac": round(ach / alu_peak, 4), "traffic": traffic_per_launch(kname),
+                 "share": round(p["ms"] / tot, 4), "launches": p["launches"],
+                 "ms_per_launch": round(p["ms"] / max(1, p["launches"]), 4)}
+            if note:
+                e["note"] = note
+            out.append(e)
+        return sorted(out, key=lambda r: -r["share"])
+
+    roofs = {"fp64_nd": kernel_roofs(prof["fp64_nd"], fp64_peak, "complex128"),
+             "fp32x2": kernel_roofs(prof["fp32x2"], fp32_peak * 8.0 / 72.0, "complex-fp32x2", ALU_NOTE)}
+    roof = {k: v[0] for k, v in roofs.items()}
     roofline = roof[head]
     launches_per_step = launches[head]
 
@@ -551,6 +562,7 @@ def main_ours(a) -> None:
             "paths": paths,
             "current_spectrum_integral_eV": {"L": float((cur[0] * weights).sum()), "R": float((cur[1] * weights).sum())},
             "roofline": roofline,
+            "roofline_kernels": roofs[head],
             "roofline_other": roof["fp64_nd" if head == "fp32x2" else "fp32x2"],
             "roofline_tensor": tensor_roof(prof["fp32x2"]),
             "kernel_profile": prof,
@@ -642,10 +654,13 @@ def main_aux(a) -> None:
         torch.cuda.synchronize()
         prof = ndgf.nd_profile(s.fact, False)
         dens[name] = out.clone()
+        alu = [p for p in prof if p["name"].startswith("gemm") and p["name"] != "gemm_tc"]
         res[name] = {"ms_per_step": round(ms, 1), "points_per_s": round(n_dev * n_e / (ms * 1e-3), 2),
                      "useful_tflops": round((s.info["flops_factor"] + s.info["flops_green_r"] +
                                              s.info["flops_green_lesser"]) * n_e / (ms * 1e-3) / 1e12, 3),
-                     "gemm": [p for p in prof if p["name"] == "gemm"][0]}
+                     "gemm": {"name": "ALU GEMM kernels", "launches": sum(p["launches"] for p in alu),
+                              "ms": sum(p["ms"] for p in alu), "flops": sum(p["flops"] for p in alu)},
+                     "kernel_profile": prof}
         del s
         torch.cuda.empty_cache()
     clocks = clk.stop()

@@ -70,6 +70,9 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
  * (complex128 / FP32 pairs: 32x32 or 16x16; complex64: 64x64 or 32x32). */
 #define ND_FACT_TILE_LARGE 2
 #define ND_FACT_TILE_SMALL 4
+/* Force the extra large tile (64 x 64 with 4 x 4 outputs per thread; 128 x 64
+ * for complex64) on every GEMM launch that is not on the tensor cores. */
+#define ND_FACT_TILE_XL 128
 /* FP32-pair precision only: the Schur products may instead run on the tensor
  * cores (tcgen05), as exact products of 8-bit digits of a 54-bit fixed-point
  * form of each row and column (BF16 in, exact FP32 group sums in tensor
@@ -379,8 +382,9 @@ typedef struct nd_kernel_stats {
 nd_status nd_profile(nd_fact* fact, int32_t enable, nd_kernel_stats* stats, int32_t max_stats, int32_t* n_stats);
 /* The launches recorded since profiling was enabled, one entry each, in launch
  * order (without clearing them; nd_profile clears): step kind (the order of
- * nd_profile's names: 0 inverse, 1 gemm, 2 scatter, ..., 11 loc, 12 gemm_tc =
- * the GEMM launches on the tensor cores), descriptors in the
+ * nd_profile's names: 0 inverse, 1 gemm (large ALU tile), 2 scatter, ..., 11 loc,
+ * 12 gemm_tc (tensor cores), 13 gemm_small, 14 gemm_direct (one CTA per
+ * block), 15 gemm_xl (extra large tile)), descriptors in the
  * launch, largest block edge, energies, CUDA-event time (ms) and algorithmic
  * flops.  n_out receives the number recorded (out may be NULL to query it). */
 typedef struct nd_launch_stats {
@@ -401,22 +405,23 @@ nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
  * Measures, on the given inputs (those of nd_factor and nd_diag_green, host
  * or device), every candidate kernel of every GEMM launch of the fold and the
  * extraction: the default rules, the large and the small tile, the tensor
- * cores (FP32 pairs) and one CTA per block (blocks up to 192): one pass per
- * candidate with all its launches on it, each after an untimed pass, `reps`
- * timed passes averaged, CUDA events on the stream.  Each launch then takes
+ * cores (FP32 pairs), one CTA per block (blocks up to 192) and an extra large
+ * tile (64 x 64, 4 x 4 outputs per thread; 128 x 64 for complex64): one pass
+ * per candidate with all its launches on it, each after an untimed pass,
+ * `reps` timed passes averaged, CUDA events on the stream.  Each launch then takes
  * its fastest kernel for every later call on the handle (the results are
- * the same up to rounding order).  The call runs 5 (reps + 1) factor +
+ * the same up to rounding order).  The call runs 6 (reps + 1) factor +
  * diag_green passes and synchronises the stream; the recorded graphs of
  * ND_FACT_GRAPH are dropped.  The adjoint solves keep the default rules.
  * info (may be NULL): summed GEMM milliseconds of one pass with the default
  * rules and with the chosen kernels, GEMM launches tuned, launches whose
  * kernel changed, passes, and the launches per kernel kind (0 large tile,
- * 1 small tile, 2 tensor cores, 3 one CTA per block).  Errors: those of
+ * 1 small tile, 2 tensor cores, 3 one CTA per block, 4 extra large tile).  Errors: those of
  * nd_factor / nd_diag_green, ND_ERR_INVALID_ARG (reps < 1). */
 typedef struct nd_tune_info {
   double ms_default, ms_tuned;
   int32_t gemm_steps, changed, passes;
-  int32_t by_kind[4];
+  int32_t by_kind[5];
 } nd_tune_info;
 nd_status nd_autotune(nd_fact* fact, const double* H_values, const double* sigma_r, const double* sigma_ph_r,
                       const double* sigma_lesser, const double* sigma_greater, const double* ph_lesser,

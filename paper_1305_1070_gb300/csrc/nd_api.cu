@@ -254,7 +254,7 @@ struct TcTables {
 
 // Kernel of a GEMM step chosen by the tuner (nd_autotune): -1 = the default
 // rules below, else a TileRange kind (0 large tile, 1 small tile, 2 tensor
-// cores, 3 one CTA per block).
+// cores, 3 one CTA per block, 4 extra-large tile).
 using Choice = std::vector<int8_t>;
 
 // Per-energy digit scratch of a step on the tensor cores (bytes).
@@ -267,9 +267,15 @@ int64_t tc_step_scratch(const Step& s, const std::vector<GemmDesc>& gd) {
   return off;
 }
 
-void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, int tile_l, int tile_s, int flags,
+// Tile edges (rows, columns) of the three ALU tile variants: large, small, extra large.
+struct TileShapes {
+  int m[3], n[3];
+};
+
+void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd, const TileShapes& ts, int flags,
                  double small_cost, bool tc_ok, int max_ne, TcTables& tct, std::vector<TileRef>& tiles,
                  std::vector<TileRange>& ranges, const Choice* forced = nullptr) {
+  const int tile_l = ts.m[0], tile_s = ts.m[1];
   ranges.assign(sched.size(), TileRange{0, 0, 0, 0, 0, 0});
   auto work = [&](const Step& s, int tile) {
     double w = 0.0;
@@ -287,7 +293,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
     if (flags & ND_FACT_TILE_SMALL) small = true;
     bool tc = false;
     if (tc_ok && !(flags & ND_FACT_GEMM_ALU)) {
-      tc = !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && s.max_dim > TC_MIN_DIM;
+      tc = !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL | ND_FACT_TILE_XL)) && s.max_dim > TC_MIN_DIM;
       if (tc) {
         int64_t off = 0;
         for (int k = s.begin; k < s.begin + s.count; ++k) {
@@ -301,15 +307,20 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
     // launches whose blocks all have edges <= DIRECT_MAX take one CTA per block
     int dim = 0;
     for (int k = s.begin; k < s.begin + s.count; ++k) dim = std::max(dim, std::max(gd[k].m, std::max(gd[k].n, gd[k].k)));
-    bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL)) && dim <= DIRECT_MAX &&
+    bool direct = !tc && !(flags & (ND_FACT_TILE_LARGE | ND_FACT_TILE_SMALL | ND_FACT_TILE_XL)) && dim <= DIRECT_MAX &&
                   (dim <= DIRECT_SMALL || int64_t(s.count) * max_ne >= DIRECT_MIN_CTAS);
+    int variant = small ? 1 : 0;  // ALU tile variant
+    if (flags & ND_FACT_TILE_XL) {
+      variant = 2;
+      direct = false;
+    }
     if (forced && (*forced)[si] >= 0) {  // the tuner's measured choice
       const int c = (*forced)[si];
       tc = c == 2;
       direct = c == 3;
-      small = c == 1;
+      variant = c == 1 ? 1 : c == 4 ? 2 : 0;
     }
-    const int tile = small ? tile_s : tile_l;
+    const int tmr = ts.m[variant], tnc = ts.n[variant];
     int b = int(tiles.size());
     if (tc) {
       const int sb = int(tct.split.size());
@@ -335,11 +346,11 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
         tiles.push_back(TileRef{k, 0, 0, 0});
         continue;
       }
-      const int tm = (g.m + tile - 1) / tile, tn = (g.n + tile - 1) / tile;
+      const int tm = (g.m + tmr - 1) / tmr, tn = (g.n + tnc - 1) / tnc;
       for (int i = 0; i < tm; ++i)
         for (int j = 0; j < tn; ++j) tiles.push_back(TileRef{k, i, j, 0});
     }
-    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : small ? 1 : 0, 0, 0, dim};
+    ranges[si] = TileRange{b, int(tiles.size()) - b, direct ? 3 : variant == 1 ? 1 : variant == 2 ? 4 : 0, 0, 0, dim};
   }
 }
 
@@ -400,8 +411,13 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
     const Step& st = sched[si];
     Profiler::Rec rec{};
     if (f->prof.on) {
-      // tensor-core GEMM launches are recorded apart (kind 12, "gemm_tc")
-      rec.kind = (st.kind == ST_GEMM && tr[si].kind == 2) ? PROF_GEMM_TC : st.kind;
+      // GEMM launches are recorded per kernel: "gemm" (large tile), "gemm_tc"
+      // (tensor cores, kind 12), "gemm_small", "gemm_direct", "gemm_xl" (13-15)
+      rec.kind = st.kind;
+      if (st.kind == ST_GEMM) {
+        const int k = tr[si].kind;
+        rec.kind = k == 2 ? PROF_GEMM_TC : k == 1 ? PROF_GEMM_TC + 1 : k == 3 ? PROF_GEMM_TC + 2 : k == 4 ? PROF_GEMM_TC + 3 : ST_GEMM;
+      }
       rec.a = f->prof.get();
       rec.b = f->prof.get();
       rec.flops = step_flops ? (*step_flops)[si] * w.n_e : 0.0;
@@ -426,7 +442,8 @@ nd_status run_schedule(nd_fact* f, const std::vector<Step>& sched, const std::ve
         else if (tr[si].kind == 3)
           Kern<T>::gemm_direct(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, s);
         else
-          Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count, tr[si].kind == 1, s);
+          Kern<T>::gemm(w, f->d_gemm, f->d_tiles + tr[si].first, tr[si].count,
+                        tr[si].kind == 1 ? 1 : tr[si].kind == 4 ? 2 : 0, s);
         break;
       case ST_SCATTER:
         Kern<T>::scatter(w, f->d_scat + st.begin, st.count, f->d_maps, s);
@@ -623,26 +640,29 @@ void free_tracked(nd_fact* f, void* p) {
 nd_status build_all_tiles(nd_fact* f, const std::array<Choice, N_SCHED>* forced) {
   const nd_plan* p = f->plan;
   const int precision = f->precision, flags = f->flags, max_ne = f->max_ne;
-  auto tile_of = [&](bool small) {
-    return precision == ND_PREC_FP64    ? Kern<double>::gemm_tile(small)
-           : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile(small)
-                                        : Kern<DF>::gemm_tile(small);
-  };
-  const int tl = tile_of(false), ts = tile_of(true);
+  TileShapes tsh;
+  for (int v = 0; v < 3; ++v) {
+    tsh.m[v] = precision == ND_PREC_FP64    ? Kern<double>::gemm_tile(v)
+               : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile(v)
+                                            : Kern<DF>::gemm_tile(v);
+    tsh.n[v] = precision == ND_PREC_FP64    ? Kern<double>::gemm_tile_n(v)
+               : precision == ND_PREC_MIXED ? Kern<float>::gemm_tile_n(v)
+                                            : Kern<DF>::gemm_tile_n(v);
+  }
   std::vector<TileRef> tiles;
   const double sc = small_tile_cost(precision);
   const bool tc_ok = precision == ND_PREC_FP32X2;
   const bool ph = (flags & ND_FACT_PHONON) != 0;  // the phonon G^< schedule runs only on a phonon workspace
   TcTables tct;
   auto fc = [&](int q) { return forced ? &(*forced)[q] : nullptr; };
-  build_tiles(p->sched_factor, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_factor, fc(0));
-  build_tiles(p->sched_green, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_green, fc(1));
-  build_tiles(p->sched_lesser[0], f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_lesser[0], fc(2));
-  build_tiles(p->sched_lesser[1], f->gemm_all, tl, ts, flags, sc, tc_ok && ph, max_ne, tct, tiles, f->tr_lesser[1],
+  build_tiles(p->sched_factor, f->gemm_all, tsh, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_factor, fc(0));
+  build_tiles(p->sched_green, f->gemm_all, tsh, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_green, fc(1));
+  build_tiles(p->sched_lesser[0], f->gemm_all, tsh, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_lesser[0], fc(2));
+  build_tiles(p->sched_lesser[1], f->gemm_all, tsh, flags, sc, tc_ok && ph, max_ne, tct, tiles, f->tr_lesser[1],
               fc(3));
   if (f->adj) {
-    build_tiles(f->sched_adj_fwd, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_fwd, fc(4));
-    build_tiles(f->sched_adj_bwd, f->gemm_all, tl, ts, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_bwd, fc(5));
+    build_tiles(f->sched_adj_fwd, f->gemm_all, tsh, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_fwd, fc(4));
+    build_tiles(f->sched_adj_bwd, f->gemm_all, tsh, flags, sc, tc_ok, max_ne, tct, tiles, f->tr_adj_bwd, fc(5));
   }
   free_tracked(f, f->d_tiles);
   free_tracked(f, f->d_tcd);
@@ -1162,7 +1182,7 @@ extern "C" nd_status nd_profile(nd_fact* f, int32_t enable, nd_kernel_stats* sta
     ND_CUDA(cudaDeviceSynchronize());
     static const char* names[] = {"inverse",    "gemm",         "scatter",   "gather_sym", "gather_skew", "zero",
                                   "nph",        "gather_anc",   "scatter_rows", "colgather", "delay",     "loc",
-                                  "gemm_tc"};
+                                  "gemm_tc",    "gemm_small",   "gemm_direct", "gemm_xl"};
     const int nk = int(sizeof(names) / sizeof(names[0]));
     std::vector<nd_kernel_stats> acc(nk);
     for (int k = 0; k < nk; ++k) {
@@ -1231,22 +1251,24 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
   const std::vector<Step>* sched[4] = {&p->sched_factor, &p->sched_green, &p->sched_lesser[0], &p->sched_lesser[1]};
   const std::vector<TileRange>* trs[4] = {&f->tr_factor, &f->tr_green, &f->tr_lesser[0], &f->tr_lesser[1]};
   // candidate kernels per GEMM step: the default rules (-1), the large and the
-  // small tile, the tensor cores (FP32 pairs, digit scratch within the limit)
-  // and one CTA per block (blocks up to 192)
+  // small tile, the tensor cores (FP32 pairs, digit scratch within the limit),
+  // one CTA per block (blocks up to 192) and the extra large tile
   auto allowed = [&](int q, int si, int c) {
     const Step& st = (*sched[q])[si];
     if (st.kind != ST_GEMM) return false;
     if (c == 2)
       return f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_step_scratch(st, f->gemm_all) <= TC_MAX_SCRATCH;
     if (c == 3) return st.max_dim <= 192;
+    if (c == 4) return st.max_dim > 32;  // the 64-row tiles only pay above the large tile's edge
     return true;
   };
-  std::array<std::vector<std::array<double, 5>>, 4> ms;  // [schedule][step][candidate + 1]
-  for (int q = 0; q < 4; ++q) ms[q].assign(sched[q]->size(), {-1.0, -1.0, -1.0, -1.0, -1.0});
+  constexpr int NC = 5;  // candidates 0..4: large tile, small tile, tensor cores, one CTA per block, extra large tile
+  std::array<std::vector<std::array<double, NC + 1>>, 4> ms;  // [schedule][step][candidate + 1]
+  for (int q = 0; q < 4; ++q) ms[q].assign(sched[q]->size(), {-1.0, -1.0, -1.0, -1.0, -1.0, -1.0});
   const bool prof_was = f->prof.on;
   nd_status st = ND_OK;
   int passes = 0;
-  for (int c = -1; c < 4 && st == ND_OK; ++c) {
+  for (int c = -1; c < NC && st == ND_OK; ++c) {
     std::array<Choice, N_SCHED> forced;
     for (int q = 0; q < N_SCHED; ++q) {
       const size_t ns = q < 4 ? sched[q]->size() : (q == 4 ? f->sched_adj_fwd.size() : f->sched_adj_bwd.size());
@@ -1292,7 +1314,7 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
   // per step the fastest measured kernel
   std::array<Choice, N_SCHED> best;
   double t_def = 0.0, t_best = 0.0;
-  int steps = 0, changed = 0, by_kind[4] = {0, 0, 0, 0};
+  int steps = 0, changed = 0, by_kind[5] = {0, 0, 0, 0, 0};
   for (int q = 0; q < N_SCHED; ++q) {
     const size_t ns = q < 4 ? sched[q]->size() : (q == 4 ? f->sched_adj_fwd.size() : f->sched_adj_bwd.size());
     best[q].assign(ns, -1);
@@ -1303,7 +1325,7 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
       if (m[0] < 0.0) continue;  // not run (the phonon schedule without phonon inputs)
       int bc = -1;
       double bt = m[0];
-      for (int c = 0; c < 4; ++c)
+      for (int c = 0; c < NC; ++c)
         if (m[c + 1] >= 0.0 && m[c + 1] < bt) {
           bt = m[c + 1];
           bc = c;
@@ -1326,7 +1348,7 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
     info->gemm_steps = steps;
     info->changed = changed;
     info->passes = passes;
-    for (int k = 0; k < 4; ++k) info->by_kind[k] = by_kind[k];
+    for (int k = 0; k < 5; ++k) info->by_kind[k] = by_kind[k];
   }
   return ND_OK;
 }

@@ -3,23 +3,26 @@
 // schedule step, with the results of k_gemm up to rounding at the FP32-pair
 // level.
 //
-// Exact products of integer digits (the splitting scheme of Ozaki, Ogita,
-// Oishi and Rump, Numer. Algorithms 59 (2012), in its fixed-point form):
+// Products of integer digits (the splitting scheme of Ozaki, Ogita, Oishi
+// and Rump, Numer. Algorithms 59 (2012), in its fixed-point form):
 //  * every row i of op(A) gets a scale 2^eA[i] >= max_k |Re a_ik| + |Im a_ik|,
 //    every column j of op(B) a scale 2^eB[j] likewise;
 //  * a real x of row i becomes the integer X = round(x 2^(54 - eA[i])),
 //    |X| < 2^54, written with 7 balanced base-256 digits,
-//    X = sum_t d_t 256^(6-t), d_t in [-128, 127] and |d_0| <= 64; digits are
-//    exact in 8 bits and in BF16;
-//  * a digit product is exact (at most 2^14, 2^13 with d_0) and so is the
-//    FP32 sum of the products of the pairs (t, t') of one group g = t + t'
-//    (at most g 2^14 per k for g >= 1) over 160 k (6 * 160 * 2^14 < 2^24), so
-//    the tensor cores sum every group exactly; pairs with t + t' >= 7 fall
-//    below the 2^-54 resolution and are dropped (28 pairs of the 49);
+//    X = sum_t d_t 256^(6-t), d_t in [-128, 127] and |d_0| <= 64; digit t is
+//    held as d_t 2^(-8t), exact in BF16 (8 significant bits, a power-of-two
+//    weight), so a product of digits t, t' carries its weight 2^(-8(t+t'));
+//  * the 28 pairs with t + t' <= 6 are kept (the rest lie below the 2^-54
+//    resolution); the products of each group g = t + t' = 0 .. 3 are summed
+//    in an FP32 accumulator of their own in TMEM, exactly (a group sum is an
+//    integer times its weight, at most 3 2^14 per k, so below 2^24 over CHUNK
+//    16-k blocks), and groups 4, 5, 6, whose weights are 2^-32 .. 2^-48 of
+//    the top, share a fifth accumulator whose FP32 rounding stays near 2^-53
+//    of the result (sharing from group 3 on would cost 2^-44);
 //  * complex products take three real products, Re a Re b, Im a Im b and
 //    (Re a + Im a)(Re b + Im b) (the sum formed exactly on the integers), so
 //    Re = P1 - P2, Im = P3 - P1 - P2.
-// The error is normwise, about 2^-54 max|a_i.| max|b_.j| k per entry.
+// The error is normwise, about 2^-52 max|a_i.| max|b_.j| k per entry.
 //
 // Two kernels per launch:
 //  * k_tc_split: the scale and the digits of Re, Im and Re + Im of every row
@@ -32,14 +35,15 @@
 //    A producer warp streams the 8-bit digit blocks into a 4-stage
 //    shared-memory ring with bulk asynchronous copies (cp.async.bulk,
 //    completion by mbarrier transaction count); eight accumulator warps widen
-//    them to BF16 into a 2-stage operand ring.  One thread issues the 28
-//    digit-pair MMAs per 16 k and component (tcgen05.mma kind::f16, M = 128,
-//    N = 64, K = 16, BF16 in, FP32 accumulators in TMEM: one 64-column
-//    accumulator per group, 448 of the 512 columns) and signals the stage free
-//    with tcgen05.commit.  Every 160 k and at the end of each component the
-//    accumulator warps read the group sums (tcgen05.ld), add them into
-//    FP32-pair accumulators of Re and Im in registers (32 outputs per thread)
-//    and hand the TMEM back.
+//    them to weighted BF16 digits into a 3-stage operand ring.  One thread
+//    issues the 28 digit-pair MMAs per 16 k and component (tcgen05.mma
+//    kind::f16, M = 128, N = 64, K = 16, BF16 in, FP32 accumulators in TMEM)
+//    into NACC 64-column accumulators (a second set when two fit in the 512
+//    columns) and signals the stage free with tcgen05.commit.  At the end of
+//    every chunk (CHUNK 16-k blocks, or a component) the accumulator warps
+//    read the set just filled (tcgen05.ld), add it into FP32-pair
+//    accumulators of Re and Im in registers (32 outputs per thread) and hand
+//    it back.
 // Every wait is bounded.  A wait that gives up raises the CTA's abort flag;
 // the CTA then drains its copies and MMAs, frees its TMEM, skips its output
 // and sets *timeout (reported by nd_fact_status as ND_ERR_TIMEOUT).
@@ -55,31 +59,41 @@ namespace {
 
 constexpr int TC_S = TC_DIGITS;  // digits per real
 constexpr int TC_F = 54;         // fixed-point bits below the row (column) scale
+constexpr int NACC = 5;          // TMEM accumulators per set: groups 0, 1, 2, 3 and 4..6
+constexpr int SET_COLS = NACC * TC_N;
+constexpr int SETS = 2 * SET_COLS <= 512 ? 2 : 1;  // accumulator sets (a second one overlaps a flush)
 // one stage: the 7 digit planes of A and of B for 16 k, as bytes and as BF16
 constexpr int SA8 = TC_S * int(TC_PLANE_A), SB8 = TC_S * int(TC_PLANE_B);
 constexpr int SA = 2 * SA8, SB = 2 * SB8;
-constexpr int S8 = 4, S16 = 2;  // byte stages (bulk copies), BF16 stages (MMA operands)
-constexpr int CHUNK = 10;     // 16-k blocks summed exactly in TMEM between two reads (160 terms)
+constexpr int S8 = 4, S16 = 3;  // byte stages (bulk copies), BF16 stages (MMA operands)
+constexpr int CHUNK = 20;     // 16-k blocks summed in TMEM between two reads (320 terms: group sums < 2^24)
 constexpr int FW = 8;         // accumulator warps: widening, flush, epilogue
 constexpr int NT = (FW + 2) * 32;  // + producer warp + MMA warp
-constexpr int TMEM_COLS = 512;     // allocated (TC_S x TC_N = 448 used)
+constexpr int TMEM_COLS = 512;     // allocated: SETS sets of NACC x TC_N columns
 constexpr size_t SMEM = size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB) + 1024;  // + alignment slack
 constexpr long SPIN = 1L << 25;    // polls before a wait gives up (default; a drain always uses it)
 
-static_assert(TC_S * TC_N <= TMEM_COLS, "group accumulators exceed the TMEM columns");
+static_assert(SETS * SET_COLS <= TMEM_COLS, "accumulator sets exceed the TMEM columns");
+static_assert(CHUNK * 16 * 3 * (1 << 14) < (1 << 24), "group sums of a chunk must stay exact in FP32");
 static_assert(TC_M == 128 && TC_N % 16 == 0 && TC_N <= 256, "tcgen05 kind::f16 shape with M = 128");
 
 __device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
   const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower address)
   return *reinterpret_cast<const unsigned*>(&p);
 }
-// Four signed bytes of w (byte 0 first) as two packed BF16 pairs (exact:
-// |value| <= 128); arithmetic shifts sign-extend each byte.
-__device__ __forceinline__ uint2 widen4(unsigned w) {
-  const int v = int(w);
-  const float f0 = float((v << 24) >> 24), f1 = float((v << 16) >> 24);
-  const float f2 = float((v << 8) >> 24), f3 = float(v >> 24);
-  return make_uint2(pack_bf16(f0, f1), pack_bf16(f2, f3));
+// Four signed bytes of w (byte 0 first) times the power of two wt as two
+// packed BF16 pairs, without conversion instructions: with u = w ^ 0x80808080
+// every byte is b = d + 128 in [0, 255]; the float with bits 0x4B0000bb is
+// 2^23 + b exactly, so fma(x, wt, -(2^23 + 128) wt) = d wt exactly, a value
+// with at most 8 significant bits, whose upper 16 bits are its BF16 form.
+__device__ __forceinline__ uint2 widen4(unsigned w, float wt, float off) {
+  const unsigned u = w ^ 0x80808080u;
+  const float f0 = fmaf(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7650)), wt, off);
+  const float f1 = fmaf(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7651)), wt, off);
+  const float f2 = fmaf(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7652)), wt, off);
+  const float f3 = fmaf(__uint_as_float(__byte_perm(u, 0x4B000000u, 0x7653)), wt, off);
+  return make_uint2(__byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632),
+                    __byte_perm(__float_as_uint(f2), __float_as_uint(f3), 0x7632));
 }
 
 // Balanced base-256 digits of an integer-valued float V (|V| < 2^54 after
@@ -340,7 +354,7 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
                                                    const unsigned char* __restrict__ scratch, int64_t ss,
                                                    int* timeout, long spin) {
   extern __shared__ unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t full8[S8], empty8[S8], full16[S16], empty16[S16], accfull, accempty, done;
+  __shared__ __align__(8) uint64_t full8[S8], empty8[S8], full16[S16], empty16[S16], accfull[SETS], accempty[SETS], done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int eA[TC_M], eB[TC_N];
@@ -375,8 +389,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
       mbar_init(&full16[s], FW);
       mbar_init(&empty16[s], 1);
     }
-    mbar_init(&accfull, 1);
-    mbar_init(&accempty, FW);
+    for (int q = 0; q < SETS; ++q) {
+      mbar_init(&accfull[q], 1);
+      mbar_init(&accempty[q], FW);
+    }
     mbar_init(&done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -409,26 +425,31 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
   } else if (warp == FW + 1) {
     // ---- MMA issue: 28 digit-pair products per 16 k into the group accumulators
     if (lane == 0) {
-      int q = 0;  // chunks handed to the accumulator warps
+      int q = 0;  // chunks handed to the accumulator warps; chunk q fills set q % SETS
       for (int j = 0; j < njobs; ++j) {
         const int s = j % S16, u = j / S16;
         const int kb = j % KB, kc = kb % CHUNK;
-        if (kc == 0 && q > 0) {
-          if (!mbar_wait(&accempty, (q - 1) & 1, abrt, spin)) break;
+        if (kc == 0 && q >= SETS) {  // the set was read back by the accumulator warps
+          if (!mbar_wait(&accempty[q % SETS], ((q - SETS) / SETS) & 1, abrt, spin)) break;
           tc_fence_after();
         }
         if (!mbar_wait(&full16[s], u & 1, abrt, spin)) break;
         tc_fence_after();
         const uint32_t a0 = smem_u32(ring16 + size_t(s) * (SA + SB)), b0 = a0 + SA;
+        const uint32_t set = tmem + uint32_t((q % SETS) * SET_COLS);
 #pragma unroll
         for (int t1 = 0; t1 < TC_S; ++t1)
 #pragma unroll
-          for (int t2 = 0; t2 < TC_S - t1; ++t2)
-            mma_bf16(tmem + uint32_t((t1 + t2) * TC_N), sdesc(a0 + t1 * uint32_t(2 * TC_PLANE_A)),
-                     sdesc(b0 + t2 * uint32_t(2 * TC_PLANE_B)), (kc == 0 && t1 == 0) ? 0u : 1u);
+          for (int t2 = 0; t2 < TC_S - t1; ++t2) {
+            const int acc = t1 + t2 < NACC - 1 ? t1 + t2 : NACC - 1;
+            // the first product into each accumulator of a chunk overwrites it
+            const uint32_t accumulate = (kc == 0 && t1 == 0 && t2 <= NACC - 1) ? 0u : 1u;
+            mma_bf16(set + uint32_t(acc * TC_N), sdesc(a0 + t1 * uint32_t(2 * TC_PLANE_A)),
+                     sdesc(b0 + t2 * uint32_t(2 * TC_PLANE_B)), accumulate);
+          }
         if (j + S16 < njobs) mma_commit(&empty16[s]);
         if (kc == CHUNK - 1 || kb == KB - 1) {
-          mma_commit(&accfull);
+          mma_commit(&accfull[q % SETS]);
           ++q;
         }
       }
@@ -450,7 +471,13 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
       uint4* dst = reinterpret_cast<uint4*>(ring16 + size_t(s16) * (SA + SB));
       for (int i = tid; i < (SA8 + SB8) / 16; i += FW * 32) {
         const uint4 v = src[i];
-        const uint2 a = widen4(v.x), b = widen4(v.y), c = widen4(v.z), w = widen4(v.w);
+        // digit plane of these 16 bytes, and its weight 2^(-8t)
+        const int byte = 16 * i;
+        const int t = byte < SA8 ? byte / int(TC_PLANE_A) : (byte - SA8) / int(TC_PLANE_B);
+        const float wt = __int_as_float((127 - 8 * t) << 23);
+        const float off = -8388736.f * wt;  // -(2^23 + 128) wt, exact
+        const uint2 a = widen4(v.x, wt, off), b = widen4(v.y, wt, off), c = widen4(v.z, wt, off),
+                    w = widen4(v.w, wt, off);
         dst[2 * i] = make_uint4(a.x, a.y, b.x, b.y);
         dst[2 * i + 1] = make_uint4(c.x, c.y, w.x, w.y);
       }
@@ -477,23 +504,24 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
         const int upto = min(njobs - 1, last + S16);
         for (; ok && jw <= upto; ++jw) ok = __all_sync(0xffffffffu, widen(jw));
         if (!ok) break;
-        ok = __all_sync(0xffffffffu, mbar_wait(&accfull, q & 1, abrt, spin));
+        ok = __all_sync(0xffffffffu, mbar_wait(&accfull[q % SETS], (q / SETS) & 1, abrt, spin));
         if (!ok) break;
         tc_fence_after();
+        const uint32_t tset = tbase + uint32_t((q % SETS) * SET_COLS);
 #pragma unroll
         for (int cs = 0; cs < 32; cs += 4) {
-          float v[TC_S][4];
+          float v[NACC][4];
 #pragma unroll
-          for (int g = 0; g < TC_S; ++g) tmem_ld4(tbase + uint32_t(g * TC_N + cs), v[g]);
+          for (int g = 0; g < NACC; ++g) tmem_ld4(tset + uint32_t(g * TC_N + cs), v[g]);
           tmem_wait_ld();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            // P = sum_g D_g 2^(-8 g) as an unnormalised pair
+            // P = the sum of the (already weighted) accumulators as an unnormalised pair
             float h = v[0][i], l = 0.f;
 #pragma unroll
-            for (int g = 1; g < TC_S; ++g) {
+            for (int g = 1; g < NACC; ++g) {
               float s, err;
-              two_sum(h, v[g][i] * __int_as_float((127 - 8 * g) << 23), s, err);
+              two_sum(h, v[g][i], s, err);
               h = s;
               l += err;
             }
@@ -511,10 +539,10 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&accempty);
+        if (lane == 0) mbar_arrive(&accempty[q % SETS]);
       }
     }
-    // ---- epilogue: scale 2^(eA + eB - 12) (the groups carry 2^96 of the 2^-108), alpha, beta D
+    // ---- epilogue: scale 2^(eA + eB - 12) (the weighted digits carry 2^96 of the 2^-108), alpha, beta D
     if (ok && !*abrt) {
       const int row = quad * 32 + lane;
       const int gm = tr.tm * TC_M + row;

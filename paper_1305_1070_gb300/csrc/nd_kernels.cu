@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include <cstdint>
@@ -250,10 +251,11 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
   }
 }
 
-// GEMM of small blocks (every edge <= 24): one CTA per descriptor and
-// energy, one thread per output, operands read through L1 without staging
-// (no tile padding, no barriers); four real products per multiply-add (the
-// 3-multiplication sums would be formed per term here).
+// GEMM of small blocks (edges up to 96): one CTA per descriptor and energy,
+// each thread a 2 x 2 block of outputs (the two rows of A and two columns of B
+// it loads serve four multiply-adds), operands read through L1 without
+// staging (no tile padding, no barriers); four real products per
+// multiply-add (the 3-multiplication sums would be formed per loaded term).
 template <typename T>
 __global__ void __launch_bounds__(128) k_gemm_direct(const GemmDesc* __restrict__ descs,
                                                      const TileRef* __restrict__ tiles, cx<T>* arena, int64_t se,
@@ -269,26 +271,47 @@ __global__ void __launch_bounds__(128) k_gemm_direct(const GemmDesc* __restrict_
   const bool transA = d.opA != OP_N;
   const bool conjB = (d.opB == OP_C || d.opB == OP_H);
   const bool transB = (d.opB == OP_T || d.opB == OP_H);
-  const int mn = d.m * d.n;
-  for (int idx = threadIdx.x; idx < mn; idx += blockDim.x) {
-    const int i = idx / d.n, j = idx % d.n;
-    typename O<T>::Acc acc = O<T>::acc_zero();
+  const int mb = (d.m + 1) >> 1, nb = (d.n + 1) >> 1;
+  const int64_t sAi = transA ? 1 : d.lda, sAk = transA ? d.lda : 1;  // A(i, k) = A[i sAi + k sAk]
+  const int64_t sBj = transB ? d.ldb : 1, sBk = transB ? 1 : d.ldb;  // B(k, j) = B[k sBk + j sBj]
+  for (int idx = threadIdx.x; idx < mb * nb; idx += blockDim.x) {
+    const int i0 = 2 * (idx / nb), j0 = 2 * (idx % nb);
+    const bool i1 = i0 + 1 < d.m, j1 = j0 + 1 < d.n;
+    const cx<T>* a0p = A + i0 * sAi;
+    const cx<T>* a1p = A + (i1 ? i0 + 1 : i0) * sAi;
+    const cx<T>* b0p = B + j0 * sBj;
+    const cx<T>* b1p = B + (j1 ? j0 + 1 : j0) * sBj;
+    typename O<T>::Acc c00 = O<T>::acc_zero(), c01 = O<T>::acc_zero(), c10 = O<T>::acc_zero(),
+                       c11 = O<T>::acc_zero();
     for (int k = 0; k < d.k; ++k) {
-      const cx<T> a = transA ? A[int64_t(k) * d.lda + i] : A[int64_t(i) * d.lda + k];
-      cx<T> b = transB ? B[int64_t(j) * d.ldb + k] : B[int64_t(k) * d.ldb + j];
-      if (conjB) b = O<T>::conj(b);
-      O<T>::acc_fma(acc, a, b);
+      const cx<T> a0 = a0p[k * sAk], a1 = a1p[k * sAk];
+      cx<T> b0 = b0p[k * sBk], b1 = b1p[k * sBk];
+      if (conjB) {
+        b0 = O<T>::conj(b0);
+        b1 = O<T>::conj(b1);
+      }
+      O<T>::acc_fma(c00, a0, b0);
+      O<T>::acc_fma(c01, a0, b1);
+      O<T>::acc_fma(c10, a1, b0);
+      O<T>::acc_fma(c11, a1, b1);
     }
-    cx<T> r = O<T>::acc_get(acc);
-    if (d.alpha == -1.0)
-      r = O<T>::neg(r);
-    else if (d.alpha != 1.0)
-      r = O<T>::scale(r, d.alpha);
-    if (d.beta != 0.0) {
-      const cx<T> dv = D[int64_t(i) * d.ldd + j];
-      r = O<T>::add(r, d.beta == 1.0 ? dv : O<T>::scale(dv, d.beta));
+    const typename O<T>::Acc* acc[4] = {&c00, &c01, &c10, &c11};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + (q >> 1), j = j0 + (q & 1);
+      if ((q >> 1) && !i1) continue;
+      if ((q & 1) && !j1) continue;
+      cx<T> r = O<T>::acc_get(*acc[q]);
+      if (d.alpha == -1.0)
+        r = O<T>::neg(r);
+      else if (d.alpha != 1.0)
+        r = O<T>::scale(r, d.alpha);
+      if (d.beta != 0.0) {
+        const cx<T> dv = D[int64_t(i) * d.ldd + j];
+        r = O<T>::add(r, d.beta == 1.0 ? dv : O<T>::scale(dv, d.beta));
+      }
+      C[int64_t(i) * d.ldc + j] = r;
     }
-    C[int64_t(i) * d.ldc + j] = r;
   }
 }
 
@@ -887,16 +910,25 @@ __global__ void k_absmax(const ZeroDesc* __restrict__ descs, const cx<T>* arena,
 // under the 48-operation FP32-pair multiply-add) is slow enough that one or
 // four outputs per thread keep it busy; the small tile wastes less on the
 // ragged 10-60 row blocks of the lower tree levels.
-template <typename T, bool SMALL> struct GemmCfg;
-template <> struct GemmCfg<double, false> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
-template <> struct GemmCfg<double, true> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1; };
-template <> struct GemmCfg<float, false> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
-template <> struct GemmCfg<float, true> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
-template <> struct GemmCfg<DF, false> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
-template <> struct GemmCfg<DF, true> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 2, TN = 2; };
+// Variant 0 large, 1 small, 2 extra large (64 x 64 tiles with 4 x 4 outputs
+// per thread: a quarter of the shared-memory reads per multiply-add of the
+// large tile, for the blocks of 64 and more rows; chosen by the tuner).
+template <typename T, int V> struct GemmCfg;
+template <> struct GemmCfg<double, 0> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<double, 1> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 1, TN = 1; };
+template <> struct GemmCfg<double, 2> { static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4; };
+template <> struct GemmCfg<float, 0> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+template <> struct GemmCfg<float, 1> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<float, 2> { static constexpr int BM = 128, BN = 64, BK = 8, TM = 8, TN = 4; };
+template <> struct GemmCfg<DF, 0> { static constexpr int BM = 32, BN = 32, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<DF, 1> { static constexpr int BM = 16, BN = 16, BK = 16, TM = 2, TN = 2; };
+template <> struct GemmCfg<DF, 2> { static constexpr int BM = 64, BN = 64, BK = 8, TM = 4, TN = 4; };
 
-template <typename T> int Kern<T>::gemm_tile(bool small) {
-  return small ? GemmCfg<T, true>::BM : GemmCfg<T, false>::BM;
+template <typename T> int Kern<T>::gemm_tile(int variant) {
+  return variant == 1 ? GemmCfg<T, 1>::BM : variant == 2 ? GemmCfg<T, 2>::BM : GemmCfg<T, 0>::BM;
+}
+template <typename T> int Kern<T>::gemm_tile_n(int variant) {
+  return variant == 1 ? GemmCfg<T, 1>::BN : variant == 2 ? GemmCfg<T, 2>::BN : GemmCfg<T, 0>::BN;
 }
 
 template <typename T>
@@ -927,10 +959,10 @@ void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, dou
                       int* n_singular, cudaStream_t s) {
   if (count <= 0 || w.n_e <= 0) return;
   const size_t base = ((size_t(max_n) * sizeof(int) + 15) & ~size_t(15)) + size_t(2) * max_n * sizeof(double2);
-  // blocks with base + n^2 elements within 72 KB (n <= 64 for 16-byte elements)
-  // are inverted in shared memory; larger ones in place in global memory
+  // blocks with base + n^2 elements within 200 KB (n <= 111 for 16-byte
+  // elements) are inverted in shared memory; larger ones in place in global memory
   int cap = 0;
-  while (base + size_t(cap + 1) * (cap + 1) * sizeof(cx<T>) <= size_t(72 * 1024)) ++cap;
+  while (base + size_t(cap + 1) * (cap + 1) * sizeof(cx<T>) <= size_t(200 * 1024)) ++cap;
   const int smem_max_n = cap < max_n ? cap : max_n;
   const size_t shm = base + size_t(smem_max_n) * smem_max_n * sizeof(cx<T>);
   // the n x n update of every pivot step is spread over the CTA: large blocks
@@ -940,9 +972,9 @@ void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, dou
                                                    n_singular, smem_max_n);
 }
 
-template <typename T, bool SMALL>
+template <typename T, int V>
 static void launch_gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s) {
-  using G = GemmCfg<T, SMALL>;
+  using G = GemmCfg<T, V>;
   constexpr int NT = (G::BM / G::TM) * (G::BN / G::TN);
   constexpr size_t shm = (sizeof(cx<T>) + sizeof(typename O<T>::S)) * 2 * G::BK * (G::BM + 1 + G::BN + 1);
   auto kern = k_gemm<T, G::BM, G::BN, G::BK, G::TM, G::TN>;
@@ -950,12 +982,14 @@ static void launch_gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, 
 }
 
 template <typename T>
-void Kern<T>::gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, bool small, cudaStream_t s) {
+void Kern<T>::gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, int variant, cudaStream_t s) {
   if (n_tiles <= 0 || w.n_e <= 0) return;
-  if (small)
-    launch_gemm<T, true>(w, d, tiles, n_tiles, s);
+  if (variant == 1)
+    launch_gemm<T, 1>(w, d, tiles, n_tiles, s);
+  else if (variant == 2)
+    launch_gemm<T, 2>(w, d, tiles, n_tiles, s);
   else
-    launch_gemm<T, false>(w, d, tiles, n_tiles, s);
+    launch_gemm<T, 0>(w, d, tiles, n_tiles, s);
 }
 
 template <typename T>
@@ -1316,7 +1350,7 @@ void Kern<T>::adj_contract(const Work& w, const AdjDesc* d, int count, int M, co
 }
 
 // Dynamic shared memory limits of every kernel that may need more than 48 KB
-// (k_delay up to ~200 KB, k_inverse 72 KB, the large GEMM tiles, k_gemm_tc),
+// (k_delay and k_inverse up to ~200 KB, the large GEMM tiles, k_gemm_tc),
 // set once per device, before any launch can be recorded into a graph.
 // The largest dynamic shared memory a kernel may take: the device's opt-in
 // limit per block less the kernel's static shared memory.
@@ -1331,10 +1365,12 @@ template <typename T>
 static void prepare_t(int optin) {
   allow_max_smem(k_delay<T>, optin);
   allow_max_smem(k_inverse<T>, optin);
-  using GL = GemmCfg<T, false>;
-  using GS = GemmCfg<T, true>;
+  using GL = GemmCfg<T, 0>;
+  using GS = GemmCfg<T, 1>;
+  using GX = GemmCfg<T, 2>;
   allow_max_smem(k_gemm<T, GL::BM, GL::BN, GL::BK, GL::TM, GL::TN>, optin);
   allow_max_smem(k_gemm<T, GS::BM, GS::BN, GS::BK, GS::TM, GS::TN>, optin);
+  allow_max_smem(k_gemm<T, GX::BM, GX::BN, GX::BK, GX::TM, GX::TN>, optin);
 }
 
 void prepare_kernels() {

@@ -68,7 +68,8 @@ struct Kern {
   static void delay(const Work& w, const DelayDesc* d, int count, int max_nf, const DelayTabs& dt, cudaStream_t s);
   static void inverse(const Work& w, const InvDesc* d, int count, int max_n, double* fp64_scratch,
                       int64_t scratch_stride, int* n_singular, cudaStream_t s);
-  static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, bool small, cudaStream_t s);
+  // variant 0 large tile, 1 small tile, 2 extra large tile (gemm_tile / gemm_tile_n: its edges)
+  static void gemm(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, int variant, cudaStream_t s);
   // one CTA per descriptor (launches whose blocks have every edge <= 96)
   static void gemm_direct(const Work& w, const GemmDesc* d, const TileRef* tiles, int n_tiles, cudaStream_t s);
   static void scatter(const Work& w, const ScatterDesc* d, int count, const int32_t* maps, cudaStream_t s);
@@ -101,8 +102,8 @@ struct Kern {
                            int n, int forward, cudaStream_t s);
   static void current(const Work& w, int64_t offPl, int64_t offPg, int ld, int row0, int m, const double* sl,
                       const double* sg, int64_t sstride, int64_t soff, double* out, double* out_im, cudaStream_t s);
-  // tile edge (BM = BN) of the large and the small GEMM configuration
-  static int gemm_tile(bool small);
+  static int gemm_tile(int variant);
+  static int gemm_tile_n(int variant);
 };
 
 // FP32-pair GEMM of one schedule step on the tensor cores (nd_gemm_tc.cu):

@@ -28,6 +28,7 @@ ND_FACT_GEMM_TC = 8
 ND_FACT_GEMM_ALU = 16
 ND_FACT_ADJOINT = 32
 ND_FACT_GRAPH = 64
+ND_FACT_TILE_XL = 128
 
 EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites", "nd_plan_destroy",
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
@@ -63,7 +64,7 @@ class nd_kernel_stats(ctypes.Structure):
 
 class nd_tune_info(ctypes.Structure):
     _fields_ = [("ms_default", ctypes.c_double), ("ms_tuned", ctypes.c_double), ("gemm_steps", ctypes.c_int32),
-                ("changed", ctypes.c_int32), ("passes", ctypes.c_int32), ("by_kind", ctypes.c_int32 * 4)]
+                ("changed", ctypes.c_int32), ("passes", ctypes.c_int32), ("by_kind", ctypes.c_int32 * 5)]
 
 
 class nd_plan_info(ctypes.Structure):
@@ -318,9 +319,9 @@ def nd_fact_density(fact: Fact, weights, scale, accumulate, out, stream=None):
 def nd_profile(fact: Fact, enable: bool) -> list:
     """Returns per-kernel-kind stats recorded since the previous call and sets
     the enable state."""
-    arr = (nd_kernel_stats * 16)()
+    arr = (nd_kernel_stats * 24)()
     cnt = _I32()
-    _check(lib().nd_profile(fact.ptr, int(enable), arr, 16, ctypes.byref(cnt)), "nd_profile")
+    _check(lib().nd_profile(fact.ptr, int(enable), arr, 24, ctypes.byref(cnt)), "nd_profile")
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "ms": arr[i].ms, "flops": arr[i].flops,
              "bytes": arr[i].bytes} for i in range(cnt.value)]
 

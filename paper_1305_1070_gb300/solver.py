@@ -42,7 +42,7 @@ class Solver:
         self.precision = precision
         flags = ndgf.ND_FACT_PHONON if tr.gamma_ph > 0.0 else 0
         flags |= {"auto": 0, "large": ndgf.ND_FACT_TILE_LARGE, "small": ndgf.ND_FACT_TILE_SMALL,
-                  "tc": ndgf.ND_FACT_GEMM_TC, "alu": ndgf.ND_FACT_GEMM_ALU}[tile]
+                  "xl": ndgf.ND_FACT_TILE_XL, "tc": ndgf.ND_FACT_GEMM_TC, "alu": ndgf.ND_FACT_GEMM_ALU}[tile]
         if adjoint:
             flags |= ndgf.ND_FACT_ADJOINT
         if graph:

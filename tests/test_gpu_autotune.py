@@ -45,7 +45,7 @@ def test_autotune_single_device(precision, tol):
     s = Solver(dev, tr, precision=precision, leaf_size=10, delay=2)
     info = s.autotune(tr.energies)
     print(f"  tuner precision {precision}: {info}")
-    assert info["passes"] == 5 and info["gemm_steps"] > 0
+    assert info["passes"] == 6 and info["gemm_steps"] > 0
     assert sum(info["by_kind"]) == info["gemm_steps"]
     assert info["ms_tuned"] <= info["ms_default"] * 1.0001
     _check(s, dev, tr, tol=tol)
@@ -68,3 +68,14 @@ def test_plan_search_small():
     assert len(table) == 4 and best["leaf"] in (8, 16) and best["chunk"] in (4, 8)
     assert s.max_ne == best["chunk"]
     _check(s, dev, workloads.Transport(energies=tr.energies[:best["chunk"]]))
+
+
+@pytest.mark.parametrize("precision,tol", [(ndgf.ND_PREC_FP64, 1e-10), (ndgf.ND_PREC_FP32X2, 1e-9),
+                                           (ndgf.ND_PREC_MIXED, 1e-3)])
+def test_extra_large_tile_every_launch(precision, tol):
+    """The extra large ALU tile (a tuner candidate) forced on every GEMM launch:
+    ragged blocks over several 64-row tiles, phonons, delayed pivots."""
+    dev = workloads.superlattice(70, 20, disorder=0.03, seed=31)
+    tr = workloads.Transport(energies=np.array([0.06, 0.29]), gamma_ph=2e-3, mu_ph=0.05)
+    s = Solver(dev, tr, precision=precision, leaf_size=40, delay=2, tile="xl")
+    _check(s, dev, tr, tol=tol)
