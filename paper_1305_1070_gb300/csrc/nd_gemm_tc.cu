@@ -7,9 +7,11 @@
 // and Rump, Numer. Algorithms 59 (2012), in its fixed-point form):
 //  * every row i of op(A) gets a scale 2^eA[i] >= max_k |Re a_ik| + |Im a_ik|,
 //    every column j of op(B) a scale 2^eB[j] likewise;
-//  * a real x of row i becomes the integer X = round(x 2^(54 - eA[i])),
-//    |X| < 2^54, written with 7 balanced base-256 digits,
-//    X = sum_t d_t 256^(6-t), d_t in [-128, 127] and |d_0| <= 64; digit t is
+//  * a real x = h + l (an FP32 pair) of row i becomes the 64-bit integer
+//    X = round(h 2^(54 - eA[i])) + round(l 2^(54 - eA[i])), |X| < 2^54,
+//    written with 7 balanced base-256 digits (the bytes of X plus a constant
+//    of 128 in every byte), X = sum_t d_t 256^(6-t), d_t in [-128, 127] and
+//    |d_0| <= 64; digit t is
 //    held as d_t 2^(-8t), exact in BF16 (8 significant bits, a power-of-two
 //    weight), so a product of digits t, t' carries its weight 2^(-8(t+t'));
 //  * the 28 pairs with t + t' <= 6 are kept (the rest lie below the 2^-54
@@ -20,7 +22,7 @@
 //    the top, share a fifth accumulator whose FP32 rounding stays near 2^-53
 //    of the result (sharing from group 3 on would cost 2^-44);
 //  * complex products take three real products, Re a Re b, Im a Im b and
-//    (Re a + Im a)(Re b + Im b) (the sum formed exactly on the integers), so
+//    (Re a + Im a)(Re b + Im b) (the sum formed exactly on the 64-bit integers), so
 //    Re = P1 - P2, Im = P3 - P1 - P2.
 // The error is normwise, about 2^-52 max|a_i.| max|b_.j| k per entry.
 //
@@ -59,6 +61,7 @@ namespace {
 
 constexpr int TC_S = TC_DIGITS;  // digits per real
 constexpr int TC_F = 54;         // fixed-point bits below the row (column) scale
+static_assert(TC_S == 7, "the byte layout of the digits assumes 7 digits per real");
 constexpr int NACC = 5;          // TMEM accumulators per set: groups 0, 1, 2, 3 and 4..6
 constexpr int SET_COLS = NACC * TC_N;
 constexpr int SETS = 2 * SET_COLS <= 512 ? 2 : 1;  // accumulator sets (a second one overlaps a flush)
@@ -72,8 +75,11 @@ constexpr int NT = (FW + 2) * 32;  // + producer warp + MMA warp
 constexpr int TMEM_COLS = 512;     // allocated: SETS sets of NACC x TC_N columns
 constexpr size_t SMEM = size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB) + 1024;  // + alignment slack
 constexpr long SPIN = 1L << 25;    // polls before a wait gives up (default; a drain always uses it)
+constexpr int TILE_LD = TC_N + 1;  // float4 row stride of the output tile staged in shared memory
 
 static_assert(SETS * SET_COLS <= TMEM_COLS, "accumulator sets exceed the TMEM columns");
+static_assert(size_t(TC_M) * TILE_LD * 16 <= size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB),
+              "the output tile must fit in the operand rings");
 static_assert(CHUNK * 16 * 3 * (1 << 14) < (1 << 24), "group sums of a chunk must stay exact in FP32");
 static_assert(TC_M == 128 && TC_N % 16 == 0 && TC_N <= 256, "tcgen05 kind::f16 shape with M = 128");
 
@@ -96,79 +102,61 @@ __device__ __forceinline__ uint2 widen4(unsigned w, float wt, float off) {
                     __byte_perm(__float_as_uint(f2), __float_as_uint(f3), 0x7632));
 }
 
-// Balanced base-256 digits of an integer-valued float V (|V| < 2^54 after
-// rounding): d[6] least significant, d[t] in [-128, 127] for t >= 1.  Each
-// step is exact: q = rint(V / 256) and V - 256 q are integers below 2^24 or
-// multiples of the ulp of V; a remainder of 128 moves to the next digit.
-__device__ __forceinline__ void digits_f(float V, float d[TC_S]) {
-  V = rintf(V);
-#pragma unroll
-  for (int t = TC_S - 1; t > 0; --t) {
-    const float q = rintf(V * 0.00390625f);
-    const float r = fmaf(q, -256.f, V);
-    const float up = r >= 128.f ? 1.f : 0.f;
-    d[t] = fmaf(up, -256.f, r);
-    V = q + up;
-  }
-  d[0] = V;
+// The fixed-point integer of one FP32 pair (h, l) of a row with scale factor
+// sc = 2^(54 - e): X = round(h sc) + round(l sc), |X| < 2^54 (the products by
+// the power of two sc are exact, the conversions round to nearest).
+__device__ __forceinline__ long long fixed_of(float h, float l, float sc) {
+  return __float2ll_rn(h * sc) + __float2ll_rn(l * sc);
 }
 
-// Brings digits in [-2^9, 2^9] back to [-128, 127] by carries toward the top.
-__device__ __forceinline__ void carry(float d[TC_S]) {
-#pragma unroll
-  for (int t = TC_S - 1; t > 0; --t) {
-    float c = rintf(d[t] * 0.00390625f);
-    float r = fmaf(c, -256.f, d[t]);
-    const float up = r >= 128.f ? 1.f : 0.f;
-    d[t] = fmaf(up, -256.f, r);
-    d[t - 1] += c + up;
-  }
+// Balanced base-256 digits of X, |X| < 2^54, as two's-complement bytes:
+// Y = X + sum_{b < 7} 128 256^b lies in [0, 2^56), so X = sum_b (y_b - 128) 256^b
+// with the bytes y_b of Y; digit t = y_(6-t) - 128 is in [-128, 127] (and in
+// [-64, 64] for t = 0), and its byte is y_(6-t) xor 0x80.  Byte b of the
+// result (b < 7) holds digit 6 - b; lo = bytes 0..3, hi = bytes 4..6.
+__device__ __forceinline__ void digit_bytes(long long X, unsigned& lo, unsigned& hi) {
+  const unsigned long long y = (unsigned long long)(X + 0x80808080808080LL) ^ 0x80808080808080ULL;
+  lo = unsigned(y);
+  hi = unsigned(y >> 32);
 }
 
-// Low byte of an integer-valued float d, |d| < 2^22: adding 1.5 * 2^23 puts d
-// in two's complement into the low bits of the significand.
-__device__ __forceinline__ unsigned byte_of(float d) { return __float_as_uint(d + 12582912.f); }
-
-// Digits of Re, Im and Re + Im of two FP32-pair complexes at consecutive k
-// (bytes q and q + 1, q even, of an 8-byte row segment) of one row (scale
-// factor sc = 2^(54 - e)), into w[c][t][q / 4].  hi and lo parts are split
-// separately and their digit sums carried; all values are integers below
-// 2^24 in magnitude.
-__device__ __forceinline__ void put2(unsigned& word, float d0, float d1, int q) {
-  const unsigned pair = __byte_perm(byte_of(d0), byte_of(d1), 0x0040);  // low half: bytes d0, d1
-  word = (q & 2) ? __byte_perm(word, pair, 0x5410) : (pair & 0xffffu);
+// 4 x 4 byte transpose: out[b] byte q = in[q] byte b.
+__device__ __forceinline__ void transpose4(const unsigned (&in)[4], unsigned (&out)[4]) {
+  const unsigned t0 = __byte_perm(in[0], in[1], 0x5140), t1 = __byte_perm(in[0], in[1], 0x7362);
+  const unsigned t2 = __byte_perm(in[2], in[3], 0x5140), t3 = __byte_perm(in[2], in[3], 0x7362);
+  out[0] = __byte_perm(t0, t2, 0x5410);
+  out[1] = __byte_perm(t0, t2, 0x7632);
+  out[2] = __byte_perm(t1, t3, 0x5410);
+  out[3] = __byte_perm(t1, t3, 0x7632);
 }
-__device__ __forceinline__ void split_pair(float4 v0, float4 v1, float sc, unsigned (&w)[3][TC_S][2], int q) {
-  float r[2][TC_S], im[2][TC_S];
-  const float4 v[2] = {v0, v1};
+
+// Digits of Re, Im and Re + Im of 8 FP32-pair complexes at consecutive k of
+// one row (scale factor sc) into w[c][t][0..1]: the 8 bytes of digit plane t,
+// element q at byte q.  Re + Im is the integer sum X_re + X_im, |X| < 2^54 as
+// the row scale bounds |Re| + |Im|.
+__device__ __forceinline__ void split8(const float4 (&v)[8], float sc, unsigned (&w)[3][TC_S][2]) {
+  unsigned lo[3][8], hi[3][8];
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    float a[TC_S], b[TC_S];
-    digits_f(v[p].x * sc, a);
-    digits_f(v[p].y * sc, b);
-#pragma unroll
-    for (int t = 0; t < TC_S; ++t) r[p][t] = a[t] + b[t];
-    carry(r[p]);
-    digits_f(v[p].z * sc, a);
-    digits_f(v[p].w * sc, b);
-#pragma unroll
-    for (int t = 0; t < TC_S; ++t) im[p][t] = a[t] + b[t];
-    carry(im[p]);
+  for (int q = 0; q < 8; ++q) {
+    const long long xr = fixed_of(v[q].x, v[q].y, sc), xi = fixed_of(v[q].z, v[q].w, sc);
+    digit_bytes(xr, lo[0][q], hi[0][q]);
+    digit_bytes(xi, lo[1][q], hi[1][q]);
+    digit_bytes(xr + xi, lo[2][q], hi[2][q]);
   }
 #pragma unroll
-  for (int t = 0; t < TC_S; ++t) {
-    put2(w[0][t][q >> 2], r[0][t], r[1][t], q);
-    put2(w[1][t][q >> 2], im[0][t], im[1][t], q);
-  }
-  float s[2][TC_S];
+  for (int c = 0; c < 3; ++c)
 #pragma unroll
-  for (int p = 0; p < 2; ++p) {
+    for (int g = 0; g < 2; ++g) {  // elements 4g .. 4g + 3: word g of every plane
+      const unsigned il[4] = {lo[c][4 * g], lo[c][4 * g + 1], lo[c][4 * g + 2], lo[c][4 * g + 3]};
+      const unsigned ih[4] = {hi[c][4 * g], hi[c][4 * g + 1], hi[c][4 * g + 2], hi[c][4 * g + 3]};
+      unsigned ol[4], oh[4];
+      transpose4(il, ol);
+      transpose4(ih, oh);
 #pragma unroll
-    for (int t = 0; t < TC_S; ++t) s[p][t] = r[p][t] + im[p][t];
-    carry(s[p]);
-  }
+      for (int b = 0; b < 4; ++b) w[c][TC_S - 1 - b][g] = ol[b];
 #pragma unroll
-  for (int t = 0; t < TC_S; ++t) put2(w[2][t][q >> 2], s[0][t], s[1][t], q);
+      for (int b = 0; b < 3; ++b) w[c][TC_S - 5 - b][g] = oh[b];
+    }
 }
 
 __device__ __forceinline__ int scale_exp(float m) {
@@ -242,9 +230,11 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
   const int rb = r / R, rr = r - rb * R;
   for (int o = w; o < n_oct; o += 8) {
     const int kb = o >> 1, k0 = o * 8;
-    unsigned wd[3][TC_S][2];
+    float4 v[8];
 #pragma unroll
-    for (int q = 0; q < 8; q += 2) split_pair(at(k0 + q), at(k0 + q + 1), sc, wd, q);
+    for (int q = 0; q < 8; ++q) v[q] = at(k0 + q);
+    unsigned wd[3][TC_S][2];
+    split8(v, sc, wd);
     const uint32_t co = core_off8(rr, (o & 1) * 8);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -338,6 +328,10 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
   v[1] = __uint_as_float(r1);
   v[2] = __uint_as_float(r2);
   v[3] = __uint_as_float(r3);
+}
+// barrier over the first `count` threads (whole warps) of the CTA
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -542,23 +536,40 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
         if (lane == 0) mbar_arrive(&accempty[q % SETS]);
       }
     }
-    // ---- epilogue: scale 2^(eA + eB - 12) (the weighted digits carry 2^96 of the 2^-108), alpha, beta D
-    if (ok && !*abrt) {
+    // ---- epilogue through shared memory, which is idle once the last chunk
+    // has been read (every copy consumed, every MMA complete): each thread
+    // puts its 32 outputs, scaled by 2^(eA + eB - 12) (the weighted digits
+    // carry 2^96 of the 2^-108), into a padded 128 x 64 tile; then whole warps
+    // write rows of C (alpha, beta D) with consecutive lanes on consecutive
+    // columns.  A warp that gave up has raised the abort flag before the
+    // first barrier, so no warp writes C then.
+    float4* tile = reinterpret_cast<float4*>(sm);  // [TC_M][TILE_LD]
+    named_sync(1, FW * 32);
+    if (ok) {
       const int row = quad * 32 + lane;
-      const int gm = tr.tm * TC_M + row;
-      if (gm < d.m) {
-        float4* C = arena + e * se + d.offC;
-        const float4* D = arena + e * se + d.offD;
-        using O = Ops<DF>;
 #pragma unroll
-        for (int o = 0; o < 32; ++o) {
-          const int jl = half * 32 + o, gn = tr.tn * TC_N + jl;
+      for (int o = 0; o < 32; ++o) {
+        const int jl = half * 32 + o;
+        const int ex = eA[row] + eB[jl] - 12;
+        f2 re, im;
+        two_sum(ac[o][0], ac[o][1], re.h, re.l);
+        two_sum(ac[o][2], ac[o][3], im.h, im.l);
+        tile[row * TILE_LD + jl] = make_float4(ldexpf(re.h, ex), ldexpf(re.l, ex), ldexpf(im.h, ex), ldexpf(im.l, ex));
+      }
+    }
+    named_sync(1, FW * 32);
+    if (!*abrt) {
+      float4* C = arena + e * se + d.offC;
+      const float4* D = arena + e * se + d.offD;
+      using O = Ops<DF>;
+      for (int r = warp; r < TC_M; r += FW) {
+        const int gm = tr.tm * TC_M + r;
+        if (gm >= d.m) break;
+#pragma unroll
+        for (int h2 = 0; h2 < TC_N / 32; ++h2) {
+          const int jl = h2 * 32 + lane, gn = tr.tn * TC_N + jl;
           if (gn < d.n) {
-            const int ex = eA[row] + eB[jl] - 12;
-            f2 re, im;
-            two_sum(ac[o][0], ac[o][1], re.h, re.l);
-            two_sum(ac[o][2], ac[o][3], im.h, im.l);
-            float4 v = make_float4(ldexpf(re.h, ex), ldexpf(re.l, ex), ldexpf(im.h, ex), ldexpf(im.l, ex));
+            float4 v = tile[r * TILE_LD + jl];
             if (d.alpha == -1.0)
               v = O::neg(v);
             else if (d.alpha != 1.0)

@@ -1,14 +1,16 @@
 """Arithmetic of the tensor-core Schur products (FP32 pairs), checked on the
 host: the fixed-point digit split (Ozaki, Ogita, Oishi and Rump, Numer.
 Algorithms 59 (2012)) that the GEMM kernel relies on, restated here in numpy
-float32 with the kernel's operation order:
+float32 and Python integers with the kernel's operation order:
 
-* every real x of a row with scale 2^e (|Re| + |Im| < 2^e) becomes
-  X = round(x 2^(54 - e)) as 7 balanced base-256 digits, d_t in [-128, 127]
-  for t >= 1 and |d_0| <= 64, formed separately for the hi and lo parts of an
-  FP32 pair and carried;
-* the digits of Re + Im are the carried sums of the digits of Re and Im, so
-  they represent X_re + X_im exactly;
+* every real x = h + l (an FP32 pair) of a row with scale 2^e
+  (|Re| + |Im| < 2^e) becomes the integer X = round(h 2^(54 - e)) +
+  round(l 2^(54 - e)), written as 7 balanced base-256 digits, d_t in
+  [-128, 127] for t >= 1 and |d_0| <= 64: the bytes of X + sum_b 128 256^b,
+  less 128 each;
+* the digits of Re + Im are those of the integer X_re + X_im;
+* the kernel stores each digit as a two's-complement byte and moves bytes
+  between elements and digit planes with byte permutations, emulated here;
 * the FP32 sums of the digit-sum groups g = 0 .. 3 over a chunk of 320 k
   stay below 2^24, the bound under which the tensor cores add them exactly;
   the groups 4, 5, 6 share one FP32 accumulator (each product weighted
@@ -23,44 +25,55 @@ import numpy as np
 
 F = np.float32
 S, FBITS, CHUNK_K, NACC = 7, 54, 320, 5
+BIAS = sum(128 * 256 ** b for b in range(S))
 
 
-def rint(x):
-    return F(np.rint(F(x)))
+def fixed(hi, lo, sc):
+    """X = round(hi sc) + round(lo sc), each rounded to nearest even (sc a power of two)."""
+    return int(np.rint(float(F(hi * sc)))) + int(np.rint(float(F(lo * sc))))
 
 
-def digits(V):
-    """Balanced base-256 digits of an integer-valued float32 V, d[6] least significant."""
-    V = rint(V)
-    d = [F(0)] * S
-    for t in range(S - 1, 0, -1):
-        q = rint(F(V * F(0.00390625)))
-        r = F(float(V) - 256.0 * float(q))  # exact: |r| <= 128
-        up = F(1) if r >= 128 else F(0)
-        d[t] = F(r - F(256) * up)
-        V = F(q + up)
-    d[0] = V
-    return d
-
-
-def carry(d):
-    d = list(d)
-    for t in range(S - 1, 0, -1):
-        c = rint(F(d[t] * F(0.00390625)))
-        r = F(d[t] - F(256) * c)
-        up = F(1) if r >= 128 else F(0)
-        d[t] = F(r - F(256) * up)
-        d[t - 1] = F(d[t - 1] + c + up)
-    return d
+def digits(X):
+    """Balanced base-256 digits of |X| < 2^54, d[0] most significant."""
+    Y = X + BIAS
+    assert 0 <= Y < 2 ** 56
+    return [((Y >> (8 * (S - 1 - t))) & 0xFF) - 128 for t in range(S)]
 
 
 def value(d):
     return sum(int(v) * 256 ** (S - 1 - t) for t, v in enumerate(d))
 
 
-def split_pair(hi, lo, sc):
-    """Digits of the FP32 pair hi + lo scaled by sc (a power of two)."""
-    return carry([a + b for a, b in zip(digits(F(hi * sc)), digits(F(lo * sc)))])
+def byte_perm(x, y, sel):
+    """CUDA __byte_perm without the sign-replication mode: byte i of the result
+    is byte (nibble i of sel) of the 8 bytes x (0..3), y (4..7)."""
+    src = (int(x) & 0xFFFFFFFF) | ((int(y) & 0xFFFFFFFF) << 32)
+    return sum(((src >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i) for i in range(4))
+
+
+def transpose4(w):
+    t0, t1 = byte_perm(w[0], w[1], 0x5140), byte_perm(w[0], w[1], 0x7362)
+    t2, t3 = byte_perm(w[2], w[3], 0x5140), byte_perm(w[2], w[3], 0x7362)
+    return [byte_perm(t0, t2, 0x5410), byte_perm(t0, t2, 0x7632), byte_perm(t1, t3, 0x5410),
+            byte_perm(t1, t3, 0x7632)]
+
+
+def byte_image(xs):
+    """The kernel's digit planes of 8 integers: plane t, word g, byte q holds digit
+    t of element 4g + q as a two's-complement byte."""
+    mask = (1 << 64) - 1
+    y = [((X + 0x80808080808080) & mask) ^ 0x80808080808080 for X in xs]
+    lo = [v & 0xFFFFFFFF for v in y]
+    hi = [(v >> 32) & 0xFFFFFFFF for v in y]
+    w = [[0, 0] for _ in range(S)]
+    for g in range(2):
+        ol = transpose4(lo[4 * g:4 * g + 4])
+        oh = transpose4(hi[4 * g:4 * g + 4])
+        for b in range(4):
+            w[S - 1 - b][g] = ol[b]
+        for b in range(3):
+            w[S - 5 - b][g] = oh[b]
+    return w
 
 
 def _pairs(rng, n):
@@ -77,17 +90,35 @@ def test_digit_ranges_and_exact_reconstruction():
         sc = F(2.0 ** (FBITS - int(e[i])))
         hx = F(x[i]); lx = F(x[i] - float(hx))
         hy = F(y[i]); ly = F(y[i] - float(hy))
-        r = split_pair(hx, lx, sc)
-        im = split_pair(hy, ly, sc)
-        s = carry([a + b for a, b in zip(r, im)])
+        xr, xi = fixed(hx, lx, sc), fixed(hy, ly, sc)
+        assert abs(xr) < 2 ** 54 and abs(xi) < 2 ** 54 and abs(xr + xi) < 2 ** 54
+        r, im, s = digits(xr), digits(xi), digits(xr + xi)
         # X = round(hi sc) + round(lo sc): the pair to 54 bits below the row scale
-        assert value(r) == int(np.rint(float(hx) * float(sc))) + int(np.rint(float(F(lx * sc))))
-        assert value(s) == value(r) + value(im)
+        assert value(r) == xr and value(im) == xi and value(s) == xr + xi
+        assert abs(xr - (float(hx) + float(lx)) * 2.0 ** (FBITS - int(e[i]))) <= 1.0
         for d in (r, im, s):
             assert all(-128 <= v <= 127 for v in d[1:])
             assert abs(d[0]) <= 64
             # every digit is exact in BF16 (8 significant bits)
             assert all(float(v) == float(np.float32(v)) and abs(v) <= 256 for v in d)
+
+
+def test_byte_image_of_the_digit_planes():
+    """The kernel's byte permutations put digit t of element q at byte q of plane
+    t, in two's complement, for integers across the whole range (extremes
+    included)."""
+    rng = np.random.default_rng(11)
+    lim = 2 ** 54 - 1
+    cases = [[lim, -lim, 0, 1, -1, 2 ** 47, -(2 ** 47) - 5, 127]]
+    cases += [[int(v) for v in rng.integers(-lim, lim, size=8, dtype=np.int64)] for _ in range(200)]
+    cases += [[int(v) for v in rng.integers(-2 ** 20, 2 ** 20, size=8)] for _ in range(50)]
+    for xs in cases:
+        w = byte_image(xs)
+        for q, X in enumerate(xs):
+            d = digits(X)
+            for t in range(S):
+                b = (w[t][q // 4] >> (8 * (q % 4))) & 0xFF
+                assert (b - 256 if b >= 128 else b) == d[t], (X, q, t)
 
 
 def test_group_sums_stay_exact_over_a_chunk():
@@ -117,17 +148,16 @@ def test_truncated_digit_product_error_bound():
     ea = int(np.floor(np.log2(np.max(np.abs(a.real) + np.abs(a.imag)) * 1.0001))) + 1
     eb = int(np.floor(np.log2(np.max(np.abs(b.real) + np.abs(b.imag)) * 1.0001))) + 1
 
-    def dig(v, e):
+    def fix(v, e):
         sc = F(2.0 ** (FBITS - e))
         h = F(v); lo = F(v - float(h))
-        return split_pair(h, lo, sc)
+        return fixed(h, lo, sc)
 
     comp = []
     for vec, e in ((a, ea), (b, eb)):
-        re = [dig(v.real, e) for v in vec]
-        im = [dig(v.imag, e) for v in vec]
-        sm = [carry([p + q for p, q in zip(x, y)]) for x, y in zip(re, im)]
-        comp.append((re, im, sm))
+        xr = [fix(v.real, e) for v in vec]
+        xi = [fix(v.imag, e) for v in vec]
+        comp.append(([digits(v) for v in xr], [digits(v) for v in xi], [digits(p + q) for p, q in zip(xr, xi)]))
     P = []
     for c in range(3):
         exact = 0          # groups 0..3, exact integers in units of 2^-24 (2^(-8g) weights)
