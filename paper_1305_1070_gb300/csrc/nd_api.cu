@@ -231,7 +231,7 @@ double small_tile_cost(int precision) { return precision == ND_PREC_FP64 ? 0.9 :
 // (FP32 pipe -> tensor cores): edges in (96, 192]: 138.0 -> 170.5 ms,
 // > 192: 139.9 -> 99.0 ms.
 constexpr int TC_MIN_DIM = 192;
-constexpr int64_t TC_MAX_SCRATCH = int64_t(256) << 20;
+constexpr int64_t TC_MAX_SCRATCH = int64_t(512) << 20;
 // Largest block edge of a GEMM launch that runs one CTA per block
 // (k_gemm_direct).  Measured per size class on the 512 x 128 workload, FP32
 // pairs, 128 energies (tiled 16 x 16 -> direct): edges <= 24: 78 -> 31 ms,

@@ -29,23 +29,22 @@
 // Two kernels per launch:
 //  * k_tc_split: the scale and the digits of Re, Im and Re + Im of every row
 //    of op(A) and column of op(B) of every descriptor, once, into a per-energy
-//    scratch, as 8-bit planes in the byte image of the tensor cores'
-//    shared-memory operand layout (K-major, core matrices of 8 rows x 8 k, no
-//    swizzle), so that the 7 planes of one tile and 16 k are one contiguous
-//    block and widening every byte to BF16 in place gives the operands;
+//    scratch as weighted BF16 digit planes in the tensor cores' K-major
+//    core-matrix layout (core matrices of 8 rows x 8 k, no swizzle), so that
+//    the 7 planes of one tile and 16 k are one contiguous block;
 //  * k_gemm_tc: one CTA per 128 x 64 output tile and energy, warp-specialised.
-//    A producer warp streams the 8-bit digit blocks into a 4-stage
-//    shared-memory ring with bulk asynchronous copies (cp.async.bulk,
-//    completion by mbarrier transaction count); eight accumulator warps widen
-//    them to weighted BF16 digits into a 3-stage operand ring.  One thread
-//    issues the 28 digit-pair MMAs per 16 k and component (tcgen05.mma
-//    kind::f16, M = 128, N = 64, K = 16, BF16 in, FP32 accumulators in TMEM)
-//    into NACC 64-column accumulators (a second set when two fit in the 512
-//    columns) and signals the stage free with tcgen05.commit.  At the end of
-//    every chunk (CHUNK 16-k blocks, or a component) the accumulator warps
-//    read the set just filled (tcgen05.ld), add it into FP32-pair
-//    accumulators of Re and Im in registers (32 outputs per thread) and hand
-//    it back.
+//    A producer warp streams the planes of each job (16 k of one component)
+//    into a 4-stage shared-memory ring with bulk asynchronous copies
+//    (cp.async.bulk, completion by mbarrier transaction count).  One thread
+//    issues the 28 digit-pair MMAs per job (tcgen05.mma kind::f16, M = 128,
+//    N = 64, K = 16, both operands from shared memory, FP32 accumulators in
+//    TMEM) into NACC 64-column accumulators; tcgen05.commit frees the stages.
+//    At the end of every chunk (CHUNK 16-k blocks, or a component) sixteen
+//    accumulator warps read the accumulators (tcgen05.ld), add them into
+//    FP32-pair accumulators of Re and Im in registers (16 outputs per
+//    thread) and hand them back.  The epilogue stages the tile in shared
+//    memory and writes rows of C with coalesced stores, the loads of D for
+//    8 rows per warp in flight together.
 // Every wait is bounded.  A wait that gives up raises the CTA's abort flag;
 // the CTA then drains its copies and MMAs, frees its TMEM, skips its output
 // and sets *timeout (reported by nd_fact_status as ND_ERR_TIMEOUT).
@@ -62,31 +61,30 @@ namespace {
 constexpr int TC_S = TC_DIGITS;  // digits per real
 constexpr int TC_F = 54;         // fixed-point bits below the row (column) scale
 static_assert(TC_S == 7, "the byte layout of the digits assumes 7 digits per real");
-constexpr int NACC = 5;          // TMEM accumulators per set: groups 0, 1, 2, 3 and 4..6
-constexpr int SET_COLS = NACC * TC_N;
-constexpr int SETS = 2 * SET_COLS <= 512 ? 2 : 1;  // accumulator sets (a second one overlaps a flush)
-// one stage: the 7 digit planes of A and of B for 16 k, as bytes and as BF16
-constexpr int SA8 = TC_S * int(TC_PLANE_A), SB8 = TC_S * int(TC_PLANE_B);
-constexpr int SA = 2 * SA8, SB = 2 * SB8;
-constexpr int S8 = 4, S16 = 3;  // byte stages (bulk copies), BF16 stages (MMA operands)
+constexpr int NACC = 5;          // TMEM accumulators: groups 0, 1, 2, 3 and 4..6
+constexpr int ACC_COLS = NACC * TC_N;
+// One stage (a job: 16 k of one component): the 7 weighted BF16 digit planes
+// of the tile's rows of op(A) and of its columns of op(B), in the tensor
+// cores' K-major core-matrix layout, as the split wrote them.
+constexpr int PA = 2 * int(TC_PLANE_A), PB = 2 * int(TC_PLANE_B);  // bytes of one BF16 plane
+constexpr int SA = TC_S * PA, SB = TC_S * PB;
+constexpr int STAGES = 4;        // shared-memory stages (bulk copies)
+constexpr int TMEM_COLS = 512;   // allocated (a power of two): the accumulators
 constexpr int CHUNK = 20;     // 16-k blocks summed in TMEM between two reads (320 terms: group sums < 2^24)
-constexpr int FW = 8;         // accumulator warps: widening, flush, epilogue
-constexpr int NT = (FW + 2) * 32;  // + producer warp + MMA warp
-constexpr int TMEM_COLS = 512;     // allocated: SETS sets of NACC x TC_N columns
-constexpr size_t SMEM = size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB) + 1024;  // + alignment slack
+constexpr int FW = 16;        // accumulator warps: flush and epilogue
+constexpr int CPT = TC_N / (FW / 4);  // accumulator columns per thread (4 warps per TMEM lane quadrant)
+constexpr int NT = (FW + 2) * 32;     // + producer warp + MMA warp
+constexpr size_t SMEM = size_t(STAGES) * (SA + SB) + 1024;  // + alignment slack
 constexpr long SPIN = 1L << 25;    // polls before a wait gives up (default; a drain always uses it)
 constexpr int TILE_LD = TC_N + 1;  // float4 row stride of the output tile staged in shared memory
+constexpr int EPI_ROWS = TC_M / FW;  // output rows per warp, their D loads in flight together
 
-static_assert(SETS * SET_COLS <= TMEM_COLS, "accumulator sets exceed the TMEM columns");
-static_assert(size_t(TC_M) * TILE_LD * 16 <= size_t(S8) * (SA8 + SB8) + size_t(S16) * (SA + SB),
-              "the output tile must fit in the operand rings");
+static_assert(ACC_COLS <= TMEM_COLS, "accumulators exceed the TMEM columns");
+static_assert(size_t(TC_M) * TILE_LD * 16 <= size_t(STAGES) * (SA + SB), "the output tile must fit in the stages");
+static_assert(CPT % 4 == 0 && TC_M % FW == 0, "accumulator warp layout");
 static_assert(CHUNK * 16 * 3 * (1 << 14) < (1 << 24), "group sums of a chunk must stay exact in FP32");
 static_assert(TC_M == 128 && TC_N % 16 == 0 && TC_N <= 256, "tcgen05 kind::f16 shape with M = 128");
 
-__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
-  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);  // .x = lo (lower address)
-  return *reinterpret_cast<const unsigned*>(&p);
-}
 // Four signed bytes of w (byte 0 first) times the power of two wt as two
 // packed BF16 pairs, without conversion instructions: with u = w ^ 0x80808080
 // every byte is b = d + 128 in [0, 255]; the float with bits 0x4B0000bb is
@@ -165,14 +163,13 @@ __device__ __forceinline__ int scale_exp(float m) {
   return e < -70 ? -70 : (e > 120 ? 120 : e);
 }
 
-// Byte offset of element (r, k), k < 16, in an 8-bit digit plane: the byte
-// image of the BF16 operand layout, where core matrices of 8 rows x 8 k take
-// 16 bytes per row and 128 bytes each, the two core matrices of a row group
-// along k are 128 bytes apart (leading byte offset) and consecutive row
-// groups 256 bytes (stride byte offset); the BF16 element sits at twice the
-// byte offset.
-__host__ __device__ constexpr uint32_t core_off8(int r, int k) {
-  return uint32_t((r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7));
+// Byte offset of element (r, k), k < 16, in a BF16 digit plane in the
+// tensor cores' K-major layout without swizzle: core matrices of 8 rows x 8 k
+// take 16 bytes per row and 128 bytes each, the two core matrices of a row
+// group along k are 128 bytes apart (leading byte offset) and consecutive row
+// groups 256 bytes (stride byte offset).
+__host__ __device__ constexpr uint32_t core_off(int r, int k) {
+  return uint32_t((r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 constexpr uint32_t CORE_LBO = 128, CORE_SBO = 256;
 
@@ -225,7 +222,7 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
   if (w == 0) reinterpret_cast<int*>(scr)[(side_a ? t.exp_a : t.exp_b) + r] = ex;
   const float sc = ldexpf(1.f, TC_F - ex);
   const int R = side_a ? TC_M : TC_N, RB = side_a ? t.rba : t.rbb;
-  const int64_t P = side_a ? TC_PLANE_A : TC_PLANE_B;
+  const int64_t P = side_a ? PA : PB;  // bytes of a BF16 plane
   unsigned char* dig = scr + (side_a ? t.dig_a : t.dig_b);
   const int rb = r / R, rr = r - rb * R;
   for (int o = w; o < n_oct; o += 8) {
@@ -235,14 +232,18 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
     for (int q = 0; q < 8; ++q) v[q] = at(k0 + q);
     unsigned wd[3][TC_S][2];
     split8(v, sc, wd);
-    const uint32_t co = core_off8(rr, (o & 1) * 8);
+    const uint32_t co = core_off(rr, (o & 1) * 8);
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+    for (int tt = 0; tt < TC_S; ++tt) {
+      const float wt = __int_as_float((127 - 8 * tt) << 23);  // digit weight 2^(-8t)
+      const float wo = -8388736.f * wt;                        // -(2^23 + 128) wt, exact
 #pragma unroll
-      for (int tt = 0; tt < TC_S; ++tt) {
+      for (int c = 0; c < 3; ++c) {
+        const uint2 lo = widen4(wd[c][tt][0], wt, wo), hi = widen4(wd[c][tt][1], wt, wo);
         unsigned char* pl = dig + (((int64_t(c) * t.kb + kb) * RB + rb) * TC_S + tt) * P + co;
-        *reinterpret_cast<uint2*>(pl) = make_uint2(wd[c][tt][0], wd[c][tt][1]);
+        *reinterpret_cast<uint4*>(pl) = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
+    }
   }
 }
 
@@ -307,6 +308,7 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(TC_N >> 3) << 17) |
                            (uint32_t(TC_M >> 4) << 24);
 
+// D (TMEM) (+)= A B, both operands in shared memory (matrix descriptors)
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -334,7 +336,6 @@ __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
 // (H, L) += (h, l), unnormalised pairs
 __device__ __forceinline__ void dd_acc(float& H, float& L, float h, float l) {
   float s, err;
@@ -348,13 +349,11 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
                                                    const unsigned char* __restrict__ scratch, int64_t ss,
                                                    int* timeout, long spin) {
   extern __shared__ unsigned char sm_raw[];
-  __shared__ __align__(8) uint64_t full8[S8], empty8[S8], full16[S16], empty16[S16], accfull[SETS], accempty[SETS], done;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], accfull, accempty, done;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   __shared__ int eA[TC_M], eB[TC_N];
-  unsigned char* sm = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);
-  unsigned char* ring8 = sm;                                   // S8 x (SA8 + SB8) bytes
-  unsigned char* ring16 = sm + size_t(S8) * (SA8 + SB8);       // S16 x (SA + SB) bytes
+  unsigned char* ring = sm_raw + ((1024u - (smem_u32(sm_raw) & 1023u)) & 1023u);  // STAGES x (SA + SB) bytes
 
   const TileRef tr = tiles[blockIdx.x];
   const TcDesc t = tcd[tr.desc];
@@ -362,12 +361,6 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
   const int64_t e = blockIdx.y;
   const unsigned char* scr = scratch + e * ss;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  {
-    const int* xa = reinterpret_cast<const int*>(scr) + t.exp_a + int64_t(tr.tm) * TC_M;
-    const int* xb = reinterpret_cast<const int*>(scr) + t.exp_b + int64_t(tr.tn) * TC_N;
-    for (int i = tid; i < TC_M; i += NT) eA[i] = xa[i];
-    for (int i = tid; i < TC_N; i += NT) eB[i] = xb[i];
-  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(TMEM_COLS)
@@ -375,18 +368,12 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 32) {
-    for (int s = 0; s < S8; ++s) {
-      mbar_init(&full8[s], 1);
-      mbar_init(&empty8[s], FW);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
     }
-    for (int s = 0; s < S16; ++s) {
-      mbar_init(&full16[s], FW);
-      mbar_init(&empty16[s], 1);
-    }
-    for (int q = 0; q < SETS; ++q) {
-      mbar_init(&accfull[q], 1);
-      mbar_init(&accempty[q], FW);
-    }
+    mbar_init(&accfull, 1);
+    mbar_init(&accempty, FW);
     mbar_init(&done, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -399,38 +386,42 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
   const int KB = t.kb, njobs = 3 * KB;  // job j: component j / KB, 16-k block j % KB
 
   if (warp == FW) {
-    // ---- producer: 8-bit digit blocks of A and B into the byte ring
+    // ---- producer: the BF16 digit planes of A and B of each job into the stages
     if (lane == 0) {
+      auto plane_a = [&](int jj) {
+        const int c = jj / KB, kb = jj - c * KB;
+        return scr + t.dig_a + ((int64_t(c) * KB + kb) * t.rba + tr.tm) * int64_t(SA);
+      };
+      auto plane_b = [&](int jj) {
+        const int c = jj / KB, kb = jj - c * KB;
+        return scr + t.dig_b + ((int64_t(c) * KB + kb) * t.rbb + tr.tn) * int64_t(SB);
+      };
       int j = 0;
       for (; j < njobs; ++j) {
-        const int s = j % S8, u = j / S8;
-        if (u > 0 && !mbar_wait(&empty8[s], (u - 1) & 1, abrt, spin)) break;
-        const int c = j / KB, kb = j - c * KB;
-        const unsigned char* ga = scr + t.dig_a + ((int64_t(c) * KB + kb) * t.rba + tr.tm) * int64_t(SA8);
-        const unsigned char* gb = scr + t.dig_b + ((int64_t(c) * KB + kb) * t.rbb + tr.tn) * int64_t(SB8);
-        unsigned char* st = ring8 + size_t(s) * (SA8 + SB8);
-        mbar_expect_tx(&full8[s], SA8 + SB8);
-        bulk_g2s(st, ga, SA8, &full8[s]);
-        bulk_g2s(st + SA8, gb, SB8, &full8[s]);
+        const int s = j % STAGES, u = j / STAGES;
+        if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, abrt, spin)) break;
+        unsigned char* st = ring + size_t(s) * (SA + SB);
+        mbar_expect_tx(&full[s], SA + SB);
+        bulk_g2s(st, plane_a(j), SA, &full[s]);
+        bulk_g2s(st + SA, plane_b(j), SB, &full[s]);
       }
       // the last copies into every stage have landed before the CTA ends
-      for (int jj = j > S8 ? j - S8 : 0; jj < j; ++jj) mbar_drain(&full8[jj % S8], (jj / S8) & 1);
+      for (int jj = j > STAGES ? j - STAGES : 0; jj < j; ++jj) mbar_drain(&full[jj % STAGES], (jj / STAGES) & 1);
     }
   } else if (warp == FW + 1) {
-    // ---- MMA issue: 28 digit-pair products per 16 k into the group accumulators
+    // ---- MMA issue: 28 digit-pair products per job into the group accumulators
     if (lane == 0) {
-      int q = 0;  // chunks handed to the accumulator warps; chunk q fills set q % SETS
+      int q = 0;  // chunks handed to the accumulator warps
       for (int j = 0; j < njobs; ++j) {
-        const int s = j % S16, u = j / S16;
+        const int s = j % STAGES, u = j / STAGES;
         const int kb = j % KB, kc = kb % CHUNK;
-        if (kc == 0 && q >= SETS) {  // the set was read back by the accumulator warps
-          if (!mbar_wait(&accempty[q % SETS], ((q - SETS) / SETS) & 1, abrt, spin)) break;
+        if (kc == 0 && q > 0) {  // the accumulators were read back by the accumulator warps
+          if (!mbar_wait(&accempty, (q - 1) & 1, abrt, spin)) break;
           tc_fence_after();
         }
-        if (!mbar_wait(&full16[s], u & 1, abrt, spin)) break;
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(ring16 + size_t(s) * (SA + SB)), b0 = a0 + SA;
-        const uint32_t set = tmem + uint32_t((q % SETS) * SET_COLS);
+        // the bulk copies of this stage have landed (the wait acquires their writes)
+        if (!mbar_wait(&full[s], u & 1, abrt, spin)) break;
+        const uint32_t sa = smem_u32(ring + size_t(s) * (SA + SB)), sb = sa + SA;
 #pragma unroll
         for (int t1 = 0; t1 < TC_S; ++t1)
 #pragma unroll
@@ -438,12 +429,11 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
             const int acc = t1 + t2 < NACC - 1 ? t1 + t2 : NACC - 1;
             // the first product into each accumulator of a chunk overwrites it
             const uint32_t accumulate = (kc == 0 && t1 == 0 && t2 <= NACC - 1) ? 0u : 1u;
-            mma_bf16(set + uint32_t(acc * TC_N), sdesc(a0 + t1 * uint32_t(2 * TC_PLANE_A)),
-                     sdesc(b0 + t2 * uint32_t(2 * TC_PLANE_B)), accumulate);
+            mma_bf16(tmem + uint32_t(acc * TC_N), sdesc(sa + uint32_t(t1 * PA)), sdesc(sb + uint32_t(t2 * PB)), accumulate);
           }
-        if (j + S16 < njobs) mma_commit(&empty16[s]);
+        if (j + STAGES < njobs) mma_commit(&empty[s]);
         if (kc == CHUNK - 1 || kb == KB - 1) {
-          mma_commit(&accfull[q % SETS]);
+          mma_commit(&accfull);
           ++q;
         }
       }
@@ -452,61 +442,26 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
       mbar_drain(&done, 0);
     }
   } else {
-    // ---- accumulator warps: widen the byte stages into the BF16 ring (up to
-    // S16 jobs ahead of the MMAs); flush the TMEM lanes 32 (warp % 4) ..,
-    // columns 32 (warp / 4) .. after every chunk
-    const int quad = warp & 3, half = warp >> 2;
-    const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(half * 32);
-    auto widen = [&](int j) -> bool {
-      const int s8 = j % S8, s16 = j % S16, u16 = j / S16;
-      if (!mbar_wait(&full8[s8], (j / S8) & 1, abrt, spin)) return false;
-      if (u16 > 0 && !mbar_wait(&empty16[s16], (u16 - 1) & 1, abrt, spin)) return false;
-      const uint4* src = reinterpret_cast<const uint4*>(ring8 + size_t(s8) * (SA8 + SB8));
-      uint4* dst = reinterpret_cast<uint4*>(ring16 + size_t(s16) * (SA + SB));
-      for (int i = tid; i < (SA8 + SB8) / 16; i += FW * 32) {
-        const uint4 v = src[i];
-        // digit plane of these 16 bytes, and its weight 2^(-8t)
-        const int byte = 16 * i;
-        const int t = byte < SA8 ? byte / int(TC_PLANE_A) : (byte - SA8) / int(TC_PLANE_B);
-        const float wt = __int_as_float((127 - 8 * t) << 23);
-        const float off = -8388736.f * wt;  // -(2^23 + 128) wt, exact
-        const uint2 a = widen4(v.x, wt, off), b = widen4(v.y, wt, off), c = widen4(v.z, wt, off),
-                    w = widen4(v.w, wt, off);
-        dst[2 * i] = make_uint4(a.x, a.y, b.x, b.y);
-        dst[2 * i + 1] = make_uint4(c.x, c.y, w.x, w.y);
-      }
-      // the generic-proxy writes are seen by the tensor cores (async proxy)
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(&full16[s16]);
-        mbar_arrive(&empty8[s8]);
-      }
-      return true;
-    };
-    float ac[32][4];  // Re (hi, lo), Im (hi, lo) of 32 outputs, unnormalised pairs
+    // ---- accumulator warps: after every chunk read the TMEM lanes 32 (warp % 4) ..,
+    // columns CPT (warp / 4) .. and fold them into FP32-pair accumulators
+    const int quad = warp & 3, cg = warp >> 2;
+    const uint32_t tbase = tmem + (uint32_t(quad * 32) << 16) + uint32_t(cg * CPT);
+    float ac[CPT][4];  // Re (hi, lo), Im (hi, lo) of CPT outputs, unnormalised pairs
 #pragma unroll
-    for (int o = 0; o < 32; ++o) ac[o][0] = ac[o][1] = ac[o][2] = ac[o][3] = 0.f;
+    for (int o = 0; o < CPT; ++o) ac[o][0] = ac[o][1] = ac[o][2] = ac[o][3] = 0.f;
     const int nch = (KB + CHUNK - 1) / CHUNK;
     bool ok = true;
-    int q = 0, jw = 0;  // chunks flushed, jobs widened
+    int q = 0;  // chunks flushed
     for (int c = 0; c < 3 && ok; ++c) {
       for (int ch = 0; ch < nch; ++ch, ++q) {
-        // jobs up to the end of this chunk and S16 beyond, so that the MMAs
-        // of the next chunk can start as soon as the flush is done
-        const int last = c * KB + min(KB, (ch + 1) * CHUNK) - 1;
-        const int upto = min(njobs - 1, last + S16);
-        for (; ok && jw <= upto; ++jw) ok = __all_sync(0xffffffffu, widen(jw));
-        if (!ok) break;
-        ok = __all_sync(0xffffffffu, mbar_wait(&accfull[q % SETS], (q / SETS) & 1, abrt, spin));
+        ok = __all_sync(0xffffffffu, mbar_wait(&accfull, q & 1, abrt, spin));
         if (!ok) break;
         tc_fence_after();
-        const uint32_t tset = tbase + uint32_t((q % SETS) * SET_COLS);
 #pragma unroll
-        for (int cs = 0; cs < 32; cs += 4) {
+        for (int cs = 0; cs < CPT; cs += 4) {
           float v[NACC][4];
 #pragma unroll
-          for (int g = 0; g < NACC; ++g) tmem_ld4(tset + uint32_t(g * TC_N + cs), v[g]);
+          for (int g = 0; g < NACC; ++g) tmem_ld4(tbase + uint32_t(g * TC_N + cs), v[g]);
           tmem_wait_ld();
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -514,9 +469,9 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
             float h = v[0][i], l = 0.f;
 #pragma unroll
             for (int g = 1; g < NACC; ++g) {
-              float s, err;
-              two_sum(h, v[g][i], s, err);
-              h = s;
+              float sum, err;
+              two_sum(h, v[g][i], sum, err);
+              h = sum;
               l += err;
             }
             float* a = ac[cs + i];
@@ -533,55 +488,72 @@ __global__ void __launch_bounds__(NT, 1) k_gemm_tc(const GemmDesc* __restrict__ 
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&accempty[q % SETS]);
+        if (lane == 0) mbar_arrive(&accempty);
       }
     }
     // ---- epilogue through shared memory, which is idle once the last chunk
     // has been read (every copy consumed, every MMA complete): each thread
-    // puts its 32 outputs, scaled by 2^(eA + eB - 12) (the weighted digits
-    // carry 2^96 of the 2^-108), into a padded 128 x 64 tile; then whole warps
-    // write rows of C (alpha, beta D) with consecutive lanes on consecutive
-    // columns.  A warp that gave up has raised the abort flag before the
-    // first barrier, so no warp writes C then.
-    float4* tile = reinterpret_cast<float4*>(sm);  // [TC_M][TILE_LD]
+    // puts its CPT outputs, scaled by 2^(eA + eB - 12) (the weighted digits
+    // carry 2^96 of the 2^-108) as 2^(eA - 6) 2^(eB - 6), into a padded
+    // 128 x 64 tile; then whole warps write rows of C (alpha, beta D) with
+    // consecutive lanes on consecutive columns.  A warp that gave up has
+    // raised the abort flag before the first barrier, so no warp writes C then.
+    float4* tile = reinterpret_cast<float4*>(ring);  // [TC_M][TILE_LD]
+    {  // the row and column exponents, loaded only now so that the start of the CTA does not wait for them
+      const int* xa = reinterpret_cast<const int*>(scr) + t.exp_a + int64_t(tr.tm) * TC_M;
+      const int* xb = reinterpret_cast<const int*>(scr) + t.exp_b + int64_t(tr.tn) * TC_N;
+      for (int i = tid; i < TC_M; i += FW * 32) eA[i] = xa[i];
+      for (int i = tid; i < TC_N; i += FW * 32) eB[i] = xb[i];
+    }
     named_sync(1, FW * 32);
     if (ok) {
       const int row = quad * 32 + lane;
+      const float fa = __int_as_float((eA[row] - 6 + 127) << 23);
 #pragma unroll
-      for (int o = 0; o < 32; ++o) {
-        const int jl = half * 32 + o;
-        const int ex = eA[row] + eB[jl] - 12;
+      for (int o = 0; o < CPT; ++o) {
+        const int jl = cg * CPT + o;
+        const float f = fa * __int_as_float((eB[jl] - 6 + 127) << 23);
         f2 re, im;
         two_sum(ac[o][0], ac[o][1], re.h, re.l);
         two_sum(ac[o][2], ac[o][3], im.h, im.l);
-        tile[row * TILE_LD + jl] = make_float4(ldexpf(re.h, ex), ldexpf(re.l, ex), ldexpf(im.h, ex), ldexpf(im.l, ex));
+        tile[row * TILE_LD + jl] = make_float4(re.h * f, re.l * f, im.h * f, im.l * f);
       }
     }
     named_sync(1, FW * 32);
     if (!*abrt) {
-      float4* C = arena + e * se + d.offC;
-      const float4* D = arena + e * se + d.offD;
       using O = Ops<DF>;
-      for (int r = warp; r < TC_M; r += FW) {
-        const int gm = tr.tm * TC_M + r;
-        if (gm >= d.m) break;
+      const int gm0 = tr.tm * TC_M, gn0 = tr.tn * TC_N;
+      float4* C = arena + e * se + d.offC + int64_t(gm0) * d.ldc + gn0;
+      const float4* D = arena + e * se + d.offD + int64_t(gm0) * d.ldd + gn0;
+      const int rows = min(TC_M, d.m - gm0), cols = min(TC_N, d.n - gn0);
+      const int amode = d.alpha == 1.0 ? 0 : (d.alpha == -1.0 ? 1 : 2);
+      const int bmode = d.beta == 0.0 ? 0 : (d.beta == 1.0 ? 1 : 2);
+      const int r0 = warp * EPI_ROWS;  // this warp's rows, their D loads in flight together
+      float4 dv[EPI_ROWS][TC_N / 32];
+      if (bmode) {
+#pragma unroll
+        for (int i = 0; i < EPI_ROWS; ++i)
+#pragma unroll
+          for (int h2 = 0; h2 < TC_N / 32; ++h2) {
+            const int r = r0 + i, jl = h2 * 32 + lane;
+            dv[i][h2] = (r < rows && jl < cols) ? D[int64_t(r) * d.ldd + jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+      }
+#pragma unroll
+      for (int i = 0; i < EPI_ROWS; ++i)
 #pragma unroll
         for (int h2 = 0; h2 < TC_N / 32; ++h2) {
-          const int jl = h2 * 32 + lane, gn = tr.tn * TC_N + jl;
-          if (gn < d.n) {
+          const int r = r0 + i, jl = h2 * 32 + lane;
+          if (r < rows && jl < cols) {
             float4 v = tile[r * TILE_LD + jl];
-            if (d.alpha == -1.0)
+            if (amode == 1)
               v = O::neg(v);
-            else if (d.alpha != 1.0)
+            else if (amode == 2)
               v = O::scale(v, d.alpha);
-            if (d.beta != 0.0) {
-              const float4 dv = D[int64_t(gm) * d.ldd + gn];
-              v = O::add(v, d.beta == 1.0 ? dv : O::scale(dv, d.beta));
-            }
-            C[int64_t(gm) * d.ldc + gn] = v;
+            if (bmode) v = O::add(v, bmode == 1 ? dv[i][h2] : O::scale(dv[i][h2], d.beta));
+            C[int64_t(r) * d.ldc + jl] = v;
           }
         }
-      }
     }
   }
   tc_fence_before();
@@ -602,9 +574,9 @@ int64_t gemm_tc_scratch(const GemmDesc& g, TcDesc& t, int64_t off) {
   t.rba = (g.m + TC_M - 1) / TC_M;
   t.rbb = (g.n + TC_N - 1) / TC_N;
   t.dig_a = off;
-  off += 3 * int64_t(t.kb) * t.rba * SA8;
+  off += 3 * int64_t(t.kb) * t.rba * SA;
   t.dig_b = off;
-  off += 3 * int64_t(t.kb) * t.rbb * SB8;
+  off += 3 * int64_t(t.kb) * t.rbb * SB;
   t.exp_a = off / 4;
   off += int64_t(t.rba) * TC_M * 4;
   t.exp_b = off / 4;
