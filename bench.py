@@ -55,16 +55,21 @@ UNIT = "energies/s"
 GATE = 1e-6
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
-# ncu capture of the launch list, averaged over the kernel's launches of one
-# step; see profiles/), valid only for the kernel sources it was measured on:
-# a source digest that no longer matches turns the figure into null.
+# DRAM traffic per launch at 128 energies (dram__bytes_read.sum +
+# dram__bytes_write.sum): one ncu capture of every launch of the 4-energy case
+# (bench.py --profile-case 4 with the tuned kernel choice of the benchmark),
+# the bytes of each kernel kind divided by its launches and scaled by 128 / 4
+# (every energy is an independent problem in every kernel); see profiles/.
+# Valid only for the kernel sources it was measured on: a source digest that
+# no longer matches turns the figure into null.
 KERNEL_SOURCES = ["nd_kernels.cu", "nd_arith.cuh", "nd_gemm_tc.cu", "nd_gj.cuh", "nd_api.cu"]
-TRAFFIC = {  # kernel name -> (bytes per launch, source digest)
-    # FP32-pipe GEMM launches (k_gemm 16 x 16 and 32 x 32 tiles, k_gemm_direct): 914.4 GB over 404 launches
-    "complex-fp32x2:gemm": (2263448330, "28a4a6eb5b1da542"),
-    # tensor-core GEMM steps (k_tc_split + k_gemm_tc): 379.7 GB over 104 steps
-    "complex-fp32x2:gemm_tc": (3650670860, "28a4a6eb5b1da542"),
+TRAFFIC = {  # kernel kind -> (bytes per launch, source digest)
+    "complex-fp32x2:gemm_tc": (4532390407, "6e0fbc706fff28a7"),  # k_tc_split + k_gemm_tc
+    "complex-fp32x2:gemm_direct": (1533666868, "6e0fbc706fff28a7"),
+    "complex-fp32x2:gemm": (2385349120, "6e0fbc706fff28a7"),
+    "complex-fp32x2:gemm_small": (445520554, "6e0fbc706fff28a7"),
+    "complex-fp32x2:inverse": (182981700, "6e0fbc706fff28a7"),
+    "complex-fp32x2:delay": (860744782, "6e0fbc706fff28a7"),
 }
 
 
@@ -112,6 +117,11 @@ def parse():
     ap.add_argument("--dump-density", default="", help="write the densities of the paths to this .npz")
     ap.add_argument("--only", default="", help="run one path only (fp64_nd, fp32x2, fp32); for profiling")
     ap.add_argument("--energies", type=int, default=0, help="use the first K energies only; for profiling")
+    ap.add_argument("--save-choice", default="", help="write the FP32-pair path's tuned kernel choice to this file")
+    ap.add_argument("--load-choice", default="",
+                    help="apply the FP32-pair kernel choice of this file (--save-choice) instead of tuning")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="run one small case of the headline FP32-pair path (this many energies per call; for ncu)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--cpu-worker", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-save", default="", help=argparse.SUPPRESS)
@@ -328,10 +338,15 @@ def main_ours(a) -> None:
             continue
         chunk = min(chunk, n_e)
         solver = Solver(dev, tr, precision=prec, max_ne=chunk, delay=delay, tile=a.tile, leaf_size=a.leaf)
-        if not a.no_tune and a.tile == "auto" and name != "fp64_nd_plain":
+        if name == "fp32x2" and a.load_choice:  # a stored tuning (--save-choice) instead of a new one
+            solver.set_choice(load_choice(a.load_choice)[2])
+            tuning[name] = {"loaded": a.load_choice}
+        elif not a.no_tune and a.tile == "auto" and name != "fp64_nd_plain":
             t0 = time.perf_counter()
             tinfo = solver.autotune(E_all[:chunk])
             tuning[name] = dict(tinfo, seconds=round(time.perf_counter() - t0, 2))
+            if name == "fp32x2" and a.save_choice:
+                save_choice(a.save_choice, solver.choice(), a.leaf, delay)
         if name == "fp64_nd":
             fallback = solver
         step = make_step(solver, chunk, name, fallback if name == "fp32x2" else None)
@@ -860,9 +875,62 @@ def main_reference(a) -> None:
     print(json.dumps(line), flush=True)
 
 
+def save_choice(path: str, choice, leaf: int, delay: int) -> None:
+    with open(path, "w") as fh:
+        fh.write(f"leaf {leaf} delay {delay}\n" + " ".join(str(int(c)) for c in choice) + "\n")
+
+
+def load_choice(path: str):
+    import numpy as np
+    with open(path) as fh:
+        head = fh.readline().split()
+        choice = np.array([int(v) for v in fh.readline().split()], dtype=np.int8)
+    return int(head[1]), int(head[3]), choice
+
+
+def main_profile(a) -> None:
+    """One small case of the headline path for ncu: the 512 x 128 superlattice
+    on the FP32-pair path with --profile-case energies per call (the workspace
+    of that many energies, a few GB, above the L2 size), the kernel of every
+    launch as --load-choice gives it (the choice the tuner made on the
+    128-energy handle of the benchmark, written by --save-choice), one warm and
+    one measured call.  Per-launch figures of this case scale to a 128-energy
+    launch by the energies, since every energy is an independent problem in
+    every kernel.  Prints one JSON line with the library's per-kind launch
+    profile of the measured call."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1070_gb300 import ndgf, workloads
+    from paper_1305_1070_gb300.solver import Solver
+
+    n = a.profile_case
+    dev, tr = workloads.workload(WORKLOAD)
+    leaf, delay, choice = (a.leaf, a.delay, None)
+    if a.load_choice:
+        leaf, delay, choice = load_choice(a.load_choice)
+    s = Solver(dev, tr, precision=ndgf.ND_PREC_FP32X2, max_ne=n, delay=delay, leaf_size=leaf)
+    if choice is not None:
+        s.set_choice(choice)
+    E = torch.as_tensor(np.asarray(tr.energies[100:100 + n]), device="cuda")
+    s.step(E)
+    torch.cuda.synchronize()
+    ndgf.nd_profile(s.fact, True)
+    s.step(E)
+    torch.cuda.synchronize()
+    stats = ndgf.nd_profile(s.fact, False)
+    print(json.dumps({"profile_case": n, "leaf": leaf, "delay": delay, "choice_loaded": choice is not None,
+                      "kinds": {p["name"]: {"launches": p["launches"], "ms": round(p["ms"], 3),
+                                            "gflop": round(p["flops"] / 1e9, 3)} for p in stats}}))
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.cpu_worker:
+    if args.profile_case:
+        main_profile(args)
+    elif args.cpu_worker:
         cpu_worker(args.cpu_worker, args.cpu_save, args.cpu_world)
     elif args.impl == "reference":
         main_reference(args)

@@ -437,6 +437,22 @@ nd_status nd_autotune(nd_fact* fact, const double* H_values, const double* sigma
  * stays usable (the next nd_factor starts clean).  Errors: ND_ERR_INVALID_ARG. */
 nd_status nd_fact_set_wait_limit(nd_fact* fact, int64_t polls);
 
+/* The kernel of every step, as nd_autotune chose it (or as nd_fact_set_choice
+ * set it; -1 everywhere on a new handle: the default rules), flattened over
+ * the schedules in this order: fold, G^r, G^<, phonon G^<, adjoint forward,
+ * adjoint backward.  Entries: -1 default rule, 0 large tile, 1 small tile,
+ * 2 tensor cores (FP32 pairs only), 3 one CTA per block (blocks up to 192),
+ * 4 extra-large tile; a step that is not a GEMM takes -1.  A stored choice
+ * applies to any handle of the same plan, precision and flags (one with fewer
+ * energies, say), which then runs the same kernels with the same results.
+ * nd_fact_get_choice writes min(count, max) entries (choice may be NULL) and
+ * the count to *n; nd_fact_set_choice takes exactly count entries and rebuilds
+ * the launch tables.  No counterpart in the paper (an implementation control,
+ * like the tuner).  Errors: ND_ERR_INVALID_ARG (count, a value out of range or
+ * not allowed on its step; max below the count), ND_ERR_OOM. */
+nd_status nd_fact_get_choice(nd_fact* fact, int8_t* choice, int32_t max, int32_t* n);
+nd_status nd_fact_set_choice(nd_fact* fact, const int8_t* choice, int32_t n);
+
 /* ---- S1a: contact self-energies (paper Sec. 2) ----------------------------
  * A lead is a semi-infinite chain of principal layers with on-site block H00
  * (m x m real symmetric), hopping H01 (m x m) from a layer to the next one

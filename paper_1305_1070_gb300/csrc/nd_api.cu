@@ -168,6 +168,7 @@ struct nd_fact {
   std::vector<TileRange> tr_factor, tr_green, tr_lesser[2];
   std::vector<GemmDesc> gemm_all;  // the plan's GEMM table plus the adjoint's (host copy)
   bool tuned = false;
+  std::array<std::vector<int8_t>, 6> choice;  // kernel per step of each schedule (-1: default rules)
   // staging buffers for host inputs / outputs
   double *st_H = nullptr, *st_sr = nullptr, *st_ph = nullptr, *st_E = nullptr;
   double *st_sl = nullptr, *st_sg = nullptr, *st_pl = nullptr, *st_pg = nullptr;
@@ -1338,6 +1339,7 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
     }
   }
   if ((st = build_all_tiles(f, &best)) != ND_OK) return st;
+  for (int q = 0; q < N_SCHED; ++q) f->choice[q] = best[q];
   for (int q = 0; q < 4; ++q)
     for (size_t si = 0; si < sched[q]->size(); ++si)
       if ((*sched[q])[si].kind == ST_GEMM && ms[q][si][0] >= 0.0) ++by_kind[(*trs[q])[si].kind];
@@ -1350,6 +1352,54 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
     info->passes = passes;
     for (int k = 0; k < 5; ++k) info->by_kind[k] = by_kind[k];
   }
+  return ND_OK;
+}
+
+// The schedules whose GEMM steps carry a kernel choice, in the order of
+// nd_fact_get_choice: fold, G^r, G^<, phonon G^<, adjoint forward and backward.
+static std::array<const std::vector<Step>*, N_SCHED> choice_scheds(const nd_fact* f) {
+  const nd_plan* p = f->plan;
+  return {&p->sched_factor, &p->sched_green, &p->sched_lesser[0], &p->sched_lesser[1], &f->sched_adj_fwd,
+          &f->sched_adj_bwd};
+}
+
+extern "C" nd_status nd_fact_get_choice(nd_fact* f, int8_t* choice, int32_t max, int32_t* n) {
+  if (!f || !n || (choice && max < 0)) return fail(ND_ERR_INVALID_ARG, "nd_fact_get_choice: bad argument");
+  const auto sc = choice_scheds(f);
+  int64_t k = 0;
+  for (int q = 0; q < N_SCHED; ++q)
+    for (size_t si = 0; si < sc[q]->size(); ++si, ++k)
+      if (choice && k < max) choice[k] = si < f->choice[q].size() ? f->choice[q][si] : int8_t(-1);
+  *n = int32_t(k);
+  if (choice && k > max) return fail(ND_ERR_INVALID_ARG, "nd_fact_get_choice: the array is too short");
+  return ND_OK;
+}
+
+extern "C" nd_status nd_fact_set_choice(nd_fact* f, const int8_t* choice, int32_t n) {
+  if (!f || !choice || n < 0) return fail(ND_ERR_INVALID_ARG, "nd_fact_set_choice: bad argument");
+  const auto sc = choice_scheds(f);
+  const bool ph = (f->flags & ND_FACT_PHONON) != 0;
+  std::array<Choice, N_SCHED> want;
+  int64_t k = 0;
+  for (int q = 0; q < N_SCHED; ++q) {
+    want[q].assign(sc[q]->size(), -1);
+    for (size_t si = 0; si < sc[q]->size(); ++si, ++k) {
+      if (k >= n) return fail(ND_ERR_INVALID_ARG, "nd_fact_set_choice: fewer entries than steps");
+      const int c = choice[k];
+      const Step& st = (*sc[q])[si];
+      bool ok = c >= -1 && c <= 4 && (c == -1 || st.kind == ST_GEMM);
+      if (ok && c == 2)
+        ok = f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_step_scratch(st, f->gemm_all) <= TC_MAX_SCRATCH;
+      if (ok && c == 3) ok = st.max_dim <= 192;
+      if (ok && c == 4) ok = st.max_dim > 32;
+      if (!ok) return fail(ND_ERR_INVALID_ARG, "nd_fact_set_choice: a kernel that this step cannot take");
+      want[q][si] = int8_t(c);
+    }
+  }
+  if (k != n) return fail(ND_ERR_INVALID_ARG, "nd_fact_set_choice: more entries than steps");
+  nd_status st = build_all_tiles(f, &want);
+  if (st != ND_OK) return st;
+  f->choice = want;
   return ND_OK;
 }
 

@@ -34,7 +34,7 @@ EXPORTS = ["nd_analyze", "nd_plan_query", "nd_plan_tree", "nd_plan_cluster_sites
            "nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate", "nd_fact_status",
            "nd_density", "nd_profile", "nd_invert_c64_noalloc",
            "nd_lead_create", "nd_lead_sigma", "nd_lead_status", "nd_lead_destroy", "nd_contact_current", "nd_density_gradient", "nd_profile_launches", "nd_sigma_lesser_fermi", "nd_phonon_const", "nd_phonon_scba",
-           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_autotune", "nd_density_jvp", "nd_poisson_create",
+           "nd_check_factor_inputs", "nd_check_lesser_inputs", "nd_selected_entries", "nd_fact_density", "nd_fact_set_wait_limit", "nd_fact_get_choice", "nd_fact_set_choice", "nd_autotune", "nd_density_jvp", "nd_poisson_create",
            "nd_poisson_apply", "nd_poisson_solve", "nd_poisson_destroy", "nd_vec_dot", "nd_vec_axpby", "nd_vec_mul", "nd_vec_scale_pos",
            "nd_last_error",
            "nd_version"]
@@ -101,6 +101,8 @@ def lib():
             "nd_diag_green": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], _I32),
             "nd_fact_status": ([_P, ctypes.POINTER(_I32)], _I32),
             "nd_fact_set_wait_limit": ([_P, _I64], _I32),
+            "nd_fact_get_choice": ([_P, _P, _I32, _P], _I32),
+            "nd_fact_set_choice": ([_P, _P, _I32], _I32),
             "nd_autotune": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _I32, _D, _I32, _P, _P], _I32),
             "nd_certificate": ([_P, _P, _P], _I32),
             "nd_selected_entries": ([_P, _P, _P, _I32, _P, _P, _P, _P, _P], _I32),
@@ -344,6 +346,21 @@ def nd_fact_status(fact: Fact) -> int:
 def nd_fact_set_wait_limit(fact: Fact, polls: int):
     """Polls before a tensor-core wait gives up (0 = default)."""
     _check(lib().nd_fact_set_wait_limit(fact.ptr, int(polls)), "nd_fact_set_wait_limit")
+
+
+def nd_fact_get_choice(fact: Fact) -> np.ndarray:
+    """The kernel of every step (int8, -1 = default rule), flattened over the schedules."""
+    n = _I32(0)
+    _check(lib().nd_fact_get_choice(fact.ptr, None, 0, ctypes.byref(n)), "nd_fact_get_choice")
+    out = np.full(n.value, -1, dtype=np.int8)
+    _check(lib().nd_fact_get_choice(fact.ptr, out.ctypes.data_as(_P), n.value, ctypes.byref(n)), "nd_fact_get_choice")
+    return out
+
+
+def nd_fact_set_choice(fact: Fact, choice) -> None:
+    """Apply a stored kernel choice (as nd_fact_get_choice returns it)."""
+    c = np.ascontiguousarray(np.asarray(choice, dtype=np.int8))
+    _check(lib().nd_fact_set_choice(fact.ptr, c.ctypes.data_as(_P), int(c.size)), "nd_fact_set_choice")
 
 
 def nd_autotune(fact: Fact, H_values, sigma_r, sigma_ph_r, sigma_lesser, sigma_greater, ph_lesser, ph_greater,

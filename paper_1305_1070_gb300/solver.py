@@ -150,6 +150,15 @@ class Solver:
         return ndgf.nd_autotune(self.fact, self.H, self.sig_r if self.leads else None, self.ph_r, self.sig_l,
                                 self.sig_g, self.ph_l, self.ph_g, E, n_e, self.tr.eta, reps)
 
+    def choice(self) -> np.ndarray:
+        """The kernel of every step (nd_fact_get_choice), to store a tuning."""
+        return ndgf.nd_fact_get_choice(self.fact)
+
+    def set_choice(self, choice) -> None:
+        """Apply a stored kernel choice (nd_fact_set_choice), e.g. one tuned on
+        a handle of the same plan with more energies."""
+        ndgf.nd_fact_set_choice(self.fact, choice)
+
     def scba(self, energies, D: float, *, mix: float = 1.0, updates: int | None = None, tol: float = 1e-13,
              max_updates: int = 2000):
         """Self-consistent Born iteration of an elastic local phonon self-energy,

@@ -79,3 +79,41 @@ def test_extra_large_tile_every_launch(precision, tol):
     tr = workloads.Transport(energies=np.array([0.06, 0.29]), gamma_ph=2e-3, mu_ph=0.05)
     s = Solver(dev, tr, precision=precision, leaf_size=40, delay=2, tile="xl")
     _check(s, dev, tr, tol=tol)
+
+
+def test_stored_choice_on_a_smaller_handle():
+    """A tuning stored with nd_fact_get_choice and applied with
+    nd_fact_set_choice to a handle of the same plan with fewer energies runs the
+    same kernels: its diagonals equal the tuned handle's bit for bit (and the
+    oracle's at the path's tolerance); out-of-range values, a wrong count and
+    the tensor cores on a complex128 handle are refused."""
+    dev = workloads.superlattice(40, 12, disorder=0.03, seed=21)
+    tr = workloads.Transport(energies=np.linspace(0.03, 0.47, 6))
+    big = Solver(dev, tr, precision=ndgf.ND_PREC_FP32X2, leaf_size=10, delay=2, max_ne=6)
+    fresh = big.choice()
+    assert (fresh == -1).all()
+    big.autotune(tr.energies)
+    choice = big.choice()
+    assert choice.size == fresh.size and (choice >= -1).all() and (choice <= 4).all() and (choice >= 0).any()
+    small = Solver(dev, tr, precision=ndgf.ND_PREC_FP32X2, leaf_size=10, delay=2, max_ne=2)
+    small.set_choice(choice)
+    assert np.array_equal(small.choice(), choice)
+    pick = tr.energies[[1, 4]]
+    want = [g.clone() for g in big.step(pick)]
+    got = small.step(pick)
+    torch.cuda.synchronize()
+    for a, b in zip(got, want):
+        assert torch.equal(a, b)
+    ref = dense.green_diag(dev, workloads.Transport(energies=pick))
+    for e in range(2):
+        assert observables.rel_err(got[0][e].cpu().numpy(), ref["Gr"][e]) < 1e-9
+    bad = choice.copy()
+    bad[np.argmax(choice >= 0)] = 7
+    with pytest.raises(ndgf.NDError):
+        small.set_choice(bad)
+    with pytest.raises(ndgf.NDError):
+        small.set_choice(choice[:-1])
+    f64 = Solver(dev, tr, precision=ndgf.ND_PREC_FP64, leaf_size=10, delay=2, max_ne=2)
+    tc = np.where(choice >= 0, 2, -1).astype(np.int8)
+    with pytest.raises(ndgf.NDError):
+        f64.set_choice(tc)
