@@ -112,6 +112,8 @@ def parse():
     ap.add_argument("--tile", default="auto", choices=["auto", "large", "small", "tc", "alu"],
                     help="GEMM kernel per launch: auto, a forced ALU tile size, tensor cores (FP32 pairs) or never")
     ap.add_argument("--no-tune", action="store_true", help="keep the default kernel rules (no nd_autotune)")
+    ap.add_argument("--graph", action="store_true",
+                    help="other workloads: replay each call's launches from a CUDA graph (ND_FACT_GRAPH)")
     ap.add_argument("--tune-plan", action="store_true",
                     help="also search leaf size and energies per call (paper_1305_1070_gb300.tune)")
     ap.add_argument("--dump-density", default="", help="write the densities of the paths to this .npz")
@@ -642,7 +644,7 @@ def main_aux(a) -> None:
     chunk = min(a.chunk_aux or cfg["chunk"], n_e)
     for name, prec, K, W in (("fp32x2", ndgf.ND_PREC_FP32X2, a.steps, max(1, min(a.warmup, 1))),
                              ("fp64_nd", ndgf.ND_PREC_FP64, 1, 0)):
-        s = Solver(dev, tr, precision=prec, max_ne=chunk, delay=a.delay, leaf_size=a.leaf)
+        s = Solver(dev, tr, precision=prec, max_ne=chunk, delay=a.delay, leaf_size=a.leaf, graph=a.graph)
         if not a.no_tune:
             t0 = time.perf_counter()
             tuned[name] = dict(s.autotune(E_all[:chunk]), seconds=round(time.perf_counter() - t0, 2))
@@ -695,7 +697,8 @@ def main_aux(a) -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "fp32x2 (FP32-pair complex) + c128 root",
             "data": cfg["data"],
             "config": {"workload": a.workload, "devices": n_dev, "sites": dev.n, "energies": n_e,
-                       "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": chunk},
+                       "leaf_size": a.leaf, "delayed_pivots_per_cluster": a.delay, "energies_per_call": chunk,
+                       "cuda_graph": a.graph},
             "paths": res, "tuning": tuned, "density_rel_err_fp32x2_vs_fp64": err, "gate_1e-6": err <= GATE,
             "roofline": {"kernel": "complex-fp32x2:gemm", "bound": "alu", "achieved": round(ach, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None},
