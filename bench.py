@@ -104,9 +104,9 @@ def parse():
                     choices=[WORKLOAD, "uneven_64", "cnt_10_0_400", "gradient_256x64", "newton_256x64"],
                     help="the headline workload, or another one (its own JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=6, help="energies of the CPU oracle sample")
-    ap.add_argument("--growth-max", type=float, default=10.0, help="fold growth above which fp32x2 redoes in FP64")
-    ap.add_argument("--resid-max", type=float, default=1e-8,
-                    help="FP64 certificate residual above which fp32x2 redoes in FP64")
+    ap.add_argument("--growth-max", type=float, default=1e4, help="fold growth above which fp32x2 redoes in FP64")
+    ap.add_argument("--resid-max", type=float, default=1e-6,
+                    help="FP64 certificate backward error above which fp32x2 redoes in FP64")
     ap.add_argument("--delay", type=int, default=2, help="delayed pivots per cluster (0 = the paper's elimination)")
     ap.add_argument("--no-plain", action="store_true", help="skip the reference timing without delayed pivots")
     ap.add_argument("--tile", default="auto", choices=["auto", "large", "small", "tc", "alu"],
@@ -254,7 +254,8 @@ def main_ours(a) -> None:
 
     def make_step(solver, chunk, name, fallback=None):
         """One pass over all energies; with a fallback solver, energies whose
-        certificate growth exceeds --growth-max are recomputed by it.
+        certificate backward errors exceed --resid-max (or whose fold growth
+        exceeds --growth-max) are recomputed by it.
         step(after_chunk) calls after_chunk(c0, m) once a call's diagonals are
         in Gr, Gl, Gg (the end-to-end step starts their host copies there)."""
         certs = torch.zeros(n_e, 8, dtype=torch.float64, device="cuda")
@@ -616,8 +617,9 @@ def main_aux(a) -> None:
     128-1024, 1.82 M sites in all) in one graph, 64 energies, one tree per
     device and every level launch spanning all devices; cnt_10_0_400 = the
     (10,0) tube, 1,024 energies, decimated leads, constant phonon broadening.
-    FP32-pair path with delayed pivots, gated on its density against the
-    complex128 path."""
+    FP32-pair path with delayed pivots and the S9 certificate (energies over
+    its thresholds recomputed on the complex128 path, which is timed first),
+    gated on its density against the complex128 path."""
     import numpy as np
     import torch
 
@@ -642,19 +644,44 @@ def main_aux(a) -> None:
     tuned = {}
     clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     chunk = min(a.chunk_aux or cfg["chunk"], n_e)
-    for name, prec, K, W in (("fp32x2", ndgf.ND_PREC_FP32X2, a.steps, max(1, min(a.warmup, 1))),
-                             ("fp64_nd", ndgf.ND_PREC_FP64, 1, 0)):
+    # complex128 first; then a complex128 handle of at most 16 energies (the
+    # workspace of both full handles can exceed the GPU) is the fallback of the
+    # certified FP32-pair steps
+    fallback = None
+    for name, prec, K, W in (("fp64_nd", ndgf.ND_PREC_FP64, 1, 0),
+                             ("fp32x2", ndgf.ND_PREC_FP32X2, a.steps, max(1, min(a.warmup, 1)))):
         s = Solver(dev, tr, precision=prec, max_ne=chunk, delay=a.delay, leaf_size=a.leaf, graph=a.graph)
         if not a.no_tune:
             t0 = time.perf_counter()
             tuned[name] = dict(s.autotune(E_all[:chunk]), seconds=round(time.perf_counter() - t0, 2))
         out = torch.zeros(dev.n, dtype=torch.float64, device="cuda")
+        cert_info = {"redone": 0, "resid_r_rel": 0.0, "resid_lesser_rel": 0.0, "growth": 0.0}
+        cert_rows = []
 
         def step():
+            redone = 0
             for c0 in range(0, n_e, chunk):
                 m = min(chunk, n_e - c0)
-                _, l, _ = s.step(E_all[c0:c0 + m])
+                if fallback is None:
+                    _, l, _ = s.step(E_all[c0:c0 + m])
+                else:  # S9: energies over the certificate's thresholds are recomputed in complex128
+                    _, l, _, cert, idx = s.step_certified(E_all[c0:c0 + m], fallback, resid_max=a.resid_max,
+                                                          growth_max=a.growth_max)
+                    redone += int(idx.numel())
+                    cert_rows.append(cert[:, [4, 6, 7]].clone())
+                    cm = cert.amax(dim=0).tolist()
+                    cert_info.update(resid_r_rel=max(cert_info["resid_r_rel"], cm[6]),
+                                     resid_lesser_rel=max(cert_info["resid_lesser_rel"], cm[7]),
+                                     growth=max(cert_info["growth"], cm[4]))
                 ndgf.nd_density(l, weights[c0:c0 + m].contiguous(), m, dev.n, 2.0 / (2.0 * np.pi), 1 if c0 else 0, out)
+            cert_info["redone"] = redone
+            if cert_rows:  # energies of the last pass over thresholds of growth and backward errors
+                c = torch.cat(cert_rows[-((n_e + chunk - 1) // chunk):]).cpu().numpy()
+                cert_rows.clear()
+                be = np.maximum(c[:, 1], c[:, 2])
+                cert_info["energies_over"] = {
+                    "backward_error": {f"{t:g}": int((be > t).sum()) for t in (1e-8, 1e-7, 1e-6, 1e-5)},
+                    "growth": {f"{t:g}": int((c[:, 0] > t).sum()) for t in (10, 100, 1000)}}
 
         for _ in range(W):
             step()
@@ -673,6 +700,7 @@ def main_aux(a) -> None:
         dens[name] = out.clone()
         alu = [p for p in prof if p["name"].startswith("gemm") and p["name"] != "gemm_tc"]
         res[name] = {"ms_per_step": round(ms, 1), "points_per_s": round(n_dev * n_e / (ms * 1e-3), 2),
+                     "certificate": dict(cert_info) if fallback is not None else None,
                      "useful_tflops": round((s.info["flops_factor"] + s.info["flops_green_r"] +
                                              s.info["flops_green_lesser"]) * n_e / (ms * 1e-3) / 1e12, 3),
                      "gemm": {"name": "ALU GEMM kernels", "launches": sum(p["launches"] for p in alu),
@@ -680,6 +708,9 @@ def main_aux(a) -> None:
                      "kernel_profile": prof}
         del s
         torch.cuda.empty_cache()
+        if fallback is None:
+            fallback = Solver(dev, tr, precision=ndgf.ND_PREC_FP64, max_ne=min(chunk, 16), delay=a.delay,
+                              leaf_size=a.leaf)
     clocks = clk.stop()
     err = float((dens["fp32x2"] - dens["fp64_nd"]).abs().max() / dens["fp64_nd"].abs().max())
     g = res["fp32x2"]["gemm"]

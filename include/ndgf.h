@@ -78,7 +78,8 @@ typedef enum { ND_PREC_FP64 = 0, ND_PREC_MIXED = 1, ND_PREC_FP32X2 = 2 } nd_prec
  * form of each row and column (BF16 in, exact FP32 group sums in tensor
  * memory, FP32-pair accumulation; same accuracy class).  By default the
  * launches whose largest block edge exceeds 192 take them, unless their digit
- * planes would exceed 256 MiB per energy; ND_FACT_GEMM_TC forces them for
+ * planes would exceed 512 MiB per energy or 64 GiB for all max_ne energies of
+ * the handle; ND_FACT_GEMM_TC forces them for
  * every GEMM launch, ND_FACT_GEMM_ALU never uses them.  Their waits are
  * bounded: a wait that gives up makes nd_fact_status return ND_ERR_TIMEOUT. */
 #define ND_FACT_GEMM_TC 8

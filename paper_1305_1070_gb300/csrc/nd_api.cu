@@ -233,6 +233,13 @@ double small_tile_cost(int precision) { return precision == ND_PREC_FP64 ? 0.9 :
 // > 192: 139.9 -> 99.0 ms.
 constexpr int TC_MIN_DIM = 192;
 constexpr int64_t TC_MAX_SCRATCH = int64_t(512) << 20;
+// ... and unless the planes of all energies of the handle exceed
+// TC_TOTAL_SCRATCH (the 512-energy calls of the nanotube would otherwise ask
+// for a few hundred GB).
+constexpr int64_t TC_TOTAL_SCRATCH = int64_t(64) << 30;
+bool tc_scratch_fits(int64_t per_energy, int max_ne) {
+  return per_energy <= TC_MAX_SCRATCH && per_energy * int64_t(max_ne) <= TC_TOTAL_SCRATCH;
+}
 // Largest block edge of a GEMM launch that runs one CTA per block
 // (k_gemm_direct).  Measured per size class on the 512 x 128 workload, FP32
 // pairs, 128 energies (tiled 16 x 16 -> direct): edges <= 24: 78 -> 31 ms,
@@ -301,7 +308,7 @@ void build_tiles(const std::vector<Step>& sched, const std::vector<GemmDesc>& gd
           TcDesc t{};
           off = gemm_tc_scratch(gd[k], t, off);
         }
-        tc = off <= TC_MAX_SCRATCH;
+        tc = tc_scratch_fits(off, max_ne);
       }
       if (flags & ND_FACT_GEMM_TC) tc = true;
     }
@@ -1258,7 +1265,7 @@ extern "C" nd_status nd_autotune(nd_fact* f, const double* H_values, const doubl
     const Step& st = (*sched[q])[si];
     if (st.kind != ST_GEMM) return false;
     if (c == 2)
-      return f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_step_scratch(st, f->gemm_all) <= TC_MAX_SCRATCH;
+      return f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_scratch_fits(tc_step_scratch(st, f->gemm_all), f->max_ne);
     if (c == 3) return st.max_dim <= 192;
     if (c == 4) return st.max_dim > 32;  // the 64-row tiles only pay above the large tile's edge
     return true;
@@ -1389,7 +1396,7 @@ extern "C" nd_status nd_fact_set_choice(nd_fact* f, const int8_t* choice, int32_
       const Step& st = (*sc[q])[si];
       bool ok = c >= -1 && c <= 4 && (c == -1 || st.kind == ST_GEMM);
       if (ok && c == 2)
-        ok = f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_step_scratch(st, f->gemm_all) <= TC_MAX_SCRATCH;
+        ok = f->precision == ND_PREC_FP32X2 && (q != 3 || ph) && tc_scratch_fits(tc_step_scratch(st, f->gemm_all), f->max_ne);
       if (ok && c == 3) ok = st.max_dim <= 192;
       if (ok && c == 4) ok = st.max_dim > 32;
       if (!ok) return fail(ND_ERR_INVALID_ARG, "nd_fact_set_choice: a kernel that this step cannot take");

@@ -883,24 +883,35 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
 }
 
 // Growth indicator: out[e * 8 + 4] = max over the listed regions of max |x|.
+// Largest |Re| or |Im| of an element, in FP32 (the leading part of an FP32
+// pair): the growth indicator needs no more, and FP64 arithmetic here would
+// run on the slow FP64 pipe.
+__device__ __forceinline__ float mag_lead(const float4& v) { return fmaxf(fabsf(v.x), fabsf(v.z)); }
+__device__ __forceinline__ float mag_lead(const float2& v) { return fmaxf(fabsf(v.x), fabsf(v.y)); }
+__device__ __forceinline__ float mag_lead(const double2& v) { return float(fmax(fabs(v.x), fabs(v.y))); }
+
+// Fold growth max |Psi| per energy: CTAs stride over the Psi blocks of all
+// clusters (most are small), one atomic maximum per CTA.
 template <typename T>
-__global__ void k_absmax(const ZeroDesc* __restrict__ descs, const cx<T>* arena, int64_t se, double* cert) {
-  const ZeroDesc d = descs[blockIdx.x];
+__global__ void __launch_bounds__(128) k_absmax(const ZeroDesc* __restrict__ descs, int n_desc, const cx<T>* arena,
+                                                int64_t se, double* cert) {
   const int e = blockIdx.y;
-  const cx<T>* p = arena + int64_t(e) * se + d.off;
-  double m = 0.0;
-  for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) {
-    const double2 v = O<T>::to_d2(p[i]);
-    const double a = fmax(fabs(v.x), fabs(v.y));
-    m = fmax(m, a == a ? a : __longlong_as_double(0x7ff0000000000000LL));  // NaN counts as infinite growth
+  float m = 0.f;
+  for (int c = blockIdx.x; c < n_desc; c += gridDim.x) {
+    const ZeroDesc d = descs[c];
+    const cx<T>* p = arena + int64_t(e) * se + d.off;
+    for (int64_t i = threadIdx.x; i < d.count; i += blockDim.x) {
+      const float a = mag_lead(p[i]);
+      m = fmaxf(m, a == a ? a : __int_as_float(0x7f800000));  // NaN counts as infinite growth
+    }
   }
-  __shared__ double red[32];
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  __shared__ float red[4];
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
-    atomic_max_pos(cert + int64_t(e) * 8 + 4, m);
+    for (int w = 1; w < int(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    atomic_max_pos(cert + int64_t(e) * 8 + 4, double(m));
   }
 }
 
@@ -1115,7 +1126,8 @@ template <typename T>
 void Kern<T>::certificate(const Work& w, const CertArgs& a, const DelayTabs& dt, cudaStream_t s) {
   if (w.n_e <= 0) return;
   if (a.n_psi > 0)
-    k_absmax<T><<<dim3(a.n_psi, w.n_e), 256, 0, s>>>(a.psi, (const cx<T>*)w.arena, w.se, a.cert);
+    k_absmax<T><<<dim3(std::min(a.n_psi, 1024), w.n_e), 128, 0, s>>>(a.psi, a.n_psi, (const cx<T>*)w.arena, w.se,
+                                                                    a.cert);
   k_certificate<T><<<dim3((a.n + 255) / 256, w.n_e), 256, 0, s>>>(a, dt, (const cx<T>*)w.arena, w.se);
   k_cert_ratio<<<(w.n_e + 127) / 128, 128, 0, s>>>(a.cert, w.n_e);
 }
