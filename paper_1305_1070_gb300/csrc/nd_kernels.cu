@@ -20,6 +20,29 @@
 
 namespace ndgf {
 
+// alpha and beta of an epilogue as a mode, decided once per CTA (the FP64
+// compares would otherwise run per output on the slow FP64 pipe): 0 = the
+// first special value (alpha 1, beta 0), 1 = the second (alpha -1, beta 1),
+// 2 = general.
+__host__ __device__ inline int scale_mode(double v, double first, double second) {
+  return v == first ? 0 : (v == second ? 1 : 2);
+}
+// C = alpha P + beta D for the modes above (alpha: 0 keep, 1 negate; beta: 0
+// none, 1 add D)
+template <typename T>
+__device__ __forceinline__ cx<T> epilogue(cx<T> r, int amode, double alpha, int bmode, double beta,
+                                          const cx<T>* __restrict__ D, int64_t at) {
+  if (amode == 1)
+    r = O<T>::neg(r);
+  else if (amode == 2)
+    r = O<T>::scale(r, alpha);
+  if (bmode) {
+    const cx<T> dv = D[at];
+    r = O<T>::add(r, bmode == 1 ? dv : O<T>::scale(dv, beta));
+  }
+  return r;
+}
+
 __device__ __forceinline__ double fermi_dev(double E, double mu, double kT) {
   double x = (E - mu) / kT;
   if (x > 0) {
@@ -229,6 +252,7 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
   }
   cx<T>* C = base + d.offC;
   const cx<T>* D = base + d.offD;
+  const int amode = scale_mode(d.alpha, 1.0, -1.0), bmode = scale_mode(d.beta, 0.0, 1.0);
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int gm = m0 + ty + i * NY;
@@ -237,16 +261,7 @@ k_gemm(const GemmDesc* __restrict__ descs, const TileRef* __restrict__ tiles, cx
     for (int j = 0; j < TN; ++j) {
       const int gn = n0 + tx + j * NX;
       if (gn >= d.n) continue;
-      cx<T> r = O<T>::acc3_get(acc[i][j]);
-      if (d.alpha == -1.0)
-        r = O<T>::neg(r);
-      else if (d.alpha != 1.0)
-        r = O<T>::scale(r, d.alpha);
-      if (d.beta != 0.0) {
-        const cx<T> dv = D[int64_t(gm) * d.ldd + gn];
-        r = O<T>::add(r, d.beta == 1.0 ? dv : O<T>::scale(dv, d.beta));
-      }
-      C[int64_t(gm) * d.ldc + gn] = r;
+      C[int64_t(gm) * d.ldc + gn] = epilogue<T>(O<T>::acc3_get(acc[i][j]), amode, d.alpha, bmode, d.beta, D, int64_t(gm) * d.ldd + gn);
     }
   }
 }
@@ -274,6 +289,7 @@ __global__ void __launch_bounds__(128) k_gemm_direct(const GemmDesc* __restrict_
   const int mb = (d.m + 1) >> 1, nb = (d.n + 1) >> 1;
   const int64_t sAi = transA ? 1 : d.lda, sAk = transA ? d.lda : 1;  // A(i, k) = A[i sAi + k sAk]
   const int64_t sBj = transB ? d.ldb : 1, sBk = transB ? 1 : d.ldb;  // B(k, j) = B[k sBk + j sBj]
+  const int amode = scale_mode(d.alpha, 1.0, -1.0), bmode = scale_mode(d.beta, 0.0, 1.0);
   for (int idx = threadIdx.x; idx < mb * nb; idx += blockDim.x) {
     const int i0 = 2 * (idx / nb), j0 = 2 * (idx % nb);
     const bool i1 = i0 + 1 < d.m, j1 = j0 + 1 < d.n;
@@ -283,9 +299,7 @@ __global__ void __launch_bounds__(128) k_gemm_direct(const GemmDesc* __restrict_
     const cx<T>* b1p = B + (j1 ? j0 + 1 : j0) * sBj;
     typename O<T>::Acc c00 = O<T>::acc_zero(), c01 = O<T>::acc_zero(), c10 = O<T>::acc_zero(),
                        c11 = O<T>::acc_zero();
-    for (int k = 0; k < d.k; ++k) {
-      const cx<T> a0 = a0p[k * sAk], a1 = a1p[k * sAk];
-      cx<T> b0 = b0p[k * sBk], b1 = b1p[k * sBk];
+    auto mac = [&](cx<T> a0, cx<T> a1, cx<T> b0, cx<T> b1) {
       if (conjB) {
         b0 = O<T>::conj(b0);
         b1 = O<T>::conj(b1);
@@ -294,23 +308,28 @@ __global__ void __launch_bounds__(128) k_gemm_direct(const GemmDesc* __restrict_
       O<T>::acc_fma(c01, a0, b1);
       O<T>::acc_fma(c10, a1, b0);
       O<T>::acc_fma(c11, a1, b1);
+    };
+    // two k per iteration: the eight loads of a pair are in flight together
+    int k = 0;
+    for (; k + 1 < d.k; k += 2) {
+      const cx<T> a0 = a0p[0], a1 = a1p[0], b0 = b0p[0], b1 = b1p[0];
+      const cx<T> a0n = a0p[sAk], a1n = a1p[sAk], b0n = b0p[sBk], b1n = b1p[sBk];
+      a0p += 2 * sAk;
+      a1p += 2 * sAk;
+      b0p += 2 * sBk;
+      b1p += 2 * sBk;
+      mac(a0, a1, b0, b1);
+      mac(a0n, a1n, b0n, b1n);
     }
+    if (k < d.k) mac(a0p[0], a1p[0], b0p[0], b1p[0]);
     const typename O<T>::Acc* acc[4] = {&c00, &c01, &c10, &c11};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int i = i0 + (q >> 1), j = j0 + (q & 1);
       if ((q >> 1) && !i1) continue;
       if ((q & 1) && !j1) continue;
-      cx<T> r = O<T>::acc_get(*acc[q]);
-      if (d.alpha == -1.0)
-        r = O<T>::neg(r);
-      else if (d.alpha != 1.0)
-        r = O<T>::scale(r, d.alpha);
-      if (d.beta != 0.0) {
-        const cx<T> dv = D[int64_t(i) * d.ldd + j];
-        r = O<T>::add(r, d.beta == 1.0 ? dv : O<T>::scale(dv, d.beta));
-      }
-      C[int64_t(i) * d.ldc + j] = r;
+      C[int64_t(i) * d.ldc + j] = epilogue<T>(O<T>::acc_get(*acc[q]), amode, d.alpha, bmode, d.beta, D,
+                                              int64_t(i) * d.ldd + j);
     }
   }
 }
