@@ -128,33 +128,34 @@ __device__ __forceinline__ void transpose4(const unsigned (&in)[4], unsigned (&o
   out[3] = __byte_perm(t1, t3, 0x7632);
 }
 
-// Digits of Re, Im and Re + Im of 8 FP32-pair complexes at consecutive k of
-// one row (scale factor sc) into w[c][t][0..1]: the 8 bytes of digit plane t,
-// element q at byte q.  Re + Im is the integer sum X_re + X_im, |X| < 2^54 as
-// the row scale bounds |Re| + |Im|.
-__device__ __forceinline__ void split8(const float4 (&v)[8], float sc, unsigned (&w)[3][TC_S][2]) {
-  unsigned lo[3][8], hi[3][8];
+// The fixed-point integer of component c of an FP32-pair complex (c = 0: Re,
+// 1: Im, 2: Re + Im, the integer sum X_re + X_im, |X| < 2^54 as the row scale
+// bounds |Re| + |Im|).
+__device__ __forceinline__ long long comp_fixed(const float4& v, float sc, int c) {
+  const long long xr = c != 1 ? fixed_of(v.x, v.y, sc) : 0;
+  const long long xi = c != 0 ? fixed_of(v.z, v.w, sc) : 0;
+  return xr + xi;
+}
+
+// Digits of component c of 8 FP32-pair complexes at consecutive k of one row
+// (scale factor sc) into w[t][0..1]: the 8 bytes of digit plane t, element q
+// at byte q.
+__device__ __forceinline__ void split8(const float4 (&v)[8], float sc, int c, unsigned (&w)[TC_S][2]) {
+  unsigned lo[8], hi[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const long long xr = fixed_of(v[q].x, v[q].y, sc), xi = fixed_of(v[q].z, v[q].w, sc);
-    digit_bytes(xr, lo[0][q], hi[0][q]);
-    digit_bytes(xi, lo[1][q], hi[1][q]);
-    digit_bytes(xr + xi, lo[2][q], hi[2][q]);
+  for (int q = 0; q < 8; ++q) digit_bytes(comp_fixed(v[q], sc, c), lo[q], hi[q]);
+#pragma unroll
+  for (int g = 0; g < 2; ++g) {  // elements 4g .. 4g + 3: word g of every plane
+    const unsigned il[4] = {lo[4 * g], lo[4 * g + 1], lo[4 * g + 2], lo[4 * g + 3]};
+    const unsigned ih[4] = {hi[4 * g], hi[4 * g + 1], hi[4 * g + 2], hi[4 * g + 3]};
+    unsigned ol[4], oh[4];
+    transpose4(il, ol);
+    transpose4(ih, oh);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) w[TC_S - 1 - b][g] = ol[b];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) w[TC_S - 5 - b][g] = oh[b];
   }
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int g = 0; g < 2; ++g) {  // elements 4g .. 4g + 3: word g of every plane
-      const unsigned il[4] = {lo[c][4 * g], lo[c][4 * g + 1], lo[c][4 * g + 2], lo[c][4 * g + 3]};
-      const unsigned ih[4] = {hi[c][4 * g], hi[c][4 * g + 1], hi[c][4 * g + 2], hi[c][4 * g + 3]};
-      unsigned ol[4], oh[4];
-      transpose4(il, ol);
-      transpose4(ih, oh);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) w[c][TC_S - 1 - b][g] = ol[b];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) w[c][TC_S - 5 - b][g] = oh[b];
-    }
 }
 
 __device__ __forceinline__ int scale_exp(float m) {
@@ -175,7 +176,7 @@ constexpr uint32_t CORE_LBO = 128, CORE_SBO = 256;
 
 // ---- split: one CTA per 32 rows of op(A) or columns of op(B); lane = row,
 // warp w takes the k octets w, w + 8, ...
-__global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ descs, const TcDesc* __restrict__ tcd,
+__global__ void __launch_bounds__(256, 4) k_tc_split(const GemmDesc* __restrict__ descs, const TcDesc* __restrict__ tcd,
                                                   const TcSplit* __restrict__ items, const float4* __restrict__ arena,
                                                   int64_t se, const float4* __restrict__ aux, int64_t sa,
                                                   unsigned char* __restrict__ scratch, int64_t ss) {
@@ -206,12 +207,13 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
   };
   const int n_oct = 2 * t.kb;
   float mx = 0.f;
-  for (int o = w; o < n_oct; o += 8)
+  for (int o = w; o < n_oct; o += 16) {  // two octets per pass: 16 loads in flight
+    float4 v[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const float4 v = at(8 * o + q);
-      mx = fmaxf(mx, fabsf(v.x) + fabsf(v.z));
-    }
+    for (int q = 0; q < 16; ++q) v[q] = at(8 * o + (q < 8 ? q : 56 + q));
+#pragma unroll
+    for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fabsf(v[q].x) + fabsf(v[q].z));
+  }
   red[w][lane] = mx;
   __syncthreads();
 #pragma unroll
@@ -230,16 +232,16 @@ __global__ void __launch_bounds__(256) k_tc_split(const GemmDesc* __restrict__ d
     float4 v[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) v[q] = at(k0 + q);
-    unsigned wd[3][TC_S][2];
-    split8(v, sc, wd);
     const uint32_t co = core_off(rr, (o & 1) * 8);
 #pragma unroll
-    for (int tt = 0; tt < TC_S; ++tt) {
-      const float wt = __int_as_float((127 - 8 * tt) << 23);  // digit weight 2^(-8t)
-      const float wo = -8388736.f * wt;                        // -(2^23 + 128) wt, exact
+    for (int c = 0; c < 3; ++c) {  // one component at a time: fewer live registers
+      unsigned wd[TC_S][2];
+      split8(v, sc, c, wd);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const uint2 lo = widen4(wd[c][tt][0], wt, wo), hi = widen4(wd[c][tt][1], wt, wo);
+      for (int tt = 0; tt < TC_S; ++tt) {
+        const float wt = __int_as_float((127 - 8 * tt) << 23);  // digit weight 2^(-8t)
+        const float wo = -8388736.f * wt;                        // -(2^23 + 128) wt, exact
+        const uint2 lo = widen4(wd[tt][0], wt, wo), hi = widen4(wd[tt][1], wt, wo);
         unsigned char* pl = dig + (((int64_t(c) * t.kb + kb) * RB + rb) * TC_S + tt) * P + co;
         *reinterpret_cast<uint4*>(pl) = make_uint4(lo.x, lo.y, hi.x, hi.y);
       }
