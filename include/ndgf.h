@@ -184,7 +184,8 @@ void nd_plan_destroy(nd_plan* plan);
  * Allocates device memory for up to max_ne energies at the given precision
  * (nd_precision).  flags: ND_FACT_*.
  * The plan must outlive the handle.  Errors: ND_ERR_OOM, ND_ERR_CUDA,
- * ND_ERR_INVALID_ARG. */
+ * ND_ERR_INVALID_ARG; ND_ERR_UNSUPPORTED for a cluster of more than 8192
+ * interior or 32768 boundary sites, or more than two contacts in one cluster. */
 nd_status nd_fact_create(const nd_plan* plan, int32_t max_ne, int32_t precision, int32_t flags, nd_fact** out);
 void nd_fact_destroy(nd_fact* fact);
 

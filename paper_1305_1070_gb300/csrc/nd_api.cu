@@ -700,6 +700,7 @@ extern "C" nd_status nd_fact_create(const nd_plan* p, int32_t max_ne, int32_t pr
   if (precision != ND_PREC_FP64 && precision != ND_PREC_MIXED && precision != ND_PREC_FP32X2)
     return fail(ND_ERR_INVALID_ARG, "nd_fact_create: unknown precision");
   if (p->max_n > 8192) return fail(ND_ERR_UNSUPPORTED, "nd_fact_create: cluster larger than 8192 sites");
+  if (p->max_b > 32768) return fail(ND_ERR_UNSUPPORTED, "nd_fact_create: cluster boundary larger than 32768 sites");
   for (const auto& c : p->cl)
     if (c.contacts.size() > 2) return fail(ND_ERR_UNSUPPORTED, "nd_fact_create: more than two contacts in one cluster");
   *out = nullptr;

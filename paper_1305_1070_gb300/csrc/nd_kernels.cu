@@ -517,9 +517,9 @@ __global__ void k_scatter(const ScatterDesc* __restrict__ descs, cx<T>* arena, i
   cx<T>* bb = base + d.off_bb;
   const int32_t* map = maps + d.map_begin;
   const int ldp = d.n_p + d.b_p, nfp = d.n_p + d.k_p;  // front rows of the parent: positions < nfp
-  const int64_t nb = int64_t(d.b) * d.b;
-  for (int64_t idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-    const int r = int(idx / d.b), s = int(idx % d.b);
+  const int nb = d.b * d.b;  // b <= 32768 (nd_fact_create): 32-bit index arithmetic
+  for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+    const int r = idx / d.b, s = idx - r * d.b;
     const int pr = map[r], ps = map[s];
     const cx<T> v = src[idx];
     if (pr < nfp) {
@@ -548,9 +548,9 @@ __global__ void k_gather(const GatherDesc* __restrict__ descs, cx<T>* arena, int
   const cx<T>* bb = base + d.off_bb;
   const int32_t* map = maps + d.map_begin;
   const int ldp = d.n_p + d.b_p;
-  const int64_t nb = int64_t(d.b) * d.b;
-  for (int64_t idx = threadIdx.x; idx < nb; idx += blockDim.x) {
-    const int r = int(idx / d.b), s = int(idx % d.b);
+  const int nb = d.b * d.b;  // b <= 32768 (nd_fact_create): 32-bit index arithmetic
+  for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+    const int r = idx / d.b, s = idx - r * d.b;
     int pr = map[r], ps = map[s];
     if (ip) {
       if (pr < nfp) pr = ip[pr];
