@@ -799,6 +799,14 @@ __device__ bool cert_entry(const CertArgs& a, const DelayTabs& dt, int64_t eb, i
   return true;
 }
 
+// |z| in FP32 for the magnitude sums of the backward errors (their
+// normalisation needs a few digits; FP64 hypot per term would run on the
+// slow FP64 pipe)
+__device__ __forceinline__ double magf(double2 z) {
+  const float x = float(z.x), y = float(z.y);
+  return double(sqrtf(fmaf(x, x, y * y)));
+}
+
 template <typename T>
 __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int64_t se) {
   const int e = blockIdx.y;
@@ -828,13 +836,13 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
     double2 rr = make_double2(d.x * gjj.x - d.y * gjj.y - 1.0, d.x * gjj.y + d.y * gjj.x);
     double2 rl = make_double2(d.x * pjj.x - d.y * pjj.y, d.x * pjj.y + d.y * pjj.x);
     double2 rhs = make_double2(0.0, 0.0);
-    const double ad = hypot(d.x, d.y);
-    double sr_sum = ad * hypot(gjj.x, gjj.y), sl_sum = ad * hypot(pjj.x, pjj.y);  // magnitudes of the terms
+    const double ad = magf(d);
+    double sr_sum = ad * magf(gjj), sl_sum = ad * magf(pjj);  // magnitudes of the terms
     if (a.lesser && ph_l) {  // ph^<_j conj(G_jj)
       const double2 q = ph_l[int64_t(e) * a.n + j];
       rhs.x += q.x * gjj.x + q.y * gjj.y;
       rhs.y += q.y * gjj.x - q.x * gjj.y;
-      sl_sum += hypot(q.x, q.y) * hypot(gjj.x, gjj.y);
+      sl_sum += magf(q) * magf(gjj);
     }
     for (int t = a.cptr[j]; t < a.cptr[j + 1]; ++t) {
       const int k = a.nb[t], src = a.coef[t];
@@ -855,19 +863,19 @@ __global__ void k_certificate(CertArgs a, DelayTabs dt, const cx<T>* arena, int6
           const double2 q2 = sl[int64_t(e) * a.sstride + (-1 - src)];
           rhs.x += q2.x * g.x + q2.y * g.y;
           rhs.y += q2.y * g.x - q2.x * g.y;
-          sl_sum += hypot(q2.x, q2.y) * hypot(g.x, g.y);
+          sl_sum += magf(q2) * magf(g);
         }
       }
-      const double aa = hypot(an.x, an.y);
+      const double aa = magf(an);
       rr.x -= an.x * g.x - an.y * g.y;
       rr.y -= an.x * g.y + an.y * g.x;
-      sr_sum += aa * hypot(g.x, g.y);
+      sr_sum += aa * magf(g);
       if (a.lesser) {
         double2 pv = O<T>::to_d2(base[a.cl[q].offP + idx]);
         if (!tr) pv = make_double2(-pv.x, pv.y);  // G<_kj = -conj(G<_jk)
         rl.x -= an.x * pv.x - an.y * pv.y;
         rl.y -= an.x * pv.y + an.y * pv.x;
-        sl_sum += aa * hypot(pv.x, pv.y);
+        sl_sum += aa * magf(pv);
       }
     }
     rl.x -= rhs.x;
