@@ -95,3 +95,29 @@ def test_host_inputs_valid_call_matches_device_inputs(solver):
     assert _status(ndgf.nd_fact_status, s.fact) == 0
     for a, b in zip((Gr, Gl, Gg), ref):
         assert np.array_equal(a, b[:n_e].cpu().numpy())
+
+
+def test_degenerate_calls():
+    """Degenerate calls on a two-site chain (one site per contact, one-site
+    leaves): nd_diag_green before any nd_factor, zero energies and more energies
+    than the handle holds are refused with ND_ERR_INVALID_ARG and leave the
+    handle usable; a call at exactly max_ne energies matches the dense
+    definition (paper Eq. (1)-(2))."""
+    from oracle import dense, observables
+    dev = workloads.chain(2, t=1.0)
+    tr = workloads.Transport(energies=np.array([-0.6, 0.1, 0.9]), mu=(0.2, -0.1), kT=0.05)
+    s = Solver(dev, tr, precision=ndgf.ND_PREC_FP64, leaf_size=1, max_ne=3)
+    out = torch.zeros(3, dev.n, dtype=torch.complex128, device="cuda")
+    assert _status(ndgf.nd_diag_green, s.fact, None, None, None, None, out, None, None) == 1
+    E = torch.as_tensor(tr.energies, device="cuda")
+    assert _status(ndgf.nd_factor, s.fact, s.H, s.sig_r, None, E, 0, tr.eta) == 1
+    E4 = torch.as_tensor(np.append(tr.energies, 0.3), device="cuda")
+    assert _status(ndgf.nd_factor, s.fact, s.H, s.sig_r, None, E4, 4, tr.eta) == 1
+    Gr, Gl, Gg = s.step(tr.energies)
+    torch.cuda.synchronize()
+    assert _status(ndgf.nd_fact_status, s.fact) == 0
+    ref = dense.green_diag(dev, tr)
+    for k, g in (("Gr", Gr), ("Gl", Gl), ("Gg", Gg)):
+        g = g.cpu().numpy()
+        for e in range(3):
+            assert observables.rel_err(g[e], ref[k][e]) < 1e-10
