@@ -12,6 +12,27 @@ namespace ndgf {
 
 template <typename T> using O = Ops<T>;
 
+// The elements start, start + step, ... of a row-major index space with
+// `cols` columns, as (row, column) pairs updated without a division per
+// element (callers keep rows * cols below 2^31).
+struct Walk2 {
+  int r, c, dr, dc, cols;
+  __device__ __forceinline__ Walk2(int start, int step, int cols_) : cols(cols_) {
+    r = start / cols;
+    c = start - r * cols;
+    dr = step / cols;
+    dc = step - dr * cols;
+  }
+  __device__ __forceinline__ void next() {
+    r += dr;
+    c += dc;
+    if (c >= cols) {
+      c -= cols;
+      ++r;
+    }
+  }
+};
+
 // Batched in-place Gauss-Jordan inversion with partial pivoting (one CTA per
 // matrix).  The matrix is n x n with leading dimension ld.
 template <typename TC>
@@ -153,9 +174,10 @@ __device__ void gj_invert2(cx<TC>* M, int n, int ld, int* piv, cx<TC>* colk, cx<
       s_key[(k + 1) & 1] = 0ull;
     }
     __syncthreads();
-    const int64_t nn = int64_t(n) * n;
-    for (int64_t idx = tid; idx < nn; idx += nt) {
-      const int i = int(idx / n), j = int(idx % n);
+    const int nn = n * n;
+    Walk2 wk(tid, nt, n);
+    for (int idx = tid; idx < nn; idx += nt, wk.next()) {
+      const int i = wk.r, j = wk.c;
       cx<TC>& a = M[int64_t(i) * ld + j];
       if (i == k) {
         a = R[j];

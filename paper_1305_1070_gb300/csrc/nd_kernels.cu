@@ -114,22 +114,30 @@ __global__ void k_inverse(const InvDesc* __restrict__ descs, cx<T>* arena, int64
   int* piv = reinterpret_cast<int*>(smem);
   const size_t colk_off = (size_t(d.n) * sizeof(int) + 15) & ~size_t(15);
   const size_t r_off = colk_off + size_t(d.n) * sizeof(double2);
-  const int64_t nn = int64_t(d.n) * d.n;
+  const int nn = d.n * d.n;  // n <= 8192 + delays (nd_fact_create): 32-bit indices
   if (!std::is_same<T, double>::value && d.fp64 && scratch) {  // root block in complex128
     double2* W = scratch + int64_t(e) * scratch_stride + d.scr;
-    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) W[i] = O<T>::to_d2(M[(i / d.n) * d.ld + i % d.n]);
+    {
+      Walk2 wk(threadIdx.x, blockDim.x, d.n);
+      for (int i = threadIdx.x; i < nn; i += blockDim.x, wk.next()) W[i] = O<T>::to_d2(M[int64_t(wk.r) * d.ld + wk.c]);
+    }
     __syncthreads();
     gj_invert2<double>(W, d.n, d.n, piv, reinterpret_cast<double2*>(smem + colk_off),
                        reinterpret_cast<double2*>(smem + r_off), n_singular);
-    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = O<T>::from_d2(W[i]);
+    Walk2 wk(threadIdx.x, blockDim.x, d.n);
+    for (int i = threadIdx.x; i < nn; i += blockDim.x, wk.next()) M[int64_t(wk.r) * d.ld + wk.c] = O<T>::from_d2(W[i]);
   } else if (d.n <= smem_max_n) {  // whole block resident in shared memory
     cx<T>* colk = reinterpret_cast<cx<T>*>(smem + colk_off);
     cx<T>* R = reinterpret_cast<cx<T>*>(smem + r_off);
     cx<T>* S = reinterpret_cast<cx<T>*>(smem + r_off + size_t(d.n) * sizeof(double2));
-    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) S[i] = M[(i / d.n) * d.ld + i % d.n];
+    {
+      Walk2 wk(threadIdx.x, blockDim.x, d.n);
+      for (int i = threadIdx.x; i < nn; i += blockDim.x, wk.next()) S[i] = M[int64_t(wk.r) * d.ld + wk.c];
+    }
     __syncthreads();
     gj_invert2<T>(S, d.n, d.n, piv, colk, R, n_singular);
-    for (int64_t i = threadIdx.x; i < nn; i += blockDim.x) M[(i / d.n) * d.ld + i % d.n] = S[i];
+    Walk2 wk(threadIdx.x, blockDim.x, d.n);
+    for (int i = threadIdx.x; i < nn; i += blockDim.x, wk.next()) M[int64_t(wk.r) * d.ld + wk.c] = S[i];
   } else {
     gj_invert2<T>(M, d.n, d.ld, piv, reinterpret_cast<cx<T>*>(smem + colk_off),
                   reinterpret_cast<cx<T>*>(smem + r_off), n_singular);
@@ -381,10 +389,13 @@ __global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64
   float2* Rrow = reinterpret_cast<float2*>(smem + oR);
   const size_t o2 = oR + size_t(nf) * sizeof(float2);
   float2* X = x_smem ? reinterpret_cast<float2*>(smem + o2) : reinterpret_cast<float2*>(S);
-  const int64_t nn = int64_t(nf) * nf;
-  for (int64_t i = tid; i < nn; i += nt) {
-    const double2 v = O<T>::to_d2(F[(i / nf) * ld + (i % nf)]);
-    X[i] = make_float2(float(v.x), float(v.y));
+  const int nn = nf * nf;  // 32-bit indices (front sizes bounded by nd_fact_create)
+  {
+    Walk2 wk(tid, nt, nf);
+    for (int i = tid; i < nn; i += nt, wk.next()) {
+      const double2 v = O<T>::to_d2(F[int64_t(wk.r) * ld + wk.c]);
+      X[i] = make_float2(float(v.x), float(v.y));
+    }
   }
   for (int i = tid; i < nf; i += nt) alive[i] = 1;
   if (tid == 0) s_nsing = 0;
@@ -437,8 +448,9 @@ __global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64
     const float den = pj.x * pj.x + pj.y * pj.y;
     if (den > 0.f) {
       const float2 inv = make_float2(pj.x / den, -pj.y / den);
-      for (int64_t i = tid; i < nn; i += nt) {
-        const int a = int(i / nf), b = int(i % nf);
+      Walk2 wk(tid, nt, nf);
+      for (int i = tid; i < nn; i += nt, wk.next()) {
+        const int a = wk.r, b = wk.c;
         if (!alive[a] || !alive[b]) continue;
         const float2 xa = X[int64_t(a) * nf + j], xb = X[int64_t(j) * nf + b];
         const float2 q = make_float2(xa.x * inv.x - xa.y * inv.y, xa.x * inv.y + xa.y * inv.x);
@@ -462,13 +474,13 @@ __global__ void k_delay(const DelayDesc* __restrict__ descs, cx<T>* arena, int64
   __syncthreads();
   for (int r = tid; r < nf; r += nt) rsite[r] = rs[r];
   for (int j = tid; j < k; j += nt) dt.rsite[int64_t(e) * dt.n_unk + d.sb_p + d.dslot + j] = rs[m + j];
-  const int64_t nfl = int64_t(nf) * ld;
-  for (int64_t i = tid; i < nfl; i += nt) {
-    const int r = int(i / ld), c = int(i % ld);
-    S[i] = F[int64_t(perm[r]) * ld + (c < nf ? perm[c] : c)];
+  const int nfl = nf * ld;
+  {
+    Walk2 wk(tid, nt, ld);
+    for (int i = tid; i < nfl; i += nt, wk.next()) S[i] = F[int64_t(perm[wk.r]) * ld + (wk.c < nf ? perm[wk.c] : wk.c)];
   }
   __syncthreads();
-  for (int64_t i = tid; i < nfl; i += nt) F[i] = S[i];
+  for (int i = tid; i < nfl; i += nt) F[i] = S[i];
   __syncthreads();
   for (int i = tid; i < k * bb; i += nt) {
     const int a = i / bb, c = i % bb;
