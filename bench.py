@@ -64,12 +64,12 @@ GATE = 1e-6
 # no longer matches turns the figure into null.
 KERNEL_SOURCES = ["nd_kernels.cu", "nd_arith.cuh", "nd_gemm_tc.cu", "nd_gj.cuh", "nd_api.cu"]
 TRAFFIC = {  # kernel kind -> (bytes per launch, source digest)
-    "complex-fp32x2:gemm_tc": (4658955157, "d1d8c4e4304e5a27"),  # k_tc_split + k_gemm_tc
-    "complex-fp32x2:gemm_direct": (1785764362, "d1d8c4e4304e5a27"),
-    "complex-fp32x2:gemm": (1875322197, "d1d8c4e4304e5a27"),
-    "complex-fp32x2:gemm_small": (445460480, "d1d8c4e4304e5a27"),
-    "complex-fp32x2:inverse": (182684057, "d1d8c4e4304e5a27"),
-    "complex-fp32x2:delay": (861170766, "d1d8c4e4304e5a27"),
+    "complex-fp32x2:gemm_tc": (4660977664, "609ae63489c28a87"),  # k_tc_split + k_gemm_tc
+    "complex-fp32x2:gemm_direct": (1781878374, "609ae63489c28a87"),
+    "complex-fp32x2:gemm": (1662333952, "609ae63489c28a87"),
+    "complex-fp32x2:gemm_small": (649684992, "609ae63489c28a87"),
+    "complex-fp32x2:inverse": (182501649, "609ae63489c28a87"),
+    "complex-fp32x2:delay": (860988022, "609ae63489c28a87"),
 }
 
 
