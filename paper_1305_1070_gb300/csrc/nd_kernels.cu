@@ -1000,7 +1000,7 @@ void Kern<T>::delay(const Work& w, const DelayDesc* d, int count, int max_nf, co
   const size_t xs = size_t(max_nf) * max_nf * sizeof(float2);
   const int x_smem = base + xs <= size_t(200 * 1024) ? 1 : 0;  // up to nf = 158
   const size_t shm = base + (x_smem ? xs : 0);
-  const int nt = max_nf <= 24 ? 64 : max_nf <= 48 ? 128 : max_nf <= 96 ? 256 : 512;
+  const int nt = max_nf <= 12 ? 32 : max_nf <= 24 ? 64 : max_nf <= 48 ? 128 : max_nf <= 96 ? 256 : 512;
   k_delay<T><<<dim3(count, w.n_e), nt, shm, s>>>(d, (cx<T>*)w.arena, w.se, dt, x_smem);
 }
 
@@ -1017,7 +1017,7 @@ void Kern<T>::inverse(const Work& w, const InvDesc* d, int count, int max_n, dou
   const size_t shm = base + size_t(smem_max_n) * smem_max_n * sizeof(cx<T>);
   // the n x n update of every pivot step is spread over the CTA: large blocks
   // (the few fronts near the root) get more threads
-  const int nt = max_n <= 24 ? 64 : max_n <= 48 ? 128 : max_n <= 64 ? 256 : (max_n <= 128 ? 512 : 1024);
+  const int nt = max_n <= 12 ? 32 : max_n <= 24 ? 64 : max_n <= 48 ? 128 : max_n <= 64 ? 256 : (max_n <= 128 ? 512 : 1024);
   k_inverse<T><<<dim3(count, w.n_e), nt, shm, s>>>(d, (cx<T>*)w.arena, w.se, (double2*)scratch, scratch_stride,
                                                    n_singular, smem_max_n);
 }
