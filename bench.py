@@ -64,12 +64,12 @@ GATE = 1e-6
 # no longer matches turns the figure into null.
 KERNEL_SOURCES = ["nd_kernels.cu", "nd_arith.cuh", "nd_gemm_tc.cu", "nd_gj.cuh", "nd_api.cu"]
 TRAFFIC = {  # kernel kind -> (bytes per launch, source digest)
-    "complex-fp32x2:gemm_tc": (4660977664, "609ae63489c28a87"),  # k_tc_split + k_gemm_tc
-    "complex-fp32x2:gemm_direct": (1781878374, "609ae63489c28a87"),
-    "complex-fp32x2:gemm": (1662333952, "609ae63489c28a87"),
-    "complex-fp32x2:gemm_small": (649684992, "609ae63489c28a87"),
-    "complex-fp32x2:inverse": (182501649, "609ae63489c28a87"),
-    "complex-fp32x2:delay": (860988022, "609ae63489c28a87"),
+    "complex-fp32x2:gemm_tc": (4659530553, "0b73ee5d812eb036"),  # k_tc_split + k_gemm_tc
+    "complex-fp32x2:gemm_direct": (1596213248, "0b73ee5d812eb036"),
+    "complex-fp32x2:gemm": (2195893101, "0b73ee5d812eb036"),
+    "complex-fp32x2:gemm_small": (445472768, "0b73ee5d812eb036"),
+    "complex-fp32x2:inverse": (182371942, "0b73ee5d812eb036"),
+    "complex-fp32x2:delay": (868719379, "0b73ee5d812eb036"),
 }
 
 
