@@ -36,6 +36,11 @@ precision).  Contents:
                     the dense Jacobian.
 * ``transfer``   -- 2x2 transfer-matrix transmission of a 1D chain, an
                     independent textbook method used to pin the oracle.
+* ``hermitian``  -- the definition for a general Hermitian H (complex
+                    hoppings, e.g. a magnetic field), where A is not complex
+                    symmetric: conjugate transpositions in the leads and the
+                    self-energies; the case the symmetric elimination cannot
+                    take.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against
 something other than itself (closed forms, brute force, invariants, independent

@@ -67,7 +67,7 @@ class Device:
     n: int
     rowptr: np.ndarray  # int32 [n+1]
     colind: np.ndarray  # int32 [nnz]
-    values: np.ndarray  # float64 [nnz], H in eV
+    values: np.ndarray  # float64 [nnz], H in eV (complex128 for a Hermitian H with complex hoppings)
     coords: np.ndarray  # float64 [n, d], nm
     layers: list  # list of int arrays, transport layers in order
     contacts: list  # list of int arrays: contact site sets (left, right)
@@ -80,7 +80,7 @@ class Device:
 
     def dense(self) -> np.ndarray:
         """Dense copy of H (only for small devices)."""
-        Hd = np.zeros((self.n, self.n))
+        Hd = np.zeros((self.n, self.n), dtype=self.values.dtype)
         for r in range(self.n):
             s, e = self.rowptr[r], self.rowptr[r + 1]
             Hd[r, self.colind[s:e]] = self.values[s:e]
@@ -160,6 +160,35 @@ def superlattice(L: int, W: int, *, a_nm: float = 0.5, m_eff: float = 0.067, v_b
     return Device(name=f"superlattice_{L}x{W}", n=n, rowptr=rowptr, colind=colind, values=values,
                   coords=coords, layers=layers, contacts=[idx[0].copy(), idx[L - 1].copy()],
                   leads=[lead, lead_r])
+
+
+def magnetic_superlattice(L: int, W: int, flux: float, **kw) -> Device:
+    """The superlattice of ``superlattice`` (same keywords) in a uniform
+    magnetic field perpendicular to the grid: a general Hermitian H, not
+    complex symmetric (Peierls substitution in the Landau gauge A = (-B y, 0)).
+    Every hopping along the transport direction from column x to x + 1 at row
+    y gets the phase exp(i 2 pi flux y), flux = B a^2 / (h / e) the flux
+    quantum fraction per plaquette; transverse hoppings keep no phase.  The
+    gauge is uniform along transport, so the leads keep it: a lead's H01 and
+    tau become -t diag(exp(+-i 2 pi flux y)), the sign set by the direction
+    from the device outwards.  H values are complex128; the leads have no
+    closed form (hop = None)."""
+    dev = superlattice(L, W, **kw)
+    t = fd_hopping(kw.get("a_nm", 0.5), kw.get("m_eff", 0.067))
+    rows = np.repeat(np.arange(dev.n), np.diff(dev.rowptr))
+    cols = dev.colind.astype(np.int64)
+    ph = 2.0 * np.pi * flux
+    values = dev.values.astype(np.complex128)
+    fwd = cols + W == rows   # hopping from column x (col) to column x + 1 (row)
+    bwd = rows + W == cols
+    y = rows % W
+    values[fwd] *= np.exp(1j * ph * y[fwd])
+    values[bwd] *= np.exp(-1j * ph * y[bwd])
+    D = np.exp(1j * ph * np.arange(W))
+    H00 = dev.leads[0].H00
+    left = Lead(H00=H00.copy(), H01=-t * np.diag(D), tau=-t * np.diag(D), hop=None)
+    right = Lead(H00=H00.copy(), H01=-t * np.diag(D.conj()), tau=-t * np.diag(D.conj()), hop=None)
+    return dataclasses.replace(dev, name=f"magnetic_superlattice_{L}x{W}", values=values, leads=[left, right])
 
 
 def chain(N: int, *, t: float = 1.0, eps0: float = 0.0, potential: np.ndarray | None = None) -> Device:
