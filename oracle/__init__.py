@@ -36,6 +36,9 @@ precision).  Contents:
                     the dense Jacobian.
 * ``transfer``   -- 2x2 transfer-matrix transmission of a 1D chain, an
                     independent textbook method used to pin the oracle.
+* ``nd_general`` -- the Sec. 3.2 algorithm as a block LU (left and right
+                    factors) for a general A, block by block: the form a
+                    general-Hermitian kernel path would run; a test aid.
 * ``hermitian``  -- the definition for a general Hermitian H (complex
                     hoppings, e.g. a magnetic field), where A is not complex
                     symmetric: conjugate transpositions in the leads and the

@@ -55,7 +55,8 @@ def self_energy(lead, E: float, eta: float) -> np.ndarray:
 
 
 def green_full(dev, tr, E: float) -> dict:
-    """A, G^r, G^<, G^> (dense) and the per-contact Sigma^r at one energy."""
+    """A, G^r, G^<, G^>, Sigma^<, Sigma^> (dense) and the per-contact Sigma^r
+    at one energy."""
     H = dev.dense().astype(complex)
     A = -H
     A[np.diag_indices(dev.n)] += E + 1j * tr.eta
@@ -69,7 +70,7 @@ def green_full(dev, tr, E: float) -> dict:
         Sg[np.ix_(idx, idx)] += selfenergy.greater(s, f)
     G = np.linalg.inv(A)
     Ga = G.conj().T
-    return {"A": A, "Gr": G, "Gl": G @ Sl @ Ga, "Gg": G @ Sg @ Ga, "sigma_r": sig}
+    return {"A": A, "Gr": G, "Gl": G @ Sl @ Ga, "Gg": G @ Sg @ Ga, "sigma_r": sig, "Sl": Sl, "Sg": Sg}
 
 
 def green_diag(dev, tr, energies=None) -> dict:

@@ -17,10 +17,14 @@ oracle's formulas:
   transmission of a ribbon in the field is the integer number of edge
   channels, 1 and 2 here, and stays so under strong disorder;
 - the broken complex symmetry of G^r in a field (why a separate elimination is
-  needed)."""
+  needed);
+- the block-LU form of the nested-dissection algorithm (oracle/nd_general.py)
+  against the definition, block by block, and its reduction to the symmetric
+  form without a field."""
 import numpy as np
+import pytest
 
-from oracle import dense, hermitian, observables, selfenergy
+from oracle import dense, hermitian, nd_general, nd_reference, observables, selfenergy
 from paper_1305_1070_gb300 import workloads
 
 
@@ -125,3 +129,48 @@ def test_field_breaks_complex_symmetry():
         G = hermitian.green_full(workloads.magnetic_superlattice(8, 5, flux, disorder=0.05, seed=1), tr, 0.3)["Gr"]
         asym = np.abs(G - G.T).max() / np.abs(G).max()
         assert (asym < 1e-12) if expect_sym else (asym > 1e-2)
+
+
+@pytest.mark.parametrize("L,W,leaf,flux", [(16, 8, 12, 0.06), (12, 10, 8, -0.03), (14, 6, 10, 0.11)])
+def test_general_nested_dissection_equals_the_definition(L, W, leaf, flux):
+    """The block-LU form of the Sec. 3.2 algorithm (oracle/nd_general.py: left
+    and right factors, G_BI from the left factors, N = Sigma^< G^a with
+    (G^a)_ij = (G_ji)^dagger) against the definition in a field: every stored
+    block of G^(0) and of P^(0) for Sigma^< and Sigma^>.  The symmetric
+    algorithm (oracle/nd_reference.py) on the same A gets the diagonal wrong."""
+    dev = workloads.magnetic_superlattice(L, W, flux, v_barrier=0.1, disorder=0.1, seed=L)
+    tr = _tr(1.3, mu=(1.4, 1.2), kT=0.03)
+    full = hermitian.green_full(dev, tr, 1.3)
+    tree = nd_reference.grid_bisection_tree(L, W, leaf)
+    tree.check_partition(dev.n)
+    nd = nd_general.NDGeneral(tree, full["A"])
+    G0 = nd.green_retarded()
+    P0, Q0 = nd.green_lesser(full["Sl"]), nd.green_lesser(full["Sg"])
+    C = tree.clusters
+    for (i, j), g in G0.items():
+        assert np.abs(g - full["Gr"][np.ix_(C[i], C[j])]).max() < 1e-10 * np.abs(full["Gr"]).max()
+    for P, key in ((P0, "Gl"), (Q0, "Gg")):
+        scale = np.abs(full[key]).max()
+        for i in range(len(C)):
+            assert np.abs(P[i, i] - full[key][np.ix_(C[i], C[i])]).max() < 1e-10 * scale
+            for j in tree.P[i]:
+                assert np.abs(P[i, j] - full[key][np.ix_(C[i], C[j])]).max() < 1e-10 * scale
+                assert np.abs(P[j, i] - full[key][np.ix_(C[j], C[i])]).max() < 1e-10 * scale
+    sym = nd_reference.NDReference(tree, full["A"])
+    assert observables.rel_err(sym.diag(sym.green_retarded()), np.diag(full["Gr"])) > 1e-3
+
+
+def test_general_nested_dissection_reduces_to_the_symmetric_one():
+    """Without a field the left factors are the transposed right factors and
+    both algorithms give the same blocks."""
+    dev = workloads.superlattice(14, 7, disorder=0.05, seed=5)
+    tr = workloads.Transport(energies=np.array([0.23]), mu=(0.3, 0.1), kT=0.03)
+    full = dense.green_full(dev, tr, 0.23)
+    from oracle.problem import dense_sigma
+    tree = nd_reference.grid_bisection_tree(14, 7, 10)
+    a, b = nd_reference.NDReference(tree, full["A"]), nd_general.NDGeneral(tree, full["A"])
+    Ga, Gb = a.green_retarded(), b.green_retarded()
+    for key in Ga:
+        assert np.abs(Ga[key] - Gb[key]).max() < 1e-11 * np.abs(full["Gr"]).max()
+    S = dense_sigma(dev, full["terms"], "lesser")
+    assert observables.rel_err(b.diag(b.green_lesser(S)), a.diag(a.green_lesser(S))) < 1e-11
