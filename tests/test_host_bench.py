@@ -1,0 +1,57 @@
+"""Host logic of bench.py that the GPU runs rely on (no GPU): the stored kernel
+choice survives a write and read, the DRAM traffic table answers only while
+the kernel sources it was measured on are unchanged, the CPU-oracle sample
+spreads over the energy grid, and the argument defaults match the documented
+certificate thresholds."""
+import importlib.util
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_choice_round_trip(tmp_path):
+    b = _bench()
+    choice = np.array([-1, 2, 3, -1, 0, 1, 4, 2], dtype=np.int8)
+    path = tmp_path / "choice.txt"
+    b.save_choice(str(path), choice, 16, 2)
+    leaf, delay, back = b.load_choice(str(path))
+    assert (leaf, delay) == (16, 2) and back.dtype == np.int8 and np.array_equal(back, choice)
+
+
+def test_traffic_table_follows_the_kernel_sources(monkeypatch):
+    b = _bench()
+    kinds = list(b.TRAFFIC)
+    assert "complex-fp32x2:gemm_tc" in kinds
+    digest = b.kernel_digest()
+    stamped = {k: (v, d) for k, (v, d) in b.TRAFFIC.items()}
+    monkeypatch.setattr(b, "TRAFFIC", {k: (v, digest) for k, (v, _) in stamped.items()})
+    assert all(b.traffic_per_launch(k) == stamped[k][0] for k in kinds)
+    monkeypatch.setattr(b, "TRAFFIC", {k: (v, "0" * 16) for k, (v, _) in stamped.items()})
+    assert all(b.traffic_per_launch(k) is None for k in kinds)
+    assert b.traffic_per_launch("no-such-kernel") is None
+
+
+def test_oracle_sample_spreads_over_the_grid():
+    b = _bench()
+    pick = np.asarray(b.oracle_pick(256, 6))
+    assert len(pick) == 6 and pick.min() == 0 and pick.max() == 255 and np.all(np.diff(pick) > 0)
+
+
+def test_argument_defaults(monkeypatch):
+    b = _bench()
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    a = b.parse()
+    from paper_1305_1070_gb300 import solver
+    assert (a.gpus, a.steps, a.impl, a.workload) == (1, 3, "ours", b.WORKLOAD)
+    assert a.warmup >= 3
+    assert a.resid_max == solver.RESID_MAX and a.growth_max == solver.GROWTH_MAX
