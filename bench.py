@@ -9,13 +9,15 @@ contact self-energies (S1a), lesser/greater self-energies, assembly and fold
 certificate (S9) and the density epilogue (S10).
 
 Paths, all with delayed pivots across clusters (--delay, default 2 rows per
-cluster), which keep the fold growth below ~2 at every energy:
+cluster), which keep the fold growth to a few units at every energy:
 "fp32x2" = cluster blocks and products in FP32-pair ("double-float")
 arithmetic on the FP32 pipe, the products of blocks above 192 rows on the
 tensor cores as exact 8-bit digit products, complex128 root inversion; an energy whose
-certificate still reports a fold growth max|Psi| above 10 is recomputed on the
-complex128 path (none on this workload: with delayed pivots the largest growth
-is 5.6, at an energy where the FP32-pair density already matches complex128); "fp64_nd" = complex128 throughout; "fp32" = plain
+certificate reports a backward error above --resid-max (1e-6, the density
+gate) or a fold growth max|Psi| above --growth-max (1e4) is recomputed on the
+complex128 path (none on this workload: with delayed pivots the largest
+backward error is 3.5e-9 and the largest growth a few units); "fp64_nd" =
+complex128 throughout; "fp32" = plain
 complex64 (reported, gated).  "fp64_nd_plain" = complex128 with the paper's
 elimination (no delayed pivots), timed once for reference.
 The reported value is the fp32x2 path when its energy-integrated density
@@ -24,11 +26,14 @@ path's diagonals are also compared with the CPU oracle (block RGF) at the
 energies of the CPU baseline sample.  Inputs (the per-energy workspace,
 ~100 GB per step) are far larger than L2, so no explicit flush is needed.
 
-The JSON line carries, besides the contract keys: "roofline" (the dominant
-kernel: the FP32-pipe GEMM launches, ALU-bound, useful complex flops against
-the FP32-pair peak, with the DRAM traffic per launch of a one-pass ncu capture
-while the kernel sources are unchanged), "roofline_tensor" (the tensor-core
-GEMM steps: executed BF16 digit-product flops against the measured BF16 peak),
+The JSON line carries, besides the contract keys: "roofline" (the kernel kind
+with the largest share of the headline path's time, from the library's event
+profile: the tensor-core GEMM steps against the measured BF16 peak, or an
+FP32-pipe kernel against the FP32-pair ALU peak, with the DRAM traffic per
+launch of a small-case ncu capture while the kernel sources are unchanged),
+"roofline_kernels" (every arithmetic kernel kind of the headline path),
+"roofline_tensor" (the tensor-core GEMM steps: executed BF16 digit-product
+flops against the measured BF16 peak),
 "roofline_other" (the complex128 path), "kernel_profile" (per kernel kind),
 "e2e" (the same step with host buffers, copies inside the timed region),
 "cpu_baseline" (the oracle on the host cores) and "clocks".
