@@ -14,9 +14,11 @@ def _tr(energies, **kw):
     return workloads.Transport(energies=np.asarray(energies, dtype=float), **kw)
 
 
-def test_invariants_superlattice_dense():
+@pytest.mark.parametrize("ph", [0.0, 4e-3])
+def test_invariants_superlattice_dense(ph):
+    # with phonons the sum rule ties Sigma^r_ph to Sigma^<_ph and Sigma^>_ph: i (S^r - S^a) = i (S^> - S^<)
     dev = workloads.superlattice(10, 5, disorder=0.05, seed=3)
-    tr = _tr([0.13], gamma_ph=0.0)
+    tr = _tr([0.13], gamma_ph=ph, mu_ph=0.05)
     full = dense.green_full(dev, tr, 0.13)
     G, Gl, Gg, A = full["Gr"], full["Gl"], full["Gg"], full["A"]
     assert np.abs(A @ G - np.eye(dev.n)).max() < 1e-9
@@ -86,9 +88,10 @@ def test_landauer_equals_transfer_matrix(E):
 
 
 def test_meir_wingreen_equals_landauer_and_conservation():
+    # 1.2 eV: one open transverse mode in the 4-wide leads (it opens at 0.87 eV), T = 0.67
     dev = workloads.superlattice(8, 4, disorder=0.1, seed=5)
-    E = 0.2
-    tr = _tr([E], mu=(0.3, 0.0), kT=0.03)
+    E = 1.2
+    tr = _tr([E], mu=(1.3, 1.0), kT=0.03)
     full = dense.green_full(dev, tr, E)
     terms = full["terms"]
     cL, cR = dev.contacts
@@ -97,7 +100,9 @@ def test_meir_wingreen_equals_landauer_and_conservation():
     iR = observables.current_spectrum(terms.sigma_lesser[1], terms.sigma_greater[1],
                                       full["Gl"][np.ix_(cR, cR)], full["Gg"][np.ix_(cR, cR)])
     T = observables.transmission(terms.sigma_r[0], terms.sigma_r[1], full["Gr"][np.ix_(cL, cR)])
-    fL, fR = terms.f
+    # occupations from the reservoirs' own Fermi levels (left 1.3 eV, right 1.0 eV), not the oracle's copy
+    fL, fR = selfenergy.fermi(E, 1.3, 0.03), selfenergy.fermi(E, 1.0, 0.03)
+    assert T > 0.5 and fL - fR > 0.9
     assert abs(iL - T * (fL - fR)) < 1e-9 * max(1.0, abs(iL))
     assert abs(iL + iR) < 1e-6 * max(1e-3, abs(iL))  # conservation up to the eta leak
 
