@@ -746,7 +746,7 @@ def main_aux(a) -> None:
 
 
 def main_gradient(a) -> None:
-    """Row c5: the density of the 256 x 64 superlattice (128 energies) and its
+    """The gradient workload: the density of the 256 x 64 superlattice (128 energies) and its
     gradient with respect to all 16,384 onsite potentials, for the loss
     L = sum_j c_j n_j with seeded weights c_j ~ U(0, 1).  Times the density
     alone and the density plus gradient (adjoint: two solves per energy with
@@ -838,7 +838,7 @@ def main_gradient(a) -> None:
 
 
 def main_newton(a) -> None:
-    """Row c5, second half: 10 Newton steps of the self-consistent
+    """The Newton workload: 10 Newton steps of the self-consistent
     Schroedinger-Poisson problem on the 256 x 64 superlattice (128 energies in
     [-0.6, 0.5] eV, eta = 9 meV: workload superlattice_256x64_sp), F(U) = K U - lam (n(U) - nD) with the five-point Poisson
     operator (Dirichlet at the ends, Neumann at the edges), lam = e^2 / (eps0

@@ -49,7 +49,7 @@ typedef enum {
   ND_ERR_OOM = 5,                /* device or host allocation failed            */
   ND_ERR_CUDA = 6,               /* a CUDA runtime call failed                  */
   ND_ERR_TIMEOUT = 7,            /* a bounded device wait gave up               */
-  ND_ERR_UNSUPPORTED = 8         /* valid request this build does not handle    */
+  ND_ERR_UNSUPPORTED = 8         /* valid request the library does not handle   */
 } nd_status;
 
 /* Arithmetic of the cluster blocks and products: complex128; complex64
@@ -275,8 +275,8 @@ nd_status nd_certificate(nd_fact* fact, double* cert, void* stream);
 nd_status nd_selected_entries(nd_fact* fact, const int32_t* x, const int32_t* y, int32_t count, double* Gr,
                               double* Gl, double* Gg, int32_t* n_missing, void* stream);
 
-/* Adjoint of the density (spec extension; the paper computes the
- * density only): for every energy of the last nd_factor / nd_diag_green pair
+/* Adjoint of the density (an extension: the paper computes the density
+ * only; its Sec. 1 motivates self-consistent device simulation): for every energy of the last nd_factor / nd_diag_green pair
  * and every site k,
  *     t_k(E) = sum_{a,b in contacts} Sigma^<_ab conj(U_kb) conj(Z_ka),
  *     U = G^r[:, contact sites],  Z = G^r diag(c) conj(U),
@@ -293,7 +293,7 @@ nd_status nd_selected_entries(nd_fact* fact, const int32_t* x, const int32_t* y,
 nd_status nd_density_gradient(nd_fact* fact, const double* c, double* t_out, void* stream);
 
 /* Forward (directional) derivative of the density, for Newton steps of the
- * self-consistent loop (spec extension): for a potential change v of
+ * self-consistent loop (an extension of the paper): for a potential change v of
  * the on-site energies (H_kk = H0_kk + V_k), every energy of the last
  * nd_factor / nd_diag_green and every site j,
  *     T_j(E) = sum_{a,b in contacts} W_ja Sigma^<_ab conj(U_jb),
@@ -307,7 +307,7 @@ nd_status nd_density_gradient(nd_fact* fact, const double* c, double* t_out, voi
  * Same requirements and errors as nd_density_gradient. */
 nd_status nd_density_jvp(nd_fact* fact, const double* v, double* t_out, void* stream);
 
-/* ---- Poisson operator of the self-consistent loop (spec extension) ----
+/* ---- Poisson operator of the self-consistent loop (an extension) -------------
  * On an nx (transport) x ny (transverse) grid, site (x, y) = x * ny + y:
  *     (K u)_j = sum_{k neighbour of j} (u_j - u_k),
  * u = 0 on ghost columns x = -1 and x = nx (Dirichlet at the ends, the leads'
@@ -403,7 +403,7 @@ nd_status nd_profile_launches(nd_fact* fact, nd_launch_stats* out, int32_t max_o
  * check, ND_ERR_SINGULAR when n_singular > 0 (the results are then invalid). */
 nd_status nd_fact_status(nd_fact* fact, int32_t* n_singular);
 
-/* ---- kernel autotuner (spec batching: tile shapes per workload) ---------
+/* ---- kernel autotuner (energy batching: kernel choice per launch) -------------
  * Measures, on the given inputs (those of nd_factor and nd_diag_green, host
  * or device), every candidate kernel of every GEMM launch of the fold and the
  * extraction: the default rules, the large and the small tile, the tensor
