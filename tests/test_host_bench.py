@@ -55,3 +55,22 @@ def test_argument_defaults(monkeypatch):
     assert (a.gpus, a.steps, a.impl, a.workload) == (1, 3, "ours", b.WORKLOAD)
     assert a.warmup >= 3
     assert a.resid_max == solver.RESID_MAX and a.growth_max == solver.GROWTH_MAX
+
+
+def test_stored_choice_of_the_profiles():
+    """The committed tuner choice that the profile commands load: the
+    benchmark's leaf size and delay, one entry per step, each a kernel the
+    choice API accepts (-1 default rule, 0 large tile, 1 small tile, 2 tensor
+    cores, 3 one CTA per block, 4 extra-large tile), tensor cores present."""
+    b = _bench()
+    path = os.path.join(ROOT, "paper_1305_1070_gb300", "choices", "superlattice_512x128_fp32x2_leaf16_delay2.txt")
+    leaf, delay, choice = b.load_choice(path)
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        a = b.parse()
+    finally:
+        sys.argv = saved
+    assert (leaf, delay) == (a.leaf, a.delay) == (16, 2)
+    assert choice.size == 356 and choice.min() >= -1 and choice.max() <= 4
+    assert (choice == 2).sum() > 0 and (choice == 3).sum() > 0
