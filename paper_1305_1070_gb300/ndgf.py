@@ -162,6 +162,28 @@ def _ptr(x, keep):
     return a.ctypes.data
 
 
+def require_real(x, name: str):
+    """The float64 array that a real Hamiltonian argument (H values, lead
+    blocks H00, H01, tau) must be.  Complex values describe a Hermitian H
+    that need not be complex symmetric (complex hoppings, e.g. a magnetic
+    field); the elimination relies on A = A^T (paper Sec. 3.1), so they are
+    rejected with ND_ERR_NOT_SYMMETRIC instead of losing their imaginary part
+    in a cast.  Other real numpy dtypes are converted; a torch tensor must
+    already be float64.  Returns the array (numpy) or the tensor unchanged."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if x.is_complex():
+            raise NDError(2, f"{name}: complex values; a Hermitian H that is not real symmetric is not supported")
+        if str(x.dtype) != "torch.float64":
+            raise NDError(1, f"{name}: expected a float64 tensor, got {x.dtype}")
+        return x
+    a = np.asarray(x)
+    if np.iscomplexobj(a):
+        raise NDError(2, f"{name}: complex values; a Hermitian H that is not real symmetric is not supported")
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -268,6 +290,7 @@ def nd_fact_create(plan: Plan, max_ne: int, precision: int = ND_PREC_FP64, flags
 
 def nd_factor(fact: Fact, H_values, sigma_r, sigma_ph_r, energies, n_e: int, eta: float, stream=None):
     keep = []
+    H_values = require_real(H_values, "nd_factor: H_values")
     _check(lib().nd_factor(fact.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), _ptr(sigma_ph_r, keep),
                            _ptr(energies, keep), n_e, eta, _stream(stream)), "nd_factor")
 
@@ -282,6 +305,7 @@ def nd_diag_green(fact: Fact, sigma_lesser, sigma_greater, ph_lesser, ph_greater
 def nd_check_factor_inputs(plan: Plan, H_values, sigma_r, n_e: int):
     """Host-side symmetry check of nd_factor's inputs (host arrays)."""
     keep = []
+    H_values = require_real(H_values, "nd_check_factor_inputs: H_values")
     _check(lib().nd_check_factor_inputs(plan.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), n_e),
            "nd_check_factor_inputs")
 
@@ -368,6 +392,7 @@ def nd_autotune(fact: Fact, H_values, sigma_r, sigma_ph_r, sigma_lesser, sigma_g
     """Measured kernel choice per GEMM launch (see ndgf.h); returns nd_tune_info as a dict."""
     keep = []
     info = nd_tune_info()
+    H_values = require_real(H_values, "nd_autotune: H_values")
     _check(lib().nd_autotune(fact.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), _ptr(sigma_ph_r, keep),
                              _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep), _ptr(ph_lesser, keep),
                              _ptr(ph_greater, keep), _ptr(energies, keep), n_e, eta, reps, ctypes.byref(info),
@@ -421,11 +446,12 @@ def nd_vec_scale_pos(a: float, x, y, n: int, stream=None):
 
 def nd_lead_create(H00, H01, tau) -> Lead:
     keep = []
-    H00 = np.ascontiguousarray(H00, dtype=np.float64)
+    H00 = require_real(H00, "nd_lead_create: H00")
+    H01 = require_real(H01, "nd_lead_create: H01")
+    tau = require_real(tau, "nd_lead_create: tau")
     m = H00.shape[0]
-    tau = np.ascontiguousarray(tau, dtype=np.float64)
     out = _P()
-    _check(lib().nd_lead_create(m, tau.shape[0], _ptr(H00, keep), _ptr(np.ascontiguousarray(H01, dtype=np.float64), keep),
+    _check(lib().nd_lead_create(m, tau.shape[0], _ptr(H00, keep), _ptr(H01, keep),
                                 _ptr(tau, keep), ctypes.byref(out)), "nd_lead_create")
     return Lead(out.value)
 

@@ -37,6 +37,11 @@ class Solver:
                  leaf_size: int = 64, split_permille: int = 0, delay: int = 0, tile: str = "auto",
                  adjoint: bool = False, graph: bool = False, device: str = "cuda"):
         self.dev, self.tr = dev, tr
+        # a complex H (or lead) is rejected before anything is allocated
+        ndgf.require_real(dev.values, "Solver: H values")
+        for lead in dev.leads:
+            for block in ("H00", "H01", "tau"):
+                ndgf.require_real(getattr(lead, block), f"Solver: lead {block}")
         self.device = torch.device(device)
         self.n = dev.n
         cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])]).astype(np.int32)

@@ -98,3 +98,32 @@ def test_bad_arguments():
     assert _status(ndgf.nd_check_factor_inputs, plan, None, sr, 3) == 1
     assert _status(ndgf.nd_check_factor_inputs, plan, dev.values, None, 3) == 1  # contacts need Sigma^r
     assert _status(ndgf.nd_check_lesser_inputs, plan, None, None, None, None, -1) == 1
+
+
+def test_complex_hamiltonian_is_rejected_not_cast():
+    """A device in a magnetic field (Peierls phases: complex hoppings, a
+    Hermitian H that is not complex symmetric) is rejected with
+    ND_ERR_NOT_SYMMETRIC by the binding, the lead constructor and the Solver,
+    before anything reaches the library or the GPU: a cast to float64 would
+    drop the phases and solve another problem.  The same device without a
+    field but stored as complex is rejected too; its real part passes."""
+    from paper_1305_1070_gb300.solver import Solver
+    dev = workloads.magnetic_superlattice(12, 5, 0.05, disorder=0.03, seed=7)
+    tr = workloads.Transport(energies=np.array([0.3]))
+    assert np.iscomplexobj(dev.values) and np.abs(dev.values.imag).max() > 0.1
+    cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])])
+    plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, np.concatenate(dev.contacts), dev.coords, 16)
+    sr = np.zeros((1, sum(len(c) ** 2 for c in dev.contacts)), dtype=complex)
+    assert _status(ndgf.nd_check_factor_inputs, plan, dev.values, sr, 1) == NOT_SYMMETRIC
+    lead = dev.leads[0]
+    assert np.iscomplexobj(lead.H01)
+    assert _status(ndgf.nd_lead_create, lead.H00, lead.H01, lead.tau) == NOT_SYMMETRIC
+    assert _status(Solver, dev, tr) == NOT_SYMMETRIC
+    zero = workloads.magnetic_superlattice(12, 5, 0.0, disorder=0.03, seed=7)
+    assert _status(ndgf.nd_check_factor_inputs, plan, zero.values, sr, 1) == NOT_SYMMETRIC
+    _, _, sr_real, _, _ = _setup(1)
+    assert _status(ndgf.nd_check_factor_inputs, plan, zero.values.real, sr_real, 1) == 0
+    with pytest.raises(ndgf.NDError) as err:
+        ndgf.require_real(np.zeros(4, dtype=np.float32).view(np.complex64), "x")
+    assert err.value.status == NOT_SYMMETRIC
+    assert ndgf.require_real(np.arange(3), "x").dtype == np.float64
