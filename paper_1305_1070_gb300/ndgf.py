@@ -184,6 +184,29 @@ def require_real(x, name: str):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def _need(x, name: str, nbytes: int, complex_ok: bool = True, output: bool = False):
+    """Buffer check of the binding (the C ABI sees raw pointers and cannot):
+    ``x`` (a numpy array or torch tensor; None passes) holds float64 or, where
+    ``complex_ok``, complex128 elements (the ABI's doubles, complex values
+    interleaved), at least ``nbytes`` bytes, and, for an output, one
+    contiguous block that the library writes in place.  A narrower element
+    type would be misread and a short buffer overrun; both are
+    ND_ERR_INVALID_ARG here."""
+    if x is None:
+        return
+    if hasattr(x, "data_ptr"):  # torch tensor
+        dt, size, contiguous = str(x.dtype).replace("torch.", ""), x.numel() * x.element_size(), x.is_contiguous()
+    else:
+        a = np.asarray(x)
+        dt, size, contiguous = str(a.dtype), a.nbytes, a.flags.c_contiguous and isinstance(x, np.ndarray)
+    if not (dt == "float64" or (complex_ok and dt == "complex128")):
+        raise NDError(1, f"{name}: elements of type {dt}, expected {'complex128 or ' if complex_ok else ''}float64")
+    if size < nbytes:
+        raise NDError(1, f"{name}: {size} bytes, the call needs {nbytes}")
+    if output and not contiguous:
+        raise NDError(1, f"{name}: an output must be one contiguous array")
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -221,6 +244,25 @@ class Fact(_Handle):
     def __init__(self, ptr, plan):
         super().__init__(ptr)
         self.plan = plan  # the plan must outlive the workspace
+        self.n_e = None  # energies of the last successful nd_factor / nd_autotune (buffer checks)
+
+
+def _factor_inputs(fact: Fact, name: str, H_values, sigma_r, sigma_ph_r, energies, n_e: int):
+    if n_e <= 0:
+        return  # the library reports the count
+    p = fact.plan
+    _need(H_values, f"{name}: H_values", 8 * p.nnz, complex_ok=False)
+    _need(sigma_r, f"{name}: sigma_r", 16 * n_e * p.sigma_elems)
+    _need(sigma_ph_r, f"{name}: sigma_ph_r", 16 * n_e * p.n)
+    _need(energies, f"{name}: energies", 8 * n_e, complex_ok=False)
+
+
+def _lesser_inputs(fact: Fact, name: str, n_e, sigma_lesser, sigma_greater, ph_lesser, ph_greater):
+    p = fact.plan
+    _need(sigma_lesser, f"{name}: sigma_lesser", 16 * n_e * p.sigma_elems)
+    _need(sigma_greater, f"{name}: sigma_greater", 16 * n_e * p.sigma_elems)
+    _need(ph_lesser, f"{name}: ph_lesser", 16 * n_e * p.n)
+    _need(ph_greater, f"{name}: ph_greater", 16 * n_e * p.n)
 
 
 class Lead(_Handle):
@@ -257,7 +299,10 @@ def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=Non
     o.delay = delay
     out = _P()
     _check(lib().nd_analyze(ctypes.byref(g), ctypes.byref(o), ctypes.byref(out)), "nd_analyze")
-    return Plan(out.value)
+    plan = Plan(out.value)
+    plan.n, plan.nnz = int(n), int(rp[-1]) if len(rp) else 0
+    plan.sigma_elems = int((np.diff(cp).astype(np.int64) ** 2).sum()) if contact_ptr is not None else 0
+    return plan
 
 
 def nd_plan_query(plan: Plan) -> dict:
@@ -285,18 +330,27 @@ def nd_plan_cluster_sites(plan: Plan, c: int, n_i: int, b_i: int):
 def nd_fact_create(plan: Plan, max_ne: int, precision: int = ND_PREC_FP64, flags: int = 0) -> Fact:
     out = _P()
     _check(lib().nd_fact_create(plan.ptr, max_ne, precision, flags, ctypes.byref(out)), "nd_fact_create")
-    return Fact(out.value, plan)
+    fact = Fact(out.value, plan)
+    fact.max_ne = int(max_ne)
+    return fact
 
 
 def nd_factor(fact: Fact, H_values, sigma_r, sigma_ph_r, energies, n_e: int, eta: float, stream=None):
     keep = []
     H_values = require_real(H_values, "nd_factor: H_values")
+    _factor_inputs(fact, "nd_factor", H_values, sigma_r, sigma_ph_r, energies, n_e)
+    fact.n_e = None
     _check(lib().nd_factor(fact.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), _ptr(sigma_ph_r, keep),
                            _ptr(energies, keep), n_e, eta, _stream(stream)), "nd_factor")
+    fact.n_e = int(n_e)
 
 
 def nd_diag_green(fact: Fact, sigma_lesser, sigma_greater, ph_lesser, ph_greater, Gr, Gl, Gg, stream=None):
     keep = []
+    if fact.n_e is not None:  # without a factorization the library refuses the call
+        _lesser_inputs(fact, "nd_diag_green", fact.n_e, sigma_lesser, sigma_greater, ph_lesser, ph_greater)
+        for g, name in ((Gr, "Gr"), (Gl, "Gl"), (Gg, "Gg")):
+            _need(g, f"nd_diag_green: {name}", 16 * fact.n_e * fact.plan.n, output=True)
     _check(lib().nd_diag_green(fact.ptr, _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep), _ptr(ph_lesser, keep),
                                _ptr(ph_greater, keep), _ptr(Gr, keep), _ptr(Gl, keep), _ptr(Gg, keep),
                                _stream(stream)), "nd_diag_green")
@@ -319,6 +373,8 @@ def nd_check_lesser_inputs(plan: Plan, sigma_lesser, sigma_greater, ph_lesser, p
 
 def nd_certificate(fact: Fact, cert, stream=None):
     keep = []
+    if fact.n_e is not None:
+        _need(cert, "nd_certificate: cert", 64 * fact.n_e, complex_ok=False, output=True)
     _check(lib().nd_certificate(fact.ptr, _ptr(cert, keep), _stream(stream)), "nd_certificate")
 
 
@@ -338,6 +394,9 @@ def nd_density(Gl, weights, n_e, n, scale, accumulate, out, stream=None):
 def nd_fact_density(fact: Fact, weights, scale, accumulate, out, stream=None):
     """Density epilogue on the handle's last diag G^< (host or device weights / out)."""
     keep = []
+    if fact.n_e is not None:
+        _need(weights, "nd_fact_density: weights", 8 * fact.n_e, complex_ok=False)
+        _need(out, "nd_fact_density: out", 8 * fact.plan.n, complex_ok=False, output=True)
     _check(lib().nd_fact_density(fact.ptr, _ptr(weights, keep), scale, int(accumulate), _ptr(out, keep),
                                  _stream(stream)), "nd_fact_density")
 
@@ -393,10 +452,15 @@ def nd_autotune(fact: Fact, H_values, sigma_r, sigma_ph_r, sigma_lesser, sigma_g
     keep = []
     info = nd_tune_info()
     H_values = require_real(H_values, "nd_autotune: H_values")
+    _factor_inputs(fact, "nd_autotune", H_values, sigma_r, sigma_ph_r, energies, n_e)
+    if n_e > 0:
+        _lesser_inputs(fact, "nd_autotune", n_e, sigma_lesser, sigma_greater, ph_lesser, ph_greater)
+    fact.n_e = None
     _check(lib().nd_autotune(fact.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), _ptr(sigma_ph_r, keep),
                              _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep), _ptr(ph_lesser, keep),
                              _ptr(ph_greater, keep), _ptr(energies, keep), n_e, eta, reps, ctypes.byref(info),
                              _stream(stream)), "nd_autotune")
+    fact.n_e = int(n_e)  # the passes leave the factorization of these energies
     return {"ms_default": info.ms_default, "ms_tuned": info.ms_tuned, "gemm_steps": info.gemm_steps,
             "changed": info.changed, "passes": info.passes, "by_kind": list(info.by_kind)}
 

@@ -127,3 +127,41 @@ def test_complex_hamiltonian_is_rejected_not_cast():
         ndgf.require_real(np.zeros(4, dtype=np.float32).view(np.complex64), "x")
     assert err.value.status == NOT_SYMMETRIC
     assert ndgf.require_real(np.arange(3), "x").dtype == np.float64
+
+
+def test_binding_checks_buffers_before_the_library():
+    """The C ABI takes raw pointers and cannot see buffer sizes or element
+    types; the binding checks them against the plan (nnz, n, contact blocks)
+    and the handle's energies, so that a short buffer is refused instead of
+    overrun and a narrower type is refused instead of misread.  A handle
+    without a workspace (NULL) shows which side answered: the binding's
+    messages name the buffer, the library's names the NULL handle."""
+    dev, plan, sr, sl, sg = _setup(n_e=3)
+    fact = ndgf.Fact(None, plan)
+    fact.max_ne, fact.n_e = 3, 3
+    E = np.linspace(0.05, 0.4, 3)
+    n = dev.n
+
+    def msg(fn, *args):
+        with pytest.raises(ndgf.NDError) as err:
+            fn(*args)
+        assert err.value.status == 1
+        return str(err.value)
+
+    assert "NULL" in msg(ndgf.nd_factor, fact, dev.values, sr, None, E, 3, 1e-6)
+    assert "sigma_r" in msg(ndgf.nd_factor, fact, dev.values, sr[:2], None, E, 3, 1e-6)
+    assert "H_values" in msg(ndgf.nd_factor, fact, dev.values[:-1], sr, None, E, 3, 1e-6)
+    assert "energies" in msg(ndgf.nd_factor, fact, dev.values, sr, None, E.astype(np.float32), 3, 1e-6)
+    assert "sigma_ph_r" in msg(ndgf.nd_factor, fact, dev.values, sr, np.zeros((3, n), np.complex64), E, 3, 1e-6)
+    fact.n_e = 3
+    out = [np.zeros((3, n), dtype=np.complex128) for _ in range(3)]
+    assert "NULL" in msg(ndgf.nd_diag_green, fact, sl, sg, None, None, *out)
+    assert "Gl" in msg(ndgf.nd_diag_green, fact, sl, sg, None, None, out[0], out[1][:2], out[2])
+    wide = np.zeros((3, 2 * n), dtype=np.complex128)
+    assert "Gg" in msg(ndgf.nd_diag_green, fact, sl, sg, None, None, out[0], out[1], wide[:, ::2])
+    assert "sigma_greater" in msg(ndgf.nd_diag_green, fact, sl, sg.astype(np.complex64), None, None, *out)
+    assert "cert" in msg(ndgf.nd_certificate, fact, np.zeros((2, 8)))
+    assert "weights" in msg(ndgf.nd_fact_density, fact, np.ones(2), 1.0, 0, np.zeros(n))
+    assert "out" in msg(ndgf.nd_fact_density, fact, np.ones(3), 1.0, 0, np.zeros(n, dtype=np.float32))
+    # float64 views of complex buffers are the ABI's own layout and pass
+    assert "NULL" in msg(ndgf.nd_diag_green, fact, sl.view(np.float64), sg, None, None, *out)
