@@ -387,6 +387,10 @@ def nd_selected_entries(fact: Fact, x, y, count: int, Gr, Gl, Gg, n_missing, str
 
 def nd_density(Gl, weights, n_e, n, scale, accumulate, out, stream=None):
     keep = []
+    if n_e > 0 and n > 0:
+        _need(Gl, "nd_density: Gl", 16 * n_e * n)
+        _need(weights, "nd_density: weights", 8 * n_e, complex_ok=False)
+        _need(out, "nd_density: out", 8 * n, complex_ok=False, output=True)
     _check(lib().nd_density(_ptr(Gl, keep), _ptr(weights, keep), n_e, n, scale, int(accumulate), _ptr(out, keep),
                             _stream(stream)), "nd_density")
 
@@ -468,6 +472,9 @@ def nd_autotune(fact: Fact, H_values, sigma_r, sigma_ph_r, sigma_lesser, sigma_g
 def nd_density_jvp(fact: Fact, v, t_out, stream=None):
     """Forward terms T[e][j] of the density's derivative along v (see ndgf.h)."""
     keep = []
+    if fact.n_e is not None:
+        _need(v, "nd_density_jvp: v", 8 * fact.plan.n, complex_ok=False)
+        _need(t_out, "nd_density_jvp: t_out", 16 * fact.n_e * fact.plan.n, output=True)
     _check(lib().nd_density_jvp(fact.ptr, _ptr(v, keep), _ptr(t_out, keep), _stream(stream)), "nd_density_jvp")
 
 
@@ -544,12 +551,18 @@ def nd_profile_launches(fact: Fact):
 def nd_density_gradient(fact: Fact, c, t_out, stream=None):
     """t_out[e][k] = sum_ab Sigma^<_ab conj(U_kb) conj(Z_ka) of the last step (see ndgf.h)."""
     keep = []
+    if fact.n_e is not None:
+        _need(c, "nd_density_gradient: c", 8 * fact.plan.n, complex_ok=False)
+        _need(t_out, "nd_density_gradient: t_out", 16 * fact.n_e * fact.plan.n, output=True)
     _check(lib().nd_density_gradient(fact.ptr, _ptr(c, keep), _ptr(t_out, keep), _stream(stream)),
            "nd_density_gradient")
 
 
 def nd_contact_current(fact: Fact, contact: int, current, current_im=None, stream=None):
     keep = []
+    if fact.n_e is not None:
+        _need(current, "nd_contact_current: current", 8 * fact.n_e, complex_ok=False, output=True)
+        _need(current_im, "nd_contact_current: current_im", 8 * fact.n_e, complex_ok=False, output=True)
     _check(lib().nd_contact_current(fact.ptr, contact, _ptr(current, keep),
                                     _ptr(current_im, keep) if current_im is not None else None, _stream(stream)),
            "nd_contact_current")

@@ -165,3 +165,34 @@ def test_binding_checks_buffers_before_the_library():
     assert "out" in msg(ndgf.nd_fact_density, fact, np.ones(3), 1.0, 0, np.zeros(n, dtype=np.float32))
     # float64 views of complex buffers are the ABI's own layout and pass
     assert "NULL" in msg(ndgf.nd_diag_green, fact, sl.view(np.float64), sg, None, None, *out)
+
+
+def test_binding_checks_the_epilogue_buffers():
+    """The same buffer checks on the density, current and response entry
+    points: short or narrower arrays are refused by the binding (their
+    messages name the buffer); well-formed ones reach the library, which here
+    refuses the NULL handle or the host arrays that these calls do not take."""
+    dev, plan, _, _, _ = _setup(n_e=3)
+    fact = ndgf.Fact(None, plan)
+    fact.max_ne, fact.n_e = 3, 3
+    n = dev.n
+
+    def msg(fn, *args):
+        with pytest.raises(ndgf.NDError) as err:
+            fn(*args)
+        assert err.value.status == 1
+        return str(err.value)
+
+    Gl = np.zeros((3, n), dtype=np.complex128)
+    assert "density: Gl: " in msg(ndgf.nd_density, Gl[:2], np.ones(3), 3, n, 1.0, 0, np.zeros(n))
+    assert "density: weights: " in msg(ndgf.nd_density, Gl, np.ones(3, dtype=np.float32), 3, n, 1.0, 0, np.zeros(n))
+    assert "density: out: " in msg(ndgf.nd_density, Gl, np.ones(3), 3, n, 1.0, 0, np.zeros(n - 1))
+    assert "current: 16 bytes" in msg(ndgf.nd_contact_current, fact, 0, np.zeros(2))
+    assert "current_im: elements of type complex128" in msg(ndgf.nd_contact_current, fact, 0, np.zeros(3), np.zeros(3, dtype=np.complex128))
+    assert "t_out: " in msg(ndgf.nd_density_gradient, fact, np.ones(n), np.zeros((2, n), dtype=np.complex128))
+    assert "gradient: c: " in msg(ndgf.nd_density_gradient, fact, np.ones(n - 1), np.zeros((3, n), dtype=np.complex128))
+    assert "jvp: v: elements" in msg(ndgf.nd_density_jvp, fact, np.ones(n, dtype=np.complex128), np.zeros((3, n), dtype=np.complex128))
+    for fn, args in ((ndgf.nd_contact_current, (fact, 0, np.zeros(3))),
+                     (ndgf.nd_density_gradient, (fact, np.ones(n), np.zeros((3, n), dtype=np.complex128))),
+                     (ndgf.nd_density_jvp, (fact, np.ones(n), np.zeros((3, n), dtype=np.complex128)))):
+        assert "bytes" not in msg(fn, *args) and "type" not in msg(fn, *args)
