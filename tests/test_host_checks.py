@@ -196,3 +196,58 @@ def test_binding_checks_the_epilogue_buffers():
                      (ndgf.nd_density_gradient, (fact, np.ones(n), np.zeros((3, n), dtype=np.complex128))),
                      (ndgf.nd_density_jvp, (fact, np.ones(n), np.zeros((3, n), dtype=np.complex128)))):
         assert "bytes" not in msg(fn, *args) and "type" not in msg(fn, *args)
+
+
+class _NoDevice:
+    """The real library for the host-only calls (analysis, plan queries,
+    errors); every call that needs a device returns ND_OK without doing
+    anything.  It lets the driver's call sequences run on the CPU to show
+    that the buffers it allocates pass the binding's checks."""
+    DEVICE = {"nd_fact_create", "nd_fact_destroy", "nd_factor", "nd_diag_green", "nd_certificate",
+              "nd_contact_current", "nd_autotune", "nd_density_gradient", "nd_density_jvp", "nd_fact_density",
+              "nd_density", "nd_lead_create", "nd_lead_destroy", "nd_lead_sigma", "nd_sigma_lesser_fermi",
+              "nd_phonon_const", "nd_phonon_scba"}
+
+    def __init__(self, real):
+        self.real = real
+
+    def __getattr__(self, name):
+        if name in self.DEVICE:
+            return lambda *args: 0
+        return getattr(self.real, name)
+
+
+@pytest.mark.parametrize("case", ["superlattice", "phonons", "cnt"])
+def test_driver_buffers_pass_the_binding_checks(monkeypatch, case):
+    """The Solver's own buffers (device ones here allocated on the CPU) and
+    its call sequences -- step, the host-buffer step, certificate, contact
+    currents, tuner, adjoint and forward products, densities -- pass every
+    check of the binding, at a full batch and at a shorter last chunk."""
+    from paper_1305_1070_gb300.solver import Solver
+    import torch
+    monkeypatch.setattr(ndgf, "_LIB", _NoDevice(ndgf.lib()))
+    if case == "cnt":
+        dev = workloads.cnt_zigzag(3, disorder=0.05, seed=1)
+        tr = workloads.Transport(energies=np.linspace(-0.5, 0.5, 5))
+    else:
+        dev = workloads.superlattice(16, 6, disorder=0.03, seed=3)
+        tr = workloads.Transport(energies=np.linspace(0.05, 0.4, 5), gamma_ph=3e-3 if case == "phonons" else 0.0)
+    s = Solver(dev, tr, leaf_size=8, max_ne=4, delay=2, adjoint=case != "phonons", device="cpu")
+    for E in (tr.energies[:4], tr.energies[4:]):
+        k = len(E)
+        s.step(E)
+        assert s.fact.n_e == k
+        s.certificate(k)
+        s.current(0, k), s.current(1, k)
+        out = [torch.zeros(k, dev.n, dtype=torch.complex128) for _ in range(3)]
+        s.step_host(torch.as_tensor(E), *out, H_host=torch.as_tensor(dev.values))
+        w = torch.full((k,), 0.01, dtype=torch.float64)
+        dens = torch.zeros(dev.n, dtype=torch.float64)
+        ndgf.nd_fact_density(s.fact, w, 1.0, 0, dens)
+        ndgf.nd_density(s.Gl[:k], w, k, dev.n, 1.0, 1, dens)
+        if case != "phonons":
+            s.density_gradient_terms(np.ones(dev.n), k)
+            ndgf.nd_density_jvp(s.fact, torch.ones(dev.n, dtype=torch.float64),
+                                torch.zeros(k, dev.n, dtype=torch.complex128))
+    s.autotune(torch.as_tensor(tr.energies[:4]))
+    assert s.fact.n_e == 4
