@@ -276,6 +276,11 @@ class Poisson(_Handle):
 def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=None, leaf_size=0,
                split_permille=0, slab=0, delay=0) -> Plan:
     keep = []
+    for arr, name in ((rowptr, "rowptr"), (colind, "colind"), (contact_ptr, "contact_ptr"), (contact_idx, "contact_idx")):
+        a = np.asarray(arr) if arr is not None else np.zeros(0, np.int32)
+        if a.size and (a.dtype.kind not in "iu" or int(a.max()) > np.iinfo(np.int32).max or int(a.min()) < 0):
+            # the ABI's indices are int32: a wider value would wrap in the cast
+            raise NDError(1, f"nd_analyze: {name} must hold integers in 0..2^31-1")
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(colind, dtype=np.int32)
     g = nd_graph()

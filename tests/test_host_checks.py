@@ -251,3 +251,19 @@ def test_driver_buffers_pass_the_binding_checks(monkeypatch, case):
                                 torch.zeros(k, dev.n, dtype=torch.complex128))
     s.autotune(torch.as_tensor(tr.energies[:4]))
     assert s.fact.n_e == 4
+
+
+def test_analysis_indices_fit_the_abi():
+    """The graph's indices are int32 in the C ABI: values that do not fit, or
+    a non-integer array, are refused instead of wrapping in the cast."""
+    dev = workloads.superlattice(6, 4)
+    cp = np.array([0, 4, 8])
+    ci = np.concatenate(dev.contacts)
+    big = dev.rowptr.astype(np.int64).copy()
+    big[-1] = 2 ** 31
+    for args in ((big, dev.colind, cp, ci), (dev.rowptr, dev.colind.astype(np.float64), cp, ci),
+                 (dev.rowptr, dev.colind, cp, ci - 1)):
+        with pytest.raises(ndgf.NDError) as err:
+            ndgf.nd_analyze(dev.n, *args, dev.coords, 8)
+        assert err.value.status == 1
+    assert ndgf.nd_plan_query(ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, 8))["n"] == dev.n
