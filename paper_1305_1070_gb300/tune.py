@@ -15,7 +15,10 @@ import time
 import numpy as np
 import torch
 
+from . import ndgf
 from .solver import Solver
+
+ND_ERR_OOM, ND_ERR_UNSUPPORTED = 5, 8
 
 
 def time_call(s: Solver, E, reps: int = 1) -> float:
@@ -46,7 +49,10 @@ def tune_plan(dev, tr, *, precision: int, delay: int, leafs=(16, 24, 32), chunks
             t0 = time.perf_counter()
             try:
                 s = Solver(dev, tr, precision=precision, max_ne=chunk, delay=delay, leaf_size=leaf)
-            except Exception as exc:  # workspace too large for the device
+            except (ndgf.NDError, torch.cuda.OutOfMemoryError) as exc:
+                # a workspace too large for the device, or a tree the library does not take; other errors propagate
+                if isinstance(exc, ndgf.NDError) and exc.status not in (ND_ERR_OOM, ND_ERR_UNSUPPORTED):
+                    raise
                 table.append({"leaf": leaf, "chunk": chunk, "skipped": str(exc)[:120]})
                 continue
             E = E_all[:chunk]
