@@ -174,3 +174,30 @@ def test_general_nested_dissection_reduces_to_the_symmetric_one():
         assert np.abs(Ga[key] - Gb[key]).max() < 1e-11 * np.abs(full["Gr"]).max()
     S = dense_sigma(dev, full["terms"], "lesser")
     assert observables.rel_err(b.diag(b.green_lesser(S)), a.diag(a.green_lesser(S))) < 1e-11
+
+
+def test_general_algorithm_on_the_library_tree():
+    """The block-LU algorithm (oracle/nd_general.py) on the cluster tree that
+    the library's planner builds (nd_analyze, host only) for a device in a
+    field: every diagonal of G^r, G^< and G^> equals the definition, so the
+    ordering (width-1 separators, contact sets kept inside one cluster, hence
+    a Sigma^< that is block diagonal over the clusters) needs no change for a
+    general Hermitian H; only the numeric steps do."""
+    from paper_1305_1070_gb300 import build, ndgf
+    build.build()
+    dev = workloads.magnetic_superlattice(24, 8, 0.07, v_barrier=0.1, disorder=0.1, seed=5)
+    cp = np.concatenate([[0], np.cumsum([len(c) for c in dev.contacts])])
+    plan = ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, np.concatenate(dev.contacts), dev.coords, 16)
+    info, tree = ndgf.nd_plan_query(plan), ndgf.nd_plan_tree(plan)
+    nc = info["n_clusters"]
+    clusters = [ndgf.nd_plan_cluster_sites(plan, c, tree["n_i"][c], tree["b_i"][c])[0] for c in range(nc)]
+    ct = nd_reference.ClusterTree(clusters, tree["parent"].tolist())
+    ct.check_partition(dev.n)
+    assert ct.L >= 4
+    tr = _tr(1.3, mu=(1.4, 1.2), kT=0.03)
+    full = hermitian.green_full(dev, tr, 1.3)
+    nd = nd_general.NDGeneral(ct, full["A"])
+    g = nd.diag(nd.green_retarded())
+    gl, gg = nd.diag(nd.green_lesser(full["Sl"])), nd.diag(nd.green_lesser(full["Sg"]))
+    for got, key in ((g, "Gr"), (gl, "Gl"), (gg, "Gg")):
+        assert observables.rel_err(got, np.diag(full[key])) < 1e-10, key
