@@ -74,3 +74,27 @@ def test_stored_choice_of_the_profiles():
     assert (leaf, delay) == (a.leaf, a.delay) == (16, 2)
     assert choice.size == 356 and choice.min() >= -1 and choice.max() <= 4
     assert (choice == 2).sum() > 0 and (choice == 3).sum() > 0
+
+
+def test_profile_commands_use_existing_options():
+    """Every `python bench.py ...` command recorded under profiles/ names only
+    options that bench.py accepts, so the summaries stay reproducible from
+    the committed files."""
+    import glob
+    import re
+    b = _bench()
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py"]
+        known = set(vars(b.parse()).keys())
+    finally:
+        sys.argv = saved
+    seen = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            if "python bench.py" not in line:
+                continue
+            for opt in re.findall(r"\s--([a-z][a-z0-9-]*)", line.split("python bench.py", 1)[1]):
+                assert opt.replace("-", "_") in known, (os.path.basename(path), opt)
+                seen += 1
+    assert seen > 10
