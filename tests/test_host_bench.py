@@ -98,3 +98,23 @@ def test_profile_commands_use_existing_options():
                 assert opt.replace("-", "_") in known, (os.path.basename(path), opt)
                 seen += 1
     assert seen > 10
+
+
+def test_traffic_table_matches_its_profile_summary():
+    """bench.py's DRAM traffic per launch is the figure of the committed
+    summary (profiles/traffic_...md, GB per 128-energy launch), kind by kind,
+    and every entry carries one digest."""
+    import re
+    b = _bench()
+    path = os.path.join(ROOT, "profiles", "traffic_fp32x2_superlattice_512x128_4_energies.md")
+    rows = {}
+    for line in open(path):
+        m = re.match(r"\|\s*(gemm_tc|gemm_direct|gemm|gemm_small|inverse|delay)\b[^|]*\|[^|]*\|\s*(\d+)\s*\|"
+                     r"\s*([\d.]+)\s*\|\s*([\d.]+)\s*\|", line)
+        if m:
+            rows[m.group(1)] = float(m.group(4))
+    assert set(rows) == {"gemm_tc", "gemm_direct", "gemm", "gemm_small", "inverse", "delay"}
+    for kind, gb in rows.items():
+        value, _ = b.TRAFFIC["complex-fp32x2:" + kind]
+        assert abs(value / 1e9 - gb) <= 0.0005 + 1e-9, (kind, value, gb)
+    assert len({d for _, d in b.TRAFFIC.values()}) == 1
