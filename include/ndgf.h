@@ -185,7 +185,10 @@ void nd_plan_destroy(nd_plan* plan);
  * (nd_precision).  flags: ND_FACT_*.
  * The plan must outlive the handle.  Errors: ND_ERR_OOM, ND_ERR_CUDA,
  * ND_ERR_INVALID_ARG; ND_ERR_UNSUPPORTED for a cluster of more than 8192
- * interior or 32768 boundary sites, or more than two contacts in one cluster. */
+ * interior or 32768 boundary sites, or more than two contacts in one cluster.
+ * The kernels put the energy on the grid's y dimension, so max_ne must not
+ * exceed 65535 (a larger value makes the launches fail with ND_ERR_CUDA; the
+ * Python binding refuses it with ND_ERR_UNSUPPORTED before allocating). */
 nd_status nd_fact_create(const nd_plan* plan, int32_t max_ne, int32_t precision, int32_t flags, nd_fact** out);
 void nd_fact_destroy(nd_fact* fact);
 

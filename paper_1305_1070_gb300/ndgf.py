@@ -333,6 +333,8 @@ def nd_plan_cluster_sites(plan: Plan, c: int, n_i: int, b_i: int):
 
 
 def nd_fact_create(plan: Plan, max_ne: int, precision: int = ND_PREC_FP64, flags: int = 0) -> Fact:
+    if max_ne > 65535:  # energies index the grid's y dimension in every launch
+        raise NDError(8, "nd_fact_create: at most 65535 energies per handle")
     out = _P()
     _check(lib().nd_fact_create(plan.ptr, max_ne, precision, flags, ctypes.byref(out)), "nd_fact_create")
     fact = Fact(out.value, plan)

@@ -267,3 +267,12 @@ def test_analysis_indices_fit_the_abi():
             ndgf.nd_analyze(dev.n, *args, dev.coords, 8)
         assert err.value.status == 1
     assert ndgf.nd_plan_query(ndgf.nd_analyze(dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords, 8))["n"] == dev.n
+
+
+def test_energies_per_handle_fit_the_grid():
+    """Energies index the y dimension of every launch grid (at most 65535):
+    a larger workspace is refused before any allocation."""
+    _, plan, _, _, _ = _setup(n_e=1)
+    with pytest.raises(ndgf.NDError) as err:
+        ndgf.nd_fact_create(plan, 65536, ndgf.ND_PREC_FP64)
+    assert err.value.status == 8
