@@ -207,6 +207,23 @@ def _need(x, name: str, nbytes: int, complex_ok: bool = True, output: bool = Fal
         raise NDError(1, f"{name}: an output must be one contiguous array")
 
 
+def _need_i32(x, name: str, count: int, output: bool = False):
+    """The int32 counterpart of ``_need``: at least ``count`` int32 elements."""
+    if x is None:
+        return
+    if hasattr(x, "data_ptr"):
+        dt, size, contiguous = str(x.dtype).replace("torch.", ""), x.numel(), x.is_contiguous()
+    else:
+        a = np.asarray(x)
+        dt, size, contiguous = str(a.dtype), a.size, a.flags.c_contiguous and isinstance(x, np.ndarray)
+    if dt != "int32":
+        raise NDError(1, f"{name}: elements of type {dt}, expected int32")
+    if size < count:
+        raise NDError(1, f"{name}: {size} elements, the call needs {count}")
+    if output and not contiguous:
+        raise NDError(1, f"{name}: an output must be one contiguous array")
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -388,6 +405,13 @@ def nd_certificate(fact: Fact, cert, stream=None):
 def nd_selected_entries(fact: Fact, x, y, count: int, Gr, Gl, Gg, n_missing, stream=None):
     """Selected entries G^r_xy, G^<_xy, G^>_xy of the last solve (device arrays)."""
     keep = []
+    if count > 0:
+        _need_i32(x, "nd_selected_entries: x", count)
+        _need_i32(y, "nd_selected_entries: y", count)
+        _need_i32(n_missing, "nd_selected_entries: n_missing", 1, output=True)
+        if fact.n_e is not None:
+            for g, name in ((Gr, "Gr"), (Gl, "Gl"), (Gg, "Gg")):
+                _need(g, f"nd_selected_entries: {name}", 16 * fact.n_e * count, output=True)
     _check(lib().nd_selected_entries(fact.ptr, _ptr(x, keep), _ptr(y, keep), count, _ptr(Gr, keep), _ptr(Gl, keep),
                                      _ptr(Gg, keep), _ptr(n_missing, keep), _stream(stream)), "nd_selected_entries")
 

@@ -276,3 +276,26 @@ def test_energies_per_handle_fit_the_grid():
     with pytest.raises(ndgf.NDError) as err:
         ndgf.nd_fact_create(plan, 65536, ndgf.ND_PREC_FP64)
     assert err.value.status == 8
+
+
+def test_selected_entries_buffers():
+    """nd_selected_entries: int32 pair lists of `count` entries, an int32
+    counter and [n_e][count] complex outputs, checked by the binding."""
+    _, plan, _, _, _ = _setup(n_e=3)
+    fact = ndgf.Fact(None, plan)
+    fact.max_ne, fact.n_e = 3, 3
+    x = np.arange(5, dtype=np.int32)
+    out = np.zeros((3, 5), dtype=np.complex128)
+    miss = np.zeros(1, dtype=np.int32)
+
+    def msg(*args):
+        with pytest.raises(ndgf.NDError) as err:
+            ndgf.nd_selected_entries(fact, *args)
+        assert err.value.status == 1
+        return str(err.value)
+
+    assert "bad argument" in msg(x, x, 5, out, None, None, miss)  # the library: NULL handle
+    assert "x: elements of type int64" in msg(x.astype(np.int64), x, 5, out, None, None, miss)
+    assert "y: 4 elements" in msg(x, x[:4], 5, out, None, None, miss)
+    assert "Gr: " in msg(x, x, 5, out[:2], None, None, miss)
+    assert "n_missing" in msg(x, x, 5, out, None, None, np.zeros(1, dtype=np.int64))
