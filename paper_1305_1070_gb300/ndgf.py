@@ -555,11 +555,17 @@ def nd_lead_create(H00, H01, tau) -> Lead:
     out = _P()
     _check(lib().nd_lead_create(m, tau.shape[0], _ptr(H00, keep), _ptr(H01, keep),
                                 _ptr(tau, keep), ctypes.byref(out)), "nd_lead_create")
-    return Lead(out.value)
+    lead = Lead(out.value)
+    lead.m_c = int(tau.shape[0])
+    return lead
 
 
 def nd_lead_sigma(lead: Lead, energies, n_e: int, eta: float, sigma_out, stride: int, offset: int, stream=None):
     keep = []
+    m_c = getattr(lead, "m_c", None)
+    if n_e > 0 and m_c is not None and stride >= 0 and offset >= 0:
+        _need(energies, "nd_lead_sigma: energies", 8 * n_e, complex_ok=False)
+        _need(sigma_out, "nd_lead_sigma: sigma_out", 16 * ((n_e - 1) * stride + offset + m_c * m_c), output=True)
     _check(lib().nd_lead_sigma(lead.ptr, _ptr(energies, keep), n_e, eta, _ptr(sigma_out, keep), stride, offset,
                                _stream(stream)), "nd_lead_sigma")
 
@@ -612,6 +618,12 @@ def nd_sigma_lesser_fermi(sigma_r, n_e, m_c, mu, kT, energies, sigma_lesser, sig
     keep = []
     mc = np.ascontiguousarray(m_c, dtype=np.int32)
     muv = np.ascontiguousarray(mu, dtype=np.float64)
+    if n_e > 0:
+        elems = int((mc.astype(np.int64) ** 2).sum())
+        _need(sigma_r, "nd_sigma_lesser_fermi: sigma_r", 16 * n_e * elems)
+        _need(energies, "nd_sigma_lesser_fermi: energies", 8 * n_e, complex_ok=False)
+        _need(sigma_lesser, "nd_sigma_lesser_fermi: sigma_lesser", 16 * n_e * elems, output=True)
+        _need(sigma_greater, "nd_sigma_lesser_fermi: sigma_greater", 16 * n_e * elems, output=True)
     _check(lib().nd_sigma_lesser_fermi(_ptr(sigma_r, keep), n_e, len(mc), _ptr(mc, keep), _ptr(muv, keep), kT,
                                        _ptr(energies, keep), _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep),
                                        _stream(stream)), "nd_sigma_lesser_fermi")
@@ -619,6 +631,10 @@ def nd_sigma_lesser_fermi(sigma_r, n_e, m_c, mu, kT, energies, sigma_lesser, sig
 
 def nd_phonon_const(n, n_e, gamma, mu, kT, energies, ph_r, ph_lesser, ph_greater, stream=None):
     keep = []
+    if n > 0 and n_e > 0:
+        _need(energies, "nd_phonon_const: energies", 8 * n_e, complex_ok=False)
+        for x, name in ((ph_r, "ph_r"), (ph_lesser, "ph_lesser"), (ph_greater, "ph_greater")):
+            _need(x, f"nd_phonon_const: {name}", 16 * n_e * n, output=True)
     _check(lib().nd_phonon_const(n, n_e, gamma, mu, kT, _ptr(energies, keep), _ptr(ph_r, keep),
                                  _ptr(ph_lesser, keep), _ptr(ph_greater, keep), _stream(stream)), "nd_phonon_const")
 
@@ -626,6 +642,12 @@ def nd_phonon_const(n, n_e, gamma, mu, kT, energies, ph_r, ph_lesser, ph_greater
 def nd_phonon_scba(n, n_e, D, mix, Gr, Gl, Gg, ph_r, ph_lesser, ph_greater, stats, stream=None):
     """Self-consistent Born update of the elastic local phonon self-energy (see ndgf.h)."""
     keep = []
+    if n > 0 and n_e > 0:
+        for x, name in ((Gr, "Gr"), (Gl, "Gl"), (Gg, "Gg")):
+            _need(x, f"nd_phonon_scba: {name}", 16 * n_e * n)
+        for x, name in ((ph_r, "ph_r"), (ph_lesser, "ph_lesser"), (ph_greater, "ph_greater")):
+            _need(x, f"nd_phonon_scba: {name}", 16 * n_e * n, output=True)
+        _need(stats, "nd_phonon_scba: stats", 16, complex_ok=False, output=True)
     _check(lib().nd_phonon_scba(n, n_e, D, mix, _ptr(Gr, keep), _ptr(Gl, keep), _ptr(Gg, keep), _ptr(ph_r, keep),
                                 _ptr(ph_lesser, keep), _ptr(ph_greater, keep), _ptr(stats, keep), _stream(stream)),
            "nd_phonon_scba")

@@ -251,6 +251,8 @@ def test_driver_buffers_pass_the_binding_checks(monkeypatch, case):
                                 torch.zeros(k, dev.n, dtype=torch.complex128))
     s.autotune(torch.as_tensor(tr.energies[:4]))
     assert s.fact.n_e == 4
+    if case == "phonons":
+        s.scba(tr.energies[:4], 0.01, updates=2)
 
 
 def test_analysis_indices_fit_the_abi():
@@ -299,3 +301,30 @@ def test_selected_entries_buffers():
     assert "y: 4 elements" in msg(x, x[:4], 5, out, None, None, miss)
     assert "Gr: " in msg(x, x, 5, out[:2], None, None, miss)
     assert "n_missing" in msg(x, x, 5, out, None, None, np.zeros(1, dtype=np.int64))
+
+
+def test_self_energy_builder_buffers():
+    """The self-energy builders and the Born update: outputs hold [n_e] blocks
+    of the contact sizes (or [n_e][n] diagonals) and the energies are float64,
+    checked by the binding before the library sees the pointers."""
+    n, n_e = 6, 3
+    E = np.linspace(0.1, 0.3, n_e)
+    sr = np.zeros((n_e, 2 * 9), dtype=np.complex128)
+
+    def msg(fn, *args):
+        with pytest.raises(ndgf.NDError) as err:
+            fn(*args)
+        assert err.value.status == 1
+        return str(err.value)
+
+    assert "sigma_lesser: " in msg(ndgf.nd_sigma_lesser_fermi, sr, n_e, [3, 3], [0.1, 0.0], 0.03, E, sr[:2], sr)
+    assert "energies: elements of type complex128" in msg(ndgf.nd_sigma_lesser_fermi, sr, n_e, [3, 3], [0.1, 0.0],
+                                                          0.03, E.astype(complex), sr, sr)
+    ph = np.zeros((n_e, n), dtype=np.complex128)
+    assert "ph_greater: " in msg(ndgf.nd_phonon_const, n, n_e, 0.01, 0.0, 0.03, E, ph, ph, ph[:, :3].copy())
+    assert "stats: " in msg(ndgf.nd_phonon_scba, n, n_e, 0.01, 1.0, ph, ph, ph, ph, ph, ph, np.zeros(1))
+    assert "Gl: " in msg(ndgf.nd_phonon_scba, n, n_e, 0.01, 1.0, ph, ph[:1], ph, ph, ph, ph, np.zeros(2))
+    lead = ndgf.Lead(None)
+    lead.m_c = 3
+    out = np.zeros((n_e, 18), dtype=np.complex128)
+    assert "sigma_out: " in msg(ndgf.nd_lead_sigma, lead, E, n_e, 1e-6, out, 18, 10)
