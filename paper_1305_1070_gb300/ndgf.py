@@ -2,7 +2,10 @@
 
 Every function keeps the C name and raises ``NDError`` on a non-OK status.
 Array arguments may be torch tensors (CUDA or CPU) or numpy arrays (host);
-complex arrays are complex128 (interleaved re, im).  ``stream=None`` means
+complex arrays are complex128 (interleaved re, im).  The C functions see raw
+pointers only, so the binding checks what they cannot: element types and
+sizes of the buffers against the plan and the handle, contiguous outputs, and
+real (not complex) Hamiltonian values (``_need``, ``require_real``).  ``stream=None`` means
 torch's current CUDA stream.  The library is loaded from the in-tree build
 ``_lib/libndgf.so``; there is no fallback when it is missing.
 """
