@@ -217,7 +217,7 @@ class _NoDevice:
         return getattr(self.real, name)
 
 
-@pytest.mark.parametrize("case", ["superlattice", "phonons", "cnt"])
+@pytest.mark.parametrize("case", ["superlattice", "phonons", "cnt", "union"])
 def test_driver_buffers_pass_the_binding_checks(monkeypatch, case):
     """The Solver's own buffers (device ones here allocated on the CPU) and
     its call sequences -- step, the host-buffer step, certificate, contact
@@ -229,10 +229,15 @@ def test_driver_buffers_pass_the_binding_checks(monkeypatch, case):
     if case == "cnt":
         dev = workloads.cnt_zigzag(3, disorder=0.05, seed=1)
         tr = workloads.Transport(energies=np.linspace(-0.5, 0.5, 5))
+    elif case == "union":
+        dev = workloads.union([workloads.superlattice(12, 4, disorder=0.02, seed=s) for s in (1, 2, 3)])
+        tr = workloads.Transport(energies=np.linspace(0.05, 0.4, 5))
     else:
         dev = workloads.superlattice(16, 6, disorder=0.03, seed=3)
         tr = workloads.Transport(energies=np.linspace(0.05, 0.4, 5), gamma_ph=3e-3 if case == "phonons" else 0.0)
-    s = Solver(dev, tr, leaf_size=8, max_ne=4, delay=2, adjoint=case != "phonons", device="cpu")
+    s = Solver(dev, tr, leaf_size=8, max_ne=4, delay=2, adjoint=case not in ("phonons", "union"), device="cpu")
+    if case == "superlattice":
+        s.set_potential(np.full(dev.n, 0.01))
     for E in (tr.energies[:4], tr.energies[4:]):
         k = len(E)
         s.step(E)
@@ -245,7 +250,7 @@ def test_driver_buffers_pass_the_binding_checks(monkeypatch, case):
         dens = torch.zeros(dev.n, dtype=torch.float64)
         ndgf.nd_fact_density(s.fact, w, 1.0, 0, dens)
         ndgf.nd_density(s.Gl[:k], w, k, dev.n, 1.0, 1, dens)
-        if case != "phonons":
+        if case not in ("phonons", "union"):
             s.density_gradient_terms(np.ones(dev.n), k)
             ndgf.nd_density_jvp(s.fact, torch.ones(dev.n, dtype=torch.float64),
                                 torch.zeros(k, dev.n, dtype=torch.complex128))
