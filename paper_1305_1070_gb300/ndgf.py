@@ -303,6 +303,15 @@ def nd_analyze(n, rowptr, colind, contact_ptr=None, contact_idx=None, coords=Non
             raise NDError(1, f"nd_analyze: {name} must hold integers in 0..2^31-1")
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(colind, dtype=np.int32)
+    # the library reads these host arrays by the lengths they imply
+    if n < 0 or rp.size != n + 1 or ci.size < (int(rp[-1]) if rp.size else 0):
+        raise NDError(1, "nd_analyze: rowptr must have n + 1 entries and colind rowptr[n]")
+    if contact_ptr is not None:
+        cpv = np.asarray(contact_ptr)
+        if contact_idx is None or cpv.size < 1 or np.asarray(contact_idx).size < int(cpv[-1]):
+            raise NDError(1, "nd_analyze: contact_idx must hold contact_ptr[-1] sites")
+    if coords is not None and (np.ndim(coords) != 2 or np.shape(coords)[0] != n):
+        raise NDError(1, "nd_analyze: coords must be [n][dim]")
     g = nd_graph()
     g.n = n
     g.rowptr = _ptr(rp, keep)
@@ -621,6 +630,8 @@ def nd_sigma_lesser_fermi(sigma_r, n_e, m_c, mu, kT, energies, sigma_lesser, sig
     keep = []
     mc = np.ascontiguousarray(m_c, dtype=np.int32)
     muv = np.ascontiguousarray(mu, dtype=np.float64)
+    if muv.size < mc.size:
+        raise NDError(1, "nd_sigma_lesser_fermi: one Fermi level per contact")
     if n_e > 0:
         elems = int((mc.astype(np.int64) ** 2).sum())
         _need(sigma_r, "nd_sigma_lesser_fermi: sigma_r", 16 * n_e * elems)

@@ -333,3 +333,24 @@ def test_self_energy_builder_buffers():
     lead.m_c = 3
     out = np.zeros((n_e, 18), dtype=np.complex128)
     assert "sigma_out: " in msg(ndgf.nd_lead_sigma, lead, E, n_e, 1e-6, out, 18, 10)
+
+
+def test_host_arrays_match_their_lengths():
+    """Host arrays that the library reads by implied lengths (the graph, the
+    contact lists, the coordinates, one Fermi level per contact) are checked
+    against those lengths by the binding."""
+    dev = workloads.superlattice(6, 4)
+    cp = np.array([0, 4, 8])
+    ci = np.concatenate(dev.contacts)
+    bad = ((dev.n + 1, dev.rowptr, dev.colind, cp, ci, dev.coords),
+           (dev.n, dev.rowptr, dev.colind[:-1], cp, ci, dev.coords),
+           (dev.n, dev.rowptr, dev.colind, cp, ci[:7], dev.coords),
+           (dev.n, dev.rowptr, dev.colind, cp, ci, dev.coords[:-1]))
+    for args in bad:
+        with pytest.raises(ndgf.NDError) as err:
+            ndgf.nd_analyze(*args, 8)
+        assert err.value.status == 1
+    sr = np.zeros((1, 32), dtype=np.complex128)
+    with pytest.raises(ndgf.NDError) as err:
+        ndgf.nd_sigma_lesser_fermi(sr, 1, [4, 4], [0.1], 0.03, np.zeros(1), sr, sr)
+    assert err.value.status == 1
