@@ -13,19 +13,22 @@ Mistakes that cannot change any result on the pinned inputs are not listed:
 for example a transpose in place of a conjugate transpose of a matrix that is
 real symmetric on every workload (the lead coupling of a square lattice)."""
 import importlib
+import os
 import sys
 import types
 
 import numpy as np
 import pytest
 
-import test_oracle_green as green
-import test_oracle_hermitian as herm
-import test_oracle_leads as leads_t
-import test_oracle_nd_reference as ndr
-import test_oracle_ribbon as ribbon
-import test_oracle_scba as scba_t
-import test_oracle_sp as sp_t
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))  # the pin modules, whatever the import mode
+
+import test_oracle_green as green  # noqa: E402
+import test_oracle_hermitian as herm  # noqa: E402
+import test_oracle_leads as leads_t  # noqa: E402
+import test_oracle_nd_reference as ndr  # noqa: E402
+import test_oracle_ribbon as ribbon  # noqa: E402
+import test_oracle_scba as scba_t  # noqa: E402
+import test_oracle_sp as sp_t  # noqa: E402
 
 PINS = {
     "dense": [green.test_invariants_superlattice_dense, green.test_uniform_chain_closed_form,
