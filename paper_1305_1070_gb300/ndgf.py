@@ -524,37 +524,59 @@ def nd_density_jvp(fact: Fact, v, t_out, stream=None):
 def nd_poisson_create(nx: int, ny: int) -> Poisson:
     out = _P()
     _check(lib().nd_poisson_create(nx, ny, ctypes.byref(out)), "nd_poisson_create")
-    return Poisson(out.value)
+    p = Poisson(out.value)
+    p.sites = int(nx) * int(ny)
+    return p
 
 
 def nd_poisson_apply(p: Poisson, u, out, batch: int = 1, stream=None):
     keep = []
+    if batch > 0 and getattr(p, "sites", None):
+        _need(u, "nd_poisson_apply: u", 8 * batch * p.sites, complex_ok=False)
+        _need(out, "nd_poisson_apply: out", 8 * batch * p.sites, complex_ok=False, output=True)
     _check(lib().nd_poisson_apply(p.ptr, _ptr(u, keep), _ptr(out, keep), batch, _stream(stream)), "nd_poisson_apply")
 
 
 def nd_poisson_solve(p: Poisson, rhs, u, batch: int = 1, shift: float = 0.0, stream=None):
     keep = []
+    if batch > 0 and getattr(p, "sites", None):
+        _need(rhs, "nd_poisson_solve: rhs", 8 * batch * p.sites, complex_ok=False)
+        _need(u, "nd_poisson_solve: u", 8 * batch * p.sites, complex_ok=False, output=True)
     _check(lib().nd_poisson_solve(p.ptr, shift, _ptr(rhs, keep), _ptr(u, keep), batch, _stream(stream)),
            "nd_poisson_solve")
 
 
 def nd_vec_dot(x, y, n: int, out, stream=None):
     keep = []
+    if n > 0:
+        _need(x, "nd_vec_dot: x", 8 * n, complex_ok=False)
+        _need(y, "nd_vec_dot: y", 8 * n, complex_ok=False)
+        _need(out, "nd_vec_dot: out", 8, complex_ok=False, output=True)
     _check(lib().nd_vec_dot(_ptr(x, keep), _ptr(y, keep), n, _ptr(out, keep), _stream(stream)), "nd_vec_dot")
 
 
 def nd_vec_axpby(a: float, x, b: float, y, n: int, stream=None):
     keep = []
+    if n > 0:
+        _need(x, "nd_vec_axpby: x", 8 * n, complex_ok=False)
+        _need(y, "nd_vec_axpby: y", 8 * n, complex_ok=False, output=True)
     _check(lib().nd_vec_axpby(a, _ptr(x, keep), b, _ptr(y, keep), n, _stream(stream)), "nd_vec_axpby")
 
 
 def nd_vec_mul(d, x, y, n: int, stream=None):
     keep = []
+    if n > 0:
+        _need(d, "nd_vec_mul: d", 8 * n, complex_ok=False)
+        _need(x, "nd_vec_mul: x", 8 * n, complex_ok=False)
+        _need(y, "nd_vec_mul: y", 8 * n, complex_ok=False, output=True)
     _check(lib().nd_vec_mul(_ptr(d, keep), _ptr(x, keep), _ptr(y, keep), n, _stream(stream)), "nd_vec_mul")
 
 
 def nd_vec_scale_pos(a: float, x, y, n: int, stream=None):
     keep = []
+    if n > 0:
+        _need(x, "nd_vec_scale_pos: x", 8 * n, complex_ok=False)
+        _need(y, "nd_vec_scale_pos: y", 8 * n, complex_ok=False, output=True)
     _check(lib().nd_vec_scale_pos(a, _ptr(x, keep), _ptr(y, keep), n, _stream(stream)), "nd_vec_scale_pos")
 
 

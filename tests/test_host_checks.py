@@ -354,3 +354,27 @@ def test_host_arrays_match_their_lengths():
     with pytest.raises(ndgf.NDError) as err:
         ndgf.nd_sigma_lesser_fermi(sr, 1, [4, 4], [0.1], 0.03, np.zeros(1), sr, sr)
     assert err.value.status == 1
+
+
+def test_poisson_and_vector_buffers():
+    """The Poisson operator and the vector operations: [batch][nx * ny] and
+    [n] float64 buffers, checked by the binding (a handle without a workspace
+    and the library's own refusal of host arrays show the rest reaches it)."""
+    p = ndgf.Poisson(None)
+    p.sites = 12
+
+    def msg(fn, *args):
+        with pytest.raises(ndgf.NDError) as err:
+            fn(*args)
+        assert err.value.status == 1
+        return str(err.value)
+
+    assert "u: 88 bytes" in msg(ndgf.nd_poisson_apply, p, np.zeros(11), np.zeros(12))
+    assert "u: " in msg(ndgf.nd_poisson_solve, p, np.zeros(24), np.zeros(23), 2)
+    assert "out: elements of type float32" in msg(ndgf.nd_vec_dot, np.zeros(4), np.zeros(4), 4,
+                                                  np.zeros(1, dtype=np.float32))
+    assert "y: 24 bytes" in msg(ndgf.nd_vec_axpby, 1.0, np.zeros(4), 1.0, np.zeros(3), 4)
+    assert "d: " in msg(ndgf.nd_vec_mul, np.zeros(3), np.zeros(4), np.zeros(4), 4)
+    assert "x: elements of type complex128" in msg(ndgf.nd_vec_scale_pos, 1.0, np.zeros(4, complex), np.zeros(4), 4)
+    # well-formed host arrays reach the library, which takes device arrays only
+    assert "bytes" not in msg(ndgf.nd_vec_axpby, 1.0, np.zeros(4), 1.0, np.zeros(4), 4)
