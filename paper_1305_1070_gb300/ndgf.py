@@ -461,6 +461,17 @@ def nd_profile(fact: Fact, enable: bool) -> list:
 def nd_invert_c64_noalloc(A, n, batch, n_singular, stream=None):
     """In-place inversion of complex64 matrices without device allocation."""
     keep = []
+    if A is not None and 0 < n <= 512 and 0 < batch and batch * n * n <= 1 << 18:  # the library refuses the rest
+        if hasattr(A, "data_ptr"):
+            dt, size, contiguous = str(A.dtype).replace("torch.", ""), A.numel() * A.element_size(), A.is_contiguous()
+        else:
+            a = np.asarray(A)
+            dt, size, contiguous = str(a.dtype), a.nbytes, a.flags.c_contiguous and isinstance(A, np.ndarray)
+        if dt not in ("complex64", "float32"):
+            raise NDError(1, f"nd_invert_c64_noalloc: A has elements of type {dt}, expected complex64")
+        if size < 8 * batch * n * n or not contiguous:
+            raise NDError(1, f"nd_invert_c64_noalloc: A must be one contiguous [batch][n][n] complex64 array")
+        _need_i32(n_singular, "nd_invert_c64_noalloc: n_singular", 1, output=True)
     _check(lib().nd_invert_c64_noalloc(_ptr(A, keep), n, batch, _ptr(n_singular, keep), _stream(stream)),
            "nd_invert_c64_noalloc")
 

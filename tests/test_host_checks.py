@@ -378,3 +378,21 @@ def test_poisson_and_vector_buffers():
     assert "x: elements of type complex128" in msg(ndgf.nd_vec_scale_pos, 1.0, np.zeros(4, complex), np.zeros(4), 4)
     # well-formed host arrays reach the library, which takes device arrays only
     assert "bytes" not in msg(ndgf.nd_vec_axpby, 1.0, np.zeros(4), 1.0, np.zeros(4), 4)
+
+
+def test_noalloc_buffers():
+    """The allocation-free inversion: A holds batch x n x n complex64 in one
+    block and the singular counter is int32, checked by the binding; sizes
+    beyond the library's cap are left to the library's own refusal."""
+    def msg(*args):
+        with pytest.raises(ndgf.NDError) as err:
+            ndgf.nd_invert_c64_noalloc(*args)
+        assert err.value.status == 1
+        return str(err.value)
+
+    cnt = np.zeros(1, dtype=np.int32)
+    assert "complex64" in msg(np.zeros((1, 8, 8), dtype=np.complex128), 8, 1, cnt)
+    assert "contiguous" in msg(np.zeros((1, 8, 7), dtype=np.complex64), 8, 1, cnt)
+    assert "n_singular" in msg(np.zeros((1, 8, 8), dtype=np.complex64), 8, 1, np.zeros(1, dtype=np.int64))
+    assert "must be device arrays" in msg(np.zeros((1, 8, 8), dtype=np.complex64), 8, 1, cnt)  # well formed: the library
+    assert "complex64" not in msg(np.zeros(1, dtype=np.complex64), 513, 1, cnt)  # over the cap: the library
