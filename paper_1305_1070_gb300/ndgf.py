@@ -396,6 +396,9 @@ def nd_check_factor_inputs(plan: Plan, H_values, sigma_r, n_e: int):
     """Host-side symmetry check of nd_factor's inputs (host arrays)."""
     keep = []
     H_values = require_real(H_values, "nd_check_factor_inputs: H_values")
+    if n_e > 0:
+        _need(H_values, "nd_check_factor_inputs: H_values", 8 * plan.nnz, complex_ok=False)
+        _need(sigma_r, "nd_check_factor_inputs: sigma_r", 16 * n_e * plan.sigma_elems)
     _check(lib().nd_check_factor_inputs(plan.ptr, _ptr(H_values, keep), _ptr(sigma_r, keep), n_e),
            "nd_check_factor_inputs")
 
@@ -403,6 +406,10 @@ def nd_check_factor_inputs(plan: Plan, H_values, sigma_r, n_e: int):
 def nd_check_lesser_inputs(plan: Plan, sigma_lesser, sigma_greater, ph_lesser, ph_greater, n_e: int):
     """Host-side skew-Hermiticity check of nd_diag_green's inputs (host arrays)."""
     keep = []
+    if n_e > 0:
+        for x, name, per in ((sigma_lesser, "sigma_lesser", plan.sigma_elems), (sigma_greater, "sigma_greater",
+                             plan.sigma_elems), (ph_lesser, "ph_lesser", plan.n), (ph_greater, "ph_greater", plan.n)):
+            _need(x, f"nd_check_lesser_inputs: {name}", 16 * n_e * per)
     _check(lib().nd_check_lesser_inputs(plan.ptr, _ptr(sigma_lesser, keep), _ptr(sigma_greater, keep),
                                         _ptr(ph_lesser, keep), _ptr(ph_greater, keep), n_e), "nd_check_lesser_inputs")
 
